@@ -1,0 +1,146 @@
+/* mdx.h — C ABI of the GB300 McMurchie-Davidson electron-repulsion-integral engine.
+ *
+ * Method: Asadchev & Valeev, "3-center and 4-center 2-particle Gaussian AO
+ * integrals on modern accelerated processors", arXiv:2405.01834.
+ * Integrals are over contracted Cartesian Gaussian shells (Eq. 3) with
+ * l <= MDX_LMAX, evaluated in FP64 by the McMurchie-Davidson scheme of Sec. 2
+ * (Boys function, Eq. boys; auxiliary Hermite integrals, Eqs. 0m and r;
+ * Hermite 2-index integrals, Eq. pq; ket then bra Hermite->Cartesian
+ * transforms, Eqs. ket-from-hermite and bra-from-hermite).
+ *
+ * Conventions shared by every entry point
+ *  - All array pointers are DEVICE pointers on the context's device, owned by
+ *    the caller, and read-only unless stated. The library never frees caller
+ *    memory. It allocates only inside the context (a workspace that grows on
+ *    demand and is released by mdx_destroy).
+ *  - Cartesian components of a shell of angular momentum l are ordered with
+ *    a_x running from l down to 0, then a_y from l-a_x down to 0
+ *    (xx, xy, xz, yy, yz, zz for l = 2).
+ *  - Coefficients multiply the UNNORMALISED primitives
+ *    x_A^ax y_A^ay z_A^az exp(-zeta r_A^2); any normalisation is folded in by
+ *    the caller. Coordinates are in bohr.
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL means
+ *    the legacy default stream). Calls that must know the class mix of their
+ *    input copy the (small) index arrays to the host and synchronise `stream`
+ *    once before launching; each such call says so.
+ *  - Every call validates its arguments on the host and returns a status; no
+ *    C++ exception crosses the ABI. Errors detected inside a kernel (bad
+ *    shell index, bounded wait expired) are recorded in a device error word of
+ *    the context and returned by the next mdx_sync() or by the next call.
+ *    mdx_last_error() gives a one-line description of the last failure.
+ */
+#ifndef MDX_H
+#define MDX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDX_LMAX 6          /* highest shell angular momentum */
+#define MDX_KMAX 32         /* highest contraction degree of one shell */
+
+typedef enum {
+  MDX_OK = 0,
+  MDX_EINVAL = 1,           /* bad argument (NULL pointer, negative size, shell index out of range) */
+  MDX_ENOMEM = 2,           /* workspace allocation failed */
+  MDX_ECUDA = 3,            /* a CUDA runtime call failed */
+  MDX_EUNSUPPORTED = 4,     /* l > MDX_LMAX or contraction degree > MDX_KMAX */
+  MDX_ECAPACITY = 5,        /* output buffer too small */
+  MDX_ETIMEOUT = 6,         /* a bounded device-side wait expired */
+  MDX_EDEVICE = 7           /* a kernel flagged invalid input */
+} mdx_status;
+
+typedef struct mdx_ctx mdx_ctx;
+
+/* A basis of contracted Cartesian shells (Eq. 3). One entry per shell in l,
+ * nprim, prim_off, ao_off, atom and center; one entry per primitive in exps
+ * and coefs (shell s owns exps[prim_off[s] .. prim_off[s]+nprim[s]-1]).
+ * ao_off[s] is the first AO (row of D and K) of shell s. atom may be NULL
+ * except for mdx_exchange_grad. All pointers are device pointers. */
+typedef struct {
+  int32_t n_shells;
+  int32_t n_prims;
+  const int32_t* l;
+  const int32_t* nprim;
+  const int32_t* prim_off;
+  const int32_t* ao_off;
+  const int32_t* atom;
+  const double* center;     /* [n_shells][3] */
+  const double* exps;       /* [n_prims] */
+  const double* coefs;      /* [n_prims] */
+} mdx_basis;
+
+/* Create a context on CUDA device `device` (made current for the call). The
+ * context builds the Boys-function interpolation table and owns all
+ * workspace. Returns MDX_OK and *ctx, or an error and *ctx = NULL. */
+mdx_status mdx_create(mdx_ctx** ctx, int device);
+
+/* Release the context and its workspace. NULL is allowed. The caller must
+ * make sure no work the context enqueued is still running. */
+void mdx_destroy(mdx_ctx* ctx);
+
+/* Description of the last error of this context ("" if none). The string
+ * lives until the next call on the context. */
+const char* mdx_last_error(const mdx_ctx* ctx);
+
+/* Synchronise `stream` and report (and clear) any error a kernel of this
+ * context recorded in the device error word. */
+mdx_status mdx_sync(mdx_ctx* ctx, void* stream);
+
+/* 4-center integrals [ab|cd] (Eq. def-abcd) for n shell quartets.
+ * quartets: [n][4] int32 shell indices (a, b, c, d) into `basis`.
+ * out: receives, for quartet q, the contracted shellset in row-major
+ *   [a][b][c][d] order (d fastest) at out + out_offsets[q]; out has room for
+ *   out_capacity doubles.
+ * out_offsets: [n+1] int64, written by the call (exclusive prefix sum of the
+ *   shellset sizes in quartet order); out_offsets[n] is the total.
+ * Returns MDX_ECAPACITY (writing nothing) if the total exceeds out_capacity.
+ * Copies the quartet list and the shell l/nprim arrays to the host and
+ * synchronises `stream` once to group quartets by class. n = 0 is allowed
+ * and writes out_offsets[0] = 0. */
+mdx_status mdx_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
+                    double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
+
+/* 3-center integrals [a|cd] (Eq. def-acd): shell a from `aux`, shells c, d
+ * from `orb`. triplets: [n][3] int32 (a, c, d). Output per triplet in
+ * row-major [a][c][d] order at out + out_offsets[q]. The bra is a single
+ * Gaussian (zeta_p = zeta_a, P = A) with the 1-center E coefficients of
+ * Eq. E1rr. Same capacity, offset and synchronisation rules as mdx_eri4. */
+mdx_status mdx_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
+                    int64_t n, double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
+
+/* Schwarz factors Q_ij = sqrt(max_ab |(ab|ab)|) over the Cartesian
+ * components a of shell i and b of shell j, for n shell pairs.
+ * pairs: [n][2] int32 shell indices. Q_out: [n] doubles (device), written.
+ * Synchronises `stream` once (class grouping). */
+mdx_status mdx_schwarz(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, int64_t n,
+                       double* Q_out, void* stream);
+
+/* Shape the engine chooses for one integral class (no GPU needed; ctx may be
+ * NULL). The class is (la lb | lc ld) with Kb = K_a K_b and Kk = K_c K_d
+ * primitive pairs; one_centre = 1 selects the 3-center bra [a| (lb must be 0).
+ * The planner applies the Hermite->Cartesian transforms of Eqs.
+ * ket-from-hermite and bra-from-hermite one Cartesian axis at a time
+ * (E factorises by axis, Sec. 2) and checks that every shared-memory access
+ * of the resulting step programs stays inside the team workspace; a class
+ * that cannot be planned returns MDX_EUNSUPPORTED.
+ * exec_fma: FP64 multiply-adds the kernel issues per contracted shellset
+ * (transforms, R recursion and Boys interpolation). */
+typedef struct {
+  int32_t team_threads;
+  int32_t teams_per_cta;
+  int32_t smem_bytes_per_team;
+  int32_t n_groups;
+  double exec_fma;
+} mdx_plan_stats;
+
+mdx_status mdx_plan_info(mdx_ctx* ctx, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
+                         mdx_plan_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDX_H */

@@ -1,0 +1,484 @@
+// Host side of the C ABI declared in include/mdx.h: context, argument
+// validation, class grouping, workspace, and the kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/mdx.h"
+#include "kernels.cuh"
+#include "mdx_internal.h"
+
+using namespace mdx;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct mdx_ctx {
+  int device = 0;
+  std::string last_error;
+  double* d_boys = nullptr;
+  uint32_t* d_hdec = nullptr;
+  int32_t* d_hdec_off = nullptr;
+  int* d_err = nullptr;
+  std::map<ClassKey, std::unique_ptr<Plan>> plans;
+  std::map<std::string, DevBuf> bufs;
+  int smem_budget = 200 * 1024;
+};
+
+namespace {
+
+mdx_status fail(mdx_ctx* c, mdx_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+mdx_status cuda_fail(mdx_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, MDX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Device buffer that grows on demand. Growing synchronises the stream first
+// so that no queued kernel still reads the old allocation.
+template <typename T>
+mdx_status ensure(mdx_ctx* c, const char* name, size_t count, T** out, cudaStream_t s) {
+  DevBuf& b = c->bufs[name];
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+  if (b.cap < bytes) {
+    if (b.p) {
+      cudaStreamSynchronize(s);
+      cudaFree(b.p);
+      b.p = nullptr;
+      b.cap = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, MDX_ENOMEM, std::string("workspace allocation failed for ") + name);
+    }
+    b.cap = want;
+  }
+  *out = (T*)b.p;
+  return MDX_OK;
+}
+
+template <typename T>
+mdx_status upload(mdx_ctx* c, const char* name, const std::vector<T>& v, T** out, cudaStream_t s) {
+  mdx_status st = ensure<T>(c, name, v.size(), out, s);
+  if (st != MDX_OK) return st;
+  if (!v.empty()) {
+    cudaError_t e = cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+  }
+  return MDX_OK;
+}
+
+mdx_status get_plan(mdx_ctx* c, const ClassKey& k, Plan** out, cudaStream_t s) {
+  auto it = c->plans.find(k);
+  if (it != c->plans.end()) { *out = it->second.get(); return MDX_OK; }
+  std::unique_ptr<Plan> p(new Plan());
+  std::string err;
+  if (!build_plan(k, c->smem_budget, *p, err)) return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
+  // one device blob: groups | kprog | b1 | b23 | colmap
+  const size_t sg = p->groups.size() * sizeof(Group), sk = p->kprog.size() * sizeof(StepEntry),
+               s1 = p->b1.size() * sizeof(StepEntry), s2 = p->b23.size() * sizeof(B23Entry),
+               sc = p->colmap.size() * sizeof(uint16_t);
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t tot = al(sg) + al(sk) + al(s1) + al(s2) + al(sc);
+  std::vector<char> blob(tot, 0);
+  size_t o = 0;
+  auto put = [&](const void* src, size_t n) { size_t at = o; if (n) memcpy(blob.data() + o, src, n); o += al(n); return at; };
+  const size_t og = put(p->groups.data(), sg), ok = put(p->kprog.data(), sk), o1 = put(p->b1.data(), s1),
+               o2 = put(p->b23.data(), s2), oc = put(p->colmap.data(), sc);
+  cudaError_t e = cudaMalloc(&p->dev_blob, tot);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MDX_ENOMEM, "plan allocation failed"); }
+  e = cudaMemcpyAsync(p->dev_blob, blob.data(), tot, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "plan upload");
+  e = cudaStreamSynchronize(s);   // blob is a local vector
+  if (e != cudaSuccess) return cuda_fail(c, e, "plan upload");
+  char* base = (char*)p->dev_blob;
+  p->d.groups = (const Group*)(base + og);
+  p->d.kprog = (const StepEntry*)(base + ok);
+  p->d.b1 = (const StepEntry*)(base + o1);
+  p->d.b23 = (const B23Entry*)(base + o2);
+  p->d.colmap = (const uint16_t*)(base + oc);
+  *out = p.get();
+  c->plans[k] = std::move(p);
+  return MDX_OK;
+}
+
+mdx_status check_device_error(mdx_ctx* c, cudaStream_t s) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device error check");
+  if (h != kDevOk) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), s);
+    if (h == kDevTimeout) return fail(c, MDX_ETIMEOUT, "a bounded device-side wait expired");
+    return fail(c, MDX_EDEVICE, "a kernel flagged invalid input");
+  }
+  return MDX_OK;
+}
+
+struct HostBasis {
+  std::vector<int32_t> l, nprim;
+  int32_t n = 0;
+};
+
+mdx_status fetch_basis(mdx_ctx* c, const mdx_basis* b, HostBasis& hb, cudaStream_t s) {
+  if (!b || b->n_shells < 0 || (b->n_shells > 0 && (!b->l || !b->nprim || !b->prim_off || !b->center ||
+                                                     !b->exps || !b->coefs)))
+    return fail(c, MDX_EINVAL, "invalid basis descriptor");
+  hb.n = b->n_shells;
+  hb.l.resize(hb.n);
+  hb.nprim.resize(hb.n);
+  if (hb.n) {
+    cudaError_t e = cudaMemcpyAsync(hb.l.data(), b->l, hb.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.nprim.data(), b->nprim, hb.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "basis download");
+  }
+  for (int i = 0; i < hb.n; ++i) {
+    if (hb.l[i] < 0 || hb.l[i] > MDX_LMAX) return fail(c, MDX_EUNSUPPORTED, "shell angular momentum outside 0..MDX_LMAX");
+    if (hb.nprim[i] < 1 || hb.nprim[i] > MDX_KMAX) return fail(c, MDX_EUNSUPPORTED, "contraction degree outside 1..MDX_KMAX");
+  }
+  return MDX_OK;
+}
+
+BasisDev to_dev(const mdx_basis* b) {
+  return BasisDev{b->l, b->nprim, b->prim_off, b->center, b->exps, b->coefs};
+}
+
+// A shell pair (i, j) of basis `which`; j = -1 is the one-centre unit partner.
+struct PairKey {
+  int32_t i, j, which;
+  bool operator==(const PairKey& o) const { return i == o.i && j == o.j && which == o.which; }
+};
+struct PairHash {
+  size_t operator()(const PairKey& k) const {
+    return std::hash<int64_t>()(((int64_t)k.i << 32) ^ ((int64_t)(k.j + 1) << 1) ^ k.which);
+  }
+};
+
+// Generic batched evaluation of quartets given as (bra pair, ket pair).
+struct Batch {
+  std::vector<PairKey> pairs;
+  std::vector<int2> qp;          // per quartet (bra pair idx, ket pair idx)
+  std::vector<int64_t> qoff;     // output offset per quartet
+};
+
+mdx_status run_batch(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const HostBasis& h0,
+                     const HostBasis& h1, const Batch& bt, double* out, cudaStream_t s) {
+  if (bt.qp.empty()) return MDX_OK;
+  const HostBasis* hb[2] = {&h0, &h1};
+  // primitive-pair records
+  std::vector<int64_t> pair_rec(bt.pairs.size());
+  std::vector<PrimPairJob> jobs;
+  int64_t roff = 0;
+  for (size_t p = 0; p < bt.pairs.size(); ++p) {
+    const PairKey& k = bt.pairs[p];
+    const HostBasis& H = *hb[k.which];
+    const int li = H.l[k.i], lj = k.j >= 0 ? H.l[k.j] : 0;
+    const int Ki = H.nprim[k.i], Kj = k.j >= 0 ? H.nprim[k.j] : 1;
+    const int rs = rec_size(li, lj);
+    pair_rec[p] = roff;
+    for (int ia = 0; ia < Ki; ++ia)
+      for (int ib = 0; ib < Kj; ++ib) {
+        jobs.push_back(PrimPairJob{k.i, k.j, ia, ib, k.which, 0, roff});
+        roff += rs;
+      }
+  }
+  PrimPairJob* d_jobs; double *d_recs, *d_recs_s; int64_t* d_pair_rec;
+  mdx_status st;
+  if ((st = upload(c, "jobs", jobs, &d_jobs, s)) != MDX_OK) return st;
+  if ((st = upload(c, "pair_rec", pair_rec, &d_pair_rec, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "recs", (size_t)roff, &d_recs, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
+  cudaError_t e = launch_pair_records(to_dev(b0), to_dev(b1 ? b1 : b0), d_jobs, (int64_t)jobs.size(), d_recs,
+                                      d_recs_s, c->d_err, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+  // group quartets by class
+  std::map<ClassKey, std::vector<int64_t>> classes;
+  for (size_t q = 0; q < bt.qp.size(); ++q) {
+    const PairKey& bp = bt.pairs[bt.qp[q].x];
+    const PairKey& kp = bt.pairs[bt.qp[q].y];
+    const HostBasis& HB = *hb[bp.which];
+    const HostBasis& HK = *hb[kp.which];
+    ClassKey key{HB.l[bp.i], bp.j >= 0 ? HB.l[bp.j] : 0, HK.l[kp.i], HK.l[kp.j],
+                 HB.nprim[bp.i] * (bp.j >= 0 ? HB.nprim[bp.j] : 1), HK.nprim[kp.i] * HK.nprim[kp.j],
+                 bp.j < 0 ? 1 : 0};
+    classes[key].push_back((int64_t)q);
+  }
+  std::vector<int2> qp_sorted;
+  std::vector<int64_t> qoff_sorted;
+  qp_sorted.reserve(bt.qp.size());
+  qoff_sorted.reserve(bt.qp.size());
+  std::vector<std::pair<ClassKey, std::pair<int64_t, int64_t>>> ranges;
+  for (auto& kv : classes) {
+    const int64_t b = (int64_t)qp_sorted.size();
+    for (int64_t q : kv.second) { qp_sorted.push_back(bt.qp[q]); qoff_sorted.push_back(bt.qoff[q]); }
+    ranges.push_back({kv.first, {b, (int64_t)qp_sorted.size() - b}});
+  }
+  int2* d_qp; int64_t* d_qoff;
+  if ((st = upload(c, "qp", qp_sorted, &d_qp, s)) != MDX_OK) return st;
+  if ((st = upload(c, "qoff", qoff_sorted, &d_qoff, s)) != MDX_OK) return st;
+  for (auto& r : ranges) {
+    Plan* plan;
+    if ((st = get_plan(c, r.first, &plan, s)) != MDX_OK) return st;
+    QuartetLaunch a{};
+    a.plan = plan->d;
+    a.nq = r.second.second;
+    a.qpairs = d_qp + r.second.first;
+    a.qout = d_qoff + r.second.first;
+    a.pair_rec = d_pair_rec;
+    a.recs = d_recs;
+    a.recs_signed = d_recs_s;
+    a.boys = c->d_boys;
+    a.hdec = c->d_hdec;
+    a.hdec_off = c->d_hdec_off;
+    a.out = out;
+    a.err = c->d_err;
+    e = launch_quartets(a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "quartet kernel launch");
+  }
+  return MDX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mdx_status mdx_create(mdx_ctx** ctx, int device) {
+  if (!ctx) return MDX_EINVAL;
+  *ctx = nullptr;
+  std::unique_ptr<mdx_ctx> c(new mdx_ctx());
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return MDX_ECUDA;
+  e = kernel_attributes_init();
+  if (e != cudaSuccess) return MDX_ECUDA;
+  std::vector<double> tab = build_boys_table();
+  if (cudaMalloc(&c->d_boys, tab.size() * sizeof(double)) != cudaSuccess) return MDX_ENOMEM;
+  if (cudaMemcpy(c->d_boys, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return MDX_ECUDA;
+  // Hermite index decode: for total order N, entry e of the [t][u][v] simplex layout
+  std::vector<uint32_t> dec;
+  std::vector<int32_t> doff;
+  for (int N = 0; N <= kLtot; ++N) {
+    doff.push_back((int32_t)dec.size());
+    for (int t = 0; t <= N; ++t)
+      for (int u = 0; t + u <= N; ++u)
+        for (int v = 0; t + u + v <= N; ++v) dec.push_back((uint32_t)t | ((uint32_t)u << 8) | ((uint32_t)v << 16));
+  }
+  if (cudaMalloc(&c->d_hdec, dec.size() * sizeof(uint32_t)) != cudaSuccess) return MDX_ENOMEM;
+  if (cudaMalloc(&c->d_hdec_off, doff.size() * sizeof(int32_t)) != cudaSuccess) return MDX_ENOMEM;
+  if (cudaMemcpy(c->d_hdec, dec.data(), dec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_hdec_off, doff.data(), doff.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    return MDX_ECUDA;
+  if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) return MDX_ENOMEM;
+  if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) return MDX_ECUDA;
+  *ctx = c.release();
+  return MDX_OK;
+}
+
+void mdx_destroy(mdx_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  for (auto& kv : c->plans) if (kv.second->dev_blob) cudaFree(kv.second->dev_blob);
+  for (auto& kv : c->bufs) if (kv.second.p) cudaFree(kv.second.p);
+  cudaFree(c->d_boys);
+  cudaFree(c->d_hdec);
+  cudaFree(c->d_hdec_off);
+  cudaFree(c->d_err);
+  delete c;
+}
+
+const char* mdx_last_error(const mdx_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+mdx_status mdx_sync(mdx_ctx* c, void* stream) {
+  if (!c) return MDX_EINVAL;
+  cudaSetDevice(c->device);
+  return check_device_error(c, (cudaStream_t)stream);
+}
+
+mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
+                    int64_t out_capacity, int64_t* out_offsets, void* stream) {
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n < 0 || !out_offsets || (n > 0 && (!quartets || !out))) return fail(c, MDX_EINVAL, "invalid arguments");
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
+    return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
+  }
+  HostBasis hb;
+  mdx_status st = fetch_basis(c, basis, hb, s);
+  if (st != MDX_OK) return st;
+  std::vector<int32_t> hq((size_t)n * 4);
+  cudaError_t e = cudaMemcpyAsync(hq.data(), quartets, hq.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "quartet download");
+  Batch bt;
+  std::unordered_map<PairKey, int32_t, PairHash> pid;
+  auto pair_index = [&](int32_t i, int32_t j) {
+    PairKey k{i, j, 0};
+    auto it = pid.find(k);
+    if (it != pid.end()) return it->second;
+    const int32_t id = (int32_t)bt.pairs.size();
+    bt.pairs.push_back(k);
+    pid.emplace(k, id);
+    return id;
+  };
+  std::vector<int64_t> offs((size_t)n + 1);
+  offs[0] = 0;
+  bt.qp.resize(n);
+  bt.qoff.resize(n);
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* s4 = &hq[(size_t)q * 4];
+    for (int k = 0; k < 4; ++k)
+      if (s4[k] < 0 || s4[k] >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
+    bt.qp[q] = make_int2(pair_index(s4[0], s4[1]), pair_index(s4[2], s4[3]));
+    bt.qoff[q] = offs[q];
+    offs[q + 1] = offs[q] + (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * ncart(hb.l[s4[2]]) * ncart(hb.l[s4[3]]);
+  }
+  if (offs[n] > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  int64_t* d_offs_tmp;
+  // out_offsets is caller memory: copy through a host staging vector kept alive until the sync below
+  e = cudaMemcpyAsync(out_offsets, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "offsets upload");
+  (void)d_offs_tmp;
+  st = run_batch(c, basis, nullptr, hb, hb, bt, out, s);
+  if (st != MDX_OK) return st;
+  e = cudaStreamSynchronize(s);   // host staging vectors go out of scope
+  if (e != cudaSuccess) return cuda_fail(c, e, "eri4");
+  return check_device_error(c, s);
+}
+
+mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
+                    double* out, int64_t out_capacity, int64_t* out_offsets, void* stream) {
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n < 0 || !out_offsets || (n > 0 && (!triplets || !out))) return fail(c, MDX_EINVAL, "invalid arguments");
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
+    return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
+  }
+  HostBasis ha, ho;
+  mdx_status st = fetch_basis(c, aux, ha, s);
+  if (st != MDX_OK) return st;
+  if ((st = fetch_basis(c, orb, ho, s)) != MDX_OK) return st;
+  std::vector<int32_t> ht((size_t)n * 3);
+  cudaError_t e = cudaMemcpyAsync(ht.data(), triplets, ht.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "triplet download");
+  Batch bt;
+  std::unordered_map<PairKey, int32_t, PairHash> pid;
+  auto pair_index = [&](int32_t i, int32_t j, int32_t which) {
+    PairKey k{i, j, which};
+    auto it = pid.find(k);
+    if (it != pid.end()) return it->second;
+    const int32_t id = (int32_t)bt.pairs.size();
+    bt.pairs.push_back(k);
+    pid.emplace(k, id);
+    return id;
+  };
+  std::vector<int64_t> offs((size_t)n + 1);
+  offs[0] = 0;
+  bt.qp.resize(n);
+  bt.qoff.resize(n);
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* t3 = &ht[(size_t)q * 3];
+    if (t3[0] < 0 || t3[0] >= ha.n || t3[1] < 0 || t3[1] >= ho.n || t3[2] < 0 || t3[2] >= ho.n)
+      return fail(c, MDX_EINVAL, "shell index out of range");
+    bt.qp[q] = make_int2(pair_index(t3[0], -1, 0), pair_index(t3[1], t3[2], 1));
+    bt.qoff[q] = offs[q];
+    offs[q + 1] = offs[q] + (int64_t)ncart(ha.l[t3[0]]) * ncart(ho.l[t3[1]]) * ncart(ho.l[t3[2]]);
+  }
+  if (offs[n] > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  e = cudaMemcpyAsync(out_offsets, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "offsets upload");
+  st = run_batch(c, aux, orb, ha, ho, bt, out, s);
+  if (st != MDX_OK) return st;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "eri3");
+  return check_device_error(c, s);
+}
+
+mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, int64_t n, double* Q_out,
+                       void* stream) {
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n < 0 || (n > 0 && (!pairs || !Q_out))) return fail(c, MDX_EINVAL, "invalid arguments");
+  if (n == 0) return MDX_OK;
+  HostBasis hb;
+  mdx_status st = fetch_basis(c, basis, hb, s);
+  if (st != MDX_OK) return st;
+  std::vector<int32_t> hp((size_t)n * 2);
+  cudaError_t e = cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair download");
+  Batch bt;
+  bt.pairs.resize(n);
+  bt.qp.resize(n);
+  bt.qoff.resize(n);
+  std::vector<int64_t> offs(n);
+  std::vector<int32_t> nab(n);
+  int64_t tot = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    const int32_t i = hp[2 * p], j = hp[2 * p + 1];
+    if (i < 0 || i >= hb.n || j < 0 || j >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
+    bt.pairs[p] = PairKey{i, j, 0};
+    bt.qp[p] = make_int2((int)p, (int)p);
+    nab[p] = ncart(hb.l[i]) * ncart(hb.l[j]);
+    offs[p] = tot;
+    bt.qoff[p] = tot;
+    tot += (int64_t)nab[p] * nab[p];
+  }
+  double* d_vals; int64_t* d_off; int32_t* d_nab;
+  if ((st = ensure(c, "schwarz_vals", (size_t)tot, &d_vals, s)) != MDX_OK) return st;
+  if ((st = upload(c, "schwarz_off", offs, &d_off, s)) != MDX_OK) return st;
+  if ((st = upload(c, "schwarz_nab", nab, &d_nab, s)) != MDX_OK) return st;
+  st = run_batch(c, basis, nullptr, hb, hb, bt, d_vals, s);
+  if (st != MDX_OK) return st;
+  e = launch_schwarz_reduce(d_off, d_nab, n, d_vals, Q_out, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "schwarz reduce");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "schwarz");
+  return check_device_error(c, s);
+}
+
+mdx_status mdx_plan_info(mdx_ctx* c, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
+                         mdx_plan_stats* out) {
+  if (!out) return MDX_EINVAL;
+  if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > MDX_LMAX || lb > MDX_LMAX || lc > MDX_LMAX || ld > MDX_LMAX ||
+      Kb < 1 || Kk < 1 || Kb > MDX_KMAX * MDX_KMAX || Kk > MDX_KMAX * MDX_KMAX)
+    return fail(c, MDX_EUNSUPPORTED, "class outside the supported range");
+  Plan p;
+  std::string err;
+  if (!build_plan(ClassKey{la, lb, lc, ld, Kb, Kk, one_centre ? 1 : 0}, c ? c->smem_budget : 200 * 1024, p, err))
+    return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
+  out->team_threads = p.d.T;
+  out->teams_per_cta = p.d.teams_per_cta;
+  out->smem_bytes_per_team = p.d.team_doubles * 8;
+  out->n_groups = p.d.ngroups;
+  out->exec_fma = p.exec_fma;
+  return MDX_OK;
+}
+
+}  // extern "C"

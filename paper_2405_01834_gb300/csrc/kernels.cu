@@ -1,0 +1,409 @@
+// CUDA kernels of the McMurchie-Davidson engine (sm_103a, FP64).
+//
+// Two kernels carry the method:
+//  * k_pair_records: per primitive pair, zeta_p, P, the prefactor
+//    c_a c_b exp(-zeta_a zeta_b |A-B|^2 / zeta_p) (Eq. E2-000 folded into one
+//    scalar) and the three per-axis Hermite tables (E_i)_{ab}^t from
+//    Eqs. E2rr1/E2rr2 (one-centre bra: Eq. E1rr), plain and with the ket sign
+//    (-1)^t of Eq. pq folded in.
+//  * k_quartets: one team of threads per shell quartet. For every primitive
+//    quartet the team forms the Boys seeds [0]^(m) (Eq. 0m), the Hermite
+//    integrals [tuv]^(0) (Eq. r) and applies the ket transform
+//    (Eq. ket-from-hermite) axis by axis; per bra primitive pair it applies
+//    the bra transform (Eq. bra-from-hermite). The transforms run from step
+//    programs the host planner emits for the class.
+//
+// GB300 executes FP64 at 2 FMA/clk/SM (measured: 1.20 TFLOP/s DFMA, 1.05
+// TFLOP/s DMMA, 74.8 TFLOP/s FFMA), so the kernels spend integer and
+// shared-memory bandwidth freely to save FP64 instructions.
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace mdx {
+
+// integers 0..63 as doubles, to multiply by small integers without an
+// int->double conversion on the FP64 pipe
+__constant__ double c_dint[64];
+// sqrt(pi)/2 * (2m-1)!! / 2^m: F_m(T) = c_gh[m] T^(-m-1/2) for large T
+__constant__ double c_gh[kBoysRow];
+
+cudaError_t kernel_attributes_init();
+
+// ----------------------------------------------------------------- pair records
+__global__ void k_pair_records(BasisDev b0, BasisDev b1, const PrimPairJob* __restrict__ jobs, int64_t njobs,
+                               double* __restrict__ recs, double* __restrict__ recs_signed, int* err) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= njobs) return;
+  const PrimPairJob jb = jobs[g];
+  const BasisDev& B = jb.which ? b1 : b0;
+  const int la = B.l[jb.i];
+  const int lb = jb.j >= 0 ? B.l[jb.j] : 0;
+  if (la < 0 || la > kLmax || lb < 0 || lb > kLmax) { atomicExch(err, kDevBadInput); return; }
+  const double za = B.exps[B.prim_off[jb.i] + jb.ia];
+  const double ca = B.coefs[B.prim_off[jb.i] + jb.ia];
+  double zb = 0.0, cb = 1.0;
+  double A[3], Bc[3];
+  for (int k = 0; k < 3; ++k) A[k] = B.center[3 * jb.i + k];
+  if (jb.j >= 0) {
+    zb = B.exps[B.prim_off[jb.j] + jb.ib];
+    cb = B.coefs[B.prim_off[jb.j] + jb.ib];
+    for (int k = 0; k < 3; ++k) Bc[k] = B.center[3 * jb.j + k];
+  } else {
+    for (int k = 0; k < 3; ++k) Bc[k] = A[k];
+  }
+  const double p = za + zb;
+  const double ip = 1.0 / p;
+  const double inv2p = 0.5 * ip;
+  double P[3], ab2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    P[k] = (za * A[k] + zb * Bc[k]) * ip;
+    const double d = A[k] - Bc[k];
+    ab2 += d * d;
+  }
+  double* r = recs + jb.off;
+  double* rs = recs_signed + jb.off;
+  const double pref = ca * cb * exp(-za * zb * ab2 * ip);
+  const double hdr[kRecHeader] = {p, ip, P[0], P[1], P[2], pref, 0.0, 0.0};
+  for (int k = 0; k < kRecHeader; ++k) { r[k] = hdr[k]; rs[k] = hdr[k]; }
+  // per-axis tables, E_00^0 = 1 (the exponential is in the prefactor)
+  int tab = 0;  // etab size
+  for (int a = 0; a <= la; ++a)
+    for (int b = 0; b <= lb; ++b) tab += a + b + 1;
+  const int nt = la + lb + 1;
+  for (int ax = 0; ax < 3; ++ax) {
+    double* E = r + kRecHeader + ax * tab;
+    double* Es = rs + kRecHeader + ax * tab;
+    const double XPA = P[ax] - A[ax], XPB = P[ax] - Bc[ax];
+    // block offsets: (a,b) at off(a,b); (a,b) block has a+b+1 entries
+    // a-major order; off(a,0) = sum_{a'<a} sum_b (a'+b+1)
+    auto off = [&](int a, int b) {
+      int s = 0;
+      for (int a2 = 0; a2 < a; ++a2) s += (lb + 1) * (a2 + 1) + lb * (lb + 1) / 2;
+      s += b * (a + 1) + b * (b - 1) / 2;
+      return s;
+    };
+    E[off(0, 0)] = 1.0;
+    // raise a with b = 0 (Eq. E2rr1; E1rr when XPA = 0 and zb = 0)
+    for (int a = 0; a < la; ++a) {
+      const double* s = E + off(a, 0);
+      double* d = E + off(a + 1, 0);
+      for (int t = 0; t <= a + 1; ++t) {
+        double v = 0.0;
+        if (t >= 1) v = inv2p * s[t - 1];
+        if (t <= a) v = fma(XPA, s[t], v);
+        if (t + 1 <= a) v = fma(c_dint[t + 1], s[t + 1], v);
+        d[t] = v;
+      }
+    }
+    // raise b (Eq. E2rr2)
+    for (int a = 0; a <= la; ++a)
+      for (int b = 0; b < lb; ++b) {
+        const double* s = E + off(a, b);
+        double* d = E + off(a, b + 1);
+        for (int t = 0; t <= a + b + 1; ++t) {
+          double v = 0.0;
+          if (t >= 1) v = inv2p * s[t - 1];
+          if (t <= a + b) v = fma(XPB, s[t], v);
+          if (t + 1 <= a + b) v = fma(c_dint[t + 1], s[t + 1], v);
+          d[t] = v;
+        }
+      }
+    for (int a = 0; a <= la; ++a)
+      for (int b = 0; b <= lb; ++b) {
+        const int o = off(a, b);
+        for (int t = 0; t <= a + b; ++t) Es[o + t] = (t & 1) ? -E[o + t] : E[o + t];
+      }
+    (void)nt;
+  }
+}
+
+cudaError_t launch_pair_records(const BasisDev& b0, const BasisDev& b1, const PrimPairJob* jobs, int64_t njobs,
+                                double* recs, double* recs_signed, int* err, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  const int bs = 128;
+  const int64_t grid = (njobs + bs - 1) / bs;
+  k_pair_records<<<(unsigned)grid, bs, 0, s>>>(b0, b1, jobs, njobs, recs, recs_signed, err);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- quartets
+template <bool CTA>
+__device__ __forceinline__ void team_sync(unsigned mask) {
+  if (CTA) __syncthreads();
+  else __syncwarp(mask);
+}
+
+// offset of row (t,u) in a [t][u][v] simplex layout of total order N
+__device__ __forceinline__ int d_tet(int n) { return n < 0 ? 0 : n * (n + 1) * (n + 2) / 6; }
+__device__ __forceinline__ int d_tri(int n) { return n < 0 ? 0 : n * (n + 1) / 2; }
+__device__ __forceinline__ int d_roff(int N, int t, int u) {
+  return d_tet(N + 1) - d_tet(N - t + 1) + d_tri(N - t + 1) - d_tri(N - t - u + 1);
+}
+
+__device__ __forceinline__ double ipow(double x, int m) {
+  double r = 1.0;
+  while (m) {
+    if (m & 1) r *= x;
+    x *= x;
+    m >>= 1;
+  }
+  return r;
+}
+
+// Boys seeds [0]^(m) = (-2 rho)^m pref F_m(T), m = 0..L (Eq. 0m), then the
+// Hermite integrals [tuv]^(0) (Eq. r), level by level, into ws[o_R0] with
+// the [t][u][v] layout of total order L.
+template <bool CTA>
+__device__ void compute_R(const QuartetLaunch& a, double* ws, int tl, unsigned mask) {
+  const PlanDev& P = a.plan;
+  const int T = P.T;
+  const int L = P.L;
+  double* scal = ws + P.o_scal;
+  double* G = ws + P.o_G;
+  const double* rb = ws + P.o_recb;
+  const double* rk = ws + P.o_reck;
+  // every lane derives the quartet scalars (cheap, avoids a barrier)
+  const double zp = rb[0], izp = rb[1], zq = rk[0], izq = rk[1];
+  const double PQx = rb[2] - rk[2], PQy = rb[3] - rk[3], PQz = rb[4] - rk[4];
+  const double s = zp + zq;
+  const double rs = rsqrt(s);
+  const double rho = zp * zq * rs * rs;
+  const double Tb = rho * (PQx * PQx + PQy * PQy + PQz * PQz);
+  // 2 pi^(5/2) / (zp zq sqrt(zp+zq)) * c_a c_b K_ab * c_c c_d K_cd
+  const double pref = 34.986836655249725693 * izp * izq * rs * rb[5] * rk[5];
+  if (tl == 0) { scal[0] = PQx; scal[1] = PQy; scal[2] = PQz; }
+  if (Tb < kBoysTmax) {
+    const int i = __double2int_rn(Tb * kBoysInvH);
+    const double d = Tb - (double)i * (1.0 / kBoysInvH);
+    // c_k = (-d)^k / k!
+    double c[kBoysTerms];
+    c[0] = 1.0;
+    const double nd = -d;
+#pragma unroll
+    for (int k = 1; k < kBoysTerms; ++k) c[k] = c[k - 1] * nd * (1.0 / (double)k);
+    const double* row = a.boys + (size_t)i * kBoysRow;
+    const double m2r = -2.0 * rho;
+    for (int m = tl; m <= L; m += T) {
+      double f = 0.0;
+#pragma unroll
+      for (int k = kBoysTerms - 1; k >= 0; --k) f = fma(c[k], __ldg(row + m + k), f);
+      G[m] = pref * ipow(m2r, m) * f;
+    }
+  } else {
+    // F_m(T) = Gamma(m+1/2) / (2 T^(m+1/2)); neglected exp(-T) terms < 1e-17 relative for m <= 25
+    const double t1 = rsqrt(Tb);
+    const double x = -2.0 * rho * t1 * t1;
+    for (int m = tl; m <= L; m += T) G[m] = pref * c_gh[m] * t1 * ipow(x, m);
+  }
+  team_sync<CTA>(mask);
+  double* R0 = ws + P.o_R0;
+  double* R1 = ws + P.o_R1;
+  if (L == 0) {
+    if (tl == 0) R0[0] = G[0];
+    team_sync<CTA>(mask);
+    return;
+  }
+  // level L holds only [000]^(L)
+  if (tl == 0) ((L & 1) ? R1 : R0)[0] = G[L];
+  team_sync<CTA>(mask);
+  for (int n = L - 1; n >= 0; --n) {
+    const int N = L - n;
+    double* dst = (n & 1) ? R1 : R0;
+    const double* src = (n & 1) ? R0 : R1;
+    const uint32_t* dec = a.hdec + a.hdec_off[N];
+    const int cnt = d_tet(N + 1);
+    const double g = G[n];
+    for (int e = tl; e < cnt; e += T) {
+      const uint32_t w = __ldg(dec + e);
+      const int t = w & 0xff, u = (w >> 8) & 0xff, v = (w >> 16) & 0xff;
+      double val;
+      if (v > 0) {
+        const int o = d_roff(N - 1, t, u) + v - 1;
+        val = PQz * src[o];
+        if (v > 1) val = fma(c_dint[v - 1], src[o - 1], val);
+      } else if (u > 0) {
+        val = PQy * src[d_roff(N - 1, t, u - 1)];
+        if (u > 1) val = fma(c_dint[u - 1], src[d_roff(N - 1, t, u - 2)], val);
+      } else if (t > 0) {
+        val = PQx * src[d_roff(N - 1, t - 1, 0)];
+        if (t > 1) val = fma(c_dint[t - 1], src[d_roff(N - 1, t - 2, 0)], val);
+      } else {
+        val = g;
+      }
+      dst[d_roff(N, t, u) + v] = val;
+    }
+    team_sync<CTA>(mask);
+  }
+}
+
+// out = (acc ? out : 0) + sum_k coef[c + k s] src[x + k s]
+__device__ __forceinline__ void run_step(const StepEntry* __restrict__ prog, int n, double* ws, int tl, int T,
+                                         bool acc) {
+  for (int e = tl; e < n; e += T) {
+    const StepEntry s = prog[e];
+    const double* c = ws + s.coef;
+    const double* x = ws + s.src;
+    const int st = s.stride;
+    double v = acc ? ws[s.out] : 0.0;
+    for (int k = 0; k < s.n; ++k) v = fma(c[k * st], x[k * st], v);
+    ws[s.out] = v;
+  }
+}
+
+__device__ __forceinline__ void load_record(double* dst, const double* __restrict__ src, int n, int tl, int T) {
+  for (int i = tl; i < n; i += T) dst[i] = __ldg(src + i);
+}
+
+template <bool CTA>
+__global__ void __launch_bounds__(256) k_quartets(const QuartetLaunch a) {
+  extern __shared__ __align__(16) double smem[];
+  const PlanDev& P = a.plan;
+  const int T = P.T;
+  const int team = threadIdx.x / T;
+  const int tl = threadIdx.x - team * T;
+  double* ws = smem + (size_t)team * P.team_doubles;
+  // lanes of this warp that exist (a partial last warp when the CTA is not a multiple of 32)
+  unsigned mask = 0xffffffffu;
+  if (!CTA) {
+    const int wbase = threadIdx.x & ~31;
+    const int live = blockDim.x - wbase;
+    if (live < 32) mask = (1u << live) - 1u;
+  }
+  int64_t q = (int64_t)blockIdx.x * P.teams_per_cta + team;
+  const bool active = q < a.nq;
+  if (!active) q = a.nq - 1;   // idle teams shadow the last quartet and store nothing
+  const int2 qp = a.qpairs[q];
+  const int64_t bra0 = a.pair_rec[qp.x];
+  const int64_t ket0 = a.pair_rec[qp.y];
+  const int Kb = P.Kb, Kk = P.Kk;
+  if (P.cache_R) {
+    load_record(ws + P.o_recb, a.recs + bra0, P.recb, tl, T);
+    load_record(ws + P.o_reck, a.recs_signed + ket0, P.reck, tl, T);
+    team_sync<CTA>(mask);
+    compute_R<CTA>(a, ws, tl, mask);
+  }
+  double* outq = a.out + a.qout[q];
+  for (int g = 0; g < P.ngroups; ++g) {
+    const Group grp = P.groups[g];
+    const int ncols = grp.ncols;
+    for (int pb = 0; pb < Kb; ++pb) {
+      if (!P.cache_R) load_record(ws + P.o_recb, a.recs + bra0 + (int64_t)pb * P.recb, P.recb, tl, T);
+      for (int pk = 0; pk < Kk; ++pk) {
+        if (!P.cache_R) {
+          load_record(ws + P.o_reck, a.recs_signed + ket0 + (int64_t)pk * P.reck, P.reck, tl, T);
+          team_sync<CTA>(mask);
+          compute_R<CTA>(a, ws, tl, mask);
+        }
+        run_step(P.kprog + grp.k1_off, grp.k1_n, ws, tl, T, false);
+        team_sync<CTA>(mask);
+        run_step(P.kprog + grp.k2_off, grp.k2_n, ws, tl, T, false);
+        team_sync<CTA>(mask);
+        run_step(P.kprog + grp.k3_off, grp.k3_n, ws, tl, T, pk > 0);
+        team_sync<CTA>(mask);
+      }
+      // b1: C1 = Ex (x) X, per column
+      {
+        const int tot = P.nb1 * ncols;
+        for (int e = tl; e < tot; e += T) {
+          const int ent = e / ncols, col = e - ent * ncols;
+          const StepEntry s = P.b1[ent];
+          const double* c = ws + s.coef;
+          const double* x = ws + P.o_X + col * P.hb + s.src;
+          const int st = s.stride;
+          double v = 0.0;
+          for (int k = 0; k < s.n; ++k) v = fma(c[k * st], x[k * st], v);
+          ws[P.o_C1 + col * P.c1size + s.out] = v;
+        }
+      }
+      team_sync<CTA>(mask);
+      // b23: OUT += Ez (x) Ey (x) C1, per column
+      {
+        const int tot = P.nb23 * ncols;
+        for (int e = tl; e < tot; e += T) {
+          const int ent = e / ncols, col = e - ent * ncols;
+          const B23Entry s = P.b23[ent];
+          const double* c1 = ws + P.o_C1 + col * P.c1size + s.src;
+          double* o = ws + P.o_OUT + s.out * ncols + col;
+          double acc = pb > 0 ? *o : 0.0;
+          const int r1 = s.r + 1;
+          for (int iv = 0; iv < s.nv; ++iv) {
+            const int v = s.v0 + iv * s.sv;
+            const double* row = c1 + v * r1 - (v * (v - 1)) / 2 + s.u0;
+            const double* ey = ws + s.ey;
+            double inner = 0.0;
+            for (int iu = 0; iu < s.nu; ++iu) inner = fma(ey[iu * s.su], row[iu * s.su], inner);
+            acc = fma(ws[s.ez + iv * s.sv], inner, acc);
+          }
+          *o = acc;
+        }
+      }
+      team_sync<CTA>(mask);
+    }
+    // store the group's columns: OUT[ab][col] -> out[ab*Nk + cd]
+    if (active) {
+      const uint16_t* cm = P.colmap + grp.col_off;
+      const int tot = P.Nb * ncols;
+      for (int e = tl; e < tot; e += T) {
+        const int ab = e / ncols, col = e - ab * ncols;
+        outq[(int64_t)ab * P.Nk + cm[col]] = ws[P.o_OUT + e];
+      }
+    }
+    team_sync<CTA>(mask);
+  }
+}
+
+cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
+  if (a.nq <= 0) return cudaSuccess;
+  const PlanDev& P = a.plan;
+  const int64_t grid = (a.nq + P.teams_per_cta - 1) / P.teams_per_cta;
+  const int block = P.teams_per_cta * P.T;
+  const size_t shm = (size_t)P.teams_per_cta * P.team_doubles * sizeof(double);
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  if (P.T > 32) k_quartets<true><<<(unsigned)grid, block, shm, s>>>(a);
+  else k_quartets<false><<<(unsigned)grid, block, shm, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- Schwarz
+__global__ void k_schwarz_reduce(const int64_t* __restrict__ off, const int32_t* __restrict__ nab, int64_t n,
+                                 const double* __restrict__ vals, double* __restrict__ Q) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int m = nab[p];
+  const double* v = vals + off[p];
+  double mx = 0.0;
+  for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(v[(int64_t)i * m + i]));
+  Q[p] = sqrt(mx);
+}
+
+cudaError_t launch_schwarz_reduce(const int64_t* off, const int32_t* nab, int64_t n, const double* vals, double* Q,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int bs = 128;
+  k_schwarz_reduce<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(off, nab, n, vals, Q);
+  return cudaGetLastError();
+}
+
+cudaError_t kernel_attributes_init() {
+  double dint[64];
+  for (int i = 0; i < 64; ++i) dint[i] = (double)i;
+  cudaError_t e = cudaMemcpyToSymbol(c_dint, dint, sizeof(dint));
+  if (e != cudaSuccess) return e;
+  double gh[kBoysRow];
+  // sqrt(pi)/2 * (2m-1)!! / 2^m
+  double v = 0.88622692545275801365;
+  for (int m = 0; m < kBoysRow; ++m) {
+    gh[m] = v;
+    v *= (2.0 * m + 1.0) * 0.5;
+  }
+  e = cudaMemcpyToSymbol(c_gh, gh, sizeof(gh));
+  if (e != cudaSuccess) return e;
+  const int maxshm = 227 * 1024;
+  e = cudaFuncSetAttribute(k_quartets<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_quartets<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
+  return e;
+}
+
+}  // namespace mdx

@@ -1,0 +1,129 @@
+// Internal definitions shared by the host planner and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace mdx {
+
+constexpr int kLmax = 6;
+constexpr int kKmax = 32;
+constexpr int kLtot = 4 * kLmax + 1;   // highest Boys order used (gradients need L+1)
+
+// ----------------------------------------------------------------- Boys table
+// F_m(T0 + d) = sum_{k<kBoysTerms} F_{m+k}(T0) (-d)^k / k!, grid T0 = i * h.
+constexpr int kBoysTerms = 8;
+constexpr int kBoysMmax = kLtot;                    // highest m evaluated
+constexpr int kBoysRow = 36;                        // >= kBoysMmax + kBoysTerms, padded
+constexpr double kBoysInvH = 16.0;                  // grid spacing h = 1/16
+constexpr double kBoysTmax = 100.0;                 // asymptotic form above
+constexpr int kBoysNgrid = 1601 + 1;                // T0 = 0 .. 100 (+1 guard row)
+
+// Builds the interpolation table [kBoysNgrid][kBoysRow] (row-major) in long
+// double by downward recursion (see boys_table.cpp).
+std::vector<double> build_boys_table();
+
+// ----------------------------------------------------------------- records
+// Primitive-pair record: header of kRecHeader doubles, then the three per-axis
+// E tables (x, y, z). Header: [0] zeta_p, [1] 1/zeta_p, [2..4] P, [5] prefactor
+// c_a c_b exp(-zeta_a zeta_b |A-B|^2 / zeta_p), [6], [7] unused.
+constexpr int kRecHeader = 8;
+
+inline int etab_size(int la, int lb) {      // sum over a<=la, b<=lb of (a+b+1)
+  int s = 0;
+  for (int a = 0; a <= la; ++a)
+    for (int b = 0; b <= lb; ++b) s += a + b + 1;
+  return s;
+}
+inline int etab_off(int la, int lb, int a, int b) {   // start of (a,b) block; t contiguous
+  (void)la;
+  int s = 0;
+  for (int a2 = 0; a2 < a; ++a2)
+    for (int b2 = 0; b2 <= lb; ++b2) s += a2 + b2 + 1;
+  for (int b2 = 0; b2 < b; ++b2) s += a + b2 + 1;
+  return s;
+}
+inline int rec_size(int la, int lb) {        // padded to a multiple of 2 doubles (16 bytes)
+  int s = kRecHeader + 3 * etab_size(la, lb);
+  return (s + 1) & ~1;
+}
+
+inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+inline int tri(int n) { return n < 0 ? 0 : n * (n + 1) / 2; }
+inline int tet(int n) { return n < 0 ? 0 : n * (n + 1) * (n + 2) / 6; }
+inline int nherm(int l) { return tet(l + 1); }
+
+// ----------------------------------------------------------------- programs
+// A "step" computes entries out = sum_{k<n} coef[c + k*s] * src[x + k*s]
+// (offsets in doubles inside the team's shared-memory workspace).
+struct StepEntry {            // 8 bytes
+  uint16_t out;
+  uint16_t src;
+  uint16_t coef;
+  uint8_t n;
+  uint8_t stride;
+};
+// Two-level bra entry: out += sum_v Ez[ez + v*sv] * sum_u Ey[ey + u*su] * C1[row(v) + u*su]
+// with row(v) = src + v*(r+1) - v*(v-1)/2 (rows of decreasing length r+1-v).
+struct B23Entry {             // 16 bytes
+  uint16_t out;
+  uint16_t src;
+  uint16_t ey;
+  uint16_t ez;
+  uint8_t u0, nu, su, v0;
+  uint8_t nv, sv, r, pad;
+};
+
+struct Group {
+  int32_t k1_off, k1_n;      // k programs are stored back to back in one array
+  int32_t k2_off, k2_n;
+  int32_t k3_off, k3_n;
+  int32_t ncols;             // columns (ket Cartesian pairs cd) of this group
+  int32_t col_off;           // into colmap
+  int32_t o_B;               // start of this group's B region (after its A region)
+  int32_t pad;
+};
+
+struct ClassKey {
+  int la, lb, lc, ld, Kb, Kk, onec;
+  bool operator<(const ClassKey& o) const {
+    const int a[7] = {la, lb, lc, ld, Kb, Kk, onec}, b[7] = {o.la, o.lb, o.lc, o.ld, o.Kb, o.Kk, o.onec};
+    for (int i = 0; i < 7; ++i) if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+
+// Everything the quartet kernel needs about one class (device-visible POD).
+struct PlanDev {
+  int32_t la, lb, lc, ld, Kb, Kk, onec;
+  int32_t L, Lb, Lk, Nb, Nk, hb;         // hb = Nt(Lb)
+  int32_t T, teams_per_cta, team_doubles;
+  int32_t recb, reck;                    // record sizes (doubles)
+  int32_t o_recb, o_reck, o_scal, o_G, o_R0, o_R1, o_A, o_B, o_X, o_C1, o_OUT;
+  int32_t c1size;                        // C1 doubles per column
+  int32_t ngroups, ncols_max;
+  int32_t nb1, nb23;
+  int32_t cache_R;                       // R computed once (single primitive quartet)
+  const Group* groups;
+  const StepEntry* kprog;
+  const StepEntry* b1;
+  const B23Entry* b23;
+  const uint16_t* colmap;
+};
+
+// Host-side plan with its program arrays.
+struct Plan {
+  PlanDev d{};
+  std::vector<Group> groups;
+  std::vector<StepEntry> kprog, b1;
+  std::vector<B23Entry> b23;
+  std::vector<uint16_t> colmap;
+  double exec_fma = 0;     // FMAs executed per primitive-quartet pass (for reports)
+  void* dev_blob = nullptr;
+};
+
+// Builds the plan of a class for a shared-memory budget per CTA (bytes).
+bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::string& err);
+
+}  // namespace mdx

@@ -1,0 +1,420 @@
+// Host planner: turns one integral class into the step programs that the
+// generic quartet kernel executes.
+//
+// The Hermite->Cartesian transforms of the paper (Eqs. ket-from-hermite and
+// bra-from-hermite) contract the 2-index Hermite integrals [p|q] (Eq. pq)
+// with E^{cd}_q and E^{ab}_p. Those matrices are products of per-axis factors
+// (Sec. 2: E_{ab}^p = prod_i (E_i)_{a_i b_i}^{p_i}), so each transform is
+// applied here one Cartesian axis at a time instead of as one dense product:
+//
+//   ket (for every ket column cd = (c, d)):
+//     k1  A_z[t',u',v]  = sum_phi (-1)^phi Ez[cz,dz][phi] R[t',u',v+phi]
+//     k2  B  [t',u ,v]  = sum_nu  (-1)^nu  Ey[cy,dy][nu]  A_z[t',u+nu,v]
+//     k3  X  [t ,u ,v] += sum_tau (-1)^tau Ex[cx,dx][tau] B[t+tau,u,v]       (X = [p|cd])
+//   bra (for every column, per bra primitive pair):
+//     b1  C1[ax,bx; u,v] = sum_t Ex[ax,bx][t] X[t,u,v]
+//     b23 OUT[ab]       += sum_v Ez[az,bz][v] sum_u Ey[ay,by][u] C1[ax,bx; u,v]
+//
+// (the signs (-1)^|q| of Eq. pq are folded into the ket-side E tables). The
+// result is identical to the dense transforms up to rounding order; the FP64
+// operation count is several times lower at l >= 2, which is what matters on a
+// part whose FP64 rate is 1/64 of its FP32 rate.
+//
+// Every step is emitted as a list of entries "out = sum_k coef[c+k*s] *
+// src[x+k*s]" over offsets in the team's shared-memory workspace; only
+// entries some output depends on are emitted.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <set>
+#include <tuple>
+
+#include "mdx_internal.h"
+
+namespace mdx {
+namespace {
+
+struct CartC { int x, y, z; };
+std::vector<CartC> carts(int l) {
+  std::vector<CartC> v;
+  for (int ax = l; ax >= 0; --ax)
+    for (int ay = l - ax; ay >= 0; --ay) v.push_back({ax, ay, l - ax - ay});
+  return v;
+}
+
+// offset of row (t,u) in a [t][u][v] simplex layout of total order N
+inline int roff(int N, int t, int u) { return tet(N + 1) - tet(N - t + 1) + tri(N - t + 1) - tri(N - t - u + 1); }
+
+struct Layout {                  // a set of rows, each a contiguous run of doubles
+  std::map<std::pair<int, int>, int> rowlen;   // row key -> length
+  std::map<std::pair<int, int>, int> rowoff;
+  int size = 0;
+  void need(int r0, int r1, int idx) {         // element idx of row (r0,r1) is used
+    auto& len = rowlen[{r0, r1}];
+    len = std::max(len, idx + 1);
+  }
+  void finalize() {
+    size = 0;
+    for (auto& kv : rowlen) { rowoff[kv.first] = size; size += kv.second; }
+  }
+  int at(int r0, int r1, int idx) const { return rowoff.at({r0, r1}) + idx; }
+};
+
+struct ColInfo { CartC c, d; int gcol; };
+
+// Builds the ket programs of one group of columns; returns false on overflow.
+// Offsets emitted are absolute in the team workspace.
+bool build_group_k(const PlanDev& P, const std::vector<ColInfo>& cols, int o_A, int o_B, int o_X,
+                   std::vector<StepEntry>& k1, std::vector<StepEntry>& k2, std::vector<StepEntry>& k3,
+                   int& a_size, int& b_size, double& fma) {
+  const int Lb = P.Lb, L = P.L;
+  const int Tcd = etab_size(P.lc, P.ld);
+  // B layout per column: rows (u,v), t' contiguous, full rows
+  std::vector<Layout> BL(cols.size());
+  std::map<std::pair<int, int>, Layout> AL;    // per z-pair (cz,dz)
+  for (size_t j = 0; j < cols.size(); ++j) {
+    const CartC& c = cols[j].c; const CartC& d = cols[j].d;
+    const int xx = c.x + d.x, yy = c.y + d.y;
+    for (int u = 0; u <= Lb; ++u)
+      for (int v = 0; u + v <= Lb; ++v) BL[j].need(u, v, Lb - u - v + xx);
+    BL[j].finalize();
+    Layout& A = AL[{c.z, d.z}];
+    for (int u = 0; u <= Lb; ++u)
+      for (int v = 0; u + v <= Lb; ++v)
+        for (int tp = 0; tp <= Lb - u - v + xx; ++tp) A.need(tp, v, u + yy);
+  }
+  // A blocks back to back
+  std::map<std::pair<int, int>, int> abase;
+  int asz = 0;
+  for (auto& kv : AL) { kv.second.finalize(); abase[kv.first] = asz; asz += kv.second.size; }
+  std::vector<int> bbase(cols.size());
+  int bsz = 0;
+  for (size_t j = 0; j < cols.size(); ++j) { bbase[j] = bsz; bsz += BL[j].size; }
+  a_size = asz; b_size = bsz;
+  const int reck = P.o_reck + kRecHeader;
+  auto push = [&](std::vector<StepEntry>& v, long out, long src, long coef, int n) {
+    if (out > 65535 || src > 65535 || coef > 65535 || n > 255) return false;
+    v.push_back(StepEntry{(uint16_t)out, (uint16_t)src, (uint16_t)coef, (uint8_t)n, (uint8_t)1});
+    fma += n;
+    return true;
+  };
+  // k1: A_z[t',u',v] = sum_phi Ez'[cz,dz][phi] R[t',u',v+phi]
+  for (auto& kv : AL) {
+    const int cz = kv.first.first, dz = kv.first.second;
+    const int coef = reck + 2 * Tcd + etab_off(P.lc, P.ld, cz, dz);
+    for (auto& row : kv.second.rowlen) {
+      const int tp = row.first.first, v = row.first.second;
+      for (int up = 0; up < row.second; ++up) {
+        if (tp + up + v + cz + dz > L) return false;   // cannot happen (see derivation)
+        if (!push(k1, o_A + abase[kv.first] + kv.second.at(tp, v, up), P.o_R0 + roff(L, tp, up) + v, coef, cz + dz + 1))
+          return false;
+      }
+    }
+  }
+  for (size_t j = 0; j < cols.size(); ++j) {
+    const CartC& c = cols[j].c; const CartC& d = cols[j].d;
+    const int xx = c.x + d.x, yy = c.y + d.y;
+    const Layout& A = AL[{c.z, d.z}];
+    const int ab0 = o_A + abase[{c.z, d.z}];
+    const int coefy = reck + Tcd + etab_off(P.lc, P.ld, c.y, d.y);
+    const int coefx = reck + etab_off(P.lc, P.ld, c.x, d.x);
+    // k2: B[t',u,v] = sum_nu Ey'[cy,dy][nu] A[t',u+nu,v]
+    for (auto& row : BL[j].rowlen) {
+      const int u = row.first.first, v = row.first.second;
+      for (int tp = 0; tp < row.second; ++tp)
+        if (!push(k2, o_B + bbase[j] + BL[j].at(u, v, tp), ab0 + A.at(tp, v, u), coefy, yy + 1)) return false;
+    }
+    // k3: X[t,u,v] += sum_tau Ex'[cx,dx][tau] B[t+tau,u,v]
+    for (int u = 0; u <= Lb; ++u)
+      for (int v = 0; u + v <= Lb; ++v)
+        for (int t = 0; t + u + v <= Lb; ++t) {
+          const int xo = o_X + (int)j * P.hb + roff(Lb, u, v) + t;   // X rows (u,v), t contiguous
+          if (!push(k3, xo, o_B + bbase[j] + BL[j].at(u, v, t), coefx, xx + 1)) return false;
+        }
+  }
+  return true;
+}
+
+// Sort a step's entries so that neighbouring lanes run loops of equal length.
+void sort_by_n(std::vector<StepEntry>& v) {
+  std::stable_sort(v.begin(), v.end(), [](const StepEntry& a, const StepEntry& b) { return a.n > b.n; });
+}
+
+// Every shared-memory access the kernel will make from these programs stays
+// inside the team's workspace and inside the region it belongs to.
+bool validate_plan(const Plan& plan, std::string& err) {
+  const PlanDev& P = plan.d;
+  const long W = P.team_doubles;
+  auto in = [&](long lo, long hi, long a) { return a >= lo && a < hi; };
+  const long xr = P.o_X, cr = P.o_C1, orr = P.o_OUT;
+  for (const Group& g : plan.groups) {
+    if (g.ncols < 1 || g.ncols > P.ncols_max) { err = "bad group width"; return false; }
+    const StepEntry* k = plan.kprog.data();
+    for (int i = 0; i < g.k1_n + g.k2_n + g.k3_n; ++i) {
+      const StepEntry& s = k[g.k1_off + i];
+      const long last = (long)(s.n - 1) * s.stride;
+      if (s.n < 1 || !in(0, W, s.out) || !in(0, W, s.src + last) || !in(0, W, s.coef + last)) {
+        err = "ket program entry out of the workspace";
+        return false;
+      }
+    }
+    // k1 reads R0 and writes A; k2 reads A writes B; k3 reads B writes X
+    for (int i = 0; i < g.k1_n; ++i) {
+      const StepEntry& s = k[g.k1_off + i];
+      if (!in(P.o_R0, P.o_R0 + tet(P.L + 1), s.src) || !in(P.o_R0, P.o_R0 + tet(P.L + 1), s.src + s.n - 1) ||
+          !in(P.o_A, g.o_B, s.out)) { err = "k1 entry outside R/A"; return false; }
+    }
+    for (int i = 0; i < g.k2_n; ++i) {
+      const StepEntry& s = k[g.k2_off + i];
+      if (!in(P.o_A, g.o_B, s.src) || !in(P.o_A, g.o_B, s.src + s.n - 1) || !in(g.o_B, P.o_X, s.out)) {
+        err = "k2 entry outside A/B"; return false;
+      }
+    }
+    for (int i = 0; i < g.k3_n; ++i) {
+      const StepEntry& s = k[g.k3_off + i];
+      if (!in(g.o_B, P.o_X, s.src) || !in(g.o_B, P.o_X, s.src + s.n - 1) ||
+          !in(xr, xr + (long)g.ncols * P.hb, s.out)) { err = "k3 entry outside B/X"; return false; }
+    }
+    for (int i = g.col_off; i < g.col_off + g.ncols; ++i)
+      if (plan.colmap[i] >= P.Nk) { err = "column map out of range"; return false; }
+  }
+  const long ncm = P.ncols_max;
+  for (const StepEntry& s : plan.b1) {
+    const long last = (long)(s.n - 1) * s.stride;
+    if (!in(0, P.hb, s.src) || !in(0, P.hb, s.src + last) || !in(0, P.c1size, s.out) ||
+        !in(P.o_recb, P.o_recb + P.recb, s.coef) || !in(P.o_recb, P.o_recb + P.recb, s.coef + last) ||
+        xr + (ncm - 1) * P.hb + P.hb > cr) { err = "b1 entry out of range"; return false; }
+  }
+  for (const B23Entry& s : plan.b23) {
+    const int vmax = s.v0 + (s.nv - 1) * s.sv;
+    const long rowmax = (long)vmax * (s.r + 1) - (long)vmax * (vmax - 1) / 2;
+    const long umax = s.u0 + (long)(s.nu - 1) * s.su;
+    if (s.out >= P.Nb || !in(0, P.c1size, s.src + rowmax + umax) || umax > s.r - vmax ||
+        !in(P.o_recb, P.o_recb + P.recb, s.ey + (long)(s.nu - 1) * s.su) ||
+        !in(P.o_recb, P.o_recb + P.recb, s.ez + (long)(s.nv - 1) * s.sv) ||
+        cr + ncm * P.c1size > orr || orr + ncm * P.Nb > W) { err = "b23 entry out of range"; return false; }
+  }
+  if (P.o_R1 + tet(P.L) > P.o_X || P.o_R0 + tet(P.L + 1) > P.o_R1 || P.o_G + P.L + 1 > P.o_R0 ||
+      P.o_reck + P.reck > P.o_scal) { err = "fixed regions overlap"; return false; }
+  return true;
+}
+
+}  // namespace
+
+bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::string& err) {
+  PlanDev& P = plan.d;
+  P = PlanDev{};
+  P.la = key.la; P.lb = key.lb; P.lc = key.lc; P.ld = key.ld;
+  P.Kb = key.Kb; P.Kk = key.Kk; P.onec = key.onec;
+  if (key.onec && key.lb != 0) { err = "one-centre bra needs lb = 0"; return false; }
+  P.Lb = key.la + key.lb; P.Lk = key.lc + key.ld; P.L = P.Lb + P.Lk;
+  P.Nb = ncart(key.la) * ncart(key.lb); P.Nk = ncart(key.lc) * ncart(key.ld);
+  P.hb = nherm(P.Lb);
+  P.recb = rec_size(key.la, key.lb);
+  P.reck = rec_size(key.lc, key.ld);
+  const int Tab = etab_size(key.la, key.lb);
+  const auto ca = carts(key.la), cb = carts(key.lb), cc = carts(key.lc), cd = carts(key.ld);
+
+  // fixed part of the workspace
+  P.o_recb = 0;
+  P.o_reck = P.recb;
+  P.o_scal = P.o_reck + P.reck;          // PQ[3], pad, Taylor c[8]
+  P.o_G = P.o_scal + 16;
+  P.o_R0 = P.o_G + ((P.L + 2 + 1) & ~1);
+  const int r0size = tet(P.L + 1);
+  const int r1size = tet(P.L);
+  const int o_region = P.o_R0 + ((r0size + 1) & ~1);
+
+  // ---- bra templates (per column) -------------------------------------
+  // C1 per column: blocks (ax,bx), rows v = 0..r, row v holds u = 0..r-v
+  std::map<std::pair<int, int>, int> c1off;
+  int c1 = 0;
+  for (int ax = 0; ax <= key.la; ++ax)
+    for (int bx = 0; bx <= key.lb; ++bx) {
+      c1off[{ax, bx}] = c1;
+      c1 += tri(P.Lb - ax - bx + 1);
+    }
+  P.c1size = c1;
+  const int recb_tab = P.o_recb + kRecHeader;
+  plan.b1.clear(); plan.b23.clear();
+  double fma_b = 0;
+  for (int ax = 0; ax <= key.la; ++ax)
+    for (int bx = 0; bx <= key.lb; ++bx) {
+      const int r = P.Lb - ax - bx;
+      const int t0 = key.onec ? (ax & 1) : 0, st = key.onec ? 2 : 1;
+      const int n = key.onec ? (ax - t0) / 2 + 1 : ax + bx + 1;
+      for (int v = 0; v <= r; ++v)
+        for (int u = 0; u + v <= r; ++u) {
+          const int out = c1off[{ax, bx}] + v * (r + 1) - v * (v - 1) / 2 + u;
+          const int src = roff(P.Lb, u, v) + t0;
+          const int coef = recb_tab + etab_off(key.la, key.lb, ax, bx) + t0;
+          plan.b1.push_back(StepEntry{(uint16_t)out, (uint16_t)src, (uint16_t)coef, (uint8_t)n, (uint8_t)st});
+          fma_b += n;
+        }
+    }
+  sort_by_n(plan.b1);
+  for (size_t ia = 0; ia < ca.size(); ++ia)
+    for (size_t ib = 0; ib < cb.size(); ++ib) {
+      const CartC a = ca[ia], b = cb[ib];
+      const int r = P.Lb - a.x - b.x;
+      B23Entry e{};
+      e.out = (uint16_t)(ia * cb.size() + ib);
+      e.src = (uint16_t)c1off[{a.x, b.x}];
+      e.r = (uint8_t)r;
+      if (key.onec) {
+        e.u0 = (uint8_t)(a.y & 1); e.su = 2; e.nu = (uint8_t)((a.y - e.u0) / 2 + 1);
+        e.v0 = (uint8_t)(a.z & 1); e.sv = 2; e.nv = (uint8_t)((a.z - e.v0) / 2 + 1);
+      } else {
+        e.u0 = 0; e.su = 1; e.nu = (uint8_t)(a.y + b.y + 1);
+        e.v0 = 0; e.sv = 1; e.nv = (uint8_t)(a.z + b.z + 1);
+      }
+      e.ey = (uint16_t)(recb_tab + Tab + etab_off(key.la, key.lb, a.y, b.y) + e.u0);
+      e.ez = (uint16_t)(recb_tab + 2 * Tab + etab_off(key.la, key.lb, a.z, b.z) + e.v0);
+      plan.b23.push_back(e);
+      fma_b += e.nv * (e.nu + 1.0);
+    }
+  std::stable_sort(plan.b23.begin(), plan.b23.end(),
+                   [](const B23Entry& x, const B23Entry& y) { return x.nu * x.nv > y.nu * y.nv; });
+  P.nb1 = (int)plan.b1.size();
+  P.nb23 = (int)plan.b23.size();
+
+  // ---- columns ----------------------------------------------------------
+  std::vector<ColInfo> allcols;
+  for (size_t ic = 0; ic < cc.size(); ++ic)
+    for (size_t id = 0; id < cd.size(); ++id) allcols.push_back({cc[ic], cd[id], (int)(ic * cd.size() + id)});
+
+  auto region_size = [&](int a_size, int b_size) { return std::max(r1size, a_size + b_size); };
+  auto team_doubles = [&](int a_size, int b_size, int ncols) {
+    int reg = (region_size(a_size, b_size) + 1) & ~1;
+    int tot = o_region + reg + ncols * P.hb + ncols * P.c1size + ncols * P.Nb;
+    return (tot + 1) & ~1;
+  };
+
+  // try a single group holding every column
+  std::vector<std::vector<ColInfo>> groups;
+  auto group_sizes = [&](const std::vector<ColInfo>& g, int& as, int& bs) {
+    std::vector<StepEntry> k1, k2, k3;
+    double f = 0;
+    return build_group_k(P, g, 0, 0, 0, k1, k2, k3, as, bs, f);
+  };
+  {
+    int as = 0, bs = 0;
+    bool ok = group_sizes(allcols, as, bs);
+    const int td = team_doubles(as, bs, (int)allcols.size());
+    if (ok && td * 8 <= std::min(smem_budget_bytes, 96 * 1024)) groups.push_back(allcols);
+  }
+  int regmax = 0, cmax = 0;
+  if (groups.empty()) {
+    // one group per z-pair, columns split into chunks of at most `cap` so that
+    // the largest region plus the widest group fit the budget together
+    std::map<std::pair<int, int>, std::vector<ColInfo>> byz;
+    for (auto& c : allcols) byz[{c.c.z, c.d.z}].push_back(c);
+    size_t cap = 0;
+    for (auto& kv : byz) cap = std::max(cap, kv.second.size());
+    while (true) {
+      groups.clear();
+      regmax = 0; cmax = 0;
+      bool ok = true;
+      for (auto& kv : byz) {
+        std::vector<ColInfo>& cs = kv.second;
+        for (size_t s0 = 0; s0 < cs.size(); s0 += cap) {
+          groups.emplace_back(cs.begin() + s0, cs.begin() + std::min(cs.size(), s0 + cap));
+          int as = 0, bs = 0;
+          if (!group_sizes(groups.back(), as, bs)) ok = false;
+          regmax = std::max(regmax, region_size(as, bs));
+          cmax = std::max(cmax, (int)groups.back().size());
+        }
+      }
+      const int td = o_region + ((regmax + 1) & ~1) + cmax * (P.hb + P.c1size + P.Nb);
+      if (ok && td * 8 <= smem_budget_bytes) break;
+      if (cap == 1) { err = "class does not fit the shared-memory budget"; return false; }
+      cap = (cap + 1) / 2;
+    }
+  } else {
+    int as = 0, bs = 0;
+    group_sizes(groups[0], as, bs);
+    regmax = region_size(as, bs);
+    cmax = (int)groups[0].size();
+  }
+  P.o_R1 = o_region;
+  P.o_A = o_region;
+  const int reg = (regmax + 1) & ~1;
+  P.o_B = o_region;   // per group: o_A + that group's A size (programs carry absolute offsets)
+  P.o_X = o_region + reg;
+  P.o_C1 = P.o_X + cmax * P.hb;
+  P.o_OUT = P.o_C1 + cmax * P.c1size;
+  P.team_doubles = ((P.o_OUT + cmax * P.Nb) + 1) & ~1;
+  P.ncols_max = cmax;
+  if (P.team_doubles >= 65536 || P.team_doubles * 8 > smem_budget_bytes) {
+    err = "workspace exceeds the shared-memory budget";
+    return false;
+  }
+
+  // emit the group programs with final offsets
+  plan.groups.clear(); plan.kprog.clear(); plan.colmap.clear();
+  double fma_k = 0;
+  for (auto& g : groups) {
+    std::vector<StepEntry> k1, k2, k3;
+    int as = 0, bs = 0; double f = 0;
+    group_sizes(g, as, bs);
+    const int oB = P.o_A + as;
+    if (!build_group_k(P, g, P.o_A, oB, P.o_X, k1, k2, k3, as, bs, f)) {
+      err = "program offsets overflow";
+      return false;
+    }
+    fma_k += f;
+    sort_by_n(k1); sort_by_n(k2); sort_by_n(k3);
+    Group G{};
+    G.k1_off = (int)plan.kprog.size(); G.k1_n = (int)k1.size();
+    plan.kprog.insert(plan.kprog.end(), k1.begin(), k1.end());
+    G.k2_off = (int)plan.kprog.size(); G.k2_n = (int)k2.size();
+    plan.kprog.insert(plan.kprog.end(), k2.begin(), k2.end());
+    G.k3_off = (int)plan.kprog.size(); G.k3_n = (int)k3.size();
+    plan.kprog.insert(plan.kprog.end(), k3.begin(), k3.end());
+    G.ncols = (int)g.size();
+    G.o_B = oB;
+    G.col_off = (int)plan.colmap.size();
+    for (auto& c : g) plan.colmap.push_back((uint16_t)c.gcol);
+    plan.groups.push_back(G);
+  }
+  P.ngroups = (int)plan.groups.size();
+  P.cache_R = (key.Kb * key.Kk == 1) ? 1 : 0;
+
+  // R recursion work: every level n < L has tet(L-n+1) - 1 entries of <= 2 ops
+  double fma_r = 0;
+  for (int n = 0; n < P.L; ++n) fma_r += tet(P.L - n + 1) - 1;
+  const double nrec = (P.cache_R || P.ngroups == 1) ? 1.0 : P.ngroups;
+  plan.exec_fma = key.Kb * key.Kk * (fma_k + nrec * (fma_r + 8.0 * (P.L + 1))) + key.Kb * fma_b * P.Nk;
+
+  if (!validate_plan(plan, err)) return false;
+
+  // ---- team shape ------------------------------------------------------
+  const int bytes = P.team_doubles * 8;
+  if (P.ngroups > 1) {
+    P.T = 256;
+    P.teams_per_cta = 1;
+  } else {
+    int tps = std::max(1, (220 * 1024) / bytes);
+    int Tocc = 1;
+    while (Tocc * tps < 256 && Tocc < 256) Tocc *= 2;
+    int work = std::max(1, P.Nb * P.Nk / 8);
+    int Twork = 1;
+    while (Twork * 2 <= work && Twork < 256) Twork *= 2;
+    P.T = std::min(Tocc, Twork);
+    if (P.T > 32) {
+      P.teams_per_cta = 1;
+    } else {
+      int tpc = std::max(1, 128 / P.T);
+      tpc = std::min(tpc, tps);
+      while (tpc > 1 && tpc * bytes > smem_budget_bytes) --tpc;
+      P.teams_per_cta = tpc;
+    }
+  }
+  if (P.T * P.teams_per_cta > 1024 || (long)P.teams_per_cta * P.team_doubles * 8 > 227 * 1024) {
+    err = "team shape exceeds the CTA limits";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace mdx

@@ -1,0 +1,183 @@
+"""Python binding of the C ABI in include/mdx.h (argument marshalling only).
+
+Every integral is computed by the CUDA kernels of libmdx.so; this module only
+moves torch tensors' device pointers and sizes across the ABI. There is no
+CPU fallback: if the library is missing or no CUDA device is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+
+
+class MdxError(RuntimeError):
+    pass
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("n_shells", ctypes.c_int32), ("n_prims", ctypes.c_int32),
+                ("l", ctypes.c_void_p), ("nprim", ctypes.c_void_p), ("prim_off", ctypes.c_void_p),
+                ("ao_off", ctypes.c_void_p), ("atom", ctypes.c_void_p), ("center", ctypes.c_void_p),
+                ("exps", ctypes.c_void_p), ("coefs", ctypes.c_void_p)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("team_threads", ctypes.c_int32), ("teams_per_cta", ctypes.c_int32),
+                ("smem_bytes_per_team", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("exec_fma", ctypes.c_double)]
+
+
+def plan_info(la, lb, lc, ld, Kb=1, Kk=1, one_centre=False) -> PlanStats:
+    """Team shape and executed FP64 FMA count per shellset of a class (host planner, no GPU)."""
+    lib = load()
+    st = PlanStats()
+    rc = lib.mdx_plan_info(None, la, lb, lc, ld, Kb, Kk, int(one_centre), ctypes.byref(st))
+    if rc != 0:
+        raise MdxError("mdx_plan_info(%d,%d,%d,%d): %s" % (la, lb, lc, ld, STATUS.get(rc, rc)))
+    return st
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmdx.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise MdxError("libmdx.so is not built (run paper_2405_01834_gb300.build)")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.mdx_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I32]
+    lib.mdx_create.restype = I32
+    lib.mdx_destroy.argtypes = [P]
+    lib.mdx_destroy.restype = None
+    lib.mdx_last_error.argtypes = [P]
+    lib.mdx_last_error.restype = ctypes.c_char_p
+    lib.mdx_sync.argtypes = [P, P]
+    lib.mdx_sync.restype = I32
+    lib.mdx_eri4.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
+    lib.mdx_eri4.restype = I32
+    lib.mdx_eri3.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
+    lib.mdx_eri3.restype = I32
+    lib.mdx_schwarz.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, P]
+    lib.mdx_schwarz.restype = I32
+    lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
+    lib.mdx_plan_info.restype = I32
+    _lib = lib
+    return lib
+
+
+STATUS = {0: "MDX_OK", 1: "MDX_EINVAL", 2: "MDX_ENOMEM", 3: "MDX_ECUDA", 4: "MDX_EUNSUPPORTED",
+          5: "MDX_ECAPACITY", 6: "MDX_ETIMEOUT", 7: "MDX_EDEVICE"}
+
+
+class DeviceBasis:
+    """A seeded `inputs.Basis` copied to the device, with its ABI descriptor."""
+
+    def __init__(self, basis, device="cuda"):
+        self.host = basis
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        self.l = t(basis.l, torch.int32)
+        self.nprim = t(basis.nprim, torch.int32)
+        self.prim_off = t(basis.prim_off, torch.int32)
+        self.ao_off = t(basis.ao_off, torch.int32)
+        self.atom = t(basis.atom, torch.int32)
+        self.center = t(basis.center, torch.float64)
+        self.exps = t(basis.exps, torch.float64)
+        self.coefs = t(basis.coefs, torch.float64)
+        self.desc = _Basis(int(basis.n_shells), int(len(basis.exps)), self.l.data_ptr(), self.nprim.data_ptr(),
+                           self.prim_off.data_ptr(), self.ao_off.data_ptr(), self.atom.data_ptr(),
+                           self.center.data_ptr(), self.exps.data_ptr(), self.coefs.data_ptr())
+        self.nc = (basis.l.astype(np.int64) + 1) * (basis.l.astype(np.int64) + 2) // 2
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Engine:
+    """One mdx context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        if not torch.cuda.is_available():
+            raise MdxError("no CUDA device: the mdx engine has no CPU path")
+        self.lib = load()
+        self.device = device
+        torch.cuda.set_device(device)
+        h = ctypes.c_void_p()
+        st = self.lib.mdx_create(ctypes.byref(h), device)
+        if st != 0:
+            raise MdxError("mdx_create failed: %s" % STATUS.get(st, st))
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            torch.cuda.synchronize()
+            self.lib.mdx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.mdx_last_error(self.ctx).decode()
+            raise MdxError("%s: %s (%s)" % (what, STATUS.get(st, st), msg))
+
+    def sync(self):
+        self._check(self.lib.mdx_sync(self.ctx, _stream()), "mdx_sync")
+
+    # ----------------------------------------------------------------
+    def eri4(self, basis: DeviceBasis, quartets, out: torch.Tensor = None):
+        """[ab|cd] for quartets [n,4] (device int32). Returns (values, offsets[n+1])."""
+        q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
+        n = q.shape[0]
+        if out is None:
+            qn = q.cpu().numpy().astype(np.int64)
+            nc = basis.nc
+            tot = int(np.sum(nc[qn[:, 0]] * nc[qn[:, 1]] * nc[qn[:, 2]] * nc[qn[:, 3]])) if n else 0
+            out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        st = self.lib.mdx_eri4(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), n, out.data_ptr(), out.numel(),
+                               offs.data_ptr(), _stream())
+        self._check(st, "mdx_eri4")
+        return out, offs
+
+    def eri3(self, aux: DeviceBasis, orb: DeviceBasis, triplets, out: torch.Tensor = None):
+        """[a|cd] for triplets [n,3] = (aux shell, orb shell, orb shell). Returns (values, offsets)."""
+        t = torch.as_tensor(triplets, dtype=torch.int32, device="cuda").contiguous()
+        n = t.shape[0]
+        if out is None:
+            tn = t.cpu().numpy().astype(np.int64)
+            tot = int(np.sum(aux.nc[tn[:, 0]] * orb.nc[tn[:, 1]] * orb.nc[tn[:, 2]])) if n else 0
+            out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        st = self.lib.mdx_eri3(self.ctx, ctypes.byref(aux.desc), ctypes.byref(orb.desc), t.data_ptr(), n,
+                               out.data_ptr(), out.numel(), offs.data_ptr(), _stream())
+        self._check(st, "mdx_eri3")
+        return out, offs
+
+    def schwarz(self, basis: DeviceBasis, pairs):
+        """Q_ij = sqrt(max |(ij|ij)|) for pairs [n,2]."""
+        p = torch.as_tensor(pairs, dtype=torch.int32, device="cuda").contiguous()
+        Q = torch.empty(max(p.shape[0], 1), dtype=torch.float64, device="cuda")
+        st = self.lib.mdx_schwarz(self.ctx, ctypes.byref(basis.desc), p.data_ptr(), p.shape[0], Q.data_ptr(),
+                                  _stream())
+        self._check(st, "mdx_schwarz")
+        return Q[: p.shape[0]]

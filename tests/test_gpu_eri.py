@@ -1,0 +1,144 @@
+"""GPU parity: the CUDA engine (through the C ABI) against the CPU oracle.
+
+Inputs are seeded and synthetic (paper_2405_01834_gb300.inputs); the oracle
+is the plain CPU McMurchie-Davidson code in oracle/. Tolerance: tests/parity.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+from paper_2405_01834_gb300 import inputs, mdx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    e = mdx.Engine(0)
+    yield e
+    e.close()
+
+
+def _gpu4(eng, basis, q):
+    db = mdx.DeviceBasis(basis)
+    v, off = eng.eri4(db, q)
+    torch.cuda.synchronize()
+    return v.cpu().numpy(), off.cpu().numpy()
+
+
+def test_small_molecule_all_unique_quartets(eng):
+    """Config-1 shape: 6 atoms with s,p,d shells, K = 3, every unique quartet."""
+    b = inputs.small_molecule()
+    q = inputs.unique_quartets(b.n_shells)
+    assert len(q) == 14706
+    v, off = _gpu4(eng, b, q)
+    ref, roff = oracle.eri4(b, q)
+    assert np.array_equal(off, roff)
+    r = parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "config-1")
+    print(r)
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4, 5, 6])
+def test_class_sweep_grid(eng, l):
+    """Config-2 shape at a size the oracle finishes in seconds: a 5 x 3 grid of
+    random bra/ket pairs of class [ll|ll], K = 1, exponents in [0.05, 50]."""
+    nb, nk = (5, 3) if l < 6 else (3, 2)
+    b, q = inputs.class_sweep((l, l, l, l), n_bra=nb, n_ket=nk, seed=77)
+    v, off = _gpu4(eng, b, q)
+    ref, roff = oracle.eri4(b, q)
+    assert np.array_equal(off, roff)
+    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "sweep l=%d" % l)
+
+
+MIXED = [(0, 1, 2, 3), (3, 2, 1, 0), (6, 0, 0, 0), (0, 0, 0, 6), (2, 6, 1, 4), (5, 0, 4, 1), (1, 3, 6, 2),
+         (4, 4, 0, 2), (6, 5, 1, 1), (0, 6, 6, 0)]
+
+
+@pytest.mark.parametrize("lq", MIXED)
+def test_mixed_classes_contracted(eng, lq):
+    """Unequal angular momenta in every position, contraction degrees 1-3."""
+    K = tuple(1 + (x % 3) for x in lq) if max(lq) < 5 else (1, 2, 1, 2)
+    b, q = inputs.class_sweep(lq, n_bra=3, n_ket=2, seed=5, K=K)
+    v, off = _gpu4(eng, b, q)
+    ref, _ = oracle.eri4(b, q)
+    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "mixed %s" % (lq,))
+
+
+def test_random_quartets_many_classes(eng):
+    """200 random quartets over a basis of s..i shells with K in 1..3: many
+    classes in one call, ragged class sizes, shells repeated across quartets."""
+    rng = np.random.Generator(np.random.PCG64(99))
+    bb = inputs.BasisBuilder()
+    for i in range(14):
+        l = i % 7
+        K = 1 if l >= 4 else 1 + i % 3
+        inputs.random_shell(rng, bb, l, rng.uniform(0, 5, 3), K, 0.1, 20.0)
+    b = bb.build()
+    q = inputs.random_quartets(b, 200, seed=3)
+    # keep the oracle time modest: drop quartets with total L > 14
+    L = b.l[q].sum(axis=1)
+    q = q[L <= 14]
+    v, off = _gpu4(eng, b, q)
+    ref, _ = oracle.eri4(b, q)
+    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "random")
+
+
+def test_empty_and_single(eng):
+    b = inputs.small_molecule(n_atoms=1)
+    db = mdx.DeviceBasis(b)
+    v, off = eng.eri4(db, np.zeros((0, 4), dtype=np.int32))
+    assert off.cpu().numpy().tolist() == [0]
+    q = np.array([[2, 2, 2, 2]], dtype=np.int32)
+    v, off = eng.eri4(db, q)
+    ref, _ = oracle.eri4(b, q)
+    parity.check(v.cpu().numpy()[: int(off[-1])], ref, None, "single")
+
+
+def test_errors_are_reported(eng):
+    b = inputs.small_molecule(n_atoms=1)
+    db = mdx.DeviceBasis(b)
+    with pytest.raises(mdx.MdxError, match="EINVAL"):
+        eng.eri4(db, np.array([[0, 0, 0, 99]], dtype=np.int32))
+    with pytest.raises(mdx.MdxError, match="ECAPACITY"):
+        eng.eri4(db, np.array([[2, 2, 2, 2]], dtype=np.int32), out=torch.empty(10, dtype=torch.float64, device="cuda"))
+    bad = inputs.small_molecule(n_atoms=1)
+    bad.l = bad.l.copy()
+    bad.l[0] = 7
+    with pytest.raises(mdx.MdxError, match="EUNSUPPORTED"):
+        eng.eri4(mdx.DeviceBasis(bad), np.array([[0, 0, 0, 0]], dtype=np.int32))
+    # the context stays usable
+    v, off = eng.eri4(db, np.array([[0, 1, 2, 0]], dtype=np.int32))
+    ref, _ = oracle.eri4(b, [[0, 1, 2, 0]])
+    parity.check(v.cpu().numpy()[: int(off[-1])], ref, None, "after errors")
+
+
+@pytest.mark.parametrize("la", [0, 1, 2, 3, 4, 5, 6])
+def test_three_center(eng, la):
+    """[a|cd]: auxiliary shell a (K=1) against contracted orbital pairs (K 6/3/1)."""
+    aux_all, orb = inputs.df_cluster(seed=11, n_atoms=3)
+    sel = np.where(aux_all.l == la)[0][:2]
+    rng = np.random.Generator(np.random.PCG64(la))
+    pairs = rng.integers(0, orb.n_shells, (6, 2))
+    t = np.array([[a, c, d] for a in sel for c, d in pairs], dtype=np.int32)
+    daux, dorb = mdx.DeviceBasis(aux_all), mdx.DeviceBasis(orb)
+    v, off = eng.eri3(daux, dorb, t)
+    torch.cuda.synchronize()
+    ref, roff = oracle.eri3(aux_all, orb, t)
+    assert np.array_equal(off.cpu().numpy(), roff)
+    parity.check(v.cpu().numpy()[: roff[-1]], ref, oracle.eri3(aux_all, orb, t, precision=1)[0], "3c la=%d" % la)
+
+
+def test_schwarz(eng):
+    b = inputs.small_molecule(n_atoms=3)
+    pairs = np.array([(i, j) for i in range(b.n_shells) for j in range(i + 1)], dtype=np.int32)
+    Q = eng.schwarz(mdx.DeviceBasis(b), pairs).cpu().numpy()
+    q4 = np.array([(i, j, i, j) for i, j in pairs], dtype=np.int32)
+    ref, off = oracle.eri4(b, q4)
+    refQ = []
+    for n, (i, j) in enumerate(pairs):
+        m = inputs.ncart(int(b.l[i])) * inputs.ncart(int(b.l[j]))
+        blk = ref[off[n]:off[n + 1]].reshape(m, m)
+        refQ.append(np.sqrt(np.max(np.abs(np.diag(blk)))))
+    np.testing.assert_allclose(Q, refQ, rtol=1e-12, atol=0)
