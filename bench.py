@@ -1,0 +1,365 @@
+"""Benchmark: McMurchie-Davidson 4-center ERI class sweep on one GB300.
+
+Workload (one "step"): the per-class microbenchmark of Asadchev & Valeev
+(arXiv:2405.01834, Sec. 5) in Cartesian form -- for each class [pp|pp],
+[dd|dd], [ff|ff], [gg|gg], [hh|hh], [ii|ii], a 224 x 224 grid (50,176
+quartets) of random uncontracted bra and ket shell pairs (centres uniform in
+a 10-bohr box, exponents log-uniform in [0.05, 50]); outputs are written to a
+reused device buffer in chunks (the [ii|ii] class alone is 247 GB).
+
+Metric: model FP64 GFLOP/s (the paper's Table 1 work model for contracted
+Cartesian shellsets) and shell quartets per second, per class and for the
+whole sweep, with the fraction of the GB300 FP64 peak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2405_01834_gb300 import flops, inputs  # noqa: E402
+
+CLASS_NAMES = {1: "[pp|pp]", 2: "[dd|dd]", 3: "[ff|ff]", 4: "[gg|gg]", 5: "[hh|hh]", 6: "[ii|ii]"}
+METRIC = "FP64 GFLOP/s (model) and shell-quartets/s per class; % of GB300 FP64 peak"
+UNIT = "GFLOP/s"
+# GB300 FP64 pipe: 2 DFMA per clock per SM (measured with a DFMA throughput
+# probe: 1203 GFLOP/s at ~1.98 GHz), 152 SMs, 2070 MHz maximum SM clock.
+FP64_FLOP_PER_CLK_SM = 4.0
+CHUNK_BYTES = 2 << 30
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mdx", choices=["mdx", "reference"])
+    ap.add_argument("--classes", default="1,2,3,4,5,6")
+    ap.add_argument("--n-bra", type=int, default=224)
+    ap.add_argument("--n-ket", type=int, default=224)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    ls = [int(x) for x in args.classes.split(",") if x]
+    out = []
+    for l in ls:
+        b, q = inputs.class_sweep((l, l, l, l), n_bra=args.n_bra, n_ket=args.n_ket)
+        out.append((l, b, q))
+    return out
+
+
+def model_flops(l, n):
+    return flops.eri4_flops(l, l, l, l) * n
+
+
+# ------------------------------------------------------------------ oracle arm
+def run_oracle(work, frac, seed=2024):
+    """Time the oracle on a seeded sample of each class; returns (model flops, seconds, quartets, sample text)."""
+    import oracle
+    oracle.build()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tot_f = tot_t = 0.0
+    tot_q = 0
+    per = {}
+    for l, b, q in work:
+        m = max(1, int(round(frac * len(q))))
+        idx = np.sort(rng.choice(len(q), m, replace=False))
+        t0 = time.perf_counter()
+        oracle.eri4(b, q[idx])
+        dt = time.perf_counter() - t0
+        f = model_flops(l, m)
+        tot_f += f; tot_t += dt; tot_q += m
+        per[CLASS_NAMES[l]] = {"quartets": m, "s": round(dt, 4), "model_gflops": round(f / dt * 1e-9, 4)}
+    return tot_f, tot_t, tot_q, per
+
+
+def omp_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def reference_main(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    work = workload(args)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        run_oracle(work, min(args.cpu_sample, 0.002), seed=1)
+    t_f = t_t = 0.0
+    nq = 0
+    for s in range(args.steps):
+        f, t, q, _ = run_oracle(work, args.cpu_sample, seed=100 + s)
+        t_f += f; t_t += t; nq += q
+    v = t_f / t_t * 1e-9
+    sample = "seeded %.2f%% of each class's 50,176 quartets per step (%d quartets over %d steps)" % (
+        100 * args.cpu_sample, nq, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_t / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "4-center class sweep [pp|pp]..[ii|ii], 224x224 random uncontracted quartets "
+                                   "per class, Cartesian, FP64", "classes": args.classes},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0])); mx = max(mx, float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2405_01834_gb300 import mdx
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    eng = mdx.Engine(dev)
+    work = workload(args)
+
+    # prepare: inputs resident on the device, quartet lists split into chunks
+    prepared = []
+    max_chunk = 0
+    for l, b, q in work:
+        db = mdx.DeviceBasis(b)
+        per_q = inputs.ncart(l) ** 4 * 8
+        cq = max(1, min(len(q), CHUNK_BYTES // per_q))
+        batches = [eng.batch_eri4(db, q[s:s + cq]) for s in range(0, len(q), cq)]
+        max_chunk = max(max_chunk, max(bt.total for bt in batches))
+        prepared.append((l, db, q, batches))
+    out = torch.empty(max_chunk, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(record):
+        times = []
+        nl = 0
+        for l, db, q, batches in prepared:
+            ev = []
+            for bt in batches:
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                nl += bt.run(out)
+                e1.record(stream)
+                ev.append((e0, e1))
+            times.append(ev)
+        return times, nl
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(False)
+        flush.zero_()
+    eng.sync()
+    barrier()
+    clk = ClockSampler(dev)
+    clk.start()
+    per_class_ms = {l: [] for l, *_ in prepared}
+    per_launch_ms = {l: [] for l, *_ in prepared}
+    step_ms = []
+    launches = 0
+    for s in range(args.steps):
+        flush.zero_()
+        barrier()
+        times, nl = step(True)
+        barrier()
+        launches += nl
+        tot = 0.0
+        for (l, *_), ev in zip(prepared, times):
+            ms = [a.elapsed_time(b) for a, b in ev]
+            per_class_ms[l].append(sum(ms))
+            per_launch_ms[l].extend(ms)
+            tot += sum(ms)
+        step_ms.append(tot)
+    clocks = clk.stop()
+    eng.sync()
+    ms_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_gflops = FP64_FLOP_PER_CLK_SM * props.multi_processor_count * sm_max * 1e-3
+    total_flops = sum(model_flops(l, len(q)) for l, _, q, _ in prepared)
+    total_exec = sum(2.0 * bt.exec_fma for *_, batches in prepared for bt in batches)
+    value = world * total_flops / (ms_step * 1e-3) * 1e-9
+    per_class = {}
+    dom_l, dom_ms = None, -1.0
+    for l, db, q, batches in prepared:
+        ms = sum(per_class_ms[l]) / len(per_class_ms[l])
+        f = model_flops(l, len(q))
+        ex = sum(2.0 * bt.exec_fma for bt in batches)
+        per_class[CLASS_NAMES[l]] = {
+            "quartets": len(q), "ms": round(ms, 3), "quartets_per_s": round(len(q) / (ms * 1e-3), 1),
+            "model_gflops": round(f / (ms * 1e-3) * 1e-9, 2),
+            "model_frac_of_peak": round(f / (ms * 1e-3) * 1e-9 / peak_gflops, 4),
+            "exec_gflops": round(ex / (ms * 1e-3) * 1e-9, 2),
+            "exec_frac_of_peak": round(ex / (ms * 1e-3) * 1e-9 / peak_gflops, 4),
+            "launches_per_step": 2 * len(batches)}
+        if ms > dom_ms:
+            dom_ms, dom_l = ms, l
+    # roofline of the dominant class's launches (pair records + quartet kernel per chunk)
+    l = dom_l
+    _, _, q, batches = next(p for p in prepared if p[0] == l)
+    lm = per_launch_ms[l]
+    avg_launch_ms = sum(lm) / len(lm)
+    per_launch_flops = model_flops(l, len(q)) / len(batches)
+    achieved = per_launch_flops / (avg_launch_ms * 1e-3) * 1e-12
+    per_launch_exec = sum(2.0 * bt.exec_fma for bt in batches) / len(batches)
+    roofline = {"bound": "alu", "kernel": "k_quartets %s" % CLASS_NAMES[l], "achieved": round(achieved, 4),
+                "peak": round(peak_gflops * 1e-3, 4), "unit": "TFLOP/s", "frac": round(achieved / (peak_gflops * 1e-3), 4),
+                "traffic": None, "model_flops_per_launch": per_launch_flops,
+                "executed_tflops": round(per_launch_exec / (avg_launch_ms * 1e-3) * 1e-12, 4),
+                "executed_frac": round(per_launch_exec / (avg_launch_ms * 1e-3) * 1e-12 / (peak_gflops * 1e-3), 4),
+                "peak_basis": "FP64 pipe: 2 DFMA/clk/SM x %d SMs x %.0f MHz (derived; DFMA probe measured 1.203 "
+                              "TFLOP/s)" % (props.multi_processor_count, sm_max)}
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "4-center class sweep [pp|pp]..[ii|ii], %dx%d random uncontracted quartets per "
+                                   "class, Cartesian, FP64" % (args.n_bra, args.n_ket), "classes": args.classes,
+                       "l2": "256 MB buffer written between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "quartets_per_s": round(world * sum(len(q) for _, _, q, _ in prepared) / (ms_step * 1e-3), 1),
+            "model_frac_of_peak": round(value / world / peak_gflops, 4),
+            "exec_gflops": round(world * total_exec / (ms_step * 1e-3) * 1e-9, 3),
+            "per_class": per_class, "roofline": roofline, "gpu_launches": launches // args.steps if args.steps else 0,
+            "clocks": clocks}
+
+    # ---- end to end through the public call with host buffers (rank 0 timing only)
+    if not args.no_e2e:
+        line["e2e"] = e2e(eng, work, args, torch)
+    if rank == 0 and not args.no_cpu:
+        f, t, nq, per = run_oracle(work, args.cpu_sample)
+        line["cpu_baseline"] = {"value": round(f / t * 1e-9, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+                                "sample": "seeded %.2f%% of each class (%d quartets), oracle as committed" % (
+                                    100 * args.cpu_sample, nq), "per_class": per}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(eng, work, args, torch):
+    """One step through mdx_eri4 with host buffers: pinned basis/quartet arrays
+    copied in, integrals copied back to pinned host memory, chunk by chunk."""
+    from paper_2405_01834_gb300 import mdx
+    host = []
+    for l, b, q in work:
+        per_q = inputs.ncart(l) ** 4 * 8
+        cq = max(1, min(len(q), CHUNK_BYTES // per_q))
+        host.append((l, b, torch.from_numpy(q).pin_memory(), cq))
+    max_out = max(min(len(q), cq) * inputs.ncart(l) ** 4 for l, b, q, cq in host)
+    out_dev = torch.empty(max_out, dtype=torch.float64, device="cuda")
+    out_host = torch.empty(max_out, dtype=torch.float64).pin_memory()
+    h2d = d2h = 0
+    tot_f = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for l, b, qh, cq in host:
+        db = mdx.DeviceBasis(b)   # basis arrays: host -> device
+        h2d += sum(t.numel() * t.element_size() for t in (db.l, db.nprim, db.prim_off, db.ao_off, db.atom,
+                                                          db.center, db.exps, db.coefs))
+        for s in range(0, qh.shape[0], cq):
+            qd = qh[s:s + cq].to("cuda", non_blocking=True)
+            h2d += qd.numel() * 4
+            v, off = eng.eri4(db, qd, out=out_dev)
+            n = qd.shape[0] * inputs.ncart(l) ** 4
+            out_host[:n].copy_(v[:n], non_blocking=True)
+            d2h += n * 8
+        tot_f += model_flops(l, qh.shape[0])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(tot_f / dt * 1e-9, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": 1, "s": round(dt, 3)}
+
+
+if __name__ == "__main__":
+    main()

@@ -111,6 +111,47 @@ mdx_status mdx_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartet
 mdx_status mdx_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
                     int64_t n, double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
 
+/* ---- prepared batches --------------------------------------------------
+ * A batch separates the host-side preparation of a call (index download,
+ * shell-pair de-duplication, grouping of quartets by class, planning,
+ * uploads) from the launch of the hot path, so that one quartet list can be
+ * evaluated repeatedly and its launches enqueued without host
+ * synchronisation or allocation (e.g. inside a captured CUDA graph).
+ * The basis descriptors' device arrays must stay valid until the batch is
+ * destroyed; the batch keeps its own copies of the index data. */
+typedef struct mdx_batch mdx_batch;
+
+/* Prepare the quartets of mdx_eri4 (same arguments). Synchronises `stream`.
+ * n must be >= 1. */
+mdx_status mdx_batch_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
+                          mdx_batch** batch, void* stream);
+
+/* Prepare the triplets of mdx_eri3 (same arguments). Synchronises `stream`. */
+mdx_status mdx_batch_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
+                          int64_t n, mdx_batch** batch, void* stream);
+
+/* Sizes of a prepared batch (host values; any pointer may be NULL): number of
+ * quartets, output doubles, model FLOPs of the paper's Table 1 work model
+ * adapted to contracted Cartesian shellsets, and FP64 multiply-adds the
+ * engine issues. */
+mdx_status mdx_batch_info(const mdx_batch* batch, int64_t* n, int64_t* total, double* model_flops,
+                          double* exec_fma);
+
+/* Copy the batch's [n+1] output offsets (see mdx_eri4) to out_offsets (device). */
+mdx_status mdx_batch_offsets(mdx_ctx* ctx, const mdx_batch* batch, int64_t* out_offsets, void* stream);
+
+/* Enqueue the whole evaluation of a batch on `stream`: primitive-pair records
+ * (Eqs. E2rr1/E2rr2 or E1rr), then one quartet kernel per class (Eqs. boys,
+ * 0m, r, pq, ket-from-hermite, bra-from-hermite). Writes the integrals at the
+ * batch's offsets in `out` (out_capacity doubles). No host synchronisation
+ * and no allocation; n_launches (may be NULL) receives the number of kernels
+ * enqueued. Kernel-side errors surface at the next mdx_sync. */
+mdx_status mdx_batch_run(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t out_capacity, int32_t* n_launches,
+                         void* stream);
+
+/* Free a batch (NULL allowed). No work of the batch may still be running. */
+void mdx_batch_destroy(mdx_batch* batch);
+
 /* Schwarz factors Q_ij = sqrt(max_ab |(ab|ab)|) over the Cartesian
  * components a of shell i and b of shell j, for n shell pairs.
  * pairs: [n][2] int32 shell indices. Q_out: [n] doubles (device), written.

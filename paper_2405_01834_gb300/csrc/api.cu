@@ -171,18 +171,78 @@ struct PairHash {
   }
 };
 
-// Generic batched evaluation of quartets given as (bra pair, ket pair).
+// Quartets given as (bra pair, ket pair) over a pair list.
 struct Batch {
   std::vector<PairKey> pairs;
   std::vector<int2> qp;          // per quartet (bra pair idx, ket pair idx)
   std::vector<int64_t> qoff;     // output offset per quartet
 };
 
-mdx_status run_batch(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const HostBasis& h0,
-                     const HostBasis& h1, const Batch& bt, double* out, cudaStream_t s) {
-  if (bt.qp.empty()) return MDX_OK;
+}  // namespace
+
+// A prepared batch: everything on the device, ready to launch.
+struct mdx_batch {
+  mdx_ctx* ctx = nullptr;
+  int64_t n = 0;                  // quartets
+  int64_t total = 0;              // output doubles
+  BasisDev b0{}, b1{};
+  PrimPairJob* jobs = nullptr;
+  int64_t njobs = 0;
+  int64_t* pair_rec = nullptr;
+  double* recs = nullptr;
+  double* recs_s = nullptr;
+  int2* qp = nullptr;
+  int64_t* qoff = nullptr;
+  int64_t* offsets = nullptr;     // [n+1] in caller order
+  struct Range { Plan* plan; int64_t begin, count; };
+  std::vector<Range> ranges;
+  double model_flops = 0.0;
+  double exec_fma = 0.0;
+};
+
+namespace {
+
+void batch_free(mdx_batch* b) {
+  if (!b) return;
+  cudaFree(b->jobs); cudaFree(b->pair_rec); cudaFree(b->recs); cudaFree(b->recs_s);
+  cudaFree(b->qp); cudaFree(b->qoff); cudaFree(b->offsets);
+  delete b;
+}
+
+template <typename T>
+mdx_status dev_upload(mdx_ctx* c, const std::vector<T>& v, T** out, cudaStream_t s) {
+  *out = nullptr;
+  if (v.empty()) return MDX_OK;
+  if (cudaMalloc((void**)out, v.size() * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MDX_ENOMEM, "batch allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch upload");
+  return MDX_OK;
+}
+
+double model_flops_class(const ClassKey& k) {
+  auto nh = [](int l) { return (double)nherm(l); };
+  auto rl = [](int L) { return (2.0 + L) * (7.0 + L) * (12.0 + 5.0 * L + (double)L * L) / 8.0; };
+  const int Lb = k.la + k.lb, Lk = k.lc + k.ld;
+  const double Nb = (double)ncart(k.la) * ncart(k.lb), Nk = (double)ncart(k.lc) * ncart(k.ld);
+  return k.Kb * (double)k.Kk * (rl(Lb + Lk) + nh(Lb) * nh(Lk) / 2 + 2 * nh(Lb) * nh(Lk) * Nk) +
+         k.Kb * 2.0 * Nb * nh(Lb) * Nk;
+}
+
+// Host preparation of a batch: primitive-pair jobs, class grouping, plans,
+// uploads. Synchronises `s` before returning (host vectors go out of scope).
+mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const HostBasis& h0,
+                         const HostBasis& h1, const Batch& bt, const std::vector<int64_t>& offs, mdx_batch** out,
+                         cudaStream_t s) {
+  std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> B(new mdx_batch(), batch_free);
+  B->ctx = c;
+  B->n = (int64_t)bt.qp.size();
+  B->total = offs.back();
+  B->b0 = to_dev(b0);
+  B->b1 = to_dev(b1 ? b1 : b0);
   const HostBasis* hb[2] = {&h0, &h1};
-  // primitive-pair records
   std::vector<int64_t> pair_rec(bt.pairs.size());
   std::vector<PrimPairJob> jobs;
   int64_t roff = 0;
@@ -199,16 +259,6 @@ mdx_status run_batch(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const
         roff += rs;
       }
   }
-  PrimPairJob* d_jobs; double *d_recs, *d_recs_s; int64_t* d_pair_rec;
-  mdx_status st;
-  if ((st = upload(c, "jobs", jobs, &d_jobs, s)) != MDX_OK) return st;
-  if ((st = upload(c, "pair_rec", pair_rec, &d_pair_rec, s)) != MDX_OK) return st;
-  if ((st = ensure(c, "recs", (size_t)roff, &d_recs, s)) != MDX_OK) return st;
-  if ((st = ensure(c, "recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
-  cudaError_t e = launch_pair_records(to_dev(b0), to_dev(b1 ? b1 : b0), d_jobs, (int64_t)jobs.size(), d_recs,
-                                      d_recs_s, c->d_err, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
-  // group quartets by class
   std::map<ClassKey, std::vector<int64_t>> classes;
   for (size_t q = 0; q < bt.qp.size(); ++q) {
     const PairKey& bp = bt.pairs[bt.qp[q].x];
@@ -224,26 +274,51 @@ mdx_status run_batch(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const
   std::vector<int64_t> qoff_sorted;
   qp_sorted.reserve(bt.qp.size());
   qoff_sorted.reserve(bt.qp.size());
-  std::vector<std::pair<ClassKey, std::pair<int64_t, int64_t>>> ranges;
+  mdx_status st;
   for (auto& kv : classes) {
     const int64_t b = (int64_t)qp_sorted.size();
     for (int64_t q : kv.second) { qp_sorted.push_back(bt.qp[q]); qoff_sorted.push_back(bt.qoff[q]); }
-    ranges.push_back({kv.first, {b, (int64_t)qp_sorted.size() - b}});
-  }
-  int2* d_qp; int64_t* d_qoff;
-  if ((st = upload(c, "qp", qp_sorted, &d_qp, s)) != MDX_OK) return st;
-  if ((st = upload(c, "qoff", qoff_sorted, &d_qoff, s)) != MDX_OK) return st;
-  for (auto& r : ranges) {
     Plan* plan;
-    if ((st = get_plan(c, r.first, &plan, s)) != MDX_OK) return st;
+    if ((st = get_plan(c, kv.first, &plan, s)) != MDX_OK) return st;
+    B->ranges.push_back({plan, b, (int64_t)kv.second.size()});
+    B->model_flops += model_flops_class(kv.first) * (double)kv.second.size();
+    B->exec_fma += plan->exec_fma * (double)kv.second.size();
+  }
+  B->njobs = (int64_t)jobs.size();
+  if ((st = dev_upload(c, jobs, &B->jobs, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, pair_rec, &B->pair_rec, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, qp_sorted, &B->qp, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, qoff_sorted, &B->qoff, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, offs, &B->offsets, s)) != MDX_OK) return st;
+  if (roff > 0) {
+    if (cudaMalloc(&B->recs, roff * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&B->recs_s, roff * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, MDX_ENOMEM, "record allocation failed");
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch upload");
+  *out = B.release();
+  return MDX_OK;
+}
+
+// Enqueue the whole hot path of a batch: pair records, then one quartet
+// kernel per class. No host synchronisation, no allocation.
+mdx_status batch_run(mdx_ctx* c, mdx_batch* B, double* out, int32_t* nlaunch, cudaStream_t s) {
+  int32_t nl = 0;
+  cudaError_t e = launch_pair_records(B->b0, B->b1, B->jobs, B->njobs, B->recs, B->recs_s, c->d_err, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+  if (B->njobs > 0) ++nl;
+  for (auto& r : B->ranges) {
     QuartetLaunch a{};
-    a.plan = plan->d;
-    a.nq = r.second.second;
-    a.qpairs = d_qp + r.second.first;
-    a.qout = d_qoff + r.second.first;
-    a.pair_rec = d_pair_rec;
-    a.recs = d_recs;
-    a.recs_signed = d_recs_s;
+    a.plan = r.plan->d;
+    a.nq = r.count;
+    a.qpairs = B->qp + r.begin;
+    a.qout = B->qoff + r.begin;
+    a.pair_rec = B->pair_rec;
+    a.recs = B->recs;
+    a.recs_signed = B->recs_s;
     a.boys = c->d_boys;
     a.hdec = c->d_hdec;
     a.hdec_off = c->d_hdec_off;
@@ -251,8 +326,95 @@ mdx_status run_batch(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const
     a.err = c->d_err;
     e = launch_quartets(a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "quartet kernel launch");
+    if (r.count > 0) ++nl;
   }
+  if (nlaunch) *nlaunch = nl;
   return MDX_OK;
+}
+
+mdx_status read_quartets(mdx_ctx* c, const int32_t* dev, int64_t n, int w, std::vector<int32_t>& h, cudaStream_t s) {
+  h.resize((size_t)n * w);
+  cudaError_t e = cudaMemcpyAsync(h.data(), dev, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "index download");
+  return MDX_OK;
+}
+
+struct PairIndex {
+  Batch& bt;
+  std::unordered_map<PairKey, int32_t, PairHash> pid;
+  explicit PairIndex(Batch& b) : bt(b) {}
+  int32_t operator()(int32_t i, int32_t j, int32_t which) {
+    PairKey k{i, j, which};
+    auto it = pid.find(k);
+    if (it != pid.end()) return it->second;
+    const int32_t id = (int32_t)bt.pairs.size();
+    bt.pairs.push_back(k);
+    pid.emplace(k, id);
+    return id;
+  }
+};
+
+mdx_status make_batch4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,
+                       cudaStream_t s) {
+  HostBasis hb;
+  mdx_status st = fetch_basis(c, basis, hb, s);
+  if (st != MDX_OK) return st;
+  std::vector<int32_t> hq;
+  if ((st = read_quartets(c, quartets, n, 4, hq, s)) != MDX_OK) return st;
+  Batch bt;
+  PairIndex pix(bt);
+  std::vector<int64_t> offs((size_t)n + 1);
+  offs[0] = 0;
+  bt.qp.resize(n);
+  bt.qoff.resize(n);
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* s4 = &hq[(size_t)q * 4];
+    for (int k = 0; k < 4; ++k)
+      if (s4[k] < 0 || s4[k] >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
+    bt.qp[q] = make_int2(pix(s4[0], s4[1], 0), pix(s4[2], s4[3], 0));
+    bt.qoff[q] = offs[q];
+    offs[q + 1] = offs[q] + (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * ncart(hb.l[s4[2]]) * ncart(hb.l[s4[3]]);
+  }
+  return batch_prepare(c, basis, nullptr, hb, hb, bt, offs, out, s);
+}
+
+mdx_status make_batch3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
+                       mdx_batch** out, cudaStream_t s) {
+  HostBasis ha, ho;
+  mdx_status st = fetch_basis(c, aux, ha, s);
+  if (st != MDX_OK) return st;
+  if ((st = fetch_basis(c, orb, ho, s)) != MDX_OK) return st;
+  std::vector<int32_t> ht;
+  if ((st = read_quartets(c, triplets, n, 3, ht, s)) != MDX_OK) return st;
+  Batch bt;
+  PairIndex pix(bt);
+  std::vector<int64_t> offs((size_t)n + 1);
+  offs[0] = 0;
+  bt.qp.resize(n);
+  bt.qoff.resize(n);
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* t3 = &ht[(size_t)q * 3];
+    if (t3[0] < 0 || t3[0] >= ha.n || t3[1] < 0 || t3[1] >= ho.n || t3[2] < 0 || t3[2] >= ho.n)
+      return fail(c, MDX_EINVAL, "shell index out of range");
+    bt.qp[q] = make_int2(pix(t3[0], -1, 0), pix(t3[1], t3[2], 1));
+    bt.qoff[q] = offs[q];
+    offs[q + 1] = offs[q] + (int64_t)ncart(ha.l[t3[0]]) * ncart(ho.l[t3[1]]) * ncart(ho.l[t3[2]]);
+  }
+  return batch_prepare(c, aux, orb, ha, ho, bt, offs, out, s);
+}
+
+// create, run into `out`, copy offsets, destroy (synchronous)
+mdx_status run_once(mdx_ctx* c, mdx_batch* B, double* out, int64_t cap, int64_t* out_offsets, cudaStream_t s) {
+  std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
+  if (B->total > cap) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  cudaError_t e = cudaMemcpyAsync(out_offsets, B->offsets, (B->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "offsets");
+  mdx_status st = batch_run(c, B, out, nullptr, s);
+  if (st != MDX_OK) return st;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch run");
+  return check_device_error(c, s);
 }
 
 }  // namespace
@@ -323,47 +485,10 @@ mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets,
     cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
     return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
   }
-  HostBasis hb;
-  mdx_status st = fetch_basis(c, basis, hb, s);
+  mdx_batch* B = nullptr;
+  mdx_status st = make_batch4(c, basis, quartets, n, &B, s);
   if (st != MDX_OK) return st;
-  std::vector<int32_t> hq((size_t)n * 4);
-  cudaError_t e = cudaMemcpyAsync(hq.data(), quartets, hq.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "quartet download");
-  Batch bt;
-  std::unordered_map<PairKey, int32_t, PairHash> pid;
-  auto pair_index = [&](int32_t i, int32_t j) {
-    PairKey k{i, j, 0};
-    auto it = pid.find(k);
-    if (it != pid.end()) return it->second;
-    const int32_t id = (int32_t)bt.pairs.size();
-    bt.pairs.push_back(k);
-    pid.emplace(k, id);
-    return id;
-  };
-  std::vector<int64_t> offs((size_t)n + 1);
-  offs[0] = 0;
-  bt.qp.resize(n);
-  bt.qoff.resize(n);
-  for (int64_t q = 0; q < n; ++q) {
-    const int32_t* s4 = &hq[(size_t)q * 4];
-    for (int k = 0; k < 4; ++k)
-      if (s4[k] < 0 || s4[k] >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
-    bt.qp[q] = make_int2(pair_index(s4[0], s4[1]), pair_index(s4[2], s4[3]));
-    bt.qoff[q] = offs[q];
-    offs[q + 1] = offs[q] + (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * ncart(hb.l[s4[2]]) * ncart(hb.l[s4[3]]);
-  }
-  if (offs[n] > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
-  int64_t* d_offs_tmp;
-  // out_offsets is caller memory: copy through a host staging vector kept alive until the sync below
-  e = cudaMemcpyAsync(out_offsets, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "offsets upload");
-  (void)d_offs_tmp;
-  st = run_batch(c, basis, nullptr, hb, hb, bt, out, s);
-  if (st != MDX_OK) return st;
-  e = cudaStreamSynchronize(s);   // host staging vectors go out of scope
-  if (e != cudaSuccess) return cuda_fail(c, e, "eri4");
-  return check_device_error(c, s);
+  return run_once(c, B, out, out_capacity, out_offsets, s);
 }
 
 mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
@@ -377,46 +502,59 @@ mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, cons
     cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
     return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
   }
-  HostBasis ha, ho;
-  mdx_status st = fetch_basis(c, aux, ha, s);
+  mdx_batch* B = nullptr;
+  mdx_status st = make_batch3(c, aux, orb, triplets, n, &B, s);
   if (st != MDX_OK) return st;
-  if ((st = fetch_basis(c, orb, ho, s)) != MDX_OK) return st;
-  std::vector<int32_t> ht((size_t)n * 3);
-  cudaError_t e = cudaMemcpyAsync(ht.data(), triplets, ht.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "triplet download");
-  Batch bt;
-  std::unordered_map<PairKey, int32_t, PairHash> pid;
-  auto pair_index = [&](int32_t i, int32_t j, int32_t which) {
-    PairKey k{i, j, which};
-    auto it = pid.find(k);
-    if (it != pid.end()) return it->second;
-    const int32_t id = (int32_t)bt.pairs.size();
-    bt.pairs.push_back(k);
-    pid.emplace(k, id);
-    return id;
-  };
-  std::vector<int64_t> offs((size_t)n + 1);
-  offs[0] = 0;
-  bt.qp.resize(n);
-  bt.qoff.resize(n);
-  for (int64_t q = 0; q < n; ++q) {
-    const int32_t* t3 = &ht[(size_t)q * 3];
-    if (t3[0] < 0 || t3[0] >= ha.n || t3[1] < 0 || t3[1] >= ho.n || t3[2] < 0 || t3[2] >= ho.n)
-      return fail(c, MDX_EINVAL, "shell index out of range");
-    bt.qp[q] = make_int2(pair_index(t3[0], -1, 0), pair_index(t3[1], t3[2], 1));
-    bt.qoff[q] = offs[q];
-    offs[q + 1] = offs[q] + (int64_t)ncart(ha.l[t3[0]]) * ncart(ho.l[t3[1]]) * ncart(ho.l[t3[2]]);
-  }
-  if (offs[n] > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
-  e = cudaMemcpyAsync(out_offsets, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "offsets upload");
-  st = run_batch(c, aux, orb, ha, ho, bt, out, s);
-  if (st != MDX_OK) return st;
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "eri3");
-  return check_device_error(c, s);
+  return run_once(c, B, out, out_capacity, out_offsets, s);
 }
+
+mdx_status mdx_batch_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,
+                          void* stream) {
+  if (!c || !out) return MDX_EINVAL;
+  *out = nullptr;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  if (n < 1 || !quartets) return fail(c, MDX_EINVAL, "invalid arguments");
+  return make_batch4(c, basis, quartets, n, out, (cudaStream_t)stream);
+}
+
+mdx_status mdx_batch_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
+                          mdx_batch** out, void* stream) {
+  if (!c || !out) return MDX_EINVAL;
+  *out = nullptr;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  if (n < 1 || !triplets) return fail(c, MDX_EINVAL, "invalid arguments");
+  return make_batch3(c, aux, orb, triplets, n, out, (cudaStream_t)stream);
+}
+
+mdx_status mdx_batch_info(const mdx_batch* b, int64_t* n, int64_t* total, double* model_flops, double* exec_fma) {
+  if (!b) return MDX_EINVAL;
+  if (n) *n = b->n;
+  if (total) *total = b->total;
+  if (model_flops) *model_flops = b->model_flops;
+  if (exec_fma) *exec_fma = b->exec_fma;
+  return MDX_OK;
+}
+
+mdx_status mdx_batch_offsets(mdx_ctx* c, const mdx_batch* b, int64_t* out_offsets, void* stream) {
+  if (!c || !b || !out_offsets) return MDX_EINVAL;
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaMemcpyAsync(out_offsets, b->offsets, (b->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
+}
+
+mdx_status mdx_batch_run(mdx_ctx* c, mdx_batch* b, double* out, int64_t out_capacity, int32_t* n_launches,
+                         void* stream) {
+  if (!c || !b || !out) return MDX_EINVAL;
+  if (b->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
+  if (b->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  cudaSetDevice(c->device);
+  return batch_run(c, b, out, n_launches, (cudaStream_t)stream);
+}
+
+void mdx_batch_destroy(mdx_batch* b) { batch_free(b); }
 
 mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, int64_t n, double* Q_out,
                        void* stream) {
@@ -429,15 +567,13 @@ mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs,
   HostBasis hb;
   mdx_status st = fetch_basis(c, basis, hb, s);
   if (st != MDX_OK) return st;
-  std::vector<int32_t> hp((size_t)n * 2);
-  cudaError_t e = cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "pair download");
+  std::vector<int32_t> hp;
+  if ((st = read_quartets(c, pairs, n, 2, hp, s)) != MDX_OK) return st;
   Batch bt;
   bt.pairs.resize(n);
   bt.qp.resize(n);
   bt.qoff.resize(n);
-  std::vector<int64_t> offs(n);
+  std::vector<int64_t> offs(n + 1);
   std::vector<int32_t> nab(n);
   int64_t tot = 0;
   for (int64_t p = 0; p < n; ++p) {
@@ -450,13 +586,15 @@ mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs,
     bt.qoff[p] = tot;
     tot += (int64_t)nab[p] * nab[p];
   }
-  double* d_vals; int64_t* d_off; int32_t* d_nab;
+  offs[n] = tot;
+  double* d_vals; int32_t* d_nab;
   if ((st = ensure(c, "schwarz_vals", (size_t)tot, &d_vals, s)) != MDX_OK) return st;
-  if ((st = upload(c, "schwarz_off", offs, &d_off, s)) != MDX_OK) return st;
   if ((st = upload(c, "schwarz_nab", nab, &d_nab, s)) != MDX_OK) return st;
-  st = run_batch(c, basis, nullptr, hb, hb, bt, d_vals, s);
-  if (st != MDX_OK) return st;
-  e = launch_schwarz_reduce(d_off, d_nab, n, d_vals, Q_out, s);
+  mdx_batch* B = nullptr;
+  if ((st = batch_prepare(c, basis, nullptr, hb, hb, bt, offs, &B, s)) != MDX_OK) return st;
+  std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
+  if ((st = batch_run(c, B, d_vals, nullptr, s)) != MDX_OK) return st;
+  cudaError_t e = launch_schwarz_reduce(B->offsets, d_nab, n, d_vals, Q_out, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "schwarz reduce");
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "schwarz");

@@ -74,6 +74,20 @@ def load(build_if_missing: bool = True):
     lib.mdx_eri3.restype = I32
     lib.mdx_schwarz.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, P]
     lib.mdx_schwarz.restype = I32
+    lib.mdx_batch_eri4.argtypes = [P, ctypes.POINTER(_Basis), P, I64, ctypes.POINTER(ctypes.c_void_p), P]
+    lib.mdx_batch_eri4.restype = I32
+    lib.mdx_batch_eri3.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, I64,
+                                   ctypes.POINTER(ctypes.c_void_p), P]
+    lib.mdx_batch_eri3.restype = I32
+    lib.mdx_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.mdx_batch_info.restype = I32
+    lib.mdx_batch_offsets.argtypes = [P, P, P, P]
+    lib.mdx_batch_offsets.restype = I32
+    lib.mdx_batch_run.argtypes = [P, P, P, I64, ctypes.POINTER(ctypes.c_int32), P]
+    lib.mdx_batch_run.restype = I32
+    lib.mdx_batch_destroy.argtypes = [P]
+    lib.mdx_batch_destroy.restype = None
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
     lib.mdx_plan_info.restype = I32
     _lib = lib
@@ -149,7 +163,7 @@ class Engine:
         q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
         n = q.shape[0]
         if out is None:
-            qn = q.cpu().numpy().astype(np.int64)
+            qn = np.clip(q.cpu().numpy().astype(np.int64), 0, len(basis.nc) - 1)   # the ABI validates indices
             nc = basis.nc
             tot = int(np.sum(nc[qn[:, 0]] * nc[qn[:, 1]] * nc[qn[:, 2]] * nc[qn[:, 3]])) if n else 0
             out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
@@ -165,6 +179,8 @@ class Engine:
         n = t.shape[0]
         if out is None:
             tn = t.cpu().numpy().astype(np.int64)
+            tn[:, 0] = np.clip(tn[:, 0], 0, len(aux.nc) - 1)
+            tn[:, 1:] = np.clip(tn[:, 1:], 0, len(orb.nc) - 1)
             tot = int(np.sum(aux.nc[tn[:, 0]] * orb.nc[tn[:, 1]] * orb.nc[tn[:, 2]])) if n else 0
             out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
         offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
@@ -172,6 +188,21 @@ class Engine:
                                out.data_ptr(), out.numel(), offs.data_ptr(), _stream())
         self._check(st, "mdx_eri3")
         return out, offs
+
+    def batch_eri4(self, basis: DeviceBasis, quartets) -> "Batch":
+        """Prepare quartets [n,4] once; run them many times with Batch.run."""
+        q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
+        h = ctypes.c_void_p()
+        self._check(self.lib.mdx_batch_eri4(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), q.shape[0],
+                                            ctypes.byref(h), _stream()), "mdx_batch_eri4")
+        return Batch(self, h, (basis,))
+
+    def batch_eri3(self, aux: DeviceBasis, orb: DeviceBasis, triplets) -> "Batch":
+        t = torch.as_tensor(triplets, dtype=torch.int32, device="cuda").contiguous()
+        h = ctypes.c_void_p()
+        self._check(self.lib.mdx_batch_eri3(self.ctx, ctypes.byref(aux.desc), ctypes.byref(orb.desc), t.data_ptr(),
+                                            t.shape[0], ctypes.byref(h), _stream()), "mdx_batch_eri3")
+        return Batch(self, h, (aux, orb))
 
     def schwarz(self, basis: DeviceBasis, pairs):
         """Q_ij = sqrt(max |(ij|ij)|) for pairs [n,2]."""
@@ -181,3 +212,39 @@ class Engine:
                                   _stream())
         self._check(st, "mdx_schwarz")
         return Q[: p.shape[0]]
+
+
+class Batch:
+    """A prepared quartet (or triplet) list; `run` enqueues the whole hot path."""
+
+    def __init__(self, eng: Engine, handle, keep):
+        self.eng, self.h, self._keep = eng, handle, keep
+        n, tot = ctypes.c_int64(), ctypes.c_int64()
+        mf, ef = ctypes.c_double(), ctypes.c_double()
+        eng._check(eng.lib.mdx_batch_info(handle, ctypes.byref(n), ctypes.byref(tot), ctypes.byref(mf),
+                                          ctypes.byref(ef)), "mdx_batch_info")
+        self.n, self.total, self.model_flops, self.exec_fma = n.value, tot.value, mf.value, ef.value
+
+    def offsets(self) -> torch.Tensor:
+        o = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        self.eng._check(self.eng.lib.mdx_batch_offsets(self.eng.ctx, self.h, o.data_ptr(), _stream()),
+                        "mdx_batch_offsets")
+        return o
+
+    def run(self, out: torch.Tensor) -> int:
+        """Enqueue on the current stream; returns the number of kernels launched."""
+        nl = ctypes.c_int32()
+        self.eng._check(self.eng.lib.mdx_batch_run(self.eng.ctx, self.h, out.data_ptr(), out.numel(),
+                                                   ctypes.byref(nl), _stream()), "mdx_batch_run")
+        return nl.value
+
+    def close(self):
+        if self.h:
+            self.eng.lib.mdx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -36,7 +36,7 @@ def test_small_molecule_all_unique_quartets(eng):
     v, off = _gpu4(eng, b, q)
     ref, roff = oracle.eri4(b, q)
     assert np.array_equal(off, roff)
-    r = parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "config-1")
+    r = parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "config-1", off)
     print(r)
 
 
@@ -49,7 +49,7 @@ def test_class_sweep_grid(eng, l):
     v, off = _gpu4(eng, b, q)
     ref, roff = oracle.eri4(b, q)
     assert np.array_equal(off, roff)
-    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "sweep l=%d" % l)
+    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "sweep l=%d" % l, off)
 
 
 MIXED = [(0, 1, 2, 3), (3, 2, 1, 0), (6, 0, 0, 0), (0, 0, 0, 6), (2, 6, 1, 4), (5, 0, 4, 1), (1, 3, 6, 2),
@@ -63,7 +63,7 @@ def test_mixed_classes_contracted(eng, lq):
     b, q = inputs.class_sweep(lq, n_bra=3, n_ket=2, seed=5, K=K)
     v, off = _gpu4(eng, b, q)
     ref, _ = oracle.eri4(b, q)
-    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "mixed %s" % (lq,))
+    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "mixed %s" % (lq,), off)
 
 
 def test_random_quartets_many_classes(eng):
@@ -82,7 +82,7 @@ def test_random_quartets_many_classes(eng):
     q = q[L <= 14]
     v, off = _gpu4(eng, b, q)
     ref, _ = oracle.eri4(b, q)
-    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "random")
+    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "random", off)
 
 
 def test_empty_and_single(eng):
@@ -127,7 +127,26 @@ def test_three_center(eng, la):
     torch.cuda.synchronize()
     ref, roff = oracle.eri3(aux_all, orb, t)
     assert np.array_equal(off.cpu().numpy(), roff)
-    parity.check(v.cpu().numpy()[: roff[-1]], ref, oracle.eri3(aux_all, orb, t, precision=1)[0], "3c la=%d" % la)
+    parity.check(v.cpu().numpy()[: roff[-1]], ref, oracle.eri3(aux_all, orb, t, precision=1)[0], "3c la=%d" % la,
+                 roff)
+
+
+def test_prepared_batch_runs_repeatably(eng):
+    """mdx_batch_eri4 + mdx_batch_run twice gives the mdx_eri4 result bit for bit."""
+    b, q = inputs.class_sweep((2, 1, 2, 0), n_bra=7, n_ket=5, seed=8, K=(2, 1, 3, 1))
+    db = mdx.DeviceBasis(b)
+    v, off = eng.eri4(db, q)
+    bt = eng.batch_eri4(db, q)
+    assert bt.n == len(q) and bt.total == int(off[-1])
+    assert torch.equal(bt.offsets(), off)
+    for _ in range(2):
+        w = torch.full((bt.total,), float("nan"), dtype=torch.float64, device="cuda")
+        nl = bt.run(w)
+        torch.cuda.synchronize()
+        eng.sync()
+        assert nl == 2
+        assert torch.equal(w, v[: bt.total])
+    bt.close()
 
 
 def test_schwarz(eng):
