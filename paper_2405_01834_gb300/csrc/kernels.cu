@@ -238,9 +238,33 @@ __device__ void compute_R(const QuartetLaunch& a, double* ws, int tl, unsigned m
 }
 
 // out = (acc ? out : 0) + sum_k coef[c + k s] src[x + k s]
+// Each lane runs two entries (e, e + T) side by side: two independent FMA
+// chains hide the FP64 pipe latency. Entries are sorted by length, so the
+// two usually have the same n.
 __device__ __forceinline__ void run_step(const StepEntry* __restrict__ prog, int n, double* ws, int tl, int T,
                                          bool acc) {
-  for (int e = tl; e < n; e += T) {
+  int e = tl;
+  for (; e + T < n; e += 2 * T) {
+    const StepEntry s0 = prog[e], s1 = prog[e + T];
+    const double* c0 = ws + s0.coef;
+    const double* x0 = ws + s0.src;
+    const double* c1 = ws + s1.coef;
+    const double* x1 = ws + s1.src;
+    const int st0 = s0.stride, st1 = s1.stride;
+    double v0 = acc ? ws[s0.out] : 0.0;
+    double v1 = acc ? ws[s1.out] : 0.0;
+    const int nm = min((int)s0.n, (int)s1.n);
+    int k = 0;
+    for (; k < nm; ++k) {
+      v0 = fma(c0[k * st0], x0[k * st0], v0);
+      v1 = fma(c1[k * st1], x1[k * st1], v1);
+    }
+    for (int k0 = k; k0 < s0.n; ++k0) v0 = fma(c0[k0 * st0], x0[k0 * st0], v0);
+    for (int k1 = k; k1 < s1.n; ++k1) v1 = fma(c1[k1 * st1], x1[k1 * st1], v1);
+    ws[s0.out] = v0;
+    ws[s1.out] = v1;
+  }
+  if (e < n) {
     const StepEntry s = prog[e];
     const double* c = ws + s.coef;
     const double* x = ws + s.src;
@@ -256,7 +280,7 @@ __device__ __forceinline__ void load_record(double* dst, const double* __restric
 }
 
 template <bool CTA>
-__global__ void __launch_bounds__(256) k_quartets(const QuartetLaunch a) {
+__global__ void __launch_bounds__(CTA ? 512 : 128) k_quartets(const QuartetLaunch a) {
   extern __shared__ __align__(16) double smem[];
   const PlanDev& P = a.plan;
   const int T = P.T;
@@ -302,38 +326,68 @@ __global__ void __launch_bounds__(256) k_quartets(const QuartetLaunch a) {
         run_step(P.kprog + grp.k3_off, grp.k3_n, ws, tl, T, pk > 0);
         team_sync<CTA>(mask);
       }
-      // b1: C1 = Ex (x) X, per column
+      // b1: C1 = Ex (x) X, per column (two entries per lane, see run_step)
       {
         const int tot = P.nb1 * ncols;
-        for (int e = tl; e < tot; e += T) {
-          const int ent = e / ncols, col = e - ent * ncols;
-          const StepEntry s = P.b1[ent];
-          const double* c = ws + s.coef;
-          const double* x = ws + P.o_X + col * P.hb + s.src;
-          const int st = s.stride;
-          double v = 0.0;
-          for (int k = 0; k < s.n; ++k) v = fma(c[k * st], x[k * st], v);
-          ws[P.o_C1 + col * P.c1size + s.out] = v;
+        int e = tl;
+        for (; e < tot; e += 2 * T) {
+          const int e1 = e + T < tot ? e + T : e;
+          const int ent0 = e / ncols, col0 = e - ent0 * ncols;
+          const int ent1 = e1 / ncols, col1 = e1 - ent1 * ncols;
+          const StepEntry s0 = P.b1[ent0], s1 = P.b1[ent1];
+          const double* c0 = ws + s0.coef;
+          const double* x0 = ws + P.o_X + col0 * P.hb + s0.src;
+          const double* c1 = ws + s1.coef;
+          const double* x1 = ws + P.o_X + col1 * P.hb + s1.src;
+          const int st0 = s0.stride, st1 = s1.stride;
+          const int nm = min((int)s0.n, (int)s1.n);
+          double v0 = 0.0, v1 = 0.0;
+          int k = 0;
+          for (; k < nm; ++k) {
+            v0 = fma(c0[k * st0], x0[k * st0], v0);
+            v1 = fma(c1[k * st1], x1[k * st1], v1);
+          }
+          for (int k0 = k; k0 < s0.n; ++k0) v0 = fma(c0[k0 * st0], x0[k0 * st0], v0);
+          for (int k1 = k; k1 < s1.n; ++k1) v1 = fma(c1[k1 * st1], x1[k1 * st1], v1);
+          ws[P.o_C1 + col0 * P.c1size + s0.out] = v0;
+          if (e1 != e) ws[P.o_C1 + col1 * P.c1size + s1.out] = v1;
         }
       }
       team_sync<CTA>(mask);
-      // b23: OUT += Ez (x) Ey (x) C1, per column
+      // b23: OUT += Ez (x) Ey (x) C1, per column; two Hermite z-indices v in
+      // flight per lane (independent inner sums over u)
       {
         const int tot = P.nb23 * ncols;
         for (int e = tl; e < tot; e += T) {
           const int ent = e / ncols, col = e - ent * ncols;
           const B23Entry s = P.b23[ent];
-          const double* c1 = ws + P.o_C1 + col * P.c1size + s.src;
+          const double* c1 = ws + P.o_C1 + col * P.c1size + s.src + s.u0;
           double* o = ws + P.o_OUT + s.out * ncols + col;
           double acc = pb > 0 ? *o : 0.0;
           const int r1 = s.r + 1;
-          for (int iv = 0; iv < s.nv; ++iv) {
-            const int v = s.v0 + iv * s.sv;
-            const double* row = c1 + v * r1 - (v * (v - 1)) / 2 + s.u0;
-            const double* ey = ws + s.ey;
-            double inner = 0.0;
-            for (int iu = 0; iu < s.nu; ++iu) inner = fma(ey[iu * s.su], row[iu * s.su], inner);
-            acc = fma(ws[s.ez + iv * s.sv], inner, acc);
+          const double* ey = ws + s.ey;
+          const double* ez = ws + s.ez;
+          const int su = s.su, sv = s.sv, nu = s.nu;
+          int iv = 0;
+          for (; iv + 1 < s.nv; iv += 2) {
+            const int va = s.v0 + iv * sv, vb = va + sv;
+            const double* ra = c1 + va * r1 - (va * (va - 1)) / 2;
+            const double* rb = c1 + vb * r1 - (vb * (vb - 1)) / 2;
+            double ia = 0.0, ib = 0.0;
+            for (int iu = 0; iu < nu; ++iu) {
+              const double y = ey[iu * su];
+              ia = fma(y, ra[iu * su], ia);
+              ib = fma(y, rb[iu * su], ib);
+            }
+            acc = fma(ez[iv * sv], ia, acc);
+            acc = fma(ez[(iv + 1) * sv], ib, acc);
+          }
+          if (iv < s.nv) {
+            const int va = s.v0 + iv * sv;
+            const double* ra = c1 + va * r1 - (va * (va - 1)) / 2;
+            double ia = 0.0;
+            for (int iu = 0; iu < nu; ++iu) ia = fma(ey[iu * su], ra[iu * su], ia);
+            acc = fma(ez[iv * sv], ia, acc);
           }
           *o = acc;
         }

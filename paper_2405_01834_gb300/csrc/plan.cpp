@@ -273,8 +273,10 @@ bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::str
       plan.b23.push_back(e);
       fma_b += e.nv * (e.nu + 1.0);
     }
-  std::stable_sort(plan.b23.begin(), plan.b23.end(),
-                   [](const B23Entry& x, const B23Entry& y) { return x.nu * x.nv > y.nu * y.nv; });
+  // equal loop shapes next to each other (lanes of a warp run the same trip counts)
+  std::stable_sort(plan.b23.begin(), plan.b23.end(), [](const B23Entry& x, const B23Entry& y) {
+    return x.nv != y.nv ? x.nv > y.nv : x.nu > y.nu;
+  });
   P.nb1 = (int)plan.b1.size();
   P.nb23 = (int)plan.b23.size();
 
@@ -391,15 +393,15 @@ bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::str
   // ---- team shape ------------------------------------------------------
   const int bytes = P.team_doubles * 8;
   if (P.ngroups > 1) {
-    P.T = 256;
+    P.T = 512;
     P.teams_per_cta = 1;
   } else {
     int tps = std::max(1, (220 * 1024) / bytes);
     int Tocc = 1;
-    while (Tocc * tps < 256 && Tocc < 256) Tocc *= 2;
+    while (Tocc * tps < 512 && Tocc < 512) Tocc *= 2;
     int work = std::max(1, P.Nb * P.Nk / 8);
     int Twork = 1;
-    while (Twork * 2 <= work && Twork < 256) Twork *= 2;
+    while (Twork * 2 <= work && Twork < 512) Twork *= 2;
     P.T = std::min(Tocc, Twork);
     if (P.T > 32) {
       P.teams_per_cta = 1;

@@ -108,9 +108,10 @@ def test_errors_are_reported(eng):
     bad.l[0] = 7
     with pytest.raises(mdx.MdxError, match="EUNSUPPORTED"):
         eng.eri4(mdx.DeviceBasis(bad), np.array([[0, 0, 0, 0]], dtype=np.int32))
-    # the context stays usable
-    v, off = eng.eri4(db, np.array([[0, 1, 2, 0]], dtype=np.int32))
-    ref, _ = oracle.eri4(b, [[0, 1, 2, 0]])
+    # the context stays usable (two atoms: no shellset that vanishes by symmetry)
+    b2 = inputs.small_molecule(n_atoms=2)
+    v, off = eng.eri4(mdx.DeviceBasis(b2), np.array([[0, 4, 2, 3]], dtype=np.int32))
+    ref, _ = oracle.eri4(b2, [[0, 4, 2, 3]])
     parity.check(v.cpu().numpy()[: int(off[-1])], ref, None, "after errors")
 
 
