@@ -51,8 +51,9 @@ def _load():
             lib.orc_rtable.argtypes = [ctypes.c_int, ctypes.c_double, P, P]
             lib.orc_eri4.argtypes = [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
             lib.orc_eri3.argtypes = [P] * 13 + [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
-            lib.orc_exchange.argtypes = [P] * 7 + [ctypes.c_int32, ctypes.c_int32, P, P, P,
-                                                   ctypes.c_int32, ctypes.c_int]
+            lib.orc_exchange.argtypes = [P] * 7 + [ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int]
+            lib.orc_exchange_rows.argtypes = [P] * 7 + [ctypes.c_int32, ctypes.c_int32, P, P, P,
+                                                        ctypes.c_int32, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -135,9 +136,11 @@ def eri3(aux, orb, triplets, nthreads: int = 0, precision: int = 0):
 
 
 def exchange(basis, D: np.ndarray, row_shells=None, nthreads: int = 0) -> np.ndarray:
-    """Dense K_ik = sum_jl D_jl (ij|kl) over all shell quartets (Sec. 6).
+    """Dense K_ik = sum_jl D_jl (ij|kl) (Sec. 6).
 
-    row_shells: optional list of shell indices; only those K rows are formed.
+    Full K: every unique shell quartet once, scattered over its distinct index
+    permutations. row_shells: only those shells' K rows, by the direct sum over
+    all (j, k, l) shells (other rows zero).
     """
     arrs = _basis_arrays(basis)
     ao_off = np.ascontiguousarray(basis.ao_off, dtype=np.int32)
@@ -146,9 +149,9 @@ def exchange(basis, D: np.ndarray, row_shells=None, nthreads: int = 0) -> np.nda
     assert D.shape == (nao, nao)
     K = np.zeros((nao, nao))
     if row_shells is None:
-        rows = np.zeros(1, dtype=np.int32); nrows = 0
+        _load().orc_exchange(*[_p(a) for a in arrs], _p(ao_off), int(basis.n_shells), nao, _p(D), _p(K), nthreads)
     else:
-        rows = np.ascontiguousarray(row_shells, dtype=np.int32); nrows = len(rows)
-    _load().orc_exchange(*[_p(a) for a in arrs], _p(ao_off), int(basis.n_shells), nao, _p(D), _p(K),
-                         _p(rows), nrows, nthreads)
+        rows = np.ascontiguousarray(row_shells, dtype=np.int32)
+        _load().orc_exchange_rows(*[_p(a) for a in arrs], _p(ao_off), int(basis.n_shells), nao, _p(D), _p(K),
+                                  _p(rows), len(rows), nthreads)
     return K

@@ -31,6 +31,7 @@
 // A 4-center shellset is stored row-major as [a][b][c][d] (d fastest);
 // a 3-center one as [a][c][d].
 
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -456,26 +457,76 @@ void orc_eri3(const int32_t* al, const int32_t* anprim, const int32_t* aprim_off
   }
 }
 
-// Dense exchange matrix K_ik = sum_jl D_jl (ij|kl) over ALL shell quartets
-// (no permutational symmetry used; Sec. 6 with a->j, b->i, c->k, d->l).
-// D and K are [nao][nao] row-major; ao_off[s] is the first AO of shell s.
-// rows: if nrows > 0, only K rows listed in row_shells (shell indices) are formed;
-// other rows are left zero.
+// Dense exchange matrix K_ik = sum_jl D_jl (ij|kl) (Sec. 6 with a->j, b->i,
+// c->k, d->l). The sum over all ordered shell quartets is regrouped by unique
+// quartets {i>=j, k>=l, ij>=kl}: each shellset is evaluated once and every
+// DISTINCT index permutation (p1,p2,p3,p4) of it adds D_{p2 p4} (p1 p2|p3 p4)
+// to K_{p1 p3}. D and K are [nao][nao] row-major; ao_off[s] is the first AO
+// of shell s.
 void orc_exchange(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,
                   const double* exps, const double* coefs, const int32_t* ao_off, int32_t n_shells,
-                  int32_t nao, const double* D, double* K, const int32_t* row_shells, int32_t nrows,
-                  int nthreads) {
+                  int32_t nao, const double* D, double* K, int nthreads) {
   Basis bs{l, nprim, prim_off, center, exps, coefs};
   for (int64_t i = 0; i < (int64_t)nao * nao; ++i) K[i] = 0.0;
-  std::vector<int32_t> rows;
-  if (nrows > 0) rows.assign(row_shells, row_shells + nrows);
-  else for (int32_t s = 0; s < n_shells; ++s) rows.push_back(s);
+  std::vector<std::array<int32_t, 4>> quarts;
+  for (int32_t i = 0; i < n_shells; ++i)
+    for (int32_t j = 0; j <= i; ++j)
+      for (int32_t k = 0; k <= i; ++k)
+        for (int32_t ll = 0; ll <= (k == i ? j : k); ++ll) quarts.push_back({i, j, k, ll});
   const int nt = nthreads_or_default(nthreads);
-  // each task owns one (i, k) shell block of K: no write conflicts
-  const int64_t ntask = (int64_t)rows.size() * n_shells;
+  std::vector<std::vector<double>> Kt(nt, std::vector<double>((size_t)nao * nao, 0.0));
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (int64_t n = 0; n < (int64_t)quarts.size(); ++n) {
+#ifdef _OPENMP
+    std::vector<double>& Kp = Kt[omp_get_thread_num()];
+#else
+    std::vector<double>& Kp = Kt[0];
+#endif
+    const auto& q = quarts[n];
+    const int nc[4] = {ncart(l[q[0]]), ncart(l[q[1]]), ncart(l[q[2]]), ncart(l[q[3]])};
+    std::vector<double> v((size_t)nc[0] * nc[1] * nc[2] * nc[3]);
+    shellset4<double>(bs, q[0], q[1], q[2], q[3], v.data());
+    // the 8 index permutations that leave (ij|kl) unchanged, as positions into (0,1,2,3)
+    static const int perms[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
+                                    {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
+    std::vector<std::array<int32_t, 4>> done;
+    for (const auto& pm : perms) {
+      const std::array<int32_t, 4> sh{q[pm[0]], q[pm[1]], q[pm[2]], q[pm[3]]};
+      bool dup = false;
+      for (const auto& d : done) dup = dup || d == sh;
+      if (dup) continue;   // identical shell tuple: the same ordered quartet, counted once
+      done.push_back(sh);
+      const int n0 = nc[pm[0]], n1 = nc[pm[1]], n2 = nc[pm[2]], n3 = nc[pm[3]];
+      int idx[4];
+      for (idx[0] = 0; idx[0] < nc[0]; ++idx[0])
+        for (idx[1] = 0; idx[1] < nc[1]; ++idx[1])
+          for (idx[2] = 0; idx[2] < nc[2]; ++idx[2])
+            for (idx[3] = 0; idx[3] < nc[3]; ++idx[3]) {
+              const double val = v[(((size_t)idx[0] * nc[1] + idx[1]) * nc[2] + idx[2]) * nc[3] + idx[3]];
+              const int a = idx[pm[0]], b = idx[pm[1]], c = idx[pm[2]], d = idx[pm[3]];
+              (void)n0; (void)n1; (void)n2; (void)n3;
+              Kp[(size_t)(ao_off[sh[0]] + a) * nao + ao_off[sh[2]] + c] +=
+                  D[(size_t)(ao_off[sh[1]] + b) * nao + ao_off[sh[3]] + d] * val;
+            }
+    }
+  }
+  for (int t = 0; t < nt; ++t)
+    for (int64_t i = 0; i < (int64_t)nao * nao; ++i) K[i] += Kt[t][i];
+}
+
+// Rows of K_ik = sum_jl D_jl (ij|kl) for the shells in row_shells only,
+// summed directly over all (j, k, l) shells; other rows are left zero.
+void orc_exchange_rows(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,
+                       const double* exps, const double* coefs, const int32_t* ao_off, int32_t n_shells,
+                       int32_t nao, const double* D, double* K, const int32_t* row_shells, int32_t nrows,
+                       int nthreads) {
+  Basis bs{l, nprim, prim_off, center, exps, coefs};
+  for (int64_t i = 0; i < (int64_t)nao * nao; ++i) K[i] = 0.0;
+  const int nt = nthreads_or_default(nthreads);
+  const int64_t ntask = (int64_t)nrows * n_shells;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
   for (int64_t task = 0; task < ntask; ++task) {
-    const int32_t si = rows[task / n_shells];
+    const int32_t si = row_shells[task / n_shells];
     const int32_t sk = (int32_t)(task % n_shells);
     const int ni = ncart(l[si]), nk = ncart(l[sk]);
     std::vector<double> blk((size_t)ni * nk, 0.0);
