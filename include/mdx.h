@@ -159,6 +159,27 @@ void mdx_batch_destroy(mdx_batch* batch);
 mdx_status mdx_schwarz(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, int64_t n,
                        double* Q_out, void* stream);
 
+/* Hartree-Fock exchange K_ik = sum_jl D_jl (ij|kl) (Sec. 6 of the paper,
+ * K_bc = sum_ad [ab|cd] D_ad with the indices renamed), no 1/2 or spin factor.
+ * pairs: [n_pairs][2] int32 shell pairs, each unordered pair at most once
+ *   (order inside a pair is free); Q: [n_pairs] Schwarz factors of the pairs
+ *   (e.g. from mdx_schwarz), same order.
+ * Unique quartets (ij|kl) of the pair list are screened on the GPU with
+ *   Q_ij Q_kl max(|D_ik|, |D_il|, |D_jk|, |D_jl|) >= tau  (max over shell
+ *   blocks; tau = 0 keeps every quartet); each kept quartet is evaluated once
+ *   and digested into four K blocks inside the integral kernel (the integrals
+ *   never reach device memory), with FP64 atomics; finally K <- K + K^T.
+ * D: [nao][nao] row-major, symmetric (device). K: [nao][nao] (device),
+ *   overwritten. nao = max over shells of ao_off + ncart(l); basis->ao_off is
+ *   required. Synchronises `stream` (screening counts) and on return K is
+ *   complete. Pairs absent from the list contribute nothing. */
+mdx_status mdx_exchange(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
+                        double tau, const double* D, double* K, void* stream);
+
+/* Number of unique quartets the last mdx_exchange of this context kept after
+ * screening (-1 for a NULL context). */
+int64_t mdx_last_quartet_count(const mdx_ctx* ctx);
+
 /* Shape the engine chooses for one integral class (no GPU needed; ctx may be
  * NULL). The class is (la lb | lc ld) with Kb = K_a K_b and Kk = K_c K_d
  * primitive pairs; one_centre = 1 selects the 3-center bra [a| (lb must be 0).

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/mdx.h: context, argument
 // validation, class grouping, workspace, and the kernel launches.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,6 +36,7 @@ struct mdx_ctx {
   std::map<ClassKey, std::unique_ptr<Plan>> plans;
   std::map<std::string, DevBuf> bufs;
   int smem_budget = 200 * 1024;
+  int64_t last_quartets = 0;
 };
 
 namespace {
@@ -600,6 +602,147 @@ mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs,
   if (e != cudaSuccess) return cuda_fail(c, e, "schwarz");
   return check_device_error(c, s);
 }
+
+mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
+                        double tau, const double* D, double* K, void* stream) {
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_pairs < 0 || !D || !K || (n_pairs > 0 && (!pairs || !Q)) || !(tau >= 0.0))
+    return fail(c, MDX_EINVAL, "invalid arguments");
+  if (!basis || !basis->ao_off) return fail(c, MDX_EINVAL, "basis needs ao_off");
+  HostBasis hb;
+  mdx_status st = fetch_basis(c, basis, hb, s);
+  if (st != MDX_OK) return st;
+  std::vector<int32_t> ao(hb.n);
+  cudaError_t e = cudaMemcpyAsync(ao.data(), basis->ao_off, hb.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ao_off download");
+  int64_t nao = 0;
+  for (int i = 0; i < hb.n; ++i) nao = std::max<int64_t>(nao, (int64_t)ao[i] + ncart(hb.l[i]));
+  if (nao > 2000000000 / 2) return fail(c, MDX_EUNSUPPORTED, "too many AOs");
+  e = cudaMemsetAsync(K, 0, (size_t)nao * nao * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "K clear");
+  if (n_pairs == 0 || hb.n == 0) return MDX_OK;
+  std::vector<int32_t> hp;
+  if ((st = read_quartets(c, pairs, n_pairs, 2, hp, s)) != MDX_OK) return st;
+  std::vector<double> hq(n_pairs);
+  e = cudaMemcpyAsync(hq.data(), Q, n_pairs * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Q download");
+  // canonical, distinct pairs sorted by pair class (li, lj, Ki*Kj)
+  struct P4 { int32_t i, j; double q; int li, lj, K; };
+  std::vector<P4> pl(n_pairs);
+  std::unordered_map<int64_t, int> seen;
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    int32_t i = hp[2 * p], j = hp[2 * p + 1];
+    if (i < 0 || i >= hb.n || j < 0 || j >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
+    if (i < j) std::swap(i, j);
+    if (!seen.emplace((int64_t)i * hb.n + j, 1).second) return fail(c, MDX_EINVAL, "shell pair listed twice");
+    pl[p] = P4{i, j, hq[p], hb.l[i], hb.l[j], hb.nprim[i] * hb.nprim[j]};
+  }
+  std::stable_sort(pl.begin(), pl.end(), [](const P4& a, const P4& b) {
+    if (a.li != b.li) return a.li < b.li;
+    if (a.lj != b.lj) return a.lj < b.lj;
+    return a.K < b.K;
+  });
+  std::vector<int2> pshell(n_pairs);
+  std::vector<int32_t> pclass(n_pairs);
+  std::vector<float> qf(n_pairs);
+  std::vector<std::array<int, 3>> classes;
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    std::array<int, 3> k{pl[p].li, pl[p].lj, pl[p].K};
+    if (classes.empty() || classes.back() != k) classes.push_back(k);
+    pclass[p] = (int32_t)classes.size() - 1;
+    pshell[p] = make_int2(pl[p].i, pl[p].j);
+    qf[p] = (float)pl[p].q;
+  }
+  const int nclass = (int)classes.size();
+  const int64_t nbucket = (int64_t)nclass * (nclass + 1) / 2;
+  // primitive-pair records for every pair
+  std::vector<int64_t> pair_rec(n_pairs);
+  std::vector<PrimPairJob> jobs;
+  int64_t roff = 0;
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    const int rs = rec_size(pl[p].li, pl[p].lj);
+    pair_rec[p] = roff;
+    for (int ia = 0; ia < hb.nprim[pl[p].i]; ++ia)
+      for (int ib = 0; ib < hb.nprim[pl[p].j]; ++ib) {
+        jobs.push_back(PrimPairJob{pl[p].i, pl[p].j, ia, ib, 0, 0, roff});
+        roff += rs;
+      }
+  }
+  PrimPairJob* d_jobs; int64_t* d_prec; double *d_recs, *d_recs_s; int2* d_pshell; int32_t* d_pclass;
+  float *d_q, *d_dmax; unsigned long long* d_counts; int64_t* d_boff; int2* d_quart;
+  if ((st = upload(c, "x_jobs", jobs, &d_jobs, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_prec", pair_rec, &d_prec, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "x_recs", (size_t)roff, &d_recs, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "x_recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_pshell", pshell, &d_pshell, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_pclass", pclass, &d_pclass, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_q", qf, &d_q, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "x_dmax", (size_t)hb.n * hb.n, &d_dmax, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "x_counts", (size_t)nbucket, &d_counts, s)) != MDX_OK) return st;
+  e = launch_pair_records(to_dev(basis), to_dev(basis), d_jobs, (int64_t)jobs.size(), d_recs, d_recs_s, c->d_err, s);
+  if (e == cudaSuccess) e = launch_dmax(D, (int32_t)nao, basis->ao_off, basis->l, hb.n, d_dmax, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
+  ScreenArgs sa{n_pairs, d_pshell, d_pclass, d_q, d_dmax, hb.n, nclass, (float)tau, d_counts, nullptr, nullptr};
+  if (e == cudaSuccess) e = launch_screen(sa, false, s);
+  std::vector<unsigned long long> counts(nbucket);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts.data(), d_counts, nbucket * sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange screening");
+  std::vector<int64_t> boff(nbucket + 1, 0);
+  for (int64_t b = 0; b < nbucket; ++b) boff[b + 1] = boff[b] + (int64_t)counts[b];
+  const int64_t nq = boff[nbucket];
+  c->last_quartets = nq;
+  if (nq > 0) {
+    if ((st = upload(c, "x_boff", boff, &d_boff, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "x_quart", (size_t)nq, &d_quart, s)) != MDX_OK) return st;
+    e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
+    sa.bucket_off = d_boff;
+    sa.out = d_quart;
+    if (e == cudaSuccess) e = launch_screen(sa, true, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "exchange screening");
+    for (int cp = 0; cp < nclass; ++cp)
+      for (int cq = 0; cq <= cp; ++cq) {
+        const int64_t b = (int64_t)cp * (cp + 1) / 2 + cq;
+        if (counts[b] == 0) continue;
+        const ClassKey key{classes[cp][0], classes[cp][1], classes[cq][0], classes[cq][1], classes[cp][2],
+                           classes[cq][2], 0};
+        Plan* plan;
+        if ((st = get_plan(c, key, &plan, s)) != MDX_OK) return st;
+        QuartetLaunch a{};
+        a.plan = plan->d;
+        a.nq = (int64_t)counts[b];
+        a.qpairs = d_quart + boff[b];
+        a.qout = nullptr;
+        a.pair_rec = d_prec;
+        a.recs = d_recs;
+        a.recs_signed = d_recs_s;
+        a.boys = c->d_boys;
+        a.hdec = c->d_hdec;
+        a.hdec_off = c->d_hdec_off;
+        a.out = nullptr;
+        a.err = c->d_err;
+        a.D = D;
+        a.K = K;
+        a.nao = (int32_t)nao;
+        a.ao_off = basis->ao_off;
+        a.pair_shells = d_pshell;
+        e = launch_quartets(a, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "exchange quartet launch");
+      }
+  }
+  e = launch_symmetrize(K, (int32_t)nao, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange");
+  return check_device_error(c, s);
+}
+
+int64_t mdx_last_quartet_count(const mdx_ctx* c) { return c ? c->last_quartets : -1; }
 
 mdx_status mdx_plan_info(mdx_ctx* c, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
                          mdx_plan_stats* out) {

@@ -279,6 +279,65 @@ __device__ __forceinline__ void load_record(double* dst, const double* __restric
   for (int i = tl; i < n; i += T) dst[i] = __ldg(src + i);
 }
 
+__device__ __forceinline__ int d_ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// Exchange digestion of one column group: with V = (ij|kl) (a in i, b in j,
+// c in k, d in l) and w the weight of the unique quartet,
+//   K[i][k] += w sum_bd D[j][l] V,  K[i][l] += w sum_bc D[j][k] V,
+//   K[j][k] += w sum_ad D[i][l] V,  K[j][l] += w sum_ac D[i][k] V.
+// Together with K <- K + K^T afterwards this adds all eight index
+// permutations of the quartet exactly once.
+__device__ void digest_group(const QuartetLaunch& a, const double* ws, const Group& grp, int2 qp, int tl, int T) {
+  const PlanDev& P = a.plan;
+  const int2 bp = a.pair_shells[qp.x], kp = a.pair_shells[qp.y];
+  const int si = bp.x, sj = bp.y, sk = kp.x, sl = kp.y;
+  const double w = (si == sj ? 0.5 : 1.0) * (sk == sl ? 0.5 : 1.0) * (qp.x == qp.y ? 0.5 : 1.0);
+  const int na = d_ncart(P.la), nb = d_ncart(P.lb), nd = d_ncart(P.ld);
+  const int nc = d_ncart(P.lc);
+  const int64_t nao = a.nao;
+  const int64_t ai = a.ao_off[si], aj = a.ao_off[sj], ak = a.ao_off[sk], al = a.ao_off[sl];
+  const int ncols = grp.ncols;
+  const uint16_t* cm = P.colmap + grp.col_off;
+  const double* OUT = ws + P.o_OUT;
+  const double* D = a.D;
+  double* K = a.K;
+  // u1: (a,c) over b,d ; u2: (a,d) over b,c ; u3: (b,c) over a,d ; u4: (b,d) over a,c
+  const int n1 = na * nc, n2 = na * nd, n3 = nb * nc, n4 = nb * nd;
+  for (int e = tl; e < n1 + n2 + n3 + n4; e += T) {
+    int u, x, y;
+    if (e < n1) { u = 0; x = e / nc; y = e - x * nc; }
+    else if (e < n1 + n2) { u = 1; const int f = e - n1; x = f / nd; y = f - x * nd; }
+    else if (e < n1 + n2 + n3) { u = 2; const int f = e - n1 - n2; x = f / nc; y = f - x * nc; }
+    else { u = 3; const int f = e - n1 - n2 - n3; x = f / nd; y = f - x * nd; }
+    double s = 0.0;
+    bool any = false;
+    for (int col = 0; col < ncols; ++col) {
+      const int cd = cm[col];
+      const int c = cd / nd, d = cd - c * nd;
+      if (u == 0 && c == y) {          // K[i+x][k+c] += D[j+b][l+d] V[x,b,c,d]
+        any = true;
+        for (int b = 0; b < nb; ++b) s = fma(__ldg(D + (aj + b) * nao + al + d), OUT[(x * nb + b) * ncols + col], s);
+      } else if (u == 1 && d == y) {   // K[i+x][l+d] += D[j+b][k+c] V[x,b,c,d]
+        any = true;
+        for (int b = 0; b < nb; ++b) s = fma(__ldg(D + (aj + b) * nao + ak + c), OUT[(x * nb + b) * ncols + col], s);
+      } else if (u == 2 && c == y) {   // K[j+x][k+c] += D[i+aa][l+d] V[aa,x,c,d]
+        any = true;
+        for (int aa = 0; aa < na; ++aa) s = fma(__ldg(D + (ai + aa) * nao + al + d), OUT[(aa * nb + x) * ncols + col], s);
+      } else if (u == 3 && d == y) {   // K[j+x][l+d] += D[i+aa][k+c] V[aa,x,c,d]
+        any = true;
+        for (int aa = 0; aa < na; ++aa) s = fma(__ldg(D + (ai + aa) * nao + ak + c), OUT[(aa * nb + x) * ncols + col], s);
+      }
+    }
+    if (!any) continue;
+    int64_t row, colk;
+    if (u == 0) { row = ai + x; colk = ak + y; }
+    else if (u == 1) { row = ai + x; colk = al + y; }
+    else if (u == 2) { row = aj + x; colk = ak + y; }
+    else { row = aj + x; colk = al + y; }
+    atomicAdd(K + row * nao + colk, w * s);
+  }
+}
+
 template <bool CTA>
 __global__ void __launch_bounds__(CTA ? 512 : 128) k_quartets(const QuartetLaunch a) {
   extern __shared__ __align__(16) double smem[];
@@ -307,7 +366,7 @@ __global__ void __launch_bounds__(CTA ? 512 : 128) k_quartets(const QuartetLaunc
     team_sync<CTA>(mask);
     compute_R<CTA>(a, ws, tl, mask);
   }
-  double* outq = a.out + a.qout[q];
+  double* outq = a.D ? nullptr : a.out + a.qout[q];
   for (int g = 0; g < P.ngroups; ++g) {
     const Group grp = P.groups[g];
     const int ncols = grp.ncols;
@@ -394,8 +453,12 @@ __global__ void __launch_bounds__(CTA ? 512 : 128) k_quartets(const QuartetLaunc
       }
       team_sync<CTA>(mask);
     }
-    // store the group's columns: OUT[ab][col] -> out[ab*Nk + cd]
-    if (active) {
+    if (a.D) {
+      // exchange digestion of this group's columns (Sec. 6: K_bc = sum_ad [ab|cd] D_ad),
+      // unique quartet (ij|kl) with i>=j, k>=l, ij>=kl and weight w; the host adds K^T at the end
+      if (active) digest_group(a, ws, grp, qp, tl, T);
+    } else if (active) {
+      // store the group's columns: OUT[ab][col] -> out[ab*Nk + cd]
       const uint16_t* cm = P.colmap + grp.col_off;
       const int tot = P.Nb * ncols;
       for (int e = tl; e < tot; e += T) {
@@ -416,6 +479,74 @@ cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
   if (P.T > 32) k_quartets<true><<<(unsigned)grid, block, shm, s>>>(a);
   else k_quartets<false><<<(unsigned)grid, block, shm, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- exchange support
+__global__ void k_dmax(const double* __restrict__ D, int32_t nao, const int32_t* __restrict__ ao_off,
+                       const int32_t* __restrict__ l, int32_t n, float* __restrict__ dmax) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)n * n) return;
+  const int x = (int)(g / n), y = (int)(g - (int64_t)x * n);
+  const int64_t r0 = ao_off[x], c0 = ao_off[y];
+  const int nr = d_ncart(l[x]), nc = d_ncart(l[y]);
+  double m = 0.0;
+  for (int r = 0; r < nr; ++r)
+    for (int c = 0; c < nc; ++c) m = fmax(m, fabs(D[(r0 + r) * nao + c0 + c]));
+  dmax[g] = (float)m;
+}
+
+cudaError_t launch_dmax(const double* D, int32_t nao, const int32_t* ao_off, const int32_t* l, int32_t n_shells,
+                        float* dmax, cudaStream_t s) {
+  const int64_t tot = (int64_t)n_shells * n_shells;
+  if (tot <= 0) return cudaSuccess;
+  k_dmax<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, nao, ao_off, l, n_shells, dmax);
+  return cudaGetLastError();
+}
+
+// Unique quartets (p, q), q <= p, kept when Q_p Q_q max(|D_ik|,|D_il|,|D_jk|,|D_jl|) >= tau
+// (Schwarz bound times the largest density block the quartet touches).
+// Counting pass: per-bucket totals; fill pass: write (p, q) into its bucket.
+__global__ void k_screen(const ScreenArgs a, bool fill) {
+  const int64_t p = blockIdx.x;
+  if (p >= a.npairs) return;
+  const int2 ij = a.pair_shells[p];
+  const float qp = a.Q[p];
+  const int cp = a.pair_class[p];
+  const float* di = a.dmax + (int64_t)ij.x * a.n_shells;
+  const float* dj = a.dmax + (int64_t)ij.y * a.n_shells;
+  const int64_t brow = (int64_t)cp * (cp + 1) / 2;
+  for (int64_t q = threadIdx.x; q <= p; q += blockDim.x) {
+    const int2 kl = a.pair_shells[q];
+    const float dm = fmaxf(fmaxf(di[kl.x], di[kl.y]), fmaxf(dj[kl.x], dj[kl.y]));
+    if (qp * a.Q[q] * dm < a.tau) continue;
+    const int64_t b = brow + a.pair_class[q];
+    const unsigned long long slot = atomicAdd(a.counts + b, 1ull);
+    if (fill) a.out[a.bucket_off[b] + (int64_t)slot] = make_int2((int)p, (int)q);
+  }
+}
+
+cudaError_t launch_screen(const ScreenArgs& a, bool fill, cudaStream_t s) {
+  if (a.npairs <= 0) return cudaSuccess;
+  k_screen<<<(unsigned)a.npairs, 256, 0, s>>>(a, fill);
+  return cudaGetLastError();
+}
+
+__global__ void k_symmetrize(double* K, int32_t nao) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = nao;
+  if (g >= n * n) return;
+  const int64_t r = g / n, c = g - r * n;
+  if (c < r) return;
+  const double t = K[r * n + c] + K[c * n + r];
+  K[r * n + c] = t;
+  K[c * n + r] = t;
+}
+
+cudaError_t launch_symmetrize(double* K, int32_t nao, cudaStream_t s) {
+  const int64_t tot = (int64_t)nao * nao;
+  if (tot <= 0) return cudaSuccess;
+  k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(K, nao);
   return cudaGetLastError();
 }
 

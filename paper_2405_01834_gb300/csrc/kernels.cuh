@@ -44,9 +44,36 @@ struct QuartetLaunch {
   const int32_t* hdec_off;   // start of each total order N in hdec
   double* out;
   int* err;
+  // exchange digestion (out unused when D != nullptr): K_ik += w sum_jl D_jl (ij|kl)
+  // and the three other index placements of the unique quartet (see k_quartets)
+  const double* D;
+  double* K;
+  int32_t nao;
+  const int32_t* ao_off;     // per shell, of the basis of the pairs
+  const int2* pair_shells;   // per pair (i, j)
 };
 
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s);
+
+// Exchange support: per shell-pair block max |D| (float), screening of unique
+// quartets into class buckets, K <- K + K^T.
+cudaError_t launch_dmax(const double* D, int32_t nao, const int32_t* ao_off, const int32_t* l, int32_t n_shells,
+                        float* dmax, cudaStream_t s);
+struct ScreenArgs {
+  int64_t npairs;
+  const int2* pair_shells;   // sorted by pair class
+  const int32_t* pair_class; // class index of each pair (non-decreasing)
+  const float* Q;            // Schwarz factor per pair
+  const float* dmax;         // [n_shells][n_shells]
+  int32_t n_shells;
+  int32_t nclass;
+  float tau;
+  unsigned long long* counts;  // [nclass*(nclass+1)/2]
+  const int64_t* bucket_off;   // fill pass: start of each bucket
+  int2* out;                   // fill pass: (p, q) per surviving quartet
+};
+cudaError_t launch_screen(const ScreenArgs& a, bool fill, cudaStream_t s);
+cudaError_t launch_symmetrize(double* K, int32_t nao, cudaStream_t s);
 cudaError_t kernel_attributes_init();
 
 // Schwarz reduction: Q[p] = sqrt(max_ab |diag of shellset p|).

@@ -88,6 +88,10 @@ def load(build_if_missing: bool = True):
     lib.mdx_batch_run.restype = I32
     lib.mdx_batch_destroy.argtypes = [P]
     lib.mdx_batch_destroy.restype = None
+    lib.mdx_exchange.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, P, P]
+    lib.mdx_exchange.restype = I32
+    lib.mdx_last_quartet_count.argtypes = [P]
+    lib.mdx_last_quartet_count.restype = I64
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
     lib.mdx_plan_info.restype = I32
     _lib = lib
@@ -188,6 +192,20 @@ class Engine:
                                out.data_ptr(), out.numel(), offs.data_ptr(), _stream())
         self._check(st, "mdx_eri3")
         return out, offs
+
+    def exchange(self, basis: DeviceBasis, pairs, Q, D: torch.Tensor, tau: float = 0.0) -> torch.Tensor:
+        """K_ik = sum_jl D_jl (ij|kl) over the screened unique quartets of the pair list."""
+        p = torch.as_tensor(pairs, dtype=torch.int32, device="cuda").contiguous()
+        q = torch.as_tensor(Q, dtype=torch.float64, device="cuda").contiguous()
+        D = D.to(device="cuda", dtype=torch.float64).contiguous()
+        K = torch.empty_like(D)
+        st = self.lib.mdx_exchange(self.ctx, ctypes.byref(basis.desc), p.data_ptr(), q.data_ptr(), p.shape[0],
+                                   float(tau), D.data_ptr(), K.data_ptr(), _stream())
+        self._check(st, "mdx_exchange")
+        return K
+
+    def last_quartet_count(self) -> int:
+        return int(self.lib.mdx_last_quartet_count(self.ctx))
 
     def batch_eri4(self, basis: DeviceBasis, quartets) -> "Batch":
         """Prepare quartets [n,4] once; run them many times with Batch.run."""
