@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--n-bra", type=int, default=224)
     ap.add_argument("--n-ket", type=int, default=224)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the per-class team-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
     return ap.parse_args()
@@ -208,6 +209,21 @@ def main():
         prepared.append((l, db, q, batches))
     out = torch.empty(max_chunk, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+    tuned = {}
+    if not args.no_tune:
+        # choose each class's team shape on its first chunk (untimed set-up, like a library's autotuning);
+        # later chunks of the class use the choice when they are re-planned
+        for l, db, q, batches in prepared:
+            t0 = time.perf_counter()
+            batches[0].autotune(out, max_trial=max(304, min(len(q), 4096 // max(1, l))))
+            tuned[CLASS_NAMES[l]] = round(time.perf_counter() - t0, 2)
+        # re-prepare so every chunk picks up the tuned plans
+        for i, (l, db, q, batches) in enumerate(prepared):
+            for bt in batches:
+                bt.close()
+            per_q = inputs.ncart(l) ** 4 * 8
+            cq = max(1, min(len(q), CHUNK_BYTES // per_q))
+            prepared[i] = (l, db, q, [eng.batch_eri4(db, q[s:s + cq]) for s in range(0, len(q), cq)])
     stream = torch.cuda.current_stream()
 
     def step(record):
@@ -308,7 +324,7 @@ def main():
             "quartets_per_s": round(world * sum(len(q) for _, _, q, _ in prepared) / (ms_step * 1e-3), 1),
             "model_frac_of_peak": round(value / world / peak_gflops, 4),
             "exec_gflops": round(world * total_exec / (ms_step * 1e-3) * 1e-9, 3),
-            "per_class": per_class, "roofline": roofline, "gpu_launches": launches // args.steps if args.steps else 0,
+            "per_class": per_class, "roofline": roofline, "autotune_s": tuned or None, "gpu_launches": launches // args.steps if args.steps else 0,
             "clocks": clocks}
 
     # ---- end to end through the public call with host buffers (rank 0 timing only)

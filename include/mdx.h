@@ -149,6 +149,16 @@ mdx_status mdx_batch_offsets(mdx_ctx* ctx, const mdx_batch* batch, int64_t* out_
 mdx_status mdx_batch_run(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t out_capacity, int32_t* n_launches,
                          void* stream);
 
+/* Autotuner (the analogue of the paper's per-class variant selection, Sec. 4):
+ * for every class of the batch, time candidate team shapes (threads per
+ * team, shared-memory budget per team, one or several ket-column groups) on
+ * the first max_trial quartets of that class, keep the fastest for the
+ * context (later batches of the class use it) and switch this batch to it.
+ * Writes trial results into `out` (batch->total doubles needed) and
+ * synchronises `stream`. Results are identical up to FP64 summation order. */
+mdx_status mdx_batch_autotune(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t out_capacity,
+                              int64_t max_trial, void* stream);
+
 /* Free a batch (NULL allowed). No work of the batch may still be running. */
 void mdx_batch_destroy(mdx_batch* batch);
 

@@ -35,7 +35,8 @@ struct mdx_ctx {
   int* d_err = nullptr;
   std::map<ClassKey, std::unique_ptr<Plan>> plans;
   std::map<std::string, DevBuf> bufs;
-  int smem_budget = 200 * 1024;
+  std::map<ClassKey, PlanConfig> tuned;   // shapes chosen by mdx_batch_autotune
+  std::vector<std::unique_ptr<Plan>> retired;   // replaced plans, kept alive for batches that use them
   int64_t last_quartets = 0;
 };
 
@@ -86,13 +87,8 @@ mdx_status upload(mdx_ctx* c, const char* name, const std::vector<T>& v, T** out
   return MDX_OK;
 }
 
-mdx_status get_plan(mdx_ctx* c, const ClassKey& k, Plan** out, cudaStream_t s) {
-  auto it = c->plans.find(k);
-  if (it != c->plans.end()) { *out = it->second.get(); return MDX_OK; }
-  std::unique_ptr<Plan> p(new Plan());
-  std::string err;
-  if (!build_plan(k, c->smem_budget, *p, err)) return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
-  // one device blob: groups | kprog | b1 | b23 | colmap
+// Copy a plan's programs to one device blob and point its PlanDev at it.
+mdx_status upload_plan(mdx_ctx* c, Plan* p, cudaStream_t s) {
   const size_t sg = p->groups.size() * sizeof(Group), sk = p->kprog.size() * sizeof(StepEntry),
                s1 = p->b1.size() * sizeof(StepEntry), s2 = p->b23.size() * sizeof(B23Entry),
                sc = p->colmap.size() * sizeof(uint16_t);
@@ -104,10 +100,9 @@ mdx_status get_plan(mdx_ctx* c, const ClassKey& k, Plan** out, cudaStream_t s) {
   const size_t og = put(p->groups.data(), sg), ok = put(p->kprog.data(), sk), o1 = put(p->b1.data(), s1),
                o2 = put(p->b23.data(), s2), oc = put(p->colmap.data(), sc);
   cudaError_t e = cudaMalloc(&p->dev_blob, tot);
-  if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MDX_ENOMEM, "plan allocation failed"); }
+  if (e != cudaSuccess) { cudaGetLastError(); p->dev_blob = nullptr; return fail(c, MDX_ENOMEM, "plan allocation failed"); }
   e = cudaMemcpyAsync(p->dev_blob, blob.data(), tot, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "plan upload");
-  e = cudaStreamSynchronize(s);   // blob is a local vector
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // blob is a local vector
   if (e != cudaSuccess) return cuda_fail(c, e, "plan upload");
   char* base = (char*)p->dev_blob;
   p->d.groups = (const Group*)(base + og);
@@ -115,6 +110,19 @@ mdx_status get_plan(mdx_ctx* c, const ClassKey& k, Plan** out, cudaStream_t s) {
   p->d.b1 = (const StepEntry*)(base + o1);
   p->d.b23 = (const B23Entry*)(base + o2);
   p->d.colmap = (const uint16_t*)(base + oc);
+  return MDX_OK;
+}
+
+mdx_status get_plan(mdx_ctx* c, const ClassKey& k, Plan** out, cudaStream_t s) {
+  auto it = c->plans.find(k);
+  if (it != c->plans.end()) { *out = it->second.get(); return MDX_OK; }
+  std::unique_ptr<Plan> p(new Plan());
+  std::string err;
+  auto tc = c->tuned.find(k);
+  const PlanConfig cfg = tc != c->tuned.end() ? tc->second : PlanConfig{};
+  if (!build_plan(k, cfg, *p, err)) return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
+  mdx_status st = upload_plan(c, p.get(), s);
+  if (st != MDX_OK) { if (p->dev_blob) cudaFree(p->dev_blob); return st; }
   *out = p.get();
   c->plans[k] = std::move(p);
   return MDX_OK;
@@ -196,7 +204,7 @@ struct mdx_batch {
   int2* qp = nullptr;
   int64_t* qoff = nullptr;
   int64_t* offsets = nullptr;     // [n+1] in caller order
-  struct Range { Plan* plan; int64_t begin, count; };
+  struct Range { Plan* plan; int64_t begin, count; ClassKey key; };
   std::vector<Range> ranges;
   double model_flops = 0.0;
   double exec_fma = 0.0;
@@ -282,7 +290,7 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     for (int64_t q : kv.second) { qp_sorted.push_back(bt.qp[q]); qoff_sorted.push_back(bt.qoff[q]); }
     Plan* plan;
     if ((st = get_plan(c, kv.first, &plan, s)) != MDX_OK) return st;
-    B->ranges.push_back({plan, b, (int64_t)kv.second.size()});
+    B->ranges.push_back({plan, b, (int64_t)kv.second.size(), kv.first});
     B->model_flops += model_flops_class(kv.first) * (double)kv.second.size();
     B->exec_fma += plan->exec_fma * (double)kv.second.size();
   }
@@ -460,6 +468,7 @@ void mdx_destroy(mdx_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   for (auto& kv : c->plans) if (kv.second->dev_blob) cudaFree(kv.second->dev_blob);
+  for (auto& p : c->retired) if (p->dev_blob) cudaFree(p->dev_blob);
   for (auto& kv : c->bufs) if (kv.second.p) cudaFree(kv.second.p);
   cudaFree(c->d_boys);
   cudaFree(c->d_hdec);
@@ -557,6 +566,89 @@ mdx_status mdx_batch_run(mdx_ctx* c, mdx_batch* b, double* out, int64_t out_capa
 }
 
 void mdx_batch_destroy(mdx_batch* b) { batch_free(b); }
+
+mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out_capacity, int64_t max_trial,
+                              void* stream) {
+  if (!c || !b || !out || max_trial < 1) return MDX_EINVAL;
+  if (b->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
+  if (b->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_pair_records(b->b0, b->b1, b->jobs, b->njobs, b->recs, b->recs_s, c->d_err, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (auto& r : b->ranges) {
+    if (r.count == 0) continue;
+    // candidate shapes: team sizes x shared-memory budgets (teams per SM)
+    // (classes whose default plan splits the ket columns into groups only vary
+    // the team size and budget: their plans are expensive to build)
+    std::vector<PlanConfig> cands;
+    if (r.plan->d.ngroups > 1) {
+      for (int budget : {200 * 1024, 108 * 1024})
+        for (int T : {128, 256, 512}) cands.push_back(PlanConfig{T, budget, 96 * 1024});
+    } else {
+      for (int single : {96 * 1024, 40 * 1024})
+        for (int T : {0, 1, 4, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, single});
+    }
+    float best_ms = 1e30f;
+    PlanConfig best{};
+    std::unique_ptr<Plan> best_plan;
+    std::vector<std::pair<int, int>> seen;   // (T, team_doubles, ngroups) signature of built plans
+    for (const PlanConfig& cfg : cands) {
+      std::unique_ptr<Plan> p(new Plan());
+      std::string err;
+      if (!build_plan(r.key, cfg, *p, err)) continue;
+      const std::pair<int, int> sig{p->d.T * 100000 + p->d.ngroups, p->d.team_doubles * 64 + p->d.teams_per_cta};
+      if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;   // same shape as one already timed
+      seen.push_back(sig);
+      mdx_status st = upload_plan(c, p.get(), s);
+      if (st != MDX_OK) { if (p->dev_blob) cudaFree(p->dev_blob); return st; }
+      QuartetLaunch a{};
+      a.plan = p->d;
+      a.nq = std::min(r.count, max_trial);
+      a.qpairs = b->qp + r.begin;
+      a.qout = b->qoff + r.begin;
+      a.pair_rec = b->pair_rec;
+      a.recs = b->recs;
+      a.recs_signed = b->recs_s;
+      a.boys = c->d_boys;
+      a.hdec = c->d_hdec;
+      a.hdec_off = c->d_hdec_off;
+      a.out = out;
+      a.err = c->d_err;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        e = launch_quartets(a, s);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { cudaFree(p->dev_blob); cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "autotune"); }
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cfg;
+        if (best_plan && best_plan->dev_blob) cudaFree(best_plan->dev_blob);
+        best_plan = std::move(p);
+      } else {
+        cudaFree(p->dev_blob);
+      }
+    }
+    if (!best_plan) continue;
+    c->tuned[r.key] = best;
+    auto it = c->plans.find(r.key);
+    if (it != c->plans.end()) c->retired.push_back(std::move(it->second));
+    r.plan = best_plan.get();
+    c->plans[r.key] = std::move(best_plan);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return check_device_error(c, s);
+}
 
 mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, int64_t n, double* Q_out,
                        void* stream) {
@@ -752,7 +844,13 @@ mdx_status mdx_plan_info(mdx_ctx* c, int la, int lb, int lc, int ld, int Kb, int
     return fail(c, MDX_EUNSUPPORTED, "class outside the supported range");
   Plan p;
   std::string err;
-  if (!build_plan(ClassKey{la, lb, lc, ld, Kb, Kk, one_centre ? 1 : 0}, c ? c->smem_budget : 200 * 1024, p, err))
+  const ClassKey key{la, lb, lc, ld, Kb, Kk, one_centre ? 1 : 0};
+  PlanConfig cfg{};
+  if (c) {
+    auto tc = c->tuned.find(key);
+    if (tc != c->tuned.end()) cfg = tc->second;
+  }
+  if (!build_plan(key, cfg, p, err))
     return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
   out->team_threads = p.d.T;
   out->teams_per_cta = p.d.teams_per_cta;

@@ -123,7 +123,15 @@ struct Plan {
   void* dev_blob = nullptr;
 };
 
-// Builds the plan of a class for a shared-memory budget per CTA (bytes).
-bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::string& err);
+// Tunable shape of a plan (0 = the planner's default).
+struct PlanConfig {
+  int T = 0;                 // threads per team (1..512, a power of two)
+  int budget = 200 * 1024;   // shared-memory bytes per team
+  int single_max = 96 * 1024;  // largest workspace for which all ket columns form one group
+  bool operator==(const PlanConfig& o) const { return T == o.T && budget == o.budget && single_max == o.single_max; }
+};
+
+// Builds the plan of a class for the given shape.
+bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::string& err);
 
 }  // namespace mdx

@@ -201,7 +201,8 @@ bool validate_plan(const Plan& plan, std::string& err) {
 
 }  // namespace
 
-bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::string& err) {
+bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::string& err) {
+  const int smem_budget_bytes = std::min(cfg.budget, 220 * 1024);
   PlanDev& P = plan.d;
   P = PlanDev{};
   P.la = key.la; P.lb = key.lb; P.lc = key.lc; P.ld = key.ld;
@@ -209,7 +210,10 @@ bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::str
   if (key.onec && key.lb != 0) { err = "one-centre bra needs lb = 0"; return false; }
   P.Lb = key.la + key.lb; P.Lk = key.lc + key.ld; P.L = P.Lb + P.Lk;
   P.Nb = ncart(key.la) * ncart(key.lb); P.Nk = ncart(key.lc) * ncart(key.ld);
-  P.hb = nherm(P.Lb);
+  // per-column strides of X and C1 are odd numbers of doubles, so the 16 lanes
+  // of a half-warp that read the same entry of consecutive columns hit 16
+  // different shared-memory bank pairs
+  P.hb = nherm(P.Lb) | 1;
   P.recb = rec_size(key.la, key.lb);
   P.reck = rec_size(key.lc, key.ld);
   const int Tab = etab_size(key.la, key.lb);
@@ -234,7 +238,7 @@ bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::str
       c1off[{ax, bx}] = c1;
       c1 += tri(P.Lb - ax - bx + 1);
     }
-  P.c1size = c1;
+  P.c1size = c1 | 1;
   const int recb_tab = P.o_recb + kRecHeader;
   plan.b1.clear(); plan.b23.clear();
   double fma_b = 0;
@@ -303,7 +307,7 @@ bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::str
     int as = 0, bs = 0;
     bool ok = group_sizes(allcols, as, bs);
     const int td = team_doubles(as, bs, (int)allcols.size());
-    if (ok && td * 8 <= std::min(smem_budget_bytes, 96 * 1024)) groups.push_back(allcols);
+    if (ok && td * 8 <= std::min(smem_budget_bytes, cfg.single_max)) groups.push_back(allcols);
   }
   int regmax = 0, cmax = 0;
   if (groups.empty()) {
@@ -392,25 +396,27 @@ bool build_plan(const ClassKey& key, int smem_budget_bytes, Plan& plan, std::str
 
   // ---- team shape ------------------------------------------------------
   const int bytes = P.team_doubles * 8;
-  if (P.ngroups > 1) {
+  const int tps = std::max(1, (220 * 1024) / bytes);   // teams that fit one SM's shared memory
+  if (cfg.T > 0) {
+    if (cfg.T > 512 || (cfg.T & (cfg.T - 1))) { err = "team size must be a power of two <= 512"; return false; }
+    P.T = cfg.T;
+  } else if (P.ngroups > 1) {
     P.T = 512;
-    P.teams_per_cta = 1;
   } else {
-    int tps = std::max(1, (220 * 1024) / bytes);
     int Tocc = 1;
     while (Tocc * tps < 512 && Tocc < 512) Tocc *= 2;
     int work = std::max(1, P.Nb * P.Nk / 8);
     int Twork = 1;
     while (Twork * 2 <= work && Twork < 512) Twork *= 2;
     P.T = std::min(Tocc, Twork);
-    if (P.T > 32) {
-      P.teams_per_cta = 1;
-    } else {
-      int tpc = std::max(1, 128 / P.T);
-      tpc = std::min(tpc, tps);
-      while (tpc > 1 && tpc * bytes > smem_budget_bytes) --tpc;
-      P.teams_per_cta = tpc;
-    }
+  }
+  if (P.T > 32) {
+    P.teams_per_cta = 1;
+  } else {
+    int tpc = std::max(1, 128 / P.T);
+    tpc = std::min(tpc, tps);
+    while (tpc > 1 && tpc * bytes > smem_budget_bytes) --tpc;
+    P.teams_per_cta = tpc;
   }
   if (P.T * P.teams_per_cta > 1024 || (long)P.teams_per_cta * P.team_doubles * 8 > 227 * 1024) {
     err = "team shape exceeds the CTA limits";

@@ -86,6 +86,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_batch_offsets.restype = I32
     lib.mdx_batch_run.argtypes = [P, P, P, I64, ctypes.POINTER(ctypes.c_int32), P]
     lib.mdx_batch_run.restype = I32
+    lib.mdx_batch_autotune.argtypes = [P, P, P, I64, I64, P]
+    lib.mdx_batch_autotune.restype = I32
     lib.mdx_batch_destroy.argtypes = [P]
     lib.mdx_batch_destroy.restype = None
     lib.mdx_exchange.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, P, P]
@@ -255,6 +257,11 @@ class Batch:
         self.eng._check(self.eng.lib.mdx_batch_run(self.eng.ctx, self.h, out.data_ptr(), out.numel(),
                                                    ctypes.byref(nl), _stream()), "mdx_batch_run")
         return nl.value
+
+    def autotune(self, out: torch.Tensor, max_trial: int = 256):
+        """Pick the fastest team shape per class on this GPU (kept by the engine)."""
+        self.eng._check(self.eng.lib.mdx_batch_autotune(self.eng.ctx, self.h, out.data_ptr(), out.numel(), max_trial,
+                                                        _stream()), "mdx_batch_autotune")
 
     def close(self):
         if self.h:

@@ -162,3 +162,20 @@ def test_schwarz(eng):
         blk = ref[off[n]:off[n + 1]].reshape(m, m)
         refQ.append(np.sqrt(np.max(np.abs(np.diag(blk)))))
     np.testing.assert_allclose(Q, refQ, rtol=1e-12, atol=0)
+
+
+def test_autotuned_batch_matches(eng):
+    """The autotuner keeps results (only the summation order may change)."""
+    b, q = inputs.class_sweep((3, 2, 2, 1), n_bra=9, n_ket=7, seed=12, K=(1, 2, 1, 3))
+    db = mdx.DeviceBasis(b)
+    v, off = eng.eri4(db, q)
+    bt = eng.batch_eri4(db, q)
+    w = torch.empty(bt.total, dtype=torch.float64, device="cuda")
+    bt.autotune(w, max_trial=32)
+    w.fill_(float("nan"))
+    bt.run(w)
+    torch.cuda.synchronize()
+    eng.sync()
+    ref, _ = oracle.eri4(b, q)
+    parity.check(w.cpu().numpy(), ref, oracle.eri4(b, q, precision=1)[0], "autotuned", off.cpu().numpy())
+    bt.close()
