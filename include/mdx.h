@@ -49,7 +49,8 @@ typedef enum {
   MDX_EUNSUPPORTED = 4,     /* l > MDX_LMAX or contraction degree > MDX_KMAX */
   MDX_ECAPACITY = 5,        /* output buffer too small */
   MDX_ETIMEOUT = 6,         /* a bounded device-side wait expired */
-  MDX_EDEVICE = 7           /* a kernel flagged invalid input */
+  MDX_EDEVICE = 7,          /* a kernel flagged invalid input */
+  MDX_ESCRATCH = 8          /* the request needs more than mdx_eri4_noalloc's fixed 32 MiB scratch */
 } mdx_status;
 
 typedef struct mdx_ctx mdx_ctx;
@@ -189,6 +190,27 @@ mdx_status mdx_exchange(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pai
 /* Number of unique quartets the last mdx_exchange of this context kept after
  * screening (-1 for a NULL context). */
 int64_t mdx_last_quartet_count(const mdx_ctx* ctx);
+
+/* mdx_eri4 without any device allocation, for callers that cannot let a
+ * library call cudaMalloc: applications that own all device memory through
+ * their own pool or budget and forbid allocations behind their back, and
+ * steady-state loops that cannot afford cudaMalloc's implicit device
+ * synchronisation. (The paper has no counterpart; this is a property of the
+ * engine, not of the method.)
+ * Same arguments and results as mdx_eri4, minus the context: it runs on the
+ * current CUDA device. All device scratch (Boys and Hermite decode tables,
+ * primitive-pair records, quartet lists, class step programs) lives in one
+ * file-scope 32 MiB __device__ array that every GPU loading the library holds
+ * until the process exits. The first call on a device sets that device up
+ * (looks up the array's address, fills the tables, synchronously); make that
+ * first call before any stream capture. A request whose records, lists and
+ * programs do not fit returns MDX_ESCRATCH and writes nothing. Every call
+ * shares the one array and rewrites what it uses (the device error word is
+ * cleared per call): calls that overlap on the GPU race and must not be
+ * issued concurrently on different streams. Synchronises `stream`. No error
+ * text is kept (no context): the status code is the report. */
+mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
+                            int64_t out_capacity, int64_t* out_offsets, void* stream);
 
 /* Shape the engine chooses for one integral class (no GPU needed; ctx may be
  * NULL). The class is (la lb | lc ld) with Kb = K_a K_b and Kk = K_c K_d

@@ -44,6 +44,18 @@ def plan_info(la, lb, lc, ld, Kb=1, Kk=1, one_centre=False) -> PlanStats:
     return st
 
 
+def eri4_noalloc(basis: "DeviceBasis", quartets, out: torch.Tensor):
+    """mdx_eri4_noalloc on the current device: [ab|cd] into the caller's `out`
+    with no device allocation by the library (for callers whose device memory
+    is owned by their own pool). Returns (status, offsets[n+1])."""
+    lib = load()
+    q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
+    offs = torch.empty(q.shape[0] + 1, dtype=torch.int64, device="cuda")
+    st = lib.mdx_eri4_noalloc(ctypes.byref(basis.desc), q.data_ptr(), q.shape[0], out.data_ptr(), out.numel(),
+                              offs.data_ptr(), _stream())
+    return st, offs
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -94,6 +106,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_exchange.restype = I32
     lib.mdx_last_quartet_count.argtypes = [P]
     lib.mdx_last_quartet_count.restype = I64
+    lib.mdx_eri4_noalloc.argtypes = [ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
+    lib.mdx_eri4_noalloc.restype = I32
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
     lib.mdx_plan_info.restype = I32
     _lib = lib
@@ -101,7 +115,7 @@ def load(build_if_missing: bool = True):
 
 
 STATUS = {0: "MDX_OK", 1: "MDX_EINVAL", 2: "MDX_ENOMEM", 3: "MDX_ECUDA", 4: "MDX_EUNSUPPORTED",
-          5: "MDX_ECAPACITY", 6: "MDX_ETIMEOUT", 7: "MDX_EDEVICE"}
+          5: "MDX_ECAPACITY", 6: "MDX_ETIMEOUT", 7: "MDX_EDEVICE", 8: "MDX_ESCRATCH"}
 
 
 class DeviceBasis:
