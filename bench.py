@@ -74,6 +74,22 @@ def model_flops(l, n):
     return flops.eri4_flops(l, l, l, l) * n
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """Slowest rank's step time (every rank runs its own replica of the workload)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_step: float) -> float:
+    """Weak scaling: all ranks' units divided by the slowest rank's time (units/s)."""
+    return world * units_per_rank / (ms_step * 1e-3)
+
+
 # ------------------------------------------------------------------ oracle arm
 def run_oracle(work, frac, seed=2024):
     """Time the oracle on a seeded sample of each class; returns (model flops, seconds, quartets, sample text)."""
@@ -272,18 +288,13 @@ def main():
         step_ms.append(tot)
     clocks = clk.stop()
     eng.sync()
-    ms_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(sum(step_ms) / len(step_ms), world, "cuda")
 
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak_gflops = FP64_FLOP_PER_CLK_SM * props.multi_processor_count * sm_max * 1e-3
     total_flops = sum(model_flops(l, len(q)) for l, _, q, _ in prepared)
     total_exec = sum(2.0 * bt.exec_fma for *_, batches in prepared for bt in batches)
-    value = world * total_flops / (ms_step * 1e-3) * 1e-9
+    value = whole_job_rate(total_flops, world, ms_step) * 1e-9
     per_class = {}
     dom_l, dom_ms = None, -1.0
     for l, db, q, batches in prepared:
@@ -321,7 +332,7 @@ def main():
             "config": {"workload": "4-center class sweep [pp|pp]..[ii|ii], %dx%d random uncontracted quartets per "
                                    "class, Cartesian, FP64" % (args.n_bra, args.n_ket), "classes": args.classes,
                        "l2": "256 MB buffer written between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "quartets_per_s": round(world * sum(len(q) for _, _, q, _ in prepared) / (ms_step * 1e-3), 1),
+            "quartets_per_s": round(whole_job_rate(sum(len(q) for _, _, q, _ in prepared), world, ms_step), 1),
             "model_frac_of_peak": round(value / world / peak_gflops, 4),
             "exec_gflops": round(world * total_exec / (ms_step * 1e-3) * 1e-9, 3),
             "per_class": per_class, "roofline": roofline, "autotune_s": tuned or None, "gpu_launches": launches // args.steps if args.steps else 0,
