@@ -54,6 +54,8 @@ def _load():
             lib.orc_exchange.argtypes = [P] * 7 + [ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int]
             lib.orc_exchange_rows.argtypes = [P] * 7 + [ctypes.c_int32, ctypes.c_int32, P, P, P,
                                                         ctypes.c_int32, ctypes.c_int]
+            lib.orc_exchange_grad.argtypes = [P] * 8 + [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
+                                                        ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -155,3 +157,23 @@ def exchange(basis, D: np.ndarray, row_shells=None, nthreads: int = 0) -> np.nda
         _load().orc_exchange_rows(*[_p(a) for a in arrs], _p(ao_off), int(basis.n_shells), nao, _p(D), _p(K),
                                   _p(rows), len(rows), nthreads)
     return K
+
+
+def exchange_energy(basis, D: np.ndarray, nthreads: int = 0) -> float:
+    """S = sum_ik D_ik K_ik with K the dense exchange matrix (E_x = alpha S)."""
+    return float(np.sum(np.asarray(D) * exchange(basis, D, nthreads=nthreads)))
+
+
+def exchange_grad(basis, D: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """dS/dR per atom, S = sum_ijkl D_ik D_jl (ij|kl), D fixed: array [n_atoms, 3].
+    Every ordered quartet and all four centres differentiated explicitly."""
+    arrs = _basis_arrays(basis)
+    ao_off = np.ascontiguousarray(basis.ao_off, dtype=np.int32)
+    atom = np.ascontiguousarray(basis.atom, dtype=np.int32)
+    nao = int(basis.nao)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    n_atoms = int(max(basis.n_atoms, int(atom.max()) + 1 if len(atom) else 0))
+    g = np.zeros((n_atoms, 3))
+    _load().orc_exchange_grad(*[_p(a) for a in arrs], _p(ao_off), _p(atom), int(basis.n_shells), nao, _p(D),
+                              n_atoms, _p(g), nthreads)
+    return g

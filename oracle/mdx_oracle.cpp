@@ -514,6 +514,104 @@ void orc_exchange(const int32_t* l, const int32_t* nprim, const int32_t* prim_of
     for (int64_t i = 0; i < (int64_t)nao * nao; ++i) K[i] += Kt[t][i];
 }
 
+// Nuclear gradient of S = sum_{ijkl} D_ik D_jl (ij|kl) (the exchange energy
+// E_x = alpha S with D held fixed; the paper lists geometric derivatives as
+// future work, Sec. 7). Every ordered shell quartet and every one of its four
+// centres is differentiated explicitly with the textbook rule for a primitive
+// Cartesian Gaussian (Eq. 1):
+//   d/dA_x [x_A^a exp(-z x_A^2)] = 2 z x_A^(a+1) exp(..) - a x_A^(a-1) exp(..),
+// i.e. the shell is replaced by a shell of l+1 with coefficients 2 z c and one
+// of l-1 with coefficients c. grad[atom][x] receives dS/dR for each centre
+// on that atom; atom[s] is the atom of shell s. Plain loops over all
+// quartets: small systems only.
+void orc_exchange_grad(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,
+                       const double* exps, const double* coefs, const int32_t* ao_off, const int32_t* atom,
+                       int32_t n_shells, int32_t nao, const double* D, int32_t n_atoms, double* grad, int nthreads) {
+  // augmented basis: original shells, then s+ (l+1, 2 z c), then s- (l-1, c; only for l >= 1)
+  const int32_t n = n_shells;
+  std::vector<int32_t> L(3 * n), NP(3 * n), PO(3 * n);
+  std::vector<double> CEN(9 * n), EX, CO;
+  for (int32_t s = 0; s < n; ++s)
+    for (int v = 0; v < 3; ++v) {
+      const int32_t t = v * n + s;
+      L[t] = v == 0 ? l[s] : (v == 1 ? l[s] + 1 : std::max(l[s] - 1, 0));
+      NP[t] = nprim[s];
+      PO[t] = (int32_t)EX.size();
+      for (int k = 0; k < 3; ++k) CEN[3 * t + k] = center[3 * s + k];
+      for (int p = 0; p < nprim[s]; ++p) {
+        const double z = exps[prim_off[s] + p], c = coefs[prim_off[s] + p];
+        EX.push_back(z);
+        CO.push_back(v == 1 ? 2.0 * z * c : c);
+      }
+    }
+  Basis bs{L.data(), NP.data(), PO.data(), CEN.data(), EX.data(), CO.data()};
+  for (int64_t i = 0; i < (int64_t)n_atoms * 3; ++i) grad[i] = 0.0;
+  const int nt = nthreads_or_default(nthreads);
+  std::vector<std::vector<double>> G(nt, std::vector<double>((size_t)n_atoms * 3, 0.0));
+  const int64_t nq = (int64_t)n * n * n * n;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (int64_t qi = 0; qi < nq; ++qi) {
+#ifdef _OPENMP
+    std::vector<double>& g = G[omp_get_thread_num()];
+#else
+    std::vector<double>& g = G[0];
+#endif
+    const int32_t sh[4] = {(int32_t)(qi / ((int64_t)n * n * n)), (int32_t)((qi / ((int64_t)n * n)) % n),
+                           (int32_t)((qi / n) % n), (int32_t)(qi % n)};
+    const int nc[4] = {ncart(l[sh[0]]), ncart(l[sh[1]]), ncart(l[sh[2]]), ncart(l[sh[3]])};
+    for (int pos = 0; pos < 4; ++pos) {
+      const int lp = l[sh[pos]];
+      const auto cp = cart_list(lp);
+      const auto cplus = cart_list(lp + 1);
+      const auto cminus = cart_list(lp > 0 ? lp - 1 : 0);
+      auto index_of = [](const std::vector<Cart>& cl, int x, int y, int z) {
+        for (size_t i = 0; i < cl.size(); ++i)
+          if (cl[i].x == x && cl[i].y == y && cl[i].z == z) return (int)i;
+        return -1;
+      };
+      int sp[4] = {sh[0], sh[1], sh[2], sh[3]}, sm[4] = {sh[0], sh[1], sh[2], sh[3]};
+      sp[pos] = n + sh[pos];
+      sm[pos] = 2 * n + sh[pos];
+      int ncp[4] = {nc[0], nc[1], nc[2], nc[3]}, ncm[4] = {nc[0], nc[1], nc[2], nc[3]};
+      ncp[pos] = ncart(lp + 1);
+      ncm[pos] = ncart(lp > 0 ? lp - 1 : 0);
+      std::vector<double> vp((size_t)ncp[0] * ncp[1] * ncp[2] * ncp[3]);
+      shellset4<double>(bs, sp[0], sp[1], sp[2], sp[3], vp.data());
+      std::vector<double> vm;
+      if (lp > 0) {
+        vm.resize((size_t)ncm[0] * ncm[1] * ncm[2] * ncm[3]);
+        shellset4<double>(bs, sm[0], sm[1], sm[2], sm[3], vm.data());
+      }
+      double acc[3] = {0.0, 0.0, 0.0};
+      int idx[4];
+      for (idx[0] = 0; idx[0] < nc[0]; ++idx[0])
+        for (idx[1] = 0; idx[1] < nc[1]; ++idx[1])
+          for (idx[2] = 0; idx[2] < nc[2]; ++idx[2])
+            for (idx[3] = 0; idx[3] < nc[3]; ++idx[3]) {
+              const double w = D[(size_t)(ao_off[sh[0]] + idx[0]) * nao + ao_off[sh[2]] + idx[2]] *
+                               D[(size_t)(ao_off[sh[1]] + idx[1]) * nao + ao_off[sh[3]] + idx[3]];
+              const Cart a = cp[idx[pos]];
+              for (int dir = 0; dir < 3; ++dir) {
+                const int dx = dir == 0, dy = dir == 1, dz = dir == 2;
+                int jp[4] = {idx[0], idx[1], idx[2], idx[3]};
+                jp[pos] = index_of(cplus, a.x + dx, a.y + dy, a.z + dz);
+                double val = vp[(((size_t)jp[0] * ncp[1] + jp[1]) * ncp[2] + jp[2]) * ncp[3] + jp[3]];
+                const int am = dir == 0 ? a.x : (dir == 1 ? a.y : a.z);
+                if (am > 0) {
+                  int jm[4] = {idx[0], idx[1], idx[2], idx[3]};
+                  jm[pos] = index_of(cminus, a.x - dx, a.y - dy, a.z - dz);
+                  val -= am * vm[(((size_t)jm[0] * ncm[1] + jm[1]) * ncm[2] + jm[2]) * ncm[3] + jm[3]];
+                }
+                acc[dir] += w * val;
+              }
+            }
+      for (int dir = 0; dir < 3; ++dir) g[(size_t)atom[sh[pos]] * 3 + dir] += acc[dir];
+    }
+  }
+  for (int t = 0; t < nt; ++t)
+    for (int64_t i = 0; i < (int64_t)n_atoms * 3; ++i) grad[i] += G[t][i];
+}
+
 // Rows of K_ik = sum_jl D_jl (ij|kl) for the shells in row_shells only,
 // summed directly over all (j, k, l) shells; other rows are left zero.
 void orc_exchange_rows(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,

@@ -333,3 +333,40 @@ def test_exchange_digestion_matches_einsum():
     Kr = oracle.exchange(b, D, row_shells=[1])
     r0, r1 = ao[1], ao[1] + nc[1]
     np.testing.assert_allclose(Kr[r0:r1], K[r0:r1], rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------------------ exchange gradient
+def test_exchange_gradient_against_finite_differences():
+    """dS/dR of S = sum D_ik D_jl (ij|kl) (all four centres differentiated with
+    d/dA x_A^a e^(-z x_A^2) = 2z x_A^(a+1) e - a x_A^(a-1) e) against central finite
+    differences (h = 1e-4 bohr) of the oracle's own S; and sum over atoms = 0."""
+    b = inputs.small_molecule(seed=41, n_atoms=3, shells=(0, 1, 2), K=2)
+    D = inputs.density(b.nao, 8, occ_fraction=0.4)
+    g = oracle.exchange_grad(b, D)
+    np.testing.assert_allclose(g.sum(axis=0), 0.0, atol=1e-12 * np.max(np.abs(g)))
+    h = 1e-4
+    for A, x in [(0, 0), (1, 2), (2, 1)]:
+        def S(delta):
+            bb = inputs.small_molecule(seed=41, n_atoms=3, shells=(0, 1, 2), K=2)
+            bb.center = bb.center.copy()
+            bb.center[bb.atom == A, x] += delta
+            return oracle.exchange_energy(bb, D)
+        fd = (S(h) - S(-h)) / (2 * h)
+        assert abs(g[A, x] - fd) <= 1e-7 * max(1.0, abs(fd)), (A, x, g[A, x], fd)
+
+
+def test_exchange_gradient_high_l_invariance():
+    """f shells (derivatives reach l = 4) on two atoms: translational invariance and FD."""
+    b = inputs.small_molecule(seed=42, n_atoms=2, shells=(1, 3), K=1)
+    D = inputs.density(b.nao, 9, occ_fraction=0.4)
+    g = oracle.exchange_grad(b, D)
+    np.testing.assert_allclose(g.sum(axis=0), 0.0, atol=1e-12 * np.max(np.abs(g)))
+    h = 1e-4
+    bb = inputs.small_molecule(seed=42, n_atoms=2, shells=(1, 3), K=1)
+    c0 = bb.center.copy()
+    bb.center = c0.copy(); bb.center[bb.atom == 1, 0] += h
+    sp = oracle.exchange_energy(bb, D)
+    bb.center = c0.copy(); bb.center[bb.atom == 1, 0] -= h
+    sm = oracle.exchange_energy(bb, D)
+    fd = (sp - sm) / (2 * h)
+    assert abs(g[1, 0] - fd) <= 1e-7 * max(1.0, abs(fd))
