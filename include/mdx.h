@@ -187,6 +187,26 @@ mdx_status mdx_schwarz(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pair
 mdx_status mdx_exchange(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
                         double tau, const double* D, double* K, void* stream);
 
+/* Nuclear gradient of the exchange energy E_x = alpha S, S = sum_ijkl D_ik D_jl
+ * (ij|kl), with D held fixed (alpha = -1 for a closed-shell D = C C^T; the
+ * paper lists geometric derivatives as future work, Sec. 7).
+ * Same pairs, Q, tau and screening as mdx_exchange. For every kept unique
+ * quartet the centres of its first three shells are differentiated through
+ * the derivative of a primitive Cartesian Gaussian (Eq. 1),
+ *   d/dA_x x_A^a e^(-zeta x_A^2) = 2 zeta x_A^(a+1) e - a x_A^(a-1) e,
+ * i.e. classes with that shell's l raised (coefficients 2 zeta c) and lowered
+ * by one, evaluated by the same Hermite machinery (Hermite index reaching
+ * L+1) with [tuv] recomputed per launch, never stored, and contracted inside
+ * the kernel with G = D_ik (x) D_jl + D_il (x) D_jk; the fourth centre follows
+ * from translational invariance.
+ * basis->atom is required (atom of each shell, 0 <= atom < n_atoms).
+ * grad: [n_atoms][3] doubles (device), overwritten with dE_x/dR (hartree/bohr
+ * for normalised inputs). energy: one double (device) receiving E_x, or NULL.
+ * Synchronises `stream`; results are complete on return. */
+mdx_status mdx_exchange_grad(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, const double* Q,
+                             int64_t n_pairs, double tau, const double* D, double alpha, int32_t n_atoms,
+                             double* grad, double* energy, void* stream);
+
 /* Number of unique quartets the last mdx_exchange of this context kept after
  * screening (-1 for a NULL context). */
 int64_t mdx_last_quartet_count(const mdx_ctx* ctx);

@@ -586,8 +586,8 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
     // the team size and budget: their plans are expensive to build)
     std::vector<PlanConfig> cands;
     if (r.plan->d.ngroups > 1) {
-      for (int budget : {200 * 1024, 108 * 1024})
-        for (int T : {128, 256, 512}) cands.push_back(PlanConfig{T, budget, 96 * 1024});
+      for (int budget : {200 * 1024, 108 * 1024, 72 * 1024})
+        for (int T : {256, 512, 1024}) cands.push_back(PlanConfig{T, budget, 96 * 1024});
     } else {
       for (int single : {96 * 1024, 40 * 1024})
         for (int T : {0, 1, 4, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, single});
@@ -695,6 +695,125 @@ mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs,
   return check_device_error(c, s);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Shared front end of the exchange build and its gradient: canonical distinct
+// pairs sorted by pair class, density-block maxima, Schwarz x density screening
+// of the unique quartets into (bra class, ket class) buckets on the GPU.
+struct XPrep {
+  HostBasis hb;
+  std::vector<int32_t> ao;
+  int64_t nao = 0, np = 0, nq = 0;
+  struct P4 { int32_t i, j; double q; int li, lj, K; };
+  std::vector<P4> pl;
+  std::vector<std::array<int, 3>> classes;
+  std::vector<unsigned long long> counts;
+  std::vector<int64_t> boff;
+  int2* d_pshell = nullptr;
+  int2* d_quart = nullptr;
+};
+
+mdx_status exchange_screen(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
+                           double tau, const double* D, XPrep& X, cudaStream_t s) {
+  if (!basis || !basis->ao_off) return fail(c, MDX_EINVAL, "basis needs ao_off");
+  mdx_status st = fetch_basis(c, basis, X.hb, s);
+  if (st != MDX_OK) return st;
+  const HostBasis& hb = X.hb;
+  X.ao.resize(hb.n);
+  cudaError_t e = cudaSuccess;
+  if (hb.n) e = cudaMemcpyAsync(X.ao.data(), basis->ao_off, hb.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ao_off download");
+  X.nao = 0;
+  for (int i = 0; i < hb.n; ++i) X.nao = std::max<int64_t>(X.nao, (int64_t)X.ao[i] + ncart(hb.l[i]));
+  if (X.nao > 2000000000 / 2) return fail(c, MDX_EUNSUPPORTED, "too many AOs");
+  X.np = n_pairs;
+  if (n_pairs == 0 || hb.n == 0) return MDX_OK;
+  std::vector<int32_t> hp;
+  if ((st = read_quartets(c, pairs, n_pairs, 2, hp, s)) != MDX_OK) return st;
+  std::vector<double> hq(n_pairs);
+  e = cudaMemcpyAsync(hq.data(), Q, n_pairs * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Q download");
+  X.pl.resize(n_pairs);
+  std::unordered_map<int64_t, int> seen;
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    int32_t i = hp[2 * p], j = hp[2 * p + 1];
+    if (i < 0 || i >= hb.n || j < 0 || j >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
+    if (i < j) std::swap(i, j);
+    if (!seen.emplace((int64_t)i * hb.n + j, 1).second) return fail(c, MDX_EINVAL, "shell pair listed twice");
+    X.pl[p] = XPrep::P4{i, j, hq[p], hb.l[i], hb.l[j], hb.nprim[i] * hb.nprim[j]};
+  }
+  std::stable_sort(X.pl.begin(), X.pl.end(), [](const XPrep::P4& a, const XPrep::P4& b) {
+    if (a.li != b.li) return a.li < b.li;
+    if (a.lj != b.lj) return a.lj < b.lj;
+    return a.K < b.K;
+  });
+  std::vector<int2> pshell(n_pairs);
+  std::vector<int32_t> pclass(n_pairs);
+  std::vector<float> qf(n_pairs);
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    std::array<int, 3> k{X.pl[p].li, X.pl[p].lj, X.pl[p].K};
+    if (X.classes.empty() || X.classes.back() != k) X.classes.push_back(k);
+    pclass[p] = (int32_t)X.classes.size() - 1;
+    pshell[p] = make_int2(X.pl[p].i, X.pl[p].j);
+    qf[p] = (float)X.pl[p].q;
+  }
+  const int nclass = (int)X.classes.size();
+  const int64_t nbucket = (int64_t)nclass * (nclass + 1) / 2;
+  int32_t* d_pclass; float *d_q, *d_dmax; unsigned long long* d_counts; int64_t* d_boff;
+  if ((st = upload(c, "x_pshell", pshell, &X.d_pshell, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_pclass", pclass, &d_pclass, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_q", qf, &d_q, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "x_dmax", (size_t)hb.n * hb.n, &d_dmax, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "x_counts", (size_t)nbucket, &d_counts, s)) != MDX_OK) return st;
+  e = launch_dmax(D, (int32_t)X.nao, basis->ao_off, basis->l, hb.n, d_dmax, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
+  ScreenArgs sa{n_pairs, X.d_pshell, d_pclass, d_q, d_dmax, hb.n, nclass, (float)tau, d_counts, nullptr, nullptr};
+  if (e == cudaSuccess) e = launch_screen(sa, false, s);
+  X.counts.assign(nbucket, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(X.counts.data(), d_counts, nbucket * sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange screening");
+  X.boff.assign(nbucket + 1, 0);
+  for (int64_t b = 0; b < nbucket; ++b) X.boff[b + 1] = X.boff[b] + (int64_t)X.counts[b];
+  X.nq = X.boff[nbucket];
+  c->last_quartets = X.nq;
+  if (X.nq > 0) {
+    if ((st = upload(c, "x_boff", X.boff, &d_boff, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "x_quart", (size_t)X.nq, &X.d_quart, s)) != MDX_OK) return st;
+    e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
+    sa.bucket_off = d_boff;
+    sa.out = X.d_quart;
+    if (e == cudaSuccess) e = launch_screen(sa, true, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "exchange screening");
+  }
+  return MDX_OK;
+}
+
+QuartetLaunch base_launch(mdx_ctx* c, Plan* plan, const int2* qp, int64_t nq, const int64_t* prec, const double* recs,
+                          const double* recs_s) {
+  QuartetLaunch a{};
+  a.plan = plan->d;
+  a.nq = nq;
+  a.qpairs = qp;
+  a.pair_rec = prec;
+  a.recs = recs;
+  a.recs_signed = recs_s;
+  a.boys = c->d_boys;
+  a.hdec = c->d_hdec;
+  a.hdec_off = c->d_hdec_off;
+  a.err = c->d_err;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
 mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
                         double tau, const double* D, double* K, void* stream) {
   if (!c) return MDX_EINVAL;
@@ -703,134 +822,176 @@ mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs
   cudaStream_t s = (cudaStream_t)stream;
   if (n_pairs < 0 || !D || !K || (n_pairs > 0 && (!pairs || !Q)) || !(tau >= 0.0))
     return fail(c, MDX_EINVAL, "invalid arguments");
-  if (!basis || !basis->ao_off) return fail(c, MDX_EINVAL, "basis needs ao_off");
-  HostBasis hb;
-  mdx_status st = fetch_basis(c, basis, hb, s);
+  XPrep X;
+  mdx_status st = exchange_screen(c, basis, pairs, Q, n_pairs, tau, D, X, s);
   if (st != MDX_OK) return st;
-  std::vector<int32_t> ao(hb.n);
-  cudaError_t e = cudaMemcpyAsync(ao.data(), basis->ao_off, hb.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "ao_off download");
-  int64_t nao = 0;
-  for (int i = 0; i < hb.n; ++i) nao = std::max<int64_t>(nao, (int64_t)ao[i] + ncart(hb.l[i]));
-  if (nao > 2000000000 / 2) return fail(c, MDX_EUNSUPPORTED, "too many AOs");
-  e = cudaMemsetAsync(K, 0, (size_t)nao * nao * sizeof(double), s);
+  cudaError_t e = cudaMemsetAsync(K, 0, (size_t)X.nao * X.nao * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "K clear");
-  if (n_pairs == 0 || hb.n == 0) return MDX_OK;
-  std::vector<int32_t> hp;
-  if ((st = read_quartets(c, pairs, n_pairs, 2, hp, s)) != MDX_OK) return st;
-  std::vector<double> hq(n_pairs);
-  e = cudaMemcpyAsync(hq.data(), Q, n_pairs * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "Q download");
-  // canonical, distinct pairs sorted by pair class (li, lj, Ki*Kj)
-  struct P4 { int32_t i, j; double q; int li, lj, K; };
-  std::vector<P4> pl(n_pairs);
-  std::unordered_map<int64_t, int> seen;
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    int32_t i = hp[2 * p], j = hp[2 * p + 1];
-    if (i < 0 || i >= hb.n || j < 0 || j >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
-    if (i < j) std::swap(i, j);
-    if (!seen.emplace((int64_t)i * hb.n + j, 1).second) return fail(c, MDX_EINVAL, "shell pair listed twice");
-    pl[p] = P4{i, j, hq[p], hb.l[i], hb.l[j], hb.nprim[i] * hb.nprim[j]};
-  }
-  std::stable_sort(pl.begin(), pl.end(), [](const P4& a, const P4& b) {
-    if (a.li != b.li) return a.li < b.li;
-    if (a.lj != b.lj) return a.lj < b.lj;
-    return a.K < b.K;
-  });
-  std::vector<int2> pshell(n_pairs);
-  std::vector<int32_t> pclass(n_pairs);
-  std::vector<float> qf(n_pairs);
-  std::vector<std::array<int, 3>> classes;
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    std::array<int, 3> k{pl[p].li, pl[p].lj, pl[p].K};
-    if (classes.empty() || classes.back() != k) classes.push_back(k);
-    pclass[p] = (int32_t)classes.size() - 1;
-    pshell[p] = make_int2(pl[p].i, pl[p].j);
-    qf[p] = (float)pl[p].q;
-  }
-  const int nclass = (int)classes.size();
-  const int64_t nbucket = (int64_t)nclass * (nclass + 1) / 2;
-  // primitive-pair records for every pair
-  std::vector<int64_t> pair_rec(n_pairs);
-  std::vector<PrimPairJob> jobs;
-  int64_t roff = 0;
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    const int rs = rec_size(pl[p].li, pl[p].lj);
-    pair_rec[p] = roff;
-    for (int ia = 0; ia < hb.nprim[pl[p].i]; ++ia)
-      for (int ib = 0; ib < hb.nprim[pl[p].j]; ++ib) {
-        jobs.push_back(PrimPairJob{pl[p].i, pl[p].j, ia, ib, 0, 0, roff});
-        roff += rs;
-      }
-  }
-  PrimPairJob* d_jobs; int64_t* d_prec; double *d_recs, *d_recs_s; int2* d_pshell; int32_t* d_pclass;
-  float *d_q, *d_dmax; unsigned long long* d_counts; int64_t* d_boff; int2* d_quart;
-  if ((st = upload(c, "x_jobs", jobs, &d_jobs, s)) != MDX_OK) return st;
-  if ((st = upload(c, "x_prec", pair_rec, &d_prec, s)) != MDX_OK) return st;
-  if ((st = ensure(c, "x_recs", (size_t)roff, &d_recs, s)) != MDX_OK) return st;
-  if ((st = ensure(c, "x_recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
-  if ((st = upload(c, "x_pshell", pshell, &d_pshell, s)) != MDX_OK) return st;
-  if ((st = upload(c, "x_pclass", pclass, &d_pclass, s)) != MDX_OK) return st;
-  if ((st = upload(c, "x_q", qf, &d_q, s)) != MDX_OK) return st;
-  if ((st = ensure(c, "x_dmax", (size_t)hb.n * hb.n, &d_dmax, s)) != MDX_OK) return st;
-  if ((st = ensure(c, "x_counts", (size_t)nbucket, &d_counts, s)) != MDX_OK) return st;
-  e = launch_pair_records(to_dev(basis), to_dev(basis), d_jobs, (int64_t)jobs.size(), d_recs, d_recs_s, c->d_err, s);
-  if (e == cudaSuccess) e = launch_dmax(D, (int32_t)nao, basis->ao_off, basis->l, hb.n, d_dmax, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
-  ScreenArgs sa{n_pairs, d_pshell, d_pclass, d_q, d_dmax, hb.n, nclass, (float)tau, d_counts, nullptr, nullptr};
-  if (e == cudaSuccess) e = launch_screen(sa, false, s);
-  std::vector<unsigned long long> counts(nbucket);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(counts.data(), d_counts, nbucket * sizeof(unsigned long long),
-                                            cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "exchange screening");
-  std::vector<int64_t> boff(nbucket + 1, 0);
-  for (int64_t b = 0; b < nbucket; ++b) boff[b + 1] = boff[b] + (int64_t)counts[b];
-  const int64_t nq = boff[nbucket];
-  c->last_quartets = nq;
-  if (nq > 0) {
-    if ((st = upload(c, "x_boff", boff, &d_boff, s)) != MDX_OK) return st;
-    if ((st = ensure(c, "x_quart", (size_t)nq, &d_quart, s)) != MDX_OK) return st;
-    e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
-    sa.bucket_off = d_boff;
-    sa.out = d_quart;
-    if (e == cudaSuccess) e = launch_screen(sa, true, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "exchange screening");
+  if (X.nq > 0) {
+    const HostBasis& hb = X.hb;
+    std::vector<int64_t> pair_rec(X.np);
+    std::vector<PrimPairJob> jobs;
+    int64_t roff = 0;
+    for (int64_t p = 0; p < X.np; ++p) {
+      pair_rec[p] = roff;
+      for (int ia = 0; ia < hb.nprim[X.pl[p].i]; ++ia)
+        for (int ib = 0; ib < hb.nprim[X.pl[p].j]; ++ib) {
+          jobs.push_back(PrimPairJob{X.pl[p].i, X.pl[p].j, ia, ib, 0, 0, roff});
+          roff += rec_size(X.pl[p].li, X.pl[p].lj);
+        }
+    }
+    PrimPairJob* d_jobs; int64_t* d_prec; double *d_recs, *d_recs_s;
+    if ((st = upload(c, "x_jobs", jobs, &d_jobs, s)) != MDX_OK) return st;
+    if ((st = upload(c, "x_prec", pair_rec, &d_prec, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "x_recs", (size_t)roff, &d_recs, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "x_recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
+    e = launch_pair_records(to_dev(basis), to_dev(basis), d_jobs, (int64_t)jobs.size(), d_recs, d_recs_s, c->d_err, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+    const int nclass = (int)X.classes.size();
     for (int cp = 0; cp < nclass; ++cp)
       for (int cq = 0; cq <= cp; ++cq) {
         const int64_t b = (int64_t)cp * (cp + 1) / 2 + cq;
-        if (counts[b] == 0) continue;
-        const ClassKey key{classes[cp][0], classes[cp][1], classes[cq][0], classes[cq][1], classes[cp][2],
-                           classes[cq][2], 0};
+        if (X.counts[b] == 0) continue;
+        const ClassKey key{X.classes[cp][0], X.classes[cp][1], X.classes[cq][0], X.classes[cq][1],
+                           X.classes[cp][2], X.classes[cq][2], 0};
         Plan* plan;
         if ((st = get_plan(c, key, &plan, s)) != MDX_OK) return st;
-        QuartetLaunch a{};
-        a.plan = plan->d;
-        a.nq = (int64_t)counts[b];
-        a.qpairs = d_quart + boff[b];
-        a.qout = nullptr;
-        a.pair_rec = d_prec;
-        a.recs = d_recs;
-        a.recs_signed = d_recs_s;
-        a.boys = c->d_boys;
-        a.hdec = c->d_hdec;
-        a.hdec_off = c->d_hdec_off;
-        a.out = nullptr;
-        a.err = c->d_err;
+        QuartetLaunch a = base_launch(c, plan, X.d_quart + X.boff[b], (int64_t)X.counts[b], d_prec, d_recs, d_recs_s);
         a.D = D;
         a.K = K;
-        a.nao = (int32_t)nao;
+        a.nao = (int32_t)X.nao;
         a.ao_off = basis->ao_off;
-        a.pair_shells = d_pshell;
+        a.pair_shells = X.d_pshell;
         e = launch_quartets(a, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "exchange quartet launch");
       }
   }
-  e = launch_symmetrize(K, (int32_t)nao, s);
+  e = launch_symmetrize(K, (int32_t)X.nao, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "exchange");
+  return check_device_error(c, s);
+}
+
+mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q,
+                             int64_t n_pairs, double tau, const double* D, double alpha, int32_t n_atoms,
+                             double* grad, double* energy, void* stream) {
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_pairs < 0 || !D || !grad || n_atoms < 1 || (n_pairs > 0 && (!pairs || !Q)) || !(tau >= 0.0))
+    return fail(c, MDX_EINVAL, "invalid arguments");
+  if (!basis || !basis->atom) return fail(c, MDX_EINVAL, "basis needs atom");
+  XPrep X;
+  mdx_status st = exchange_screen(c, basis, pairs, Q, n_pairs, tau, D, X, s);
+  if (st != MDX_OK) return st;
+  const HostBasis& hb = X.hb;
+  const int32_t n = hb.n;
+  cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)n_atoms * 3 * sizeof(double), s);
+  if (e == cudaSuccess && energy) e = cudaMemsetAsync(energy, 0, sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient clear");
+  std::vector<int32_t> atom(n);
+  if (n) e = cudaMemcpyAsync(atom.data(), basis->atom, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "atom download");
+  for (int i = 0; i < n; ++i)
+    if (atom[i] < 0 || atom[i] >= n_atoms) return fail(c, MDX_EINVAL, "atom index out of range");
+  if (X.nq == 0) return MDX_OK;
+  // extended basis: shell s, s+ = n+s (l+1, coefficients 2 zeta c), s- = 2n+s (l-1, coefficients c):
+  // d/dA_x of a primitive x_A^a e^(-zeta x_A^2) is 2 zeta x_A^(a+1) e - a x_A^(a-1) e
+  const int32_t npr = basis->n_prims;
+  std::vector<int32_t> po(n);
+  std::vector<double> cen(3 * (size_t)n), ex(npr), co(npr);
+  if (n) e = cudaMemcpyAsync(po.data(), basis->prim_off, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(cen.data(), basis->center, cen.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && npr) e = cudaMemcpyAsync(ex.data(), basis->exps, npr * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && npr) e = cudaMemcpyAsync(co.data(), basis->coefs, npr * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "basis download");
+  std::vector<int32_t> L3(3 * (size_t)n), K3(3 * (size_t)n), PO3(3 * (size_t)n);
+  std::vector<double> C3(9 * (size_t)n), E3, W3;
+  for (int v = 0; v < 3; ++v)
+    for (int32_t sh = 0; sh < n; ++sh) {
+      const size_t t = (size_t)v * n + sh;
+      L3[t] = v == 0 ? hb.l[sh] : (v == 1 ? hb.l[sh] + 1 : std::max(hb.l[sh] - 1, 0));
+      K3[t] = hb.nprim[sh];
+      PO3[t] = (int32_t)E3.size();
+      for (int k = 0; k < 3; ++k) C3[3 * t + k] = cen[3 * (size_t)sh + k];
+      for (int q = 0; q < hb.nprim[sh]; ++q) {
+        const int32_t g = po[sh] + q;
+        if (g < 0 || g >= npr) return fail(c, MDX_EINVAL, "primitive index out of range");
+        E3.push_back(ex[g]);
+        W3.push_back(v == 1 ? 2.0 * ex[g] * co[g] : co[g]);
+      }
+    }
+  int32_t *dL3, *dK3, *dPO3, *datom; double *dC3, *dE3, *dW3;
+  if ((st = upload(c, "g_l", L3, &dL3, s)) != MDX_OK) return st;
+  if ((st = upload(c, "g_k", K3, &dK3, s)) != MDX_OK) return st;
+  if ((st = upload(c, "g_po", PO3, &dPO3, s)) != MDX_OK) return st;
+  if ((st = upload(c, "g_c", C3, &dC3, s)) != MDX_OK) return st;
+  if ((st = upload(c, "g_e", E3, &dE3, s)) != MDX_OK) return st;
+  if ((st = upload(c, "g_w", W3, &dW3, s)) != MDX_OK) return st;
+  if ((st = upload(c, "g_atom", atom, &datom, s)) != MDX_OK) return st;
+  const BasisDev b3{dL3, dK3, dPO3, dC3, dE3, dW3};
+  // five record variants per pair: (i,j), (i+,j), (i-,j), (i,j+), (i,j-)
+  std::vector<int64_t> prec(5 * X.np);
+  std::vector<PrimPairJob> jobs;
+  int64_t roff = 0;
+  for (int v = 0; v < 5; ++v)
+    for (int64_t p = 0; p < X.np; ++p) {
+      int32_t i = X.pl[p].i, j = X.pl[p].j;
+      if (v == 1) i += n; else if (v == 2) i += 2 * n; else if (v == 3) j += n; else if (v == 4) j += 2 * n;
+      prec[v * X.np + p] = roff;
+      for (int ia = 0; ia < K3[i]; ++ia)
+        for (int ib = 0; ib < K3[j]; ++ib) {
+          jobs.push_back(PrimPairJob{i, j, ia, ib, 0, 0, roff});
+          roff += rec_size(L3[i], L3[j]);
+        }
+    }
+  PrimPairJob* d_jobs; int64_t* d_prec; double *d_recs, *d_recs_s;
+  if ((st = upload(c, "g_jobs", jobs, &d_jobs, s)) != MDX_OK) return st;
+  if ((st = upload(c, "g_prec", prec, &d_prec, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "g_recs", (size_t)roff, &d_recs, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "g_recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
+  e = launch_pair_records(b3, b3, d_jobs, (int64_t)jobs.size(), d_recs, d_recs_s, c->d_err, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+  // per bucket: centre A (+/-), B (+/-), C (+/-) and, if asked, the energy
+  struct Var { int bra, ket, pos, sign; };
+  const Var vars[7] = {{1, 0, 0, 1}, {2, 0, 0, -1}, {3, 0, 1, 1}, {4, 0, 1, -1}, {0, 1, 2, 1}, {0, 2, 2, -1}, {0, 0, -1, 0}};
+  const int nclass = (int)X.classes.size();
+  for (int cp = 0; cp < nclass; ++cp)
+    for (int cq = 0; cq <= cp; ++cq) {
+      const int64_t b = (int64_t)cp * (cp + 1) / 2 + cq;
+      if (X.counts[b] == 0) continue;
+      const int l0[4] = {X.classes[cp][0], X.classes[cp][1], X.classes[cq][0], X.classes[cq][1]};
+      for (const Var& v : vars) {
+        if (v.pos < 0 && !energy) continue;
+        if (v.sign < 0 && l0[v.pos] == 0) continue;   // no l-1 term for s shells
+        int ls[4] = {l0[0], l0[1], l0[2], l0[3]};
+        if (v.pos >= 0) ls[v.pos] += v.sign;
+        const ClassKey key{ls[0], ls[1], ls[2], ls[3], X.classes[cp][2], X.classes[cq][2], 0};
+        Plan* plan;
+        if ((st = get_plan(c, key, &plan, s)) != MDX_OK) return st;
+        QuartetLaunch a = base_launch(c, plan, X.d_quart + X.boff[b], (int64_t)X.counts[b], d_prec, d_recs, d_recs_s);
+        a.bra_var_off = (int64_t)v.bra * X.np;
+        a.ket_var_off = (int64_t)v.ket * X.np;
+        a.D = D;
+        a.nao = (int32_t)X.nao;
+        a.ao_off = basis->ao_off;
+        a.pair_shells = X.d_pshell;
+        a.grad = grad;
+        a.energy = energy;
+        a.atom = datom;
+        a.alpha = alpha;
+        a.gpos = v.pos;
+        a.gsign = v.sign;
+        for (int k = 0; k < 4; ++k) a.lorig[k] = l0[k];
+        e = launch_quartets(a, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "gradient quartet launch");
+      }
+    }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange gradient");
   return check_device_error(c, s);
 }
 

@@ -27,6 +27,8 @@ namespace mdx {
 __constant__ double c_dint[64];
 // sqrt(pi)/2 * (2m-1)!! / 2^m: F_m(T) = c_gh[m] T^(-m-1/2) for large T
 __constant__ double c_gh[kBoysRow];
+// Cartesian components of shells l <= 7 in library order, packed x | y << 8 | z << 16
+__constant__ uint32_t c_cart[8][36];
 
 cudaError_t kernel_attributes_init();
 
@@ -338,8 +340,92 @@ __device__ void digest_group(const QuartetLaunch& a, const double* ws, const Gro
   }
 }
 
+__device__ __forceinline__ double dens_G(const double* __restrict__ D, int64_t nao, int64_t ri, int64_t rj,
+                                         int64_t ck, int64_t cl) {
+  // G = D_ik D_jl + D_il D_jk for AO rows ri (of i), rj (of j) and columns ck (of k), cl (of l)
+  return __ldg(D + ri * nao + ck) * __ldg(D + rj * nao + cl) + __ldg(D + ri * nao + cl) * __ldg(D + rj * nao + ck);
+}
+
+// Exchange-energy gradient of one column group. S = sum_ijkl D_ik D_jl (ij|kl)
+// restricted to the unique quartet is 4 w sum_abcd G_abcd (ab|cd) with
+// G = D_ik (x) D_jl + D_il (x) D_jk; its derivative with respect to the centre
+// of the shell at position gpos uses
+//   d/dA_x phi_a = 2 zeta phi_{a+1_x} - a_x phi_{a-1_x},
+// i.e. this launch's shifted class: every element of the l+1 shellset feeds
+// each direction x whose component is >= 1 (weight +1), every element of the
+// l-1 shellset each direction (weight -(a_x + 1)). The fourth centre follows
+// from translational invariance: what centre gpos gains, the atom of shell l
+// loses. gpos = -1 accumulates the energy alpha S instead.
 template <bool CTA>
-__global__ void __launch_bounds__(CTA ? 512 : 128) k_quartets(const QuartetLaunch a) {
+__device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group& grp, int2 qp, int tl, int T,
+                           bool active, unsigned mask) {
+  const PlanDev& P = a.plan;
+  const int2 bp = a.pair_shells[qp.x], kp = a.pair_shells[qp.y];
+  const int si = bp.x, sj = bp.y, sk = kp.x, sl = kp.y;
+  const double w = (si == sj ? 0.5 : 1.0) * (sk == sl ? 0.5 : 1.0) * (qp.x == qp.y ? 0.5 : 1.0);
+  const int nb_s = d_ncart(P.lb), nd_s = d_ncart(P.ld);
+  const int64_t nao = a.nao;
+  const int64_t ai = a.ao_off[si], aj = a.ao_off[sj], ak = a.ao_off[sk], al = a.ao_off[sl];
+  const int ncols = grp.ncols;
+  const uint16_t* cm = P.colmap + grp.col_off;
+  const double* OUT = ws + P.o_OUT;
+  const int pos = a.gpos, sg = a.gsign;
+  const int lsh = pos == 0 ? P.la : (pos == 1 ? P.lb : P.lc);
+  const int lorg = pos >= 0 ? a.lorig[pos] : 0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  const int tot = P.Nb * ncols;
+  for (int e = tl; e < tot; e += T) {
+    const int ab = e / ncols, col = e - ab * ncols;
+    const double v = OUT[e];
+    const int cd = cm[col];
+    const int ia = ab / nb_s, ib = ab - ia * nb_s, ic = cd / nd_s, id = cd - ic * nd_s;
+    if (pos < 0) {
+      s0 = fma(v, dens_G(a.D, nao, ai + ia, aj + ib, ak + ic, al + id), s0);
+      continue;
+    }
+    const int sidx = pos == 0 ? ia : (pos == 1 ? ib : ic);
+    const uint32_t xyz = c_cart[lsh][sidx];
+    const int cmp[3] = {(int)(xyz & 0xff), (int)((xyz >> 8) & 0xff), (int)((xyz >> 16) & 0xff)};
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+      int o[3] = {cmp[0], cmp[1], cmp[2]};
+      double wt;
+      if (sg > 0) {
+        if (o[dir] == 0) continue;
+        o[dir] -= 1;
+        wt = 1.0;
+      } else {
+        o[dir] += 1;
+        wt = -(double)o[dir];
+      }
+      const int oidx = d_tri(lorg - o[0]) + o[2];
+      const int ja = pos == 0 ? oidx : ia, jb = pos == 1 ? oidx : ib, jc = pos == 2 ? oidx : ic;
+      const double t = wt * v * dens_G(a.D, nao, ai + ja, aj + jb, ak + jc, al + id);
+      if (dir == 0) s0 += t; else if (dir == 1) s1 += t; else s2 += t;
+    }
+  }
+  // reduce over the lanes of the team (whole warps for CTA teams, aligned lane groups otherwise)
+  const int width = CTA ? 32 : T;
+  for (int off = width / 2; off > 0; off >>= 1) {
+    s0 += __shfl_xor_sync(mask, s0, off);
+    s1 += __shfl_xor_sync(mask, s1, off);
+    s2 += __shfl_xor_sync(mask, s2, off);
+  }
+  if (!active || (threadIdx.x & (width - 1)) != 0) return;
+  const double f = a.alpha * 4.0 * w;
+  if (pos < 0) {
+    atomicAdd(a.energy, f * s0);
+    return;
+  }
+  const int sh = pos == 0 ? si : (pos == 1 ? sj : sk);
+  double* gA = a.grad + 3 * (int64_t)a.atom[sh];
+  double* gD = a.grad + 3 * (int64_t)a.atom[sl];
+  atomicAdd(gA + 0, f * s0); atomicAdd(gA + 1, f * s1); atomicAdd(gA + 2, f * s2);
+  atomicAdd(gD + 0, -f * s0); atomicAdd(gD + 1, -f * s1); atomicAdd(gD + 2, -f * s2);
+}
+
+template <bool CTA>
+__global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaunch a) {
   extern __shared__ __align__(16) double smem[];
   const PlanDev& P = a.plan;
   const int T = P.T;
@@ -357,8 +443,8 @@ __global__ void __launch_bounds__(CTA ? 512 : 128) k_quartets(const QuartetLaunc
   const bool active = q < a.nq;
   if (!active) q = a.nq - 1;   // idle teams shadow the last quartet and store nothing
   const int2 qp = a.qpairs[q];
-  const int64_t bra0 = a.pair_rec[qp.x];
-  const int64_t ket0 = a.pair_rec[qp.y];
+  const int64_t bra0 = a.pair_rec[qp.x + a.bra_var_off];
+  const int64_t ket0 = a.pair_rec[qp.y + a.ket_var_off];
   const int Kb = P.Kb, Kk = P.Kk;
   if (P.cache_R) {
     load_record(ws + P.o_recb, a.recs + bra0, P.recb, tl, T);
@@ -453,7 +539,9 @@ __global__ void __launch_bounds__(CTA ? 512 : 128) k_quartets(const QuartetLaunc
       }
       team_sync<CTA>(mask);
     }
-    if (a.D) {
+    if (a.grad) {
+      grad_group<CTA>(a, ws, grp, qp, tl, T, active, mask);
+    } else if (a.D) {
       // exchange digestion of this group's columns (Sec. 6: K_bc = sum_ad [ab|cd] D_ad),
       // unique quartet (ij|kl) with i>=j, k>=l, ij>=kl and weight w; the host adds K^T at the end
       if (active) digest_group(a, ws, grp, qp, tl, T);
@@ -583,6 +671,14 @@ cudaError_t kernel_attributes_init() {
     v *= (2.0 * m + 1.0) * 0.5;
   }
   e = cudaMemcpyToSymbol(c_gh, gh, sizeof(gh));
+  if (e != cudaSuccess) return e;
+  uint32_t cart[8][36] = {};
+  for (int l = 0; l < 8; ++l) {
+    int i = 0;
+    for (int ax = l; ax >= 0; --ax)
+      for (int ay = l - ax; ay >= 0; --ay) cart[l][i++] = (uint32_t)ax | ((uint32_t)ay << 8) | ((uint32_t)(l - ax - ay) << 16);
+  }
+  e = cudaMemcpyToSymbol(c_cart, cart, sizeof(cart));
   if (e != cudaSuccess) return e;
   const int maxshm = 227 * 1024;
   e = cudaFuncSetAttribute(k_quartets<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);

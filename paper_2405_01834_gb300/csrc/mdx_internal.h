@@ -125,7 +125,7 @@ struct Plan {
 
 // Tunable shape of a plan (0 = the planner's default).
 struct PlanConfig {
-  int T = 0;                 // threads per team (1..512, a power of two)
+  int T = 0;                 // threads per team (1..1024, a power of two)
   int budget = 200 * 1024;   // shared-memory bytes per team
   int single_max = 96 * 1024;  // largest workspace for which all ket columns form one group
   bool operator==(const PlanConfig& o) const { return T == o.T && budget == o.budget && single_max == o.single_max; }

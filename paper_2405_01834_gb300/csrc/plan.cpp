@@ -398,7 +398,7 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   const int bytes = P.team_doubles * 8;
   const int tps = std::max(1, (220 * 1024) / bytes);   // teams that fit one SM's shared memory
   if (cfg.T > 0) {
-    if (cfg.T > 512 || (cfg.T & (cfg.T - 1))) { err = "team size must be a power of two <= 512"; return false; }
+    if (cfg.T > 1024 || (cfg.T & (cfg.T - 1))) { err = "team size must be a power of two <= 1024"; return false; }
     P.T = cfg.T;
   } else if (P.ngroups > 1) {
     P.T = 512;

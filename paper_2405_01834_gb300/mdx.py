@@ -104,6 +104,9 @@ def load(build_if_missing: bool = True):
     lib.mdx_batch_destroy.restype = None
     lib.mdx_exchange.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, P, P]
     lib.mdx_exchange.restype = I32
+    lib.mdx_exchange_grad.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, ctypes.c_double,
+                                      ctypes.c_int32, P, P, P]
+    lib.mdx_exchange_grad.restype = I32
     lib.mdx_last_quartet_count.argtypes = [P]
     lib.mdx_last_quartet_count.restype = I64
     lib.mdx_eri4_noalloc.argtypes = [ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
@@ -220,6 +223,22 @@ class Engine:
         self._check(st, "mdx_exchange")
         return K
 
+    def exchange_grad(self, basis: DeviceBasis, pairs, Q, D: torch.Tensor, tau: float = 0.0, alpha: float = -1.0,
+                      n_atoms: int = None, with_energy: bool = True):
+        """(dE_x/dR [n_atoms, 3], E_x) for E_x = alpha sum_ijkl D_ik D_jl (ij|kl), D fixed."""
+        p = torch.as_tensor(pairs, dtype=torch.int32, device="cuda").contiguous()
+        q = torch.as_tensor(Q, dtype=torch.float64, device="cuda").contiguous()
+        D = D.to(device="cuda", dtype=torch.float64).contiguous()
+        if n_atoms is None:
+            n_atoms = int(basis.host.atom.max()) + 1
+        g = torch.empty((n_atoms, 3), dtype=torch.float64, device="cuda")
+        e = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = self.lib.mdx_exchange_grad(self.ctx, ctypes.byref(basis.desc), p.data_ptr(), q.data_ptr(), p.shape[0],
+                                        float(tau), D.data_ptr(), float(alpha), int(n_atoms), g.data_ptr(),
+                                        e.data_ptr() if with_energy else None, _stream())
+        self._check(st, "mdx_exchange_grad")
+        return g, (e[0] if with_energy else None)
+
     def last_quartet_count(self) -> int:
         return int(self.lib.mdx_last_quartet_count(self.ctx))
 
@@ -287,3 +306,53 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def basis_with_centers(basis: DeviceBasis, coords: torch.Tensor) -> DeviceBasis:
+    """A copy of `basis` whose shell centres are coords[atom of shell] (coords: [n_atoms, 3], device)."""
+    nb = DeviceBasis.__new__(DeviceBasis)
+    nb.__dict__.update(basis.__dict__)
+    nb.center = coords.detach().to(dtype=torch.float64)[basis.atom.long()].contiguous()
+    nb.desc = _Basis(basis.desc.n_shells, basis.desc.n_prims, basis.l.data_ptr(), basis.nprim.data_ptr(),
+                     basis.prim_off.data_ptr(), basis.ao_off.data_ptr(), basis.atom.data_ptr(), nb.center.data_ptr(),
+                     basis.exps.data_ptr(), basis.coefs.data_ptr())
+    return nb
+
+
+class ExchangeEnergy(torch.autograd.Function):
+    """E_x = alpha sum_ijkl D_ik D_jl (ij|kl) as a differentiable function of the
+    atom coordinates and of D. Forward: mdx_exchange (E_x = alpha sum D o K).
+    Backward: mdx_exchange_grad for the coordinates (derivative integrals
+    contracted with D (x) D inside the kernel) and 2 alpha K for D (symmetric D)."""
+
+    @staticmethod
+    def forward(ctx, coords, D, eng, basis, pairs, tau, alpha):
+        db = basis_with_centers(basis, coords)
+        Q = eng.schwarz(db, pairs)
+        Dd = D.detach().to(device="cuda", dtype=torch.float64).contiguous()
+        K = eng.exchange(db, pairs, Q, Dd, tau)
+        ctx.eng, ctx.db, ctx.pairs, ctx.tau, ctx.alpha = eng, db, pairs, tau, alpha
+        ctx.n_atoms = coords.shape[0]
+        ctx.save_for_backward(Dd, K, Q)
+        return alpha * torch.sum(Dd * K)
+
+    @staticmethod
+    def backward(ctx, gE):
+        Dd, K, Q = ctx.saved_tensors
+        gcoords = gD = None
+        if ctx.needs_input_grad[0]:
+            g, _ = ctx.eng.exchange_grad(ctx.db, ctx.pairs, Q, Dd, tau=ctx.tau, alpha=ctx.alpha, n_atoms=ctx.n_atoms,
+                                         with_energy=False)
+            gcoords = gE * g
+        if ctx.needs_input_grad[1]:
+            gD = gE * 2.0 * ctx.alpha * K
+        return gcoords, gD, None, None, None, None, None
+
+
+def exchange_energy(eng: Engine, basis: DeviceBasis, coords: torch.Tensor, D: torch.Tensor, pairs=None,
+                    tau: float = 0.0, alpha: float = -1.0) -> torch.Tensor:
+    """Differentiable exchange energy (see ExchangeEnergy); pairs default to all shell pairs."""
+    if pairs is None:
+        n = basis.desc.n_shells
+        pairs = torch.tensor([(i, j) for i in range(n) for j in range(i + 1)], dtype=torch.int32, device="cuda")
+    return ExchangeEnergy.apply(coords, D, eng, basis, pairs, tau, alpha)
