@@ -36,6 +36,10 @@ UNIT = "GFLOP/s"
 # probe: 1203 GFLOP/s at ~1.98 GHz), 152 SMs, 2070 MHz maximum SM clock.
 FP64_FLOP_PER_CLK_SM = 4.0
 CHUNK_BYTES = 2 << 30
+# DRAM bytes (read + write) per [ii|ii] quartet of the k_quartets launch, from the ncu capture summarised
+# in profiles/k_quartets_ii_16x16.md (256 quartets: 2.743 GB read + 3.876 GB written); scaled by the
+# quartets of a launch when the dominant class is [ii|ii]
+NCU_DRAM_BYTES_PER_II_QUARTET = (2.742647e9 + 3.875670e9) / 256
 
 
 def parse():
@@ -320,7 +324,9 @@ def main():
     per_launch_exec = sum(2.0 * bt.exec_fma for bt in batches) / len(batches)
     roofline = {"bound": "alu", "kernel": "k_quartets %s" % CLASS_NAMES[l], "achieved": round(achieved, 4),
                 "peak": round(peak_gflops * 1e-3, 4), "unit": "TFLOP/s", "frac": round(achieved / (peak_gflops * 1e-3), 4),
-                "traffic": None, "model_flops_per_launch": per_launch_flops,
+                "traffic": (round(NCU_DRAM_BYTES_PER_II_QUARTET * len(q) / len(batches)) if l == 6 else None),
+                "traffic_unit": "bytes per launch (ncu capture of 256 quartets, scaled)",
+                "model_flops_per_launch": per_launch_flops,
                 "executed_tflops": round(per_launch_exec / (avg_launch_ms * 1e-3) * 1e-12, 4),
                 "executed_frac": round(per_launch_exec / (avg_launch_ms * 1e-3) * 1e-12 / (peak_gflops * 1e-3), 4),
                 "peak_basis": "FP64 pipe: 2 DFMA/clk/SM x %d SMs x %.0f MHz (derived; DFMA probe measured 1.203 "

@@ -84,4 +84,5 @@ def test_autograd_function(eng):
     np.testing.assert_allclose(gc.cpu().numpy(), ref_g, rtol=0, atol=1e-11 * np.max(np.abs(ref_g)))
     K = oracle.exchange(b, D.detach().cpu().numpy())
     np.testing.assert_allclose(gD.cpu().numpy(), -2.0 * K, rtol=0, atol=1e-11 * np.max(np.abs(K)))
-    assert abs(float(E) + float(np.sum(D.detach().cpu().numpy() * K))) <= 1e-11 * abs(float(E))
+    E = float(E.detach())
+    assert abs(E + float(np.sum(D.detach().cpu().numpy() * K))) <= 1e-11 * abs(E)
