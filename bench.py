@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the per-class team-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch"],
+                    help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules")
+    ap.add_argument("--n-mol", type=int, default=64)
+    ap.add_argument("--atoms", default="2,5", help="xbatch: atoms per molecule, uniform in [lo,hi]")
+    ap.add_argument("--tau", type=float, default=1e-11)
     return ap.parse_args()
 
 
@@ -199,10 +204,83 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
+def xbatch_main(args):
+    """Exchange builds of n_mol uneven molecules (heavy 5s4p3d2f1g / light 4s3p2d1f shells, K = 6 s shells,
+    D = C C^T): per-molecule mdx_exchange calls vs one launch per class vs one persistent launch vs the
+    persistent launch replayed from a CUDA graph."""
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    lo, hi = (int(x) for x in args.atoms.split(","))
+    rng = np.random.Generator(np.random.PCG64(1004))
+    sizes = rng.integers(lo, hi + 1, args.n_mol)
+    mols = [inputs.molecule(1004 * 1000 + i, int(n)) for i, n in enumerate(sizes)]
+    bases = [mdx.DeviceBasis(b) for b in mols]
+    Ds = [torch.from_numpy(inputs.density(b.nao, 7 + i)) for i, b in enumerate(mols)]
+    pairs = [torch.tensor([(i, j) for i in range(b.n_shells) for j in range(i + 1)], dtype=torch.int32,
+                          device="cuda") for b in mols]
+    res = {}
+    # (a) one mdx_exchange call per molecule (Schwarz factors computed once, outside the timing)
+    Qs = [eng.schwarz(db, p) for db, p in zip(bases, pairs)]
+    Dd = [D.cuda() for D in Ds]
+    for _ in range(max(1, args.warmup)):
+        for db, p, Q, D in zip(bases, pairs, Qs, Dd):
+            eng.exchange(db, p, Q, D, args.tau)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for db, p, Q, D in zip(bases, pairs, Qs, Dd):
+            eng.exchange(db, p, Q, D, args.tau)
+    torch.cuda.synchronize()
+    res["per_molecule_calls_ms"] = round(1e3 * (time.perf_counter() - t0) / args.steps, 3)
+    xb = eng.xbatch(bases, Ds, tau=args.tau)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    res["per_class_launches_ms"] = round(timed(lambda: xb.run(persistent=False)), 3)
+    res["persistent_ms"] = round(timed(lambda: xb.run(persistent=True)), 3)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            xb.run(persistent=True)
+    torch.cuda.synchronize()
+    res["persistent_graph_ms"] = round(timed(g.replay), 3)
+    eng.sync()
+    best = min(res["per_class_launches_ms"], res["persistent_ms"], res["persistent_graph_ms"])
+    line = {"metric": "batched exchange build: model FP64 GFLOP/s and shell quartets/s", "unit": UNIT,
+            "value": round(xb.model_flops / (best * 1e-3) * 1e-9, 3), "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "exchange K_m of %d molecules of %d-%d atoms (heavy 5s4p3d2f1g / light 4s3p2d1f, "
+                                   "K = 6 s shells), tau = %g" % (args.n_mol, lo, hi, args.tau),
+                       "n_ao_total": int(sum(b.nao for b in mols))},
+            "quartets": xb.n_quartets, "model_flops": xb.model_flops, "work_items": xb.n_items,
+            "class_launches": xb.n_class_launches, "modes_ms": res,
+            "quartets_per_s": {k.replace("_ms", ""): round(xb.n_quartets / (v * 1e-3), 1) for k, v in res.items()}}
+    print(json.dumps(line), flush=True)
+    xb.close()
+    eng.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.workload == "xbatch":
+        return xbatch_main(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

@@ -207,6 +207,38 @@ mdx_status mdx_exchange_grad(mdx_ctx* ctx, const mdx_basis* basis, const int32_t
                              int64_t n_pairs, double tau, const double* D, double alpha, int32_t n_atoms,
                              double* grad, double* energy, void* stream);
 
+/* ---- batched exchange of many molecules ---------------------------------
+ * Exchange matrices K_m = sum_jl D_m,jl (ij|kl) of n_mol independent molecules
+ * (uneven sizes, mixed classes and contraction degrees) prepared once and run
+ * as either one launch per integral class across all molecules or one
+ * persistent launch whose CTAs pull work items (a class's quartets for one
+ * block of teams, heaviest first) from a queue with a single atomicAdd each.
+ * bases: host array of n_mol basis descriptors (device arrays, ao_off
+ * required); D, K: host arrays of n_mol device pointers ([nao_m][nao_m]
+ * row-major; D read, K overwritten by run). Every shell pair of every
+ * molecule is used; its Schwarz factor is computed here, and unique quartets
+ * are screened with Q_ij Q_kl max|D block| >= tau using each D as given at
+ * creation. Synchronises `stream`. The D and K buffers must stay valid until
+ * the batch is destroyed. */
+typedef struct mdx_xbatch mdx_xbatch;
+mdx_status mdx_xbatch_create(mdx_ctx* ctx, int32_t n_mol, const mdx_basis* bases, const double* const* D,
+                             double* const* K, double tau, mdx_xbatch** xbatch, void* stream);
+
+/* Kept quartets, persistent work items, per-class launches and the Table-1
+ * model FLOPs of the kept shellsets of a batch (any pointer may be NULL). */
+mdx_status mdx_xbatch_info(const mdx_xbatch* xbatch, int64_t* n_quartets, int64_t* n_items,
+                           int32_t* n_class_launches, double* model_flops);
+
+/* Enqueue K_m <- 0, the integral kernels with fused digestion (persistent = 1:
+ * one persistent launch; 0: one launch per class) and K_m <- K_m + K_m^T.
+ * No host synchronisation and no allocation: the enqueued work can be
+ * captured in a CUDA graph and replayed. n_launches (may be NULL) receives
+ * the kernels enqueued. */
+mdx_status mdx_xbatch_run(mdx_ctx* ctx, mdx_xbatch* xbatch, int32_t persistent, int32_t* n_launches, void* stream);
+
+/* Free a batched exchange (NULL allowed). No work of it may still be running. */
+void mdx_xbatch_destroy(mdx_xbatch* xbatch);
+
 /* Number of unique quartets the last mdx_exchange of this context kept after
  * screening (-1 for a NULL context). */
 int64_t mdx_last_quartet_count(const mdx_ctx* ctx);

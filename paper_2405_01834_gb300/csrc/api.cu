@@ -210,7 +210,42 @@ struct mdx_batch {
   double exec_fma = 0.0;
 };
 
+// Several molecules' exchange builds prepared together (one super basis, one
+// screened quartet list per class bucket across molecules).
+struct mdx_xbatch {
+  mdx_ctx* ctx = nullptr;
+  int32_t nmol = 0;
+  int64_t max_nao = 0, nq = 0, nitems = 0, smem = 0;
+  int grid = 0;
+  double model_flops = 0.0;
+  mdx_basis sb{};
+  int32_t *l = nullptr, *nprim = nullptr, *prim_off = nullptr, *ao_off = nullptr;
+  double *center = nullptr, *exps = nullptr, *coefs = nullptr;
+  const double** molD = nullptr;
+  double** molK = nullptr;
+  int32_t* molnao = nullptr;
+  int2* pshell = nullptr;
+  int32_t* pmol = nullptr;
+  int64_t* prec = nullptr;
+  double *recs = nullptr, *recs_s = nullptr;
+  int2* quart = nullptr;
+  std::vector<QuartetLaunch> launches, plaunches;
+  QuartetLaunch* d_plaunches = nullptr;
+  WorkItem* items = nullptr;
+  unsigned long long* counter = nullptr;
+};
+
 namespace {
+
+void xbatch_free(mdx_xbatch* x) {
+  if (!x) return;
+  cudaFree(x->l); cudaFree(x->nprim); cudaFree(x->prim_off); cudaFree(x->ao_off);
+  cudaFree(x->center); cudaFree(x->exps); cudaFree(x->coefs);
+  cudaFree(x->molD); cudaFree(x->molK); cudaFree(x->molnao);
+  cudaFree(x->pshell); cudaFree(x->pmol); cudaFree(x->prec); cudaFree(x->recs); cudaFree(x->recs_s);
+  cudaFree(x->quart); cudaFree(x->d_plaunches); cudaFree(x->items); cudaFree(x->counter);
+  delete x;
+}
 
 void batch_free(mdx_batch* b) {
   if (!b) return;
@@ -769,9 +804,10 @@ mdx_status exchange_screen(mdx_ctx* c, const mdx_basis* basis, const int32_t* pa
   if ((st = upload(c, "x_q", qf, &d_q, s)) != MDX_OK) return st;
   if ((st = ensure(c, "x_dmax", (size_t)hb.n * hb.n, &d_dmax, s)) != MDX_OK) return st;
   if ((st = ensure(c, "x_counts", (size_t)nbucket, &d_counts, s)) != MDX_OK) return st;
-  e = launch_dmax(D, (int32_t)X.nao, basis->ao_off, basis->l, hb.n, d_dmax, s);
+  e = launch_dmax(D, (int32_t)X.nao, basis->ao_off, basis->l, hb.n, d_dmax, hb.n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
-  ScreenArgs sa{n_pairs, X.d_pshell, d_pclass, d_q, d_dmax, hb.n, nclass, (float)tau, d_counts, nullptr, nullptr};
+  ScreenArgs sa{n_pairs, X.d_pshell, d_pclass, d_q, d_dmax, hb.n, nclass, (float)tau, d_counts, nullptr, nullptr,
+                nullptr};
   if (e == cudaSuccess) e = launch_screen(sa, false, s);
   X.counts.assign(nbucket, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(X.counts.data(), d_counts, nbucket * sizeof(unsigned long long),
@@ -1020,5 +1056,321 @@ mdx_status mdx_plan_info(mdx_ctx* c, int la, int lb, int lc, int ld, int Kb, int
   out->exec_fma = p.exec_fma;
   return MDX_OK;
 }
+
+
+// ---------------------------------------------------------------- batched exchange
+mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, const double* const* D,
+                             double* const* K, double tau, mdx_xbatch** out, void* stream) {
+  if (!c || !out) return MDX_EINVAL;
+  *out = nullptr;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_mol < 1 || !bases || !D || !K || !(tau >= 0.0)) return fail(c, MDX_EINVAL, "invalid arguments");
+  std::unique_ptr<mdx_xbatch, void (*)(mdx_xbatch*)> X(new mdx_xbatch(), xbatch_free);
+  X->ctx = c;
+  X->nmol = n_mol;
+  // super basis: every molecule's shells back to back; AO offsets stay local to the molecule
+  std::vector<int32_t> L, NP, PO, AO, MOLSH, mol_nao(n_mol);
+  std::vector<double> CEN, EX, CO;
+  std::vector<int32_t> shell_first(n_mol + 1, 0);
+  for (int m = 0; m < n_mol; ++m) {
+    const mdx_basis& b = bases[m];
+    if (!b.ao_off || b.n_shells < 1) return fail(c, MDX_EINVAL, "every molecule needs shells and ao_off");
+    HostBasis hb;
+    mdx_status st = fetch_basis(c, &b, hb, s);
+    if (st != MDX_OK) return st;
+    const int n = hb.n;
+    std::vector<int32_t> po(n), ao(n);
+    std::vector<double> cen(3 * (size_t)n), ex(b.n_prims), co(b.n_prims);
+    cudaError_t e = cudaMemcpyAsync(po.data(), b.prim_off, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ao.data(), b.ao_off, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cen.data(), b.center, cen.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && b.n_prims) e = cudaMemcpyAsync(ex.data(), b.exps, ex.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && b.n_prims) e = cudaMemcpyAsync(co.data(), b.coefs, co.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "basis download");
+    int64_t nao = 0;
+    for (int i = 0; i < n; ++i) {
+      nao = std::max<int64_t>(nao, (int64_t)ao[i] + ncart(hb.l[i]));
+      L.push_back(hb.l[i]);
+      NP.push_back(hb.nprim[i]);
+      PO.push_back((int32_t)EX.size());
+      AO.push_back(ao[i]);
+      MOLSH.push_back(m);
+      for (int k = 0; k < 3; ++k) CEN.push_back(cen[3 * (size_t)i + k]);
+      for (int q = 0; q < hb.nprim[i]; ++q) {
+        if (po[i] + q < 0 || po[i] + q >= b.n_prims) return fail(c, MDX_EINVAL, "primitive index out of range");
+        EX.push_back(ex[po[i] + q]);
+        CO.push_back(co[po[i] + q]);
+      }
+    }
+    mol_nao[m] = (int32_t)nao;
+    shell_first[m + 1] = shell_first[m] + n;
+  }
+  const int32_t ntot = shell_first[n_mol];
+  mdx_status st;
+  if ((st = dev_upload(c, L, &X->l, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, NP, &X->nprim, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, PO, &X->prim_off, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, AO, &X->ao_off, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, CEN, &X->center, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, EX, &X->exps, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, CO, &X->coefs, s)) != MDX_OK) return st;
+  std::vector<const double*> hD(D, D + n_mol);
+  std::vector<double*> hK(K, K + n_mol);
+  if ((st = dev_upload(c, hD, &X->molD, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, hK, &X->molK, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, mol_nao, &X->molnao, s)) != MDX_OK) return st;
+  X->max_nao = *std::max_element(mol_nao.begin(), mol_nao.end());
+  const mdx_basis sb{ntot, (int32_t)EX.size(), X->l, X->nprim, X->prim_off, X->ao_off, nullptr, X->center, X->exps,
+                     X->coefs};
+  X->sb = sb;
+  // all shell pairs i >= j of every molecule, sorted by (molecule, class)
+  struct PP { int32_t i, j, m, li, lj, K; };
+  std::vector<PP> pl;
+  for (int m = 0; m < n_mol; ++m)
+    for (int32_t i = shell_first[m]; i < shell_first[m + 1]; ++i)
+      for (int32_t j = shell_first[m]; j <= i; ++j) pl.push_back(PP{i, j, m, L[i], L[j], NP[i] * NP[j]});
+  std::stable_sort(pl.begin(), pl.end(), [](const PP& a, const PP& b) {
+    if (a.m != b.m) return a.m < b.m;
+    if (a.li != b.li) return a.li < b.li;
+    if (a.lj != b.lj) return a.lj < b.lj;
+    return a.K < b.K;
+  });
+  const int64_t np = (int64_t)pl.size();
+  std::map<std::array<int, 3>, int> cid;
+  std::vector<std::array<int, 3>> classes;
+  std::vector<int2> pshell(np);
+  std::vector<int32_t> pclass_raw(np), pmol(np);
+  std::vector<int64_t> pfirst(np);
+  for (int64_t p = 0; p < np; ++p) {
+    std::array<int, 3> k{pl[p].li, pl[p].lj, pl[p].K};
+    auto it = cid.find(k);
+    if (it == cid.end()) it = cid.emplace(k, 0).first;
+    pshell[p] = make_int2(pl[p].i, pl[p].j);
+    pmol[p] = pl[p].m;
+    pfirst[p] = (p > 0 && pl[p - 1].m == pl[p].m) ? pfirst[p - 1] : p;
+  }
+  // class ids ordered like the in-molecule sort, so class(q) <= class(p) for q <= p in a molecule
+  { int k = 0; for (auto& kv : cid) { kv.second = k++; classes.push_back(kv.first); } }
+  for (int64_t p = 0; p < np; ++p) pclass_raw[p] = cid[{pl[p].li, pl[p].lj, pl[p].K}];
+  const int nclass = (int)classes.size();
+  const int64_t nbucket = (int64_t)nclass * (nclass + 1) / 2;
+  if ((st = dev_upload(c, pshell, &X->pshell, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, pmol, &X->pmol, s)) != MDX_OK) return st;
+  int32_t* d_pclass; int64_t* d_pfirst;
+  if ((st = upload(c, "xb_pclass", pclass_raw, &d_pclass, s)) != MDX_OK) return st;
+  if ((st = upload(c, "xb_pfirst", pfirst, &d_pfirst, s)) != MDX_OK) return st;
+  // Schwarz factors and primitive-pair records of every pair (records stay with the batch)
+  std::vector<int64_t> prec(np);
+  std::vector<PrimPairJob> jobs;
+  int64_t roff = 0;
+  std::vector<int32_t> nab(np);
+  std::vector<int64_t> doffs(np + 1, 0);
+  for (int64_t p = 0; p < np; ++p) {
+    prec[p] = roff;
+    for (int ia = 0; ia < NP[pl[p].i]; ++ia)
+      for (int ib = 0; ib < NP[pl[p].j]; ++ib) {
+        jobs.push_back(PrimPairJob{pl[p].i, pl[p].j, ia, ib, 0, 0, roff});
+        roff += rec_size(pl[p].li, pl[p].lj);
+      }
+    nab[p] = ncart(pl[p].li) * ncart(pl[p].lj);
+    doffs[p + 1] = doffs[p] + (int64_t)nab[p] * nab[p];
+  }
+  PrimPairJob* d_jobs;
+  if ((st = dev_upload(c, prec, &X->prec, s)) != MDX_OK) return st;
+  if ((st = upload(c, "xb_jobs", jobs, &d_jobs, s)) != MDX_OK) return st;
+  if (cudaMalloc(&X->recs, roff * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&X->recs_s, roff * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MDX_ENOMEM, "record allocation failed");
+  }
+  const BasisDev bd{X->l, X->nprim, X->prim_off, X->center, X->exps, X->coefs};
+  cudaError_t e = launch_pair_records(bd, bd, d_jobs, (int64_t)jobs.size(), X->recs, X->recs_s, c->d_err, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+  {
+    // diagonal quartets (ij|ij) for Q_ij, per class
+    std::map<ClassKey, std::vector<int64_t>> dcls;
+    for (int64_t p = 0; p < np; ++p)
+      dcls[ClassKey{pl[p].li, pl[p].lj, pl[p].li, pl[p].lj, pl[p].K, pl[p].K, 0}].push_back(p);
+    double* d_vals; int64_t* d_doff; int32_t* d_nab; int2* d_dq; int64_t* d_dqo;
+    std::vector<int2> dq;
+    std::vector<int64_t> dqo;
+    for (auto& kv : dcls) for (int64_t p : kv.second) { dq.push_back(make_int2((int)p, (int)p)); dqo.push_back(doffs[p]); }
+    if ((st = ensure(c, "xb_dvals", (size_t)doffs[np], &d_vals, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_doff", doffs, &d_doff, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_nab", nab, &d_nab, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_dq", dq, &d_dq, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_dqo", dqo, &d_dqo, s)) != MDX_OK) return st;
+    int64_t at = 0;
+    for (auto& kv : dcls) {
+      Plan* plan;
+      if ((st = get_plan(c, kv.first, &plan, s)) != MDX_OK) return st;
+      QuartetLaunch a = base_launch(c, plan, d_dq + at, (int64_t)kv.second.size(), X->prec, X->recs, X->recs_s);
+      a.qout = d_dqo + at;
+      a.out = d_vals;
+      e = launch_quartets(a, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "Schwarz quartets");
+      at += (int64_t)kv.second.size();
+    }
+    double* d_Q;
+    if ((st = ensure(c, "xb_Q", (size_t)np, &d_Q, s)) != MDX_OK) return st;
+    e = launch_schwarz_reduce(d_doff, d_nab, np, d_vals, d_Q, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Schwarz reduce");
+    std::vector<double> hQ(np);
+    e = cudaMemcpyAsync(hQ.data(), d_Q, np * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Schwarz");
+    std::vector<float> qf(np);
+    for (int64_t p = 0; p < np; ++p) qf[p] = (float)hQ[p];
+    float* d_qf;
+    if ((st = upload(c, "xb_qf", qf, &d_qf, s)) != MDX_OK) return st;
+    // density-block maxima of every molecule (block diagonal of one n_tot x n_tot table)
+    float* d_dmax;
+    if ((st = ensure(c, "xb_dmax", (size_t)ntot * ntot, &d_dmax, s)) != MDX_OK) return st;
+    for (int m = 0; m < n_mol; ++m) {
+      const int32_t f = shell_first[m], nm = shell_first[m + 1] - f;
+      e = launch_dmax(D[m], mol_nao[m], X->ao_off + f, X->l + f, nm, d_dmax + (int64_t)f * ntot + f, ntot, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "density maxima");
+    }
+    unsigned long long* d_counts;
+    if ((st = ensure(c, "xb_counts", (size_t)nbucket, &d_counts, s)) != MDX_OK) return st;
+    e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
+    ScreenArgs sa{np, X->pshell, d_pclass, d_qf, d_dmax, ntot, nclass, (float)tau, d_counts, nullptr, nullptr, d_pfirst};
+    if (e == cudaSuccess) e = launch_screen(sa, false, s);
+    std::vector<unsigned long long> counts(nbucket);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts.data(), d_counts, nbucket * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "screening");
+    std::vector<int64_t> boff(nbucket + 1, 0);
+    for (int64_t b = 0; b < nbucket; ++b) boff[b + 1] = boff[b] + (int64_t)counts[b];
+    X->nq = boff[nbucket];
+    if (X->nq > 0) {
+      int64_t* d_boff;
+      if ((st = upload(c, "xb_boff", boff, &d_boff, s)) != MDX_OK) return st;
+      if (cudaMalloc(&X->quart, X->nq * sizeof(int2)) != cudaSuccess) { cudaGetLastError(); return fail(c, MDX_ENOMEM, "quartet list"); }
+      e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
+      sa.bucket_off = d_boff;
+      sa.out = X->quart;
+      if (e == cudaSuccess) e = launch_screen(sa, true, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "screening");
+    }
+    // one launch descriptor per non-empty bucket, plus the persistent work items
+    std::vector<WorkItem> items;
+    std::vector<double> cost;
+    int64_t smem = 0;
+    for (int cp = 0; cp < nclass; ++cp)
+      for (int cq = 0; cq <= cp; ++cq) {
+        const int64_t b = (int64_t)cp * (cp + 1) / 2 + cq;
+        if (counts[b] == 0) continue;
+        const ClassKey key{classes[cp][0], classes[cp][1], classes[cq][0], classes[cq][1], classes[cp][2],
+                           classes[cq][2], 0};
+        Plan* plan;
+        if ((st = get_plan(c, key, &plan, s)) != MDX_OK) return st;
+        QuartetLaunch a = base_launch(c, plan, X->quart + boff[b], (int64_t)counts[b], X->prec, X->recs, X->recs_s);
+        a.D = D[0];                     // any non-null D selects the digestion epilogue
+        a.ao_off = X->ao_off;
+        a.pair_shells = X->pshell;
+        a.pair_mol = X->pmol;
+        a.mol_D = X->molD;
+        a.mol_K = X->molK;
+        a.mol_nao = X->molnao;
+        X->launches.push_back(a);
+        X->model_flops += model_flops_class(key) * (double)counts[b];
+        // persistent shape: teams of T threads filling the 512-thread block
+        const int64_t tb = (int64_t)plan->d.team_doubles * 8;
+        int tpb = std::max(1, std::min<int>(kPersistBlock / plan->d.T, (int)((220 * 1024) / tb)));
+        int p2 = 1;
+        while (p2 * 2 <= tpb) p2 *= 2;
+        tpb = p2;
+        Plan* pp = plan;
+        if (kPersistBlock / tpb != plan->d.T) {
+          std::unique_ptr<Plan> np2(new Plan());
+          std::string err;
+          PlanConfig cfg{};
+          auto tc = c->tuned.find(key);
+          if (tc != c->tuned.end()) cfg = tc->second;
+          cfg.T = kPersistBlock / tpb;
+          if (!build_plan(key, cfg, *np2, err)) return fail(c, MDX_EUNSUPPORTED, "persistent planner: " + err);
+          if ((int64_t)np2->d.team_doubles * 8 * tpb > 226 * 1024) return fail(c, MDX_EUNSUPPORTED, "persistent shape");
+          if ((st = upload_plan(c, np2.get(), s)) != MDX_OK) return st;
+          pp = np2.get();
+          c->retired.push_back(std::move(np2));
+        }
+        QuartetLaunch ap = a;
+        ap.plan = pp->d;
+        X->plaunches.push_back(ap);
+        smem = std::max<int64_t>(smem, (int64_t)pp->d.team_doubles * 8 * tpb);
+        for (int64_t q0 = 0; q0 < (int64_t)counts[b]; q0 += tpb) {
+          const int cnt = (int)std::min<int64_t>(tpb, (int64_t)counts[b] - q0);
+          items.push_back(WorkItem{(int32_t)(X->plaunches.size() - 1), cnt, q0});
+          cost.push_back(pp->exec_fma * cnt);
+        }
+      }
+    // heaviest items first (the queue hands them out in order)
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<WorkItem> sorted;
+    for (size_t i : order) sorted.push_back(items[i]);
+    X->nitems = (int64_t)sorted.size();
+    X->smem = smem;
+    if ((st = dev_upload(c, X->plaunches, &X->d_plaunches, s)) != MDX_OK) return st;
+    if ((st = dev_upload(c, sorted, &X->items, s)) != MDX_OK) return st;
+    if (cudaMalloc(&X->counter, sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); return fail(c, MDX_ENOMEM, "counter"); }
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, persistent_kernel_ptr(), kPersistBlock, (size_t)std::max<int64_t>(smem, 1));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    X->grid = std::max(1, bps) * std::max(1, sms);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batched exchange set-up");
+  st = check_device_error(c, s);
+  if (st != MDX_OK) return st;
+  *out = X.release();
+  return MDX_OK;
+}
+
+mdx_status mdx_xbatch_info(const mdx_xbatch* xb, int64_t* n_quartets, int64_t* n_items, int32_t* n_class_launches,
+                           double* model_flops) {
+  if (!xb) return MDX_EINVAL;
+  if (model_flops) *model_flops = xb->model_flops;
+  if (n_quartets) *n_quartets = xb->nq;
+  if (n_items) *n_items = xb->nitems;
+  if (n_class_launches) *n_class_launches = (int32_t)xb->launches.size();
+  return MDX_OK;
+}
+
+mdx_status mdx_xbatch_run(mdx_ctx* c, mdx_xbatch* xb, int32_t persistent, int32_t* n_launches, void* stream) {
+  if (!c || !xb || xb->ctx != c) return MDX_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t nl = 0;
+  cudaError_t e = launch_multi_k(xb->molK, xb->molnao, xb->nmol, xb->max_nao, true, s);
+  ++nl;
+  if (e == cudaSuccess && xb->nq > 0) {
+    if (persistent) {
+      e = cudaMemsetAsync(xb->counter, 0, sizeof(unsigned long long), s);
+      PersistLaunch pl{xb->d_plaunches, xb->items, xb->nitems, xb->counter};
+      if (e == cudaSuccess) e = launch_persistent(pl, xb->smem, xb->grid, s);
+      ++nl;
+    } else {
+      for (const QuartetLaunch& a : xb->launches) {
+        e = launch_quartets(a, s);
+        if (e != cudaSuccess) break;
+        ++nl;
+      }
+    }
+  }
+  if (e == cudaSuccess) e = launch_multi_k(xb->molK, xb->molnao, xb->nmol, xb->max_nao, false, s);
+  ++nl;
+  if (e != cudaSuccess) return cuda_fail(c, e, "batched exchange launch");
+  if (n_launches) *n_launches = nl;
+  return MDX_OK;
+}
+
+void mdx_xbatch_destroy(mdx_xbatch* xb) { xbatch_free(xb); }
 
 }  // extern "C"

@@ -16,6 +16,7 @@
 // GB300 executes FP64 at 2 FMA/clk/SM (measured: 1.20 TFLOP/s DFMA, 1.05
 // TFLOP/s DMMA, 74.8 TFLOP/s FFMA), so the kernels spend integer and
 // shared-memory bandwidth freely to save FP64 instructions.
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -239,30 +240,43 @@ __device__ void compute_R(const QuartetLaunch& a, double* ws, int tl, unsigned m
   }
 }
 
+// Two dot products side by side, operands loaded one term ahead of the FMAs
+// that consume them (shared-memory latency overlaps the FP64 pipe).
+__device__ __forceinline__ void dual_dot(const double* __restrict__ c0, const double* __restrict__ x0, int st0, int n0,
+                                         const double* __restrict__ c1, const double* __restrict__ x1, int st1, int n1,
+                                         double& v0, double& v1) {
+  const int nm = min(n0, n1);
+  if (nm > 0) {
+    double a0 = c0[0], b0 = x0[0], a1 = c1[0], b1 = x1[0];
+    for (int k = 1; k < nm; ++k) {
+      const double na0 = c0[k * st0], nb0 = x0[k * st0], na1 = c1[k * st1], nb1 = x1[k * st1];
+      v0 = fma(a0, b0, v0);
+      v1 = fma(a1, b1, v1);
+      a0 = na0; b0 = nb0; a1 = na1; b1 = nb1;
+    }
+    v0 = fma(a0, b0, v0);
+    v1 = fma(a1, b1, v1);
+  }
+  for (int k = nm; k < n0; ++k) v0 = fma(c0[k * st0], x0[k * st0], v0);
+  for (int k = nm; k < n1; ++k) v1 = fma(c1[k * st1], x1[k * st1], v1);
+}
+
 // out = (acc ? out : 0) + sum_k coef[c + k s] src[x + k s]
 // Each lane runs two entries (e, e + T) side by side: two independent FMA
 // chains hide the FP64 pipe latency. Entries are sorted by length, so the
-// two usually have the same n.
+// two usually have the same n. The next pair of entries is fetched while the
+// current pair is computed.
 __device__ __forceinline__ void run_step(const StepEntry* __restrict__ prog, int n, double* ws, int tl, int T,
                                          bool acc) {
   int e = tl;
+  StepEntry p0{}, p1{};
+  if (e + T < n) { p0 = prog[e]; p1 = prog[e + T]; }
   for (; e + T < n; e += 2 * T) {
-    const StepEntry s0 = prog[e], s1 = prog[e + T];
-    const double* c0 = ws + s0.coef;
-    const double* x0 = ws + s0.src;
-    const double* c1 = ws + s1.coef;
-    const double* x1 = ws + s1.src;
-    const int st0 = s0.stride, st1 = s1.stride;
+    const StepEntry s0 = p0, s1 = p1;
+    if (e + 3 * T < n) { p0 = prog[e + 2 * T]; p1 = prog[e + 3 * T]; }
     double v0 = acc ? ws[s0.out] : 0.0;
     double v1 = acc ? ws[s1.out] : 0.0;
-    const int nm = min((int)s0.n, (int)s1.n);
-    int k = 0;
-    for (; k < nm; ++k) {
-      v0 = fma(c0[k * st0], x0[k * st0], v0);
-      v1 = fma(c1[k * st1], x1[k * st1], v1);
-    }
-    for (int k0 = k; k0 < s0.n; ++k0) v0 = fma(c0[k0 * st0], x0[k0 * st0], v0);
-    for (int k1 = k; k1 < s1.n; ++k1) v1 = fma(c1[k1 * st1], x1[k1 * st1], v1);
+    dual_dot(ws + s0.coef, ws + s0.src, s0.stride, s0.n, ws + s1.coef, ws + s1.src, s1.stride, s1.n, v0, v1);
     ws[s0.out] = v0;
     ws[s1.out] = v1;
   }
@@ -296,13 +310,14 @@ __device__ void digest_group(const QuartetLaunch& a, const double* ws, const Gro
   const double w = (si == sj ? 0.5 : 1.0) * (sk == sl ? 0.5 : 1.0) * (qp.x == qp.y ? 0.5 : 1.0);
   const int na = d_ncart(P.la), nb = d_ncart(P.lb), nd = d_ncart(P.ld);
   const int nc = d_ncart(P.lc);
-  const int64_t nao = a.nao;
+  const int mol = a.pair_mol ? a.pair_mol[qp.x] : -1;
+  const int64_t nao = mol >= 0 ? a.mol_nao[mol] : a.nao;
   const int64_t ai = a.ao_off[si], aj = a.ao_off[sj], ak = a.ao_off[sk], al = a.ao_off[sl];
   const int ncols = grp.ncols;
   const uint16_t* cm = P.colmap + grp.col_off;
   const double* OUT = ws + P.o_OUT;
-  const double* D = a.D;
-  double* K = a.K;
+  const double* D = mol >= 0 ? a.mol_D[mol] : a.D;
+  double* K = mol >= 0 ? a.mol_K[mol] : a.K;
   // u1: (a,c) over b,d ; u2: (a,d) over b,c ; u3: (b,c) over a,d ; u4: (b,d) over a,c
   const int n1 = na * nc, n2 = na * nd, n3 = nb * nc, n4 = nb * nd;
   for (int e = tl; e < n1 + n2 + n3 + n4; e += T) {
@@ -405,7 +420,7 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
     }
   }
   // reduce over the lanes of the team (whole warps for CTA teams, aligned lane groups otherwise)
-  const int width = CTA ? 32 : T;
+  const int width = T < 32 ? T : 32;
   for (int off = width / 2; off > 0; off >>= 1) {
     s0 += __shfl_xor_sync(mask, s0, off);
     s1 += __shfl_xor_sync(mask, s1, off);
@@ -424,24 +439,14 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
   atomicAdd(gD + 0, -f * s0); atomicAdd(gD + 1, -f * s1); atomicAdd(gD + 2, -f * s2);
 }
 
+// The work of one team on one shell quartet q (all groups, all primitives,
+// store / digestion / gradient epilogue). Inactive teams run the same control
+// flow on a shadow quartet (so that barriers match) and write nothing global.
 template <bool CTA>
-__global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaunch a) {
-  extern __shared__ __align__(16) double smem[];
+__device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws, int64_t q, bool active, int tl,
+                                             unsigned mask) {
   const PlanDev& P = a.plan;
   const int T = P.T;
-  const int team = threadIdx.x / T;
-  const int tl = threadIdx.x - team * T;
-  double* ws = smem + (size_t)team * P.team_doubles;
-  // lanes of this warp that exist (a partial last warp when the CTA is not a multiple of 32)
-  unsigned mask = 0xffffffffu;
-  if (!CTA) {
-    const int wbase = threadIdx.x & ~31;
-    const int live = blockDim.x - wbase;
-    if (live < 32) mask = (1u << live) - 1u;
-  }
-  int64_t q = (int64_t)blockIdx.x * P.teams_per_cta + team;
-  const bool active = q < a.nq;
-  if (!active) q = a.nq - 1;   // idle teams shadow the last quartet and store nothing
   const int2 qp = a.qpairs[q];
   const int64_t bra0 = a.pair_rec[qp.x + a.bra_var_off];
   const int64_t ket0 = a.pair_rec[qp.y + a.ket_var_off];
@@ -484,16 +489,8 @@ __global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaun
           const double* x0 = ws + P.o_X + col0 * P.hb + s0.src;
           const double* c1 = ws + s1.coef;
           const double* x1 = ws + P.o_X + col1 * P.hb + s1.src;
-          const int st0 = s0.stride, st1 = s1.stride;
-          const int nm = min((int)s0.n, (int)s1.n);
           double v0 = 0.0, v1 = 0.0;
-          int k = 0;
-          for (; k < nm; ++k) {
-            v0 = fma(c0[k * st0], x0[k * st0], v0);
-            v1 = fma(c1[k * st1], x1[k * st1], v1);
-          }
-          for (int k0 = k; k0 < s0.n; ++k0) v0 = fma(c0[k0 * st0], x0[k0 * st0], v0);
-          for (int k1 = k; k1 < s1.n; ++k1) v1 = fma(c1[k1 * st1], x1[k1 * st1], v1);
+          dual_dot(c0, x0, s0.stride, s0.n, c1, x1, s1.stride, s1.n, v0, v1);
           ws[P.o_C1 + col0 * P.c1size + s0.out] = v0;
           if (e1 != e) ws[P.o_C1 + col1 * P.c1size + s1.out] = v1;
         }
@@ -519,11 +516,15 @@ __global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaun
             const double* ra = c1 + va * r1 - (va * (va - 1)) / 2;
             const double* rb = c1 + vb * r1 - (vb * (vb - 1)) / 2;
             double ia = 0.0, ib = 0.0;
-            for (int iu = 0; iu < nu; ++iu) {
-              const double y = ey[iu * su];
-              ia = fma(y, ra[iu * su], ia);
-              ib = fma(y, rb[iu * su], ib);
+            double y = ey[0], xa = ra[0], xb = rb[0];
+            for (int iu = 1; iu < nu; ++iu) {
+              const double ny = ey[iu * su], nxa = ra[iu * su], nxb = rb[iu * su];
+              ia = fma(y, xa, ia);
+              ib = fma(y, xb, ib);
+              y = ny; xa = nxa; xb = nxb;
             }
+            ia = fma(y, xa, ia);
+            ib = fma(y, xb, ib);
             acc = fma(ez[iv * sv], ia, acc);
             acc = fma(ez[(iv + 1) * sv], ib, acc);
           }
@@ -558,6 +559,60 @@ __global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaun
   }
 }
 
+template <bool CTA>
+__global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaunch a) {
+  extern __shared__ __align__(16) double smem[];
+  const PlanDev& P = a.plan;
+  const int T = P.T;
+  const int team = threadIdx.x / T;
+  const int tl = threadIdx.x - team * T;
+  double* ws = smem + (size_t)team * P.team_doubles;
+  // lanes of this warp that exist (a partial last warp when the CTA is not a multiple of 32)
+  unsigned mask = 0xffffffffu;
+  if (!CTA) {
+    const int wbase = threadIdx.x & ~31;
+    const int live = blockDim.x - wbase;
+    if (live < 32) mask = (1u << live) - 1u;
+  }
+  int64_t q = (int64_t)blockIdx.x * P.teams_per_cta + team;
+  const bool active = q < a.nq;
+  if (!active) q = a.nq - 1;   // idle teams shadow the last quartet and store nothing
+  quartet_body<CTA>(a, ws, q, active, tl, mask);
+}
+
+// Persistent kernel over a queue of work items from many launches (classes,
+// molecules): each CTA takes the next item with one atomicAdd (no waiting on
+// other CTAs), adopts that item's plan (teams of T threads, T x teams = the
+// block size, CTA-wide barriers) and runs its quartets.
+__global__ void __launch_bounds__(kPersistBlock) k_persistent(const PersistLaunch pl) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ long long s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(pl.counter, 1ull);
+    __syncthreads();
+    const long long it = s_item;
+    __syncthreads();
+    if (it >= pl.nitems) return;
+    const WorkItem w = pl.items[it];
+    const QuartetLaunch& a = pl.launches[w.launch];
+    const int T = a.plan.T;
+    const int team = threadIdx.x / T;
+    const int tl = threadIdx.x - team * T;
+    double* ws = smem + (size_t)team * a.plan.team_doubles;
+    const bool active = team < w.count;
+    const int64_t q = w.begin + (active ? team : 0);
+    quartet_body<true>(a, ws, q, active, tl, 0xffffffffu);
+  }
+}
+
+const void* persistent_kernel_ptr() { return (const void*)k_persistent; }
+
+cudaError_t launch_persistent(const PersistLaunch& pl, int64_t smem_bytes, int grid, cudaStream_t s) {
+  if (pl.nitems <= 0) return cudaSuccess;
+  k_persistent<<<grid, kPersistBlock, (size_t)smem_bytes, s>>>(pl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
   if (a.nq <= 0) return cudaSuccess;
   const PlanDev& P = a.plan;
@@ -572,7 +627,7 @@ cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
 
 // ----------------------------------------------------------------- exchange support
 __global__ void k_dmax(const double* __restrict__ D, int32_t nao, const int32_t* __restrict__ ao_off,
-                       const int32_t* __restrict__ l, int32_t n, float* __restrict__ dmax) {
+                       const int32_t* __restrict__ l, int32_t n, float* __restrict__ dmax, int64_t ld) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)n * n) return;
   const int x = (int)(g / n), y = (int)(g - (int64_t)x * n);
@@ -581,14 +636,14 @@ __global__ void k_dmax(const double* __restrict__ D, int32_t nao, const int32_t*
   double m = 0.0;
   for (int r = 0; r < nr; ++r)
     for (int c = 0; c < nc; ++c) m = fmax(m, fabs(D[(r0 + r) * nao + c0 + c]));
-  dmax[g] = (float)m;
+  dmax[(int64_t)x * ld + y] = (float)m;
 }
 
 cudaError_t launch_dmax(const double* D, int32_t nao, const int32_t* ao_off, const int32_t* l, int32_t n_shells,
-                        float* dmax, cudaStream_t s) {
+                        float* dmax, int64_t ld, cudaStream_t s) {
   const int64_t tot = (int64_t)n_shells * n_shells;
   if (tot <= 0) return cudaSuccess;
-  k_dmax<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, nao, ao_off, l, n_shells, dmax);
+  k_dmax<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, nao, ao_off, l, n_shells, dmax, ld);
   return cudaGetLastError();
 }
 
@@ -604,7 +659,8 @@ __global__ void k_screen(const ScreenArgs a, bool fill) {
   const float* di = a.dmax + (int64_t)ij.x * a.n_shells;
   const float* dj = a.dmax + (int64_t)ij.y * a.n_shells;
   const int64_t brow = (int64_t)cp * (cp + 1) / 2;
-  for (int64_t q = threadIdx.x; q <= p; q += blockDim.x) {
+  const int64_t q0 = a.pair_first ? a.pair_first[p] : 0;   // quartets stay inside one molecule
+  for (int64_t q = q0 + threadIdx.x; q <= p; q += blockDim.x) {
     const int2 kl = a.pair_shells[q];
     const float dm = fmaxf(fmaxf(di[kl.x], di[kl.y]), fmaxf(dj[kl.x], dj[kl.y]));
     if (qp * a.Q[q] * dm < a.tau) continue;
@@ -635,6 +691,43 @@ cudaError_t launch_symmetrize(double* K, int32_t nao, cudaStream_t s) {
   const int64_t tot = (int64_t)nao * nao;
   if (tot <= 0) return cudaSuccess;
   k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(K, nao);
+  return cudaGetLastError();
+}
+
+// K <- K + K^T for several molecules at once: blockIdx.y is the molecule.
+__global__ void k_symmetrize_multi(double* const* K, const int32_t* nao) {
+  const int m = blockIdx.y;
+  const int64_t n = nao[m];
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * n) return;
+  const int64_t r = g / n, c = g - r * n;
+  if (c < r) return;
+  double* k = K[m];
+  const double t = k[r * n + c] + k[c * n + r];
+  k[r * n + c] = t;
+  k[c * n + r] = t;
+}
+
+// K = 0 for several molecules at once.
+__global__ void k_zero_multi(double* const* K, const int32_t* nao) {
+  const int m = blockIdx.y;
+  const int64_t n = nao[m];
+  double* k = K[m];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n * n; g += (int64_t)gridDim.x * blockDim.x)
+    k[g] = 0.0;
+}
+
+cudaError_t launch_multi_k(double* const* K, const int32_t* nao, int32_t nmol, int64_t max_nao, bool zero,
+                           cudaStream_t s) {
+  if (nmol <= 0 || max_nao <= 0) return cudaSuccess;
+  const int64_t tot = max_nao * max_nao;
+  if (zero) {
+    dim3 grid((unsigned)std::min<int64_t>((tot + 255) / 256, 4096), (unsigned)nmol);
+    k_zero_multi<<<grid, 256, 0, s>>>(K, nao);
+  } else {
+    dim3 grid((unsigned)((tot + 255) / 256), (unsigned)nmol);
+    k_symmetrize_multi<<<grid, 256, 0, s>>>(K, nao);
+  }
   return cudaGetLastError();
 }
 
@@ -684,6 +777,8 @@ cudaError_t kernel_attributes_init() {
   e = cudaFuncSetAttribute(k_quartets<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_quartets<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm - 64);
   return e;
 }
 

@@ -62,14 +62,35 @@ struct QuartetLaunch {
   double alpha;
   int32_t gpos, gsign;
   int32_t lorig[4];          // unshifted l of positions i, j, k, l
+  // several molecules in one launch (exchange): molecule of each pair and its D, K, nao
+  const int32_t* pair_mol;
+  const double* const* mol_D;
+  double* const* mol_K;
+  const int32_t* mol_nao;
 };
+
+// Persistent launch over work items of many QuartetLaunch descriptors.
+constexpr int kPersistBlock = 512;
+struct WorkItem {
+  int32_t launch;   // index into PersistLaunch::launches
+  int32_t count;    // quartets of this item (one per team, <= teams per block)
+  int64_t begin;    // first quartet (index into that launch's qpairs)
+};
+struct PersistLaunch {
+  const QuartetLaunch* launches;   // device array
+  const WorkItem* items;           // device array, heaviest first
+  int64_t nitems;
+  unsigned long long* counter;     // next item; zero before the launch
+};
+cudaError_t launch_persistent(const PersistLaunch& pl, int64_t smem_bytes, int grid, cudaStream_t s);
+const void* persistent_kernel_ptr();
 
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s);
 
 // Exchange support: per shell-pair block max |D| (float), screening of unique
 // quartets into class buckets, K <- K + K^T.
 cudaError_t launch_dmax(const double* D, int32_t nao, const int32_t* ao_off, const int32_t* l, int32_t n_shells,
-                        float* dmax, cudaStream_t s);
+                        float* dmax, int64_t ld, cudaStream_t s);
 struct ScreenArgs {
   int64_t npairs;
   const int2* pair_shells;   // sorted by pair class
@@ -82,9 +103,13 @@ struct ScreenArgs {
   unsigned long long* counts;  // [nclass*(nclass+1)/2]
   const int64_t* bucket_off;   // fill pass: start of each bucket
   int2* out;                   // fill pass: (p, q) per surviving quartet
+  const int64_t* pair_first;   // first pair of p's molecule (NULL: one molecule)
 };
 cudaError_t launch_screen(const ScreenArgs& a, bool fill, cudaStream_t s);
 cudaError_t launch_symmetrize(double* K, int32_t nao, cudaStream_t s);
+// K <- 0 (zero = true) or K <- K + K^T (zero = false) for nmol molecules; K and nao are device arrays
+cudaError_t launch_multi_k(double* const* K, const int32_t* nao, int32_t nmol, int64_t max_nao, bool zero,
+                           cudaStream_t s);
 cudaError_t kernel_attributes_init();
 
 // Schwarz reduction: Q[p] = sqrt(max_ab |diag of shellset p|).

@@ -111,6 +111,15 @@ def load(build_if_missing: bool = True):
     lib.mdx_last_quartet_count.restype = I64
     lib.mdx_eri4_noalloc.argtypes = [ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
     lib.mdx_eri4_noalloc.restype = I32
+    lib.mdx_xbatch_create.argtypes = [P, I32, P, P, P, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p), P]
+    lib.mdx_xbatch_create.restype = I32
+    lib.mdx_xbatch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+    lib.mdx_xbatch_info.restype = I32
+    lib.mdx_xbatch_run.argtypes = [P, P, I32, ctypes.POINTER(ctypes.c_int32), P]
+    lib.mdx_xbatch_run.restype = I32
+    lib.mdx_xbatch_destroy.argtypes = [P]
+    lib.mdx_xbatch_destroy.restype = None
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
     lib.mdx_plan_info.restype = I32
     _lib = lib
@@ -242,6 +251,10 @@ class Engine:
     def last_quartet_count(self) -> int:
         return int(self.lib.mdx_last_quartet_count(self.ctx))
 
+    def xbatch(self, bases, Ds, tau: float = 0.0) -> "ExchangeBatch":
+        """Prepare the exchange builds of several molecules (see mdx_xbatch_create)."""
+        return ExchangeBatch(self, bases, Ds, tau)
+
     def batch_eri4(self, basis: DeviceBasis, quartets) -> "Batch":
         """Prepare quartets [n,4] once; run them many times with Batch.run."""
         q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
@@ -356,3 +369,44 @@ def exchange_energy(eng: Engine, basis: DeviceBasis, coords: torch.Tensor, D: to
         n = basis.desc.n_shells
         pairs = torch.tensor([(i, j) for i in range(n) for j in range(i + 1)], dtype=torch.int32, device="cuda")
     return ExchangeEnergy.apply(coords, D, eng, basis, pairs, tau, alpha)
+
+
+class ExchangeBatch:
+    """Exchange matrices of several molecules: one launch per class or one persistent launch."""
+
+    def __init__(self, eng: Engine, bases, Ds, tau: float):
+        self.eng = eng
+        self.bases = list(bases)
+        self.Ds = [D.to(device="cuda", dtype=torch.float64).contiguous() for D in Ds]
+        self.Ks = [torch.empty_like(D) for D in self.Ds]
+        n = len(self.bases)
+        arr = (_Basis * n)(*[b.desc for b in self.bases])
+        dp = (ctypes.c_void_p * n)(*[D.data_ptr() for D in self.Ds])
+        kp = (ctypes.c_void_p * n)(*[K.data_ptr() for K in self.Ks])
+        h = ctypes.c_void_p()
+        eng._check(eng.lib.mdx_xbatch_create(eng.ctx, n, arr, dp, kp, float(tau), ctypes.byref(h), _stream()),
+                   "mdx_xbatch_create")
+        self.h = h
+        nq, ni, nl, mf = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+        eng._check(eng.lib.mdx_xbatch_info(h, ctypes.byref(nq), ctypes.byref(ni), ctypes.byref(nl), ctypes.byref(mf)),
+                   "mdx_xbatch_info")
+        self.n_quartets, self.n_items, self.n_class_launches = nq.value, ni.value, nl.value
+        self.model_flops = mf.value
+
+    def run(self, persistent: bool = True) -> int:
+        """Enqueue on the current stream (capturable); returns kernels launched. Results in self.Ks."""
+        nl = ctypes.c_int32()
+        self.eng._check(self.eng.lib.mdx_xbatch_run(self.eng.ctx, self.h, int(persistent), ctypes.byref(nl),
+                                                    _stream()), "mdx_xbatch_run")
+        return nl.value
+
+    def close(self):
+        if self.h:
+            self.eng.lib.mdx_xbatch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

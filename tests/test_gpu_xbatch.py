@@ -1,0 +1,81 @@
+"""Batched exchange of several uneven molecules: per-class launches and one persistent
+launch (optionally replayed from a CUDA graph) against per-molecule mdx_exchange and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_01834_gb300 import inputs, mdx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    e = mdx.Engine(0)
+    yield e
+    e.close()
+
+
+def _molecules():
+    mols = [inputs.small_molecule(seed=80 + i, n_atoms=1 + i % 3, shells=(0, 1, 2), K=1 + i % 3) for i in range(5)]
+    mols.append(inputs.molecule(seed=90, n_atoms=2))        # heavy/light shells up to g, K = 6 s shells
+    return mols
+
+
+def _pairs(b):
+    return np.array([(i, j) for i in range(b.n_shells) for j in range(i + 1)], dtype=np.int32)
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batched_exchange_matches_single(eng, persistent):
+    mols = _molecules()
+    bases = [mdx.DeviceBasis(b) for b in mols]
+    Ds = [torch.from_numpy(inputs.density(b.nao, 3 + i)) for i, b in enumerate(mols)]
+    xb = eng.xbatch(bases, Ds, tau=0.0)
+    n = xb.run(persistent=persistent)
+    torch.cuda.synchronize()
+    eng.sync()
+    assert n == (3 if persistent else 2 + xb.n_class_launches)
+    tot = 0
+    for i, (b, db) in enumerate(zip(mols, bases)):
+        p = _pairs(b)
+        Q = eng.schwarz(db, p)
+        K1 = eng.exchange(db, p, Q, Ds[i], 0.0).cpu().numpy()
+        tot += eng.last_quartet_count()
+        K = xb.Ks[i].cpu().numpy()
+        np.testing.assert_allclose(K, K1, rtol=0, atol=1e-13 * np.max(np.abs(K1)))
+    assert xb.n_quartets == tot
+    # two molecules straight against the oracle
+    for i in (0, 2):
+        ref = oracle.exchange(mols[i], Ds[i].numpy())
+        np.testing.assert_allclose(xb.Ks[i].cpu().numpy(), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+    xb.close()
+
+
+def test_persistent_launch_in_cuda_graph(eng):
+    mols = _molecules()[:4]
+    bases = [mdx.DeviceBasis(b) for b in mols]
+    Ds = [torch.from_numpy(inputs.density(b.nao, 30 + i)) for i, b in enumerate(mols)]
+    xb = eng.xbatch(bases, Ds, tau=1e-12)
+    xb.run(persistent=True)
+    torch.cuda.synchronize()
+    ref = [K.clone() for K in xb.Ks]
+    for K in xb.Ks:
+        K.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            xb.run(persistent=True)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        for K in xb.Ks:
+            K.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for K, R in zip(xb.Ks, ref):
+            torch.testing.assert_close(K, R, rtol=0, atol=1e-13 * float(R.abs().max()))
+    eng.sync()
+    xb.close()
