@@ -56,6 +56,8 @@ def _load():
                                                         ctypes.c_int32, ctypes.c_int]
             lib.orc_exchange_grad.argtypes = [P] * 8 + [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
                                                         ctypes.c_int]
+            lib.orc_solid_coefs.argtypes = [ctypes.c_int, P]
+            lib.orc_eri4_sph.argtypes = [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -177,3 +179,24 @@ def exchange_grad(basis, D: np.ndarray, nthreads: int = 0) -> np.ndarray:
     _load().orc_exchange_grad(*[_p(a) for a in arrs], _p(ao_off), _p(atom), int(basis.n_shells), nao, _p(D),
                               n_atoms, _p(g), nthreads)
     return g
+
+
+def solid_coefs(l: int) -> np.ndarray:
+    """Real solid harmonics S_lm as Cartesian polynomials: [2l+1 (m = -l..l), ncart(l)]."""
+    C = np.zeros((2 * l + 1) * ncart(l))
+    _load().orc_solid_coefs(l, _p(C))
+    return C.reshape(2 * l + 1, ncart(l))
+
+
+def eri4_sph(basis, quartets, nthreads: int = 0):
+    """[ab|cd] over real solid harmonics (m = -l..l per shell); returns (values, offsets)."""
+    q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
+    l = np.asarray(basis.l)
+    ns = 2 * l + 1
+    sizes = (ns[q[:, 0]] * ns[q[:, 1]] * ns[q[:, 2]] * ns[q[:, 3]]).astype(np.int64)
+    off = np.zeros(len(q) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    out = np.zeros(int(off[-1]))
+    arrs = _basis_arrays(basis)
+    _load().orc_eri4_sph(*[_p(a) for a in arrs], _p(q), len(q), _p(out), _p(off), nthreads)
+    return out, off

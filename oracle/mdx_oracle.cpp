@@ -413,6 +413,45 @@ void orc_rtable(int L, double rho, const double* PQ, double* R) {
   std::memcpy(R, v.data(), v.size() * sizeof(double));
 }
 
+// Real solid harmonics as Cartesian polynomials (the transformation the paper
+// applies through its C coefficients, Eqs. solid2herm-1/2): the explicit form
+//   S_lm = N_lm sum_t sum_u sum_v C_tuv x^(2t+|m|-2(u+v)) y^(2(u+v)) z^(l-2t-|m|),
+//   C_tuv = (-1)^(t+v-v_m) (1/4)^t binom(l,t) binom(l-t,|m|+t) binom(t,u) binom(|m|,2v),
+//   N_lm = sqrt(2 (l+|m|)! (l-|m|)! / 2^delta_m0) / (2^|m| l!),
+// v_m = 0 (m >= 0) or 1/2 (m < 0), t <= (l-|m|)/2, u <= t, v from v_m in steps of 1
+// up to |m|/2. Rows m = -l..l, columns the Cartesian components in library
+// order: C[(m+l)*ncart(l) + k]. With this normalisation every S_lm has the
+// angular norm of z^l, so functions built on x^l-normalised primitives stay
+// normalised.
+double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+double fact(int n) { double r = 1.0; for (int i = 2; i <= n; ++i) r *= i; return r; }
+
+std::vector<double> solid_coefs(int l) {
+  const auto cl = cart_list(l);
+  std::vector<double> C((size_t)(2 * l + 1) * cl.size(), 0.0);
+  for (int m = -l; m <= l; ++m) {
+    const int am = m < 0 ? -m : m;
+    const int vv0 = m < 0 ? 1 : 0;   // 2 v_m
+    const double N = std::sqrt(2.0 * fact(l + am) * fact(l - am) / (m == 0 ? 2.0 : 1.0)) / (std::pow(2.0, am) * fact(l));
+    for (int t = 0; 2 * t <= l - am; ++t)
+      for (int u = 0; u <= t; ++u)
+        for (int vv = vv0; vv <= am; vv += 2) {   // vv = 2v
+          const int sgn_exp = t + (vv - vv0) / 2;
+          const double c = ((sgn_exp & 1) ? -1.0 : 1.0) * std::pow(0.25, t) * binom(l, t) * binom(l - t, am + t) *
+                           binom(t, u) * binom(am, vv);
+          const int px = 2 * t + am - 2 * u - vv, py = 2 * u + vv, pz = l - 2 * t - am;
+          for (size_t k = 0; k < cl.size(); ++k)
+            if (cl[k].x == px && cl[k].y == py && cl[k].z == pz) C[(size_t)(m + l) * cl.size() + k] += N * c;
+        }
+  }
+  return C;
+}
+
 // Batch of 4-center shellsets. quartets[n][4] are shell indices into the basis;
 // shellset q is written at out + offsets[q]. precision 1 runs the long double build.
 void orc_eri4(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,
@@ -431,6 +470,47 @@ void orc_eri4(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, c
     for (int64_t i = 0; i < total; ++i) out[i] = (double)tmp[i];
   } else {
     eri4_batch<double>(bs, quartets, n, out, offsets, nthreads);
+  }
+}
+
+// Solid-harmonic coefficient matrix of one l (see solid_coefs): C[(2l+1)][ncart(l)].
+void orc_solid_coefs(int l, double* C) {
+  const auto v = solid_coefs(l);
+  std::memcpy(C, v.data(), v.size() * sizeof(double));
+}
+
+// Batch of 4-center shellsets over real solid harmonics: the Cartesian shellset of
+// shellset4 transformed index by index with solid_coefs, written [a][b][c][d] with
+// m = -l..l in every position; shellset q at out + offsets[q].
+void orc_eri4_sph(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,
+                  const double* exps, const double* coefs, const int32_t* quartets, int64_t n, double* out,
+                  const int64_t* offsets, int nthreads) {
+  Basis bs{l, nprim, prim_off, center, exps, coefs};
+  const int nt = nthreads_or_default(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* s4 = quartets + 4 * q;
+    const int L[4] = {l[s4[0]], l[s4[1]], l[s4[2]], l[s4[3]]};
+    const int nc[4] = {ncart(L[0]), ncart(L[1]), ncart(L[2]), ncart(L[3])};
+    const int ns[4] = {2 * L[0] + 1, 2 * L[1] + 1, 2 * L[2] + 1, 2 * L[3] + 1};
+    std::vector<double> v((size_t)nc[0] * nc[1] * nc[2] * nc[3]);
+    shellset4<double>(bs, s4[0], s4[1], s4[2], s4[3], v.data());
+    std::vector<double> C[4];
+    for (int k = 0; k < 4; ++k) C[k] = solid_coefs(L[k]);
+    double* o = out + offsets[q];
+    for (int a = 0; a < ns[0]; ++a)
+      for (int b = 0; b < ns[1]; ++b)
+        for (int c = 0; c < ns[2]; ++c)
+          for (int d = 0; d < ns[3]; ++d) {
+            double acc = 0.0;
+            for (int i = 0; i < nc[0]; ++i)
+              for (int j = 0; j < nc[1]; ++j)
+                for (int k = 0; k < nc[2]; ++k)
+                  for (int m = 0; m < nc[3]; ++m)
+                    acc += C[0][(size_t)a * nc[0] + i] * C[1][(size_t)b * nc[1] + j] * C[2][(size_t)c * nc[2] + k] *
+                           C[3][(size_t)d * nc[3] + m] * v[(((size_t)i * nc[1] + j) * nc[2] + k) * nc[3] + m];
+            o[((a * ns[1] + b) * ns[2] + c) * ns[3] + d] = acc;
+          }
   }
 }
 

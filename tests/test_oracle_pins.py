@@ -370,3 +370,67 @@ def test_exchange_gradient_high_l_invariance():
     sm = oracle.exchange_energy(bb, D)
     fd = (sp - sm) / (2 * h)
     assert abs(g[1, 0] - fd) <= 1e-7 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------------------ solid harmonics (Eqs. solid2herm)
+def _sphere_moment(a, b, c):
+    """int x^a y^b z^c dOmega over the unit sphere (zero unless a, b, c are even)."""
+    if a % 2 or b % 2 or c % 2:
+        return 0.0
+    return 2.0 * math.gamma((a + 1) / 2) * math.gamma((b + 1) / 2) * math.gamma((c + 1) / 2) / math.gamma((a + b + c + 3) / 2)
+
+
+@pytest.mark.parametrize("l", range(7))
+def test_solid_harmonics_orthonormal_on_sphere(l):
+    """int S_lm S_lm' dOmega = 4 pi / (2l+1) delta_mm' (the angular norm of z^l), exact monomial moments."""
+    C = oracle.solid_coefs(l)
+    comps = [(ax, ay, l - ax - ay) for ax in range(l, -1, -1) for ay in range(l - ax, -1, -1)]
+    M = np.array([[_sphere_moment(a[0] + b[0], a[1] + b[1], a[2] + b[2]) for b in comps] for a in comps])
+    np.testing.assert_allclose(C @ M @ C.T, 4 * math.pi / (2 * l + 1) * np.eye(2 * l + 1), atol=1e-12)
+
+
+@pytest.mark.parametrize("l", range(7))
+def test_solid_harmonics_are_spherical_harmonics(l):
+    """S_lm(r) = c_l r^l Y_lm(theta, phi) with real Y built from scipy's complex harmonics; |c_l| equal
+    for every m (per-m sign is the convention)."""
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.Generator(np.random.PCG64(l))
+    pts = rng.normal(size=(40, 3))
+    r = np.linalg.norm(pts, axis=1)
+    theta = np.arccos(pts[:, 2] / r)
+    phi = np.arctan2(pts[:, 1], pts[:, 0])
+    C = oracle.solid_coefs(l)
+    comps = [(ax, ay, l - ax - ay) for ax in range(l, -1, -1) for ay in range(l - ax, -1, -1)]
+    mono = np.array([pts[:, 0] ** a * pts[:, 1] ** b * pts[:, 2] ** c for a, b, c in comps])
+    S = C @ mono
+    ratios = []
+    for m in range(-l, l + 1):
+        if hasattr(sp, "sph_harm_y"):
+            Y = sp.sph_harm_y(l, abs(m), theta, phi)
+        else:
+            Y = sp.sph_harm(abs(m), l, phi, theta)
+        if m > 0:
+            Yr = math.sqrt(2) * Y.real
+        elif m < 0:
+            Yr = math.sqrt(2) * Y.imag
+        else:
+            Yr = Y.real
+        ratio = S[m + l] / (r ** l * Yr)
+        np.testing.assert_allclose(ratio, ratio[0], rtol=1e-10)
+        ratios.append(abs(ratio[0]))
+    np.testing.assert_allclose(ratios, ratios[0], rtol=1e-12)
+    assert abs(ratios[0] - math.sqrt(4 * math.pi / (2 * l + 1))) < 1e-12
+
+
+def test_spherical_eri_transform():
+    """[ab|cd] over solid harmonics = C_a C_b C_c C_d applied to the Cartesian shellset, checked with
+    einsum; s and p shells are the Cartesian values reordered (y, z, x)."""
+    b, _ = _random_basis([2, 1, 3, 0], 44)
+    v, _ = oracle.eri4(b, [[0, 1, 2, 3]])
+    w, _ = oracle.eri4_sph(b, [[0, 1, 2, 3]])
+    cart = v.reshape(6, 3, 10, 1)
+    Cs = [oracle.solid_coefs(l) for l in (2, 1, 3, 0)]
+    ref = np.einsum("ai,bj,ck,dl,ijkl->abcd", *Cs, cart).reshape(-1)
+    np.testing.assert_allclose(w, ref, rtol=0, atol=1e-14 * np.max(np.abs(ref)))
+    np.testing.assert_allclose(w.reshape(5, 3, 7, 1)[:, [2, 0, 1]], np.einsum("ai,ck,ijkl->ajcl", Cs[0], Cs[2], cart),
+                               rtol=0, atol=1e-14 * np.max(np.abs(ref)))
