@@ -104,6 +104,18 @@ mdx_status mdx_sync(mdx_ctx* ctx, void* stream);
 mdx_status mdx_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
                     double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
 
+/* mdx_eri4 over real solid harmonics (the paper's basis, Eqs. solid2herm):
+ * shell of angular momentum l contributes 2l+1 functions S_lm, m = -l..l,
+ * S_lm = N_lm sum C x^.. y^.. z^.. with the standard real-solid-harmonic
+ * coefficients, each with the angular norm of z^l (so x^l-normalised
+ * contraction coefficients give normalised spherical functions). The
+ * Cartesian shellsets are evaluated first into context workspace and
+ * transformed index by index on the GPU. Output per quartet [a][b][c][d] in
+ * solid-harmonic components at out + out_offsets[q]. Same synchronisation and
+ * errors as mdx_eri4. */
+mdx_status mdx_eri4_sph(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
+                        int64_t out_capacity, int64_t* out_offsets, void* stream);
+
 /* 3-center integrals [a|cd] (Eq. def-acd): shell a from `aux`, shells c, d
  * from `orb`. triplets: [n][3] int32 (a, c, d). Output per triplet in
  * row-major [a][c][d] order at out + out_offsets[q]. The bra is a single

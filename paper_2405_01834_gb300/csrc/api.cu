@@ -206,6 +206,7 @@ struct mdx_batch {
   int64_t* offsets = nullptr;     // [n+1] in caller order
   struct Range { Plan* plan; int64_t begin, count; ClassKey key; };
   std::vector<Range> ranges;
+  std::vector<int64_t> qorig;     // caller index of each class-sorted quartet
   double model_flops = 0.0;
   double exec_fma = 0.0;
 };
@@ -322,7 +323,7 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
   mdx_status st;
   for (auto& kv : classes) {
     const int64_t b = (int64_t)qp_sorted.size();
-    for (int64_t q : kv.second) { qp_sorted.push_back(bt.qp[q]); qoff_sorted.push_back(bt.qoff[q]); }
+    for (int64_t q : kv.second) { qp_sorted.push_back(bt.qp[q]); qoff_sorted.push_back(bt.qoff[q]); B->qorig.push_back(q); }
     Plan* plan;
     if ((st = get_plan(c, kv.first, &plan, s)) != MDX_OK) return st;
     B->ranges.push_back({plan, b, (int64_t)kv.second.size(), kv.first});
@@ -535,6 +536,63 @@ mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets,
   mdx_status st = make_batch4(c, basis, quartets, n, &B, s);
   if (st != MDX_OK) return st;
   return run_once(c, B, out, out_capacity, out_offsets, s);
+}
+
+mdx_status mdx_eri4_sph(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
+                        int64_t out_capacity, int64_t* out_offsets, void* stream) {
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n < 0 || !out_offsets || (n > 0 && (!quartets || !out))) return fail(c, MDX_EINVAL, "invalid arguments");
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
+    return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
+  }
+  mdx_batch* B = nullptr;
+  mdx_status st = make_batch4(c, basis, quartets, n, &B, s);
+  if (st != MDX_OK) return st;
+  std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
+  // spherical sizes and offsets in caller order; scratch offsets in class order
+  HostBasis hb;
+  if ((st = fetch_basis(c, basis, hb, s)) != MDX_OK) return st;
+  std::vector<int32_t> hq;
+  if ((st = read_quartets(c, quartets, n, 4, hq, s)) != MDX_OK) return st;
+  std::vector<int64_t> soff(n + 1, 0);
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* s4 = &hq[(size_t)q * 4];
+    soff[q + 1] = soff[q] + (int64_t)(2 * hb.l[s4[0]] + 1) * (2 * hb.l[s4[1]] + 1) * (2 * hb.l[s4[2]] + 1) *
+                                (2 * hb.l[s4[3]] + 1);
+  }
+  if (soff[n] > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  std::vector<int64_t> coff_s(n), toff_s(n), ooff_s(n);
+  std::vector<int64_t> cart_off(n);
+  int64_t ttot = 0;
+  for (size_t i = 0; i < B->qorig.size(); ++i) {
+    const int64_t q = B->qorig[i];
+    const int32_t* s4 = &hq[(size_t)q * 4];
+    ooff_s[i] = soff[q];
+    toff_s[i] = ttot;
+    ttot += (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * (2 * hb.l[s4[2]] + 1) * (2 * hb.l[s4[3]] + 1);
+  }
+  double *d_cart, *d_tmp; int64_t *d_co, *d_to, *d_oo;
+  if ((st = ensure(c, "sph_cart", (size_t)B->total, &d_cart, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "sph_tmp", (size_t)std::max<int64_t>(ttot, 1), &d_tmp, s)) != MDX_OK) return st;
+  if ((st = upload(c, "sph_to", toff_s, &d_to, s)) != MDX_OK) return st;
+  if ((st = upload(c, "sph_oo", ooff_s, &d_oo, s)) != MDX_OK) return st;
+  d_co = B->qoff;   // the batch's class-sorted Cartesian offsets
+  cudaError_t e = cudaMemcpyAsync(out_offsets, soff.data(), soff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "offsets");
+  if ((st = batch_run(c, B, d_cart, nullptr, s)) != MDX_OK) return st;
+  for (auto& r : B->ranges) {
+    SphLaunch a{r.key.la, r.key.lb, r.key.lc, r.key.ld, r.count, d_cart, d_co + r.begin, d_tmp, d_to + r.begin, out,
+                d_oo + r.begin};
+    e = launch_cart2sph(a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "solid-harmonic transform");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "eri4_sph");
+  return check_device_error(c, s);
 }
 
 mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
@@ -1278,21 +1336,28 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
         a.mol_nao = X->molnao;
         X->launches.push_back(a);
         X->model_flops += model_flops_class(key) * (double)counts[b];
-        // persistent shape: teams of T threads filling the 512-thread block
+        // persistent shape: teams of T threads filling the 512-thread block, at most
+        // kPersistSmem of shared memory per block so that two blocks share an SM
         const int64_t tb = (int64_t)plan->d.team_doubles * 8;
-        int tpb = std::max(1, std::min<int>(kPersistBlock / plan->d.T, (int)((220 * 1024) / tb)));
+        int tpb = std::max(1, std::min<int>(kPersistBlock / plan->d.T, (int)(kPersistSmem / tb)));
         int p2 = 1;
         while (p2 * 2 <= tpb) p2 *= 2;
         tpb = p2;
         Plan* pp = plan;
-        if (kPersistBlock / tpb != plan->d.T) {
+        if (kPersistBlock / tpb != plan->d.T || tb * tpb > kPersistSmem) {
           std::unique_ptr<Plan> np2(new Plan());
           std::string err;
           PlanConfig cfg{};
           auto tc = c->tuned.find(key);
           if (tc != c->tuned.end()) cfg = tc->second;
           cfg.T = kPersistBlock / tpb;
-          if (!build_plan(key, cfg, *np2, err)) return fail(c, MDX_EUNSUPPORTED, "persistent planner: " + err);
+          cfg.budget = std::min<int>(cfg.budget, (int)(kPersistSmem / tpb));
+          if (!build_plan(key, cfg, *np2, err)) {        // fall back to one full-size team per block
+            cfg = PlanConfig{};
+            cfg.T = kPersistBlock;
+            tpb = 1;
+            if (!build_plan(key, cfg, *np2, err)) return fail(c, MDX_EUNSUPPORTED, "persistent planner: " + err);
+          }
           if ((int64_t)np2->d.team_doubles * 8 * tpb > 226 * 1024) return fail(c, MDX_EUNSUPPORTED, "persistent shape");
           if ((st = upload_plan(c, np2.get(), s)) != MDX_OK) return st;
           pp = np2.get();
@@ -1302,8 +1367,9 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
         ap.plan = pp->d;
         X->plaunches.push_back(ap);
         smem = std::max<int64_t>(smem, (int64_t)pp->d.team_doubles * 8 * tpb);
-        for (int64_t q0 = 0; q0 < (int64_t)counts[b]; q0 += tpb) {
-          const int cnt = (int)std::min<int64_t>(tpb, (int64_t)counts[b] - q0);
+        const int per_item = tpb * kPersistRounds;
+        for (int64_t q0 = 0; q0 < (int64_t)counts[b]; q0 += per_item) {
+          const int cnt = (int)std::min<int64_t>(per_item, (int64_t)counts[b] - q0);
           items.push_back(WorkItem{(int32_t)(X->plaunches.size() - 1), cnt, q0});
           cost.push_back(pp->exec_fma * cnt);
         }

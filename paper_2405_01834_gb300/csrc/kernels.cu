@@ -30,6 +30,9 @@ __constant__ double c_dint[64];
 __constant__ double c_gh[kBoysRow];
 // Cartesian components of shells l <= 7 in library order, packed x | y << 8 | z << 16
 __constant__ uint32_t c_cart[8][36];
+// real solid harmonics l <= 6 as Cartesian polynomials: c_sph[c_sph_off[l] + (m+l)*ncart(l) + k]
+__constant__ double c_sph[840];
+__constant__ int c_sph_off[kLmax + 2];
 
 cudaError_t kernel_attributes_init();
 
@@ -596,12 +599,15 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(const PersistLaunc
     const WorkItem w = pl.items[it];
     const QuartetLaunch& a = pl.launches[w.launch];
     const int T = a.plan.T;
+    const int tpb = kPersistBlock / T;
     const int team = threadIdx.x / T;
     const int tl = threadIdx.x - team * T;
     double* ws = smem + (size_t)team * a.plan.team_doubles;
-    const bool active = team < w.count;
-    const int64_t q = w.begin + (active ? team : 0);
-    quartet_body<true>(a, ws, q, active, tl, 0xffffffffu);
+    for (int64_t sub = 0; sub < w.count; sub += tpb) {   // an item holds a few rounds of teams
+      const bool active = team < w.count - sub;
+      const int64_t q = w.begin + sub + (active ? team : 0);
+      quartet_body<true>(a, ws, q, active, tl, 0xffffffffu);
+    }
   }
 }
 
@@ -731,6 +737,71 @@ cudaError_t launch_multi_k(double* const* K, const int32_t* nao, int32_t nmol, i
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------- solid harmonics
+// y[j] = sum_i C[j][i] x[i*stride] over the non-zero coefficients of one l.
+__device__ __forceinline__ double sph_row(const double* __restrict__ C, int nc, int j, const double* x, int64_t stride) {
+  double acc = 0.0;
+  for (int i = 0; i < nc; ++i) {
+    const double cv = C[j * nc + i];
+    if (cv != 0.0) acc = fma(cv, x[i * stride], acc);
+  }
+  return acc;
+}
+
+// Cartesian -> real-solid-harmonic transform of one class of shellsets, one
+// CTA per shellset: pass A turns every row [ab] of [ab][cd] into [ab][c'd']
+// (scratch), pass B every column [c'd'] of that into [a'b'][c'd'].
+__global__ void __launch_bounds__(256) k_cart2sph(const SphLaunch a) {
+  extern __shared__ __align__(16) double sb[];
+  const int64_t q = blockIdx.x;
+  if (q >= a.nq) return;
+  const int nca = d_ncart(a.la), ncb = d_ncart(a.lb), ncc = d_ncart(a.lc), ncd = d_ncart(a.ld);
+  const int nsa = 2 * a.la + 1, nsb = 2 * a.lb + 1, nsc = 2 * a.lc + 1, nsd = 2 * a.ld + 1;
+  const double* Ca = c_sph + c_sph_off[a.la];
+  const double* Cb = c_sph + c_sph_off[a.lb];
+  const double* Cc = c_sph + c_sph_off[a.lc];
+  const double* Cd = c_sph + c_sph_off[a.ld];
+  const double* in = a.cart + a.coff[q];
+  double* t1 = a.tmp + a.toff[q];
+  double* out = a.out + a.ooff[q];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* buf = sb + warp * (28 * 13);
+  const int nk_s = nsc * nsd;
+  for (int row = warp; row < nca * ncb; row += nw) {
+    const double* r = in + (int64_t)row * ncc * ncd;
+    for (int e = lane; e < ncc * nsd; e += 32) {
+      const int c = e / nsd, dp = e - c * nsd;
+      buf[c * nsd + dp] = sph_row(Cd, ncd, dp, r + c * ncd, 1);
+    }
+    __syncwarp();
+    for (int e = lane; e < nk_s; e += 32) {
+      const int cp = e / nsd, dp = e - cp * nsd;
+      t1[(int64_t)row * nk_s + e] = sph_row(Cc, ncc, cp, buf + dp, nsd);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int col = warp; col < nk_s; col += nw) {
+    for (int e = lane; e < nca * nsb; e += 32) {
+      const int ai = e / nsb, bp = e - ai * nsb;
+      buf[ai * nsb + bp] = sph_row(Cb, ncb, bp, t1 + (int64_t)(ai * ncb) * nk_s + col, nk_s);
+    }
+    __syncwarp();
+    for (int e = lane; e < nsa * nsb; e += 32) {
+      const int ap = e / nsb, bp = e - ap * nsb;
+      out[(int64_t)e * nk_s + col] = sph_row(Ca, nca, ap, buf + bp, nsb);
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_cart2sph(const SphLaunch& a, cudaStream_t s) {
+  if (a.nq <= 0) return cudaSuccess;
+  const size_t shm = 8 * 28 * 13 * sizeof(double);
+  k_cart2sph<<<(unsigned)a.nq, 256, shm, s>>>(a);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- Schwarz
 __global__ void k_schwarz_reduce(const int64_t* __restrict__ off, const int32_t* __restrict__ nab, int64_t n,
                                  const double* __restrict__ vals, double* __restrict__ Q) {
@@ -773,6 +844,17 @@ cudaError_t kernel_attributes_init() {
   }
   e = cudaMemcpyToSymbol(c_cart, cart, sizeof(cart));
   if (e != cudaSuccess) return e;
+  {
+    const auto tabs = build_solid_tables(kLmax);
+    std::vector<double> flat;
+    int offs[kLmax + 2];
+    for (int l = 0; l <= kLmax; ++l) { offs[l] = (int)flat.size(); flat.insert(flat.end(), tabs[l].begin(), tabs[l].end()); }
+    offs[kLmax + 1] = (int)flat.size();
+    if (flat.size() > 840) return cudaErrorInvalidValue;
+    e = cudaMemcpyToSymbol(c_sph, flat.data(), flat.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sph_off, offs, sizeof(offs));
+    if (e != cudaSuccess) return e;
+  }
   const int maxshm = 227 * 1024;
   e = cudaFuncSetAttribute(k_quartets<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
   if (e != cudaSuccess) return e;

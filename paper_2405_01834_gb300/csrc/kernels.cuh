@@ -71,9 +71,11 @@ struct QuartetLaunch {
 
 // Persistent launch over work items of many QuartetLaunch descriptors.
 constexpr int kPersistBlock = 512;
+constexpr int64_t kPersistSmem = 110 * 1024;   // shared memory per persistent block (two blocks per SM)
+constexpr int kPersistRounds = 4;              // rounds of teams per work item
 struct WorkItem {
   int32_t launch;   // index into PersistLaunch::launches
-  int32_t count;    // quartets of this item (one per team, <= teams per block)
+  int32_t count;    // quartets of this item (rounds of one quartet per team)
   int64_t begin;    // first quartet (index into that launch's qpairs)
 };
 struct PersistLaunch {
@@ -111,6 +113,19 @@ cudaError_t launch_symmetrize(double* K, int32_t nao, cudaStream_t s);
 cudaError_t launch_multi_k(double* const* K, const int32_t* nao, int32_t nmol, int64_t max_nao, bool zero,
                            cudaStream_t s);
 cudaError_t kernel_attributes_init();
+
+// Cartesian -> real solid harmonic transform of one class of 4-center shellsets.
+struct SphLaunch {
+  int32_t la, lb, lc, ld;
+  int64_t nq;
+  const double* cart;        // Cartesian shellsets
+  const int64_t* coff;       // per shellset: offset in cart
+  double* tmp;               // scratch [ab][c'd'] per shellset
+  const int64_t* toff;
+  double* out;               // solid-harmonic shellsets [a'][b'][c'][d'], m = -l..l
+  const int64_t* ooff;
+};
+cudaError_t launch_cart2sph(const SphLaunch& a, cudaStream_t s);
 
 // Schwarz reduction: Q[p] = sqrt(max_ab |diag of shellset p|).
 cudaError_t launch_schwarz_reduce(const int64_t* off, const int32_t* nab, int64_t n, const double* vals,

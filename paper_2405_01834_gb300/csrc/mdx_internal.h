@@ -135,3 +135,9 @@ struct PlanConfig {
 bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::string& err);
 
 }  // namespace mdx
+
+namespace mdx {
+// Real solid harmonics as Cartesian polynomials, rows m = -l..l, columns the
+// Cartesian components in library order: tables[l][(m+l)*ncart(l) + k].
+std::vector<std::vector<double>> build_solid_tables(int lmax);
+}  // namespace mdx

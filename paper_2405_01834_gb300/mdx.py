@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_sync.restype = I32
     lib.mdx_eri4.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
     lib.mdx_eri4.restype = I32
+    lib.mdx_eri4_sph.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
+    lib.mdx_eri4_sph.restype = I32
     lib.mdx_eri3.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
     lib.mdx_eri3.restype = I32
     lib.mdx_schwarz.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, P]
@@ -203,6 +205,21 @@ class Engine:
         st = self.lib.mdx_eri4(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), n, out.data_ptr(), out.numel(),
                                offs.data_ptr(), _stream())
         self._check(st, "mdx_eri4")
+        return out, offs
+
+    def eri4_sph(self, basis: DeviceBasis, quartets, out: torch.Tensor = None):
+        """[ab|cd] over real solid harmonics (m = -l..l per shell). Returns (values, offsets)."""
+        q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
+        n = q.shape[0]
+        if out is None:
+            qn = np.clip(q.cpu().numpy().astype(np.int64), 0, len(basis.nc) - 1)
+            ns = 2 * basis.host.l.astype(np.int64) + 1
+            tot = int(np.sum(ns[qn[:, 0]] * ns[qn[:, 1]] * ns[qn[:, 2]] * ns[qn[:, 3]])) if n else 0
+            out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        st = self.lib.mdx_eri4_sph(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), n, out.data_ptr(), out.numel(),
+                                   offs.data_ptr(), _stream())
+        self._check(st, "mdx_eri4_sph")
         return out, offs
 
     def eri3(self, aux: DeviceBasis, orb: DeviceBasis, triplets, out: torch.Tensor = None):

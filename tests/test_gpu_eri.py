@@ -179,3 +179,16 @@ def test_autotuned_batch_matches(eng):
     ref, _ = oracle.eri4(b, q)
     parity.check(w.cpu().numpy(), ref, oracle.eri4(b, q, precision=1)[0], "autotuned", off.cpu().numpy())
     bt.close()
+
+
+@pytest.mark.parametrize("lq", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 1, 0, 3), (3, 3, 2, 2), (4, 2, 4, 1), (6, 5, 6, 4)])
+def test_solid_harmonic_eri4(eng, lq):
+    """mdx_eri4_sph against the oracle's spherical shellsets (solid harmonics, m = -l..l)."""
+    K = (1, 2, 1, 2) if max(lq) < 4 else (1, 1, 1, 1)
+    b, q = inputs.class_sweep(lq, n_bra=3, n_ket=2, seed=13, K=K)
+    db = mdx.DeviceBasis(b)
+    v, off = eng.eri4_sph(db, q)
+    torch.cuda.synchronize()
+    ref, roff = oracle.eri4_sph(b, q)
+    assert np.array_equal(off.cpu().numpy(), roff)
+    parity.check(v.cpu().numpy()[: roff[-1]], ref, None, "solid %s" % (lq,))
