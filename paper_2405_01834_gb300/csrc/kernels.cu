@@ -590,14 +590,23 @@ __global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaun
 __global__ void __launch_bounds__(kPersistBlock) k_persistent(const PersistLaunch pl) {
   extern __shared__ __align__(16) double smem[];
   __shared__ long long s_item;
+  __shared__ __align__(16) QuartetLaunch s_launch;   // the item's descriptor, read in every inner loop
+  int cur = -1;
   for (;;) {
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(pl.counter, 1ull);
     __syncthreads();
     const long long it = s_item;
-    __syncthreads();
     if (it >= pl.nitems) return;
     const WorkItem w = pl.items[it];
-    const QuartetLaunch& a = pl.launches[w.launch];
+    if (w.launch != cur) {   // uniform across the block
+      const int nw = (int)(sizeof(QuartetLaunch) / sizeof(int));
+      const int* src = reinterpret_cast<const int*>(pl.launches + w.launch);
+      int* dst = reinterpret_cast<int*>(&s_launch);
+      for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+      cur = w.launch;
+    }
+    __syncthreads();
+    const QuartetLaunch& a = s_launch;
     const int T = a.plan.T;
     const int tpb = kPersistBlock / T;
     const int team = threadIdx.x / T;

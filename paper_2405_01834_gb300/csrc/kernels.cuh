@@ -69,6 +69,8 @@ struct QuartetLaunch {
   const int32_t* mol_nao;
 };
 
+static_assert(sizeof(QuartetLaunch) % sizeof(int) == 0, "descriptor copied word by word");
+
 // Persistent launch over work items of many QuartetLaunch descriptors.
 constexpr int kPersistBlock = 512;
 constexpr int64_t kPersistSmem = 110 * 1024;   // shared memory per persistent block (two blocks per SM)

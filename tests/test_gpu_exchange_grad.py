@@ -86,3 +86,39 @@ def test_autograd_function(eng):
     np.testing.assert_allclose(gD.cpu().numpy(), -2.0 * K, rtol=0, atol=1e-11 * np.max(np.abs(K)))
     E = float(E.detach())
     assert abs(E + float(np.sum(D.detach().cpu().numpy() * K))) <= 1e-11 * abs(E)
+
+
+def test_gradient_ten_atom_cluster_fd_eight_atoms(eng):
+    """Config-5 shape at reduced size: a 10-atom heavy/light cluster (quadruple-zeta-like shells,
+    Schwarz x density screening at 1e-11); dE_x/dR against central differences of the GPU forward
+    energy on 8 seeded atoms (one seeded axis each), and translational invariance."""
+    b = inputs.molecule(seed=1005, n_atoms=10)
+    D = inputs.density(b.nao, 1005)
+    tau = 1e-11
+    db = mdx.DeviceBasis(b)
+    pairs = _pairs(b)
+    Q = eng.schwarz(db, pairs)
+    g, E = eng.exchange_grad(db, pairs, Q, torch.from_numpy(D), tau=tau, alpha=-1.0, n_atoms=b.n_atoms)
+    g = g.cpu().numpy()
+    np.testing.assert_allclose(g.sum(axis=0), 0.0, atol=1e-9 * np.max(np.abs(g)))
+    rng = np.random.Generator(np.random.PCG64(1005))
+    atoms = rng.choice(b.n_atoms, 8, replace=False)
+    axes = rng.integers(0, 3, 8)
+    h = 1e-4
+
+    def energy(bb):
+        dbb = mdx.DeviceBasis(bb)
+        Qb = eng.schwarz(dbb, pairs)
+        K = eng.exchange(dbb, pairs, Qb, torch.from_numpy(D), tau)
+        return -float(torch.sum(torch.from_numpy(D).cuda() * K).cpu())
+
+    for A, x in zip(atoms, axes):
+        vals = []
+        for d in (h, -h):
+            bb = inputs.molecule(seed=1005, n_atoms=10)
+            bb.center = bb.center.copy()
+            bb.center[bb.atom == A, x] += d
+            vals.append(energy(bb))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        # screening at tau moves E by far less than the FD resolution here
+        assert abs(g[A, x] - fd) <= 1e-6 * max(1.0, abs(fd)), (A, x, g[A, x], fd)
