@@ -869,7 +869,8 @@ cudaError_t kernel_attributes_init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_quartets<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm - 64);
+  // the persistent kernel also holds ~0.5 KB of static shared memory (item index, launch descriptor)
+  e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm - 1024);
   return e;
 }
 
