@@ -55,8 +55,12 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the per-class team-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch"],
-                    help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad"],
+                    help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules; "
+                         "df: per-class 3-center rates on the density-fitting cluster; grad: exchange energy "
+                         "and its nuclear gradient against the exchange build alone")
+    ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
+    ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
     ap.add_argument("--n-mol", type=int, default=64)
     ap.add_argument("--atoms", default="2,5", help="xbatch: atoms per molecule, uniform in [lo,hi]")
     ap.add_argument("--tau", type=float, default=1e-11)
@@ -259,6 +263,27 @@ def xbatch_main(args):
             xb.run(persistent=True)
     torch.cuda.synchronize()
     res["persistent_graph_ms"] = round(timed(g.replay), 3)
+    # per-class breakdown: every class launch alone, bracketed by events (one pass after the runs above)
+    n_l = xb.n_class_launches
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_l + 1)]
+    evs[0].record(stream)
+    for i in range(n_l):
+        xb.run_class(i)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    by_class = {}
+    for i in range(n_l):
+        lk, nq, mf = xb.launch_info(i)
+        key = "[%d%d|%d%d]" % lk[:4]
+        r = by_class.setdefault(key, [0.0, 0, 0.0])
+        r[0] += evs[i].elapsed_time(evs[i + 1])
+        r[1] += nq
+        r[2] += mf
+    tot_ms = sum(r[0] for r in by_class.values())
+    per_class = [{"class": k, "ms": round(r[0], 3), "share": round(r[0] / tot_ms, 4), "quartets": r[1],
+                  "quartets_per_s": round(r[1] / (r[0] * 1e-3), 1),
+                  "model_gflops": round(r[2] / (r[0] * 1e-3) * 1e-9, 2)}
+                 for k, r in sorted(by_class.items(), key=lambda kv: -kv[1][0])]
     eng.sync()
     best = min(res["per_class_launches_ms"], res["persistent_ms"], res["persistent_graph_ms"])
     line = {"metric": "batched exchange build: model FP64 GFLOP/s and shell quartets/s", "unit": UNIT,
@@ -269,10 +294,128 @@ def xbatch_main(args):
                        "n_ao_total": int(sum(b.nao for b in mols))},
             "quartets": xb.n_quartets, "model_flops": xb.model_flops, "work_items": xb.n_items,
             "class_launches": xb.n_class_launches, "modes_ms": res,
-            "quartets_per_s": {k.replace("_ms", ""): round(xb.n_quartets / (v * 1e-3), 1) for k, v in res.items()}}
+            "quartets_per_s": {k.replace("_ms", ""): round(xb.n_quartets / (v * 1e-3), 1) for k, v in res.items()},
+            "per_class": per_class}
     print(json.dumps(line), flush=True)
     xb.close()
     eng.close()
+
+
+def _event_ms(torch, stream, fn, steps, warmup):
+    for _ in range(max(1, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def df_main(args):
+    """3-center [a|cd] rates per class on the density-fitting cluster (100 atoms, orbital 4s3p2d1f at
+    K 6/3/1/1, auxiliary s..i): orbital pairs Schwarz-screened at 1e-12, then for every (l_a | l_c l_d)
+    class a seeded grid of up to --df-sample triplets (auxiliary shells x kept pairs of the class) is
+    timed alone; the full tensor's time is extrapolated from the per-class rates."""
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    aux, orb = inputs.df_cluster()
+    dorb, daux = mdx.DeviceBasis(orb), mdx.DeviceBasis(aux)
+    ii, jj = np.tril_indices(orb.n_shells)
+    pairs = np.stack([ii, jj], axis=1).astype(np.int32)
+    Q = eng.schwarz(dorb, pairs).cpu().numpy()
+    kept = pairs[Q >= 1e-12]
+    lo = np.asarray(orb.l); la_aux = np.asarray(aux.l)
+    rng = np.random.Generator(np.random.PCG64(1003))
+    stream = torch.cuda.current_stream()
+    rows, tot_ms, tot_flops, full_s, full_trip = [], 0.0, 0.0, 0.0, 0
+    for la in range(int(la_aux.max()) + 1):
+        a_sh = np.where(la_aux == la)[0]
+        for lc in range(int(lo.max()) + 1):
+            for ld in range(int(lo.max()) + 1):
+                pc = kept[(lo[kept[:, 0]] == lc) & (lo[kept[:, 1]] == ld)]
+                if len(pc) == 0 or len(a_sh) == 0:
+                    continue
+                na = min(len(a_sh), 64)
+                npr = max(1, min(len(pc), args.df_sample // na))
+                A = rng.choice(a_sh, na, replace=False)
+                Pp = pc[rng.choice(len(pc), npr, replace=False)]
+                trip = np.stack([np.repeat(A, npr), np.tile(Pp[:, 0], na), np.tile(Pp[:, 1], na)],
+                                axis=1).astype(np.int32)
+                bt = eng.batch_eri3(daux, dorb, trip)
+                out = torch.empty(max(bt.total, 1), dtype=torch.float64, device="cuda")
+                ms = _event_ms(torch, stream, lambda: bt.run(out), args.steps, args.warmup)
+                Kc, Kd = int(orb.nprim[Pp[0, 0]]), int(orb.nprim[Pp[0, 1]])
+                n = len(trip)
+                f = bt.model_flops
+                full = len(a_sh) * len(pc)
+                rows.append({"class": "[%d|%d%d]" % (la, lc, ld), "K_cd": Kc * Kd, "triplets": n,
+                             "ms": round(ms, 4), "triplets_per_s": round(n / (ms * 1e-3), 1),
+                             "model_gflops": round(f / (ms * 1e-3) * 1e-9, 2),
+                             "executed_frac": round(2 * bt.exec_fma / (ms * 1e-3) / peak_fp64(torch), 4),
+                             "full_tensor_triplets": full})
+                tot_ms += ms; tot_flops += f
+                full_s += full / (n / (ms * 1e-3)); full_trip += full
+                bt.close()
+    eng.sync()
+    line = {"metric": "3-center [a|cd] integrals: model FP64 GFLOP/s and triplets/s per class", "unit": UNIT,
+            "value": round(tot_flops / (tot_ms * 1e-3) * 1e-9, 3), "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "density-fitting cluster: 100 atoms (>= 2.8 bohr apart), orbital 4s3p2d1f "
+                                   "(K 6/3/1/1), auxiliary s..i (K 1, even-tempered ratio 2.5); orbital pairs "
+                                   "kept at Q >= 1e-12; per class a grid of <= 64 auxiliary shells x kept pairs",
+                       "orbital_pairs": int(len(pairs)), "kept_pairs": int(len(kept)),
+                       "aux_shells": int(aux.n_shells)},
+            "full_tensor": {"triplets": int(full_trip), "estimated_s": round(full_s, 3)},
+            "per_class": rows}
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
+def grad_main(args):
+    """Exchange energy and its nuclear gradient (adjoint kernel) on one cluster molecule (heavy
+    5s4p3d2f1g / light 4s3p2d1f, K = 6 s shells, D = C C^T, tau): the gradient call against the
+    exchange build alone on the same quartets (whole calls, host screening included)."""
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    mol = inputs.molecule(1005, args.grad_atoms)
+    db = mdx.DeviceBasis(mol)
+    D = torch.from_numpy(inputs.density(mol.nao, 1005)).cuda()
+    pairs = torch.tensor([(i, j) for i in range(mol.n_shells) for j in range(i + 1)], dtype=torch.int32,
+                         device="cuda")
+    Q = eng.schwarz(db, pairs)
+    stream = torch.cuda.current_stream()
+    ms_k = _event_ms(torch, stream, lambda: eng.exchange(db, pairs, Q, D, args.tau), args.steps, args.warmup)
+    nq = eng.last_quartet_count()
+    res = {}
+    ms_g = _event_ms(torch, stream, lambda: res.__setitem__("g", eng.exchange_grad(db, pairs, Q, D, args.tau)),
+                     args.steps, args.warmup)
+    eng.sync()
+    g = res["g"][0] if isinstance(res["g"], tuple) else res["g"]
+    line = {"metric": "exchange energy nuclear gradient (adjoint) vs exchange build: ms and shell quartets/s",
+            "unit": "ms", "value": round(ms_g, 3), "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "cluster molecule of %d atoms (heavy 5s4p3d2f1g / light 4s3p2d1f, K = 6 s "
+                                   "shells), D = C C^T, tau = %g" % (args.grad_atoms, args.tau),
+                       "n_ao": int(mol.nao), "n_shells": int(mol.n_shells)},
+            "quartets": nq, "exchange_ms": round(ms_k, 3), "gradient_ms": round(ms_g, 3),
+            "gradient_over_exchange": round(ms_g / ms_k, 3),
+            "quartets_per_s": {"exchange": round(nq / (ms_k * 1e-3), 1), "gradient": round(nq / (ms_g * 1e-3), 1)},
+            "translational_residual": float(torch.as_tensor(g).sum(0).abs().max())}
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
+def peak_fp64(torch, sm_mhz: float = 2070.0):
+    """FP64 pipe peak of this GPU at the given SM clock (default: the GB300 maximum), FLOP/s."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return FP64_FLOP_PER_CLK_SM * props.multi_processor_count * sm_mhz * 1e6
 
 
 def main():
@@ -281,6 +424,10 @@ def main():
         return reference_main(args)
     if args.workload == "xbatch":
         return xbatch_main(args)
+    if args.workload == "df":
+        return df_main(args)
+    if args.workload == "grad":
+        return grad_main(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

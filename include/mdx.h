@@ -248,6 +248,19 @@ mdx_status mdx_xbatch_info(const mdx_xbatch* xbatch, int64_t* n_quartets, int64_
  * the kernels enqueued. */
 mdx_status mdx_xbatch_run(mdx_ctx* ctx, mdx_xbatch* xbatch, int32_t persistent, int32_t* n_launches, void* stream);
 
+/* Per-class launch i of a batch (0 <= i < n_class_launches): its class
+ * lk = {la, lb, lc, ld, K_ab, K_cd} (K = primitive pairs of the bra / ket
+ * shell pairs), its kept quartets and their Table-1 model FLOPs (any output
+ * pointer may be NULL). MDX_EINVAL for an index out of range. */
+mdx_status mdx_xbatch_launch_info(const mdx_xbatch* xbatch, int32_t i, int32_t* lk, int64_t* n_quartets,
+                                  double* model_flops);
+
+/* Enqueue only the integral kernel (with fused digestion into the K_m) of
+ * per-class launch i, without zeroing or symmetrising K_m: for timing one
+ * class of a batch. Running every i between the zeroing and symmetrisation of
+ * mdx_xbatch_run gives the same K_m. */
+mdx_status mdx_xbatch_run_class(mdx_ctx* ctx, mdx_xbatch* xbatch, int32_t i, void* stream);
+
 /* Free a batched exchange (NULL allowed). No work of it may still be running. */
 void mdx_xbatch_destroy(mdx_xbatch* xbatch);
 

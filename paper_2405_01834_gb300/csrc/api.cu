@@ -231,6 +231,8 @@ struct mdx_xbatch {
   double *recs = nullptr, *recs_s = nullptr;
   int2* quart = nullptr;
   std::vector<QuartetLaunch> launches, plaunches;
+  std::vector<ClassKey> lkey;          // class of each per-class launch
+  std::vector<double> lflops;          // its Table-1 model FLOPs
   QuartetLaunch* d_plaunches = nullptr;
   WorkItem* items = nullptr;
   unsigned long long* counter = nullptr;
@@ -1335,7 +1337,9 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
         a.mol_K = X->molK;
         a.mol_nao = X->molnao;
         X->launches.push_back(a);
-        X->model_flops += model_flops_class(key) * (double)counts[b];
+        X->lkey.push_back(key);
+        X->lflops.push_back(model_flops_class(key) * (double)counts[b]);
+        X->model_flops += X->lflops.back();
         // persistent shape: teams of T threads filling the 512-thread block, at most
         // kPersistSmem of shared memory per block so that two blocks share an SM
         const int64_t tb = (int64_t)plan->d.team_doubles * 8;
@@ -1434,6 +1438,26 @@ mdx_status mdx_xbatch_run(mdx_ctx* c, mdx_xbatch* xb, int32_t persistent, int32_
   ++nl;
   if (e != cudaSuccess) return cuda_fail(c, e, "batched exchange launch");
   if (n_launches) *n_launches = nl;
+  return MDX_OK;
+}
+
+mdx_status mdx_xbatch_launch_info(const mdx_xbatch* xb, int32_t i, int32_t* lk, int64_t* n_quartets,
+                                  double* model_flops) {
+  if (!xb || i < 0 || i >= (int32_t)xb->launches.size()) return MDX_EINVAL;
+  const ClassKey& k = xb->lkey[i];
+  if (lk) {
+    lk[0] = k.la; lk[1] = k.lb; lk[2] = k.lc; lk[3] = k.ld; lk[4] = k.Kb; lk[5] = k.Kk;
+  }
+  if (n_quartets) *n_quartets = xb->launches[i].nq;
+  if (model_flops) *model_flops = xb->lflops[i];
+  return MDX_OK;
+}
+
+mdx_status mdx_xbatch_run_class(mdx_ctx* c, mdx_xbatch* xb, int32_t i, void* stream) {
+  if (!c || !xb || xb->ctx != c || i < 0 || i >= (int32_t)xb->launches.size()) return MDX_EINVAL;
+  cudaSetDevice(c->device);
+  const cudaError_t e = launch_quartets(xb->launches[i], (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batched exchange class launch");
   return MDX_OK;
 }
 

@@ -27,7 +27,7 @@ namespace mdx {
 // int->double conversion on the FP64 pipe
 __constant__ double c_dint[64];
 // sqrt(pi)/2 * (2m-1)!! / 2^m: F_m(T) = c_gh[m] T^(-m-1/2) for large T
-__constant__ double c_gh[kBoysRow];
+__constant__ double c_gh[kBoysOrders];
 // Cartesian components of shells l <= 7 in library order, packed x | y << 8 | z << 16
 __constant__ uint32_t c_cart[8][36];
 // real solid harmonics l <= 6 as Cartesian polynomials: c_sph[c_sph_off[l] + (m+l)*ncart(l) + k]
@@ -169,38 +169,50 @@ __device__ void compute_R(const QuartetLaunch& a, double* ws, int tl, unsigned m
   double* G = ws + P.o_G;
   const double* rb = ws + P.o_recb;
   const double* rk = ws + P.o_reck;
-  // every lane derives the quartet scalars (cheap, avoids a barrier)
-  const double zp = rb[0], izp = rb[1], zq = rk[0], izq = rk[1];
+  // every lane needs P - Q for the R levels; the Boys lanes (m = tl, tl + T,
+  // ... <= L) also derive rho, T and the prefactor (no barrier needed)
   const double PQx = rb[2] - rk[2], PQy = rb[3] - rk[3], PQz = rb[4] - rk[4];
-  const double s = zp + zq;
-  const double rs = rsqrt(s);
-  const double rho = zp * zq * rs * rs;
-  const double Tb = rho * (PQx * PQx + PQy * PQy + PQz * PQz);
-  // 2 pi^(5/2) / (zp zq sqrt(zp+zq)) * c_a c_b K_ab * c_c c_d K_cd
-  const double pref = 34.986836655249725693 * izp * izq * rs * rb[5] * rk[5];
   if (tl == 0) { scal[0] = PQx; scal[1] = PQy; scal[2] = PQz; }
-  if (Tb < kBoysTmax) {
-    const int i = __double2int_rn(Tb * kBoysInvH);
-    const double d = Tb - (double)i * (1.0 / kBoysInvH);
-    // c_k = (-d)^k / k!
-    double c[kBoysTerms];
-    c[0] = 1.0;
-    const double nd = -d;
-#pragma unroll
-    for (int k = 1; k < kBoysTerms; ++k) c[k] = c[k - 1] * nd * (1.0 / (double)k);
-    const double* row = a.boys + (size_t)i * kBoysRow;
+  if (tl <= L) {
+    const double zp = rb[0], izp = rb[1], zq = rk[0], izq = rk[1];
+    const double s = zp + zq;
+    const double rs = rsqrt(s);
+    const double rho = zp * zq * rs * rs;
+    const double Tb = rho * (PQx * PQx + PQy * PQy + PQz * PQz);
+    // 2 pi^(5/2) / (zp zq sqrt(zp+zq)) * c_a c_b K_ab * c_c c_d K_cd
+    const double pref = 34.986836655249725693 * izp * izq * rs * rb[5] * rk[5];
     const double m2r = -2.0 * rho;
-    for (int m = tl; m <= L; m += T) {
-      double f = 0.0;
-#pragma unroll
-      for (int k = kBoysTerms - 1; k >= 0; --k) f = fma(c[k], __ldg(row + m + k), f);
-      G[m] = pref * ipow(m2r, m) * f;
+    if (Tb < kBoysTmax) {
+      const int i = __double2int_rn(Tb * kBoysInvH);
+      const double nd = (double)i * (1.0 / kBoysInvH) - Tb;   // -d
+      // (-2 rho)^m pref, stepped by (-2 rho)^T from lane to lane's next m
+      double pw = pref * ipow(m2r, tl);
+      const double step = T <= L ? ipow(m2r, T) : 1.0;
+      const double* row = a.boys + (size_t)i * kBoysRow;
+      for (int m = tl; m <= L; m += T) {
+        const double2* c = reinterpret_cast<const double2*>(row + m * kBoysTerms);
+        const double2 c01 = __ldg(c), c23 = __ldg(c + 1), c45 = __ldg(c + 2), c67 = __ldg(c + 3);
+        double f = fma(c67.y, nd, c67.x);
+        f = fma(f, nd, c45.y);
+        f = fma(f, nd, c45.x);
+        f = fma(f, nd, c23.y);
+        f = fma(f, nd, c23.x);
+        f = fma(f, nd, c01.y);
+        f = fma(f, nd, c01.x);
+        G[m] = pw * f;
+        pw *= step;
+      }
+    } else {
+      // F_m(T) = Gamma(m+1/2) / (2 T^(m+1/2)); neglected exp(-T) terms < 1e-17 relative for m <= 25
+      const double t1 = rsqrt(Tb);
+      const double x = m2r * t1 * t1;
+      double pw = pref * t1 * ipow(x, tl);
+      const double step = T <= L ? ipow(x, T) : 1.0;
+      for (int m = tl; m <= L; m += T) {
+        G[m] = c_gh[m] * pw;
+        pw *= step;
+      }
     }
-  } else {
-    // F_m(T) = Gamma(m+1/2) / (2 T^(m+1/2)); neglected exp(-T) terms < 1e-17 relative for m <= 25
-    const double t1 = rsqrt(Tb);
-    const double x = -2.0 * rho * t1 * t1;
-    for (int m = tl; m <= L; m += T) G[m] = pref * c_gh[m] * t1 * ipow(x, m);
   }
   team_sync<CTA>(mask);
   double* R0 = ws + P.o_R0;
@@ -836,10 +848,10 @@ cudaError_t kernel_attributes_init() {
   for (int i = 0; i < 64; ++i) dint[i] = (double)i;
   cudaError_t e = cudaMemcpyToSymbol(c_dint, dint, sizeof(dint));
   if (e != cudaSuccess) return e;
-  double gh[kBoysRow];
+  double gh[kBoysOrders];
   // sqrt(pi)/2 * (2m-1)!! / 2^m
   double v = 0.88622692545275801365;
-  for (int m = 0; m < kBoysRow; ++m) {
+  for (int m = 0; m < kBoysOrders; ++m) {
     gh[m] = v;
     v *= (2.0 * m + 1.0) * 0.5;
   }

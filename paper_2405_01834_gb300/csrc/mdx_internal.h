@@ -12,16 +12,18 @@ constexpr int kKmax = 32;
 constexpr int kLtot = 4 * kLmax + 1;   // highest Boys order used (gradients need L+1)
 
 // ----------------------------------------------------------------- Boys table
-// F_m(T0 + d) = sum_{k<kBoysTerms} F_{m+k}(T0) (-d)^k / k!, grid T0 = i * h.
+// F_m(T0 + d) = sum_{k<kBoysTerms} F_{m+k}(T0) (-d)^k / k!, grid T0 = i * h,
+// evaluated by Horner's rule in -d from coefficients F_{m+k}(T0) / k!.
 constexpr int kBoysTerms = 8;
 constexpr int kBoysMmax = kLtot;                    // highest m evaluated
-constexpr int kBoysRow = 36;                        // >= kBoysMmax + kBoysTerms, padded
+constexpr int kBoysOrders = kBoysMmax + 1;          // m = 0 .. kBoysMmax
+constexpr int kBoysRow = kBoysOrders * kBoysTerms;  // one grid point: [m][k]
 constexpr double kBoysInvH = 16.0;                  // grid spacing h = 1/16
 constexpr double kBoysTmax = 100.0;                 // asymptotic form above
 constexpr int kBoysNgrid = 1601 + 1;                // T0 = 0 .. 100 (+1 guard row)
 
-// Builds the interpolation table [kBoysNgrid][kBoysRow] (row-major) in long
-// double by downward recursion (see boys_table.cpp).
+// Builds the interpolation table [kBoysNgrid][kBoysOrders][kBoysTerms]
+// (row-major) in long double by downward recursion (see boys_table.cpp).
 std::vector<double> build_boys_table();
 
 // ----------------------------------------------------------------- records

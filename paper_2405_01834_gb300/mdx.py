@@ -120,6 +120,11 @@ def load(build_if_missing: bool = True):
     lib.mdx_xbatch_info.restype = I32
     lib.mdx_xbatch_run.argtypes = [P, P, I32, ctypes.POINTER(ctypes.c_int32), P]
     lib.mdx_xbatch_run.restype = I32
+    lib.mdx_xbatch_launch_info.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double)]
+    lib.mdx_xbatch_launch_info.restype = I32
+    lib.mdx_xbatch_run_class.argtypes = [P, P, I32, P]
+    lib.mdx_xbatch_run_class.restype = I32
     lib.mdx_xbatch_destroy.argtypes = [P]
     lib.mdx_xbatch_destroy.restype = None
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
@@ -416,6 +421,19 @@ class ExchangeBatch:
         self.eng._check(self.eng.lib.mdx_xbatch_run(self.eng.ctx, self.h, int(persistent), ctypes.byref(nl),
                                                     _stream()), "mdx_xbatch_run")
         return nl.value
+
+    def launch_info(self, i: int):
+        """(la, lb, lc, ld, K_ab, K_cd), kept quartets and model FLOPs of per-class launch i."""
+        lk = (ctypes.c_int32 * 6)()
+        nq, mf = ctypes.c_int64(), ctypes.c_double()
+        self.eng._check(self.eng.lib.mdx_xbatch_launch_info(self.h, int(i), lk, ctypes.byref(nq), ctypes.byref(mf)),
+                        "mdx_xbatch_launch_info")
+        return tuple(lk), nq.value, mf.value
+
+    def run_class(self, i: int):
+        """Enqueue the integral kernel of per-class launch i alone (no K zeroing / symmetrisation)."""
+        self.eng._check(self.eng.lib.mdx_xbatch_run_class(self.eng.ctx, self.h, int(i), _stream()),
+                        "mdx_xbatch_run_class")
 
     def close(self):
         if self.h:

@@ -79,3 +79,34 @@ def test_persistent_launch_in_cuda_graph(eng):
             torch.testing.assert_close(K, R, rtol=0, atol=1e-13 * float(R.abs().max()))
     eng.sync()
     xb.close()
+
+
+def test_class_launches_one_by_one(eng):
+    """Every per-class launch run alone, then K + K^T, reproduces the batched K; the
+    launch info adds up to the batch totals."""
+    mols = _molecules()[:3]
+    bases = [mdx.DeviceBasis(b) for b in mols]
+    Ds = [torch.from_numpy(inputs.density(b.nao, 60 + i)) for i, b in enumerate(mols)]
+    xb = eng.xbatch(bases, Ds, tau=1e-12)
+    xb.run(persistent=False)
+    torch.cuda.synchronize()
+    ref = [K.clone() for K in xb.Ks]
+    nq, mf = 0, 0.0
+    for K in xb.Ks:
+        K.zero_()
+    for i in range(xb.n_class_launches):
+        lk, n, f = xb.launch_info(i)
+        assert all(0 <= l <= 6 for l in lk[:4]) and lk[4] >= 1 and lk[5] >= 1 and n > 0 and f > 0
+        nq += n
+        mf += f
+        xb.run_class(i)
+    torch.cuda.synchronize()
+    eng.sync()
+    assert nq == xb.n_quartets
+    assert mf == pytest.approx(xb.model_flops, rel=1e-12)
+    for K, R in zip(xb.Ks, ref):
+        np.testing.assert_allclose((K + K.T).cpu().numpy(), R.cpu().numpy(), rtol=0,
+                                   atol=1e-13 * float(R.abs().max()))
+    with pytest.raises(mdx.MdxError):
+        xb.launch_info(xb.n_class_launches)
+    xb.close()
