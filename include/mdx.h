@@ -305,10 +305,28 @@ typedef struct {
   int32_t smem_bytes_per_team;
   int32_t n_groups;
   double exec_fma;
+  int32_t register_kernel;   /* 1: store / digestion launches of the class use the register kernel */
+  int32_t pad;
 } mdx_plan_stats;
 
+/* register_kernel: small classes (total angular momentum <= 4, whose Hermite
+ * table R, [p|cd] block and shellset hold at most 100 doubles together) also
+ * have a kernel with one
+ * thread per quartet and every intermediate in registers (the paper's
+ * smallest variant, Sec. 4); it is the default for them, and the autotuner
+ * times it against the team shapes. Gradient launches always use teams. */
 mdx_status mdx_plan_info(mdx_ctx* ctx, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
                          mdx_plan_stats* out);
+
+/* Fix the shape of one class for later calls of this context (what the
+ * autotuner does after timing): team_threads (a power of two <= 1024, 0 for
+ * the planner's choice), smem_budget (shared-memory bytes per team, 0 for the
+ * default 200 KB) and variant (0: register kernel where the class has one,
+ * else teams; 1: teams; 2: register kernel, MDX_EUNSUPPORTED when the class
+ * has none). Plans already built for the class are replaced; batches
+ * prepared before keep theirs. */
+mdx_status mdx_set_class_shape(mdx_ctx* ctx, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
+                               int team_threads, int smem_budget, int variant);
 
 #ifdef __cplusplus
 }

@@ -11,6 +11,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mdx.h"
 #include "kernels.cuh"
 #include "mdx_internal.h"
@@ -25,6 +27,13 @@ struct DevBuf {
 };
 
 }  // namespace
+
+// NVTX range around each entry point that enqueues GPU work, so that
+// profilers can select an entry point's kernels (no effect without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct mdx_ctx {
   int device = 0;
@@ -525,6 +534,7 @@ mdx_status mdx_sync(mdx_ctx* c, void* stream) {
 
 mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
                     int64_t out_capacity, int64_t* out_offsets, void* stream) {
+  const NvtxRange nvtx_range("mdx_eri4");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
@@ -542,6 +552,7 @@ mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets,
 
 mdx_status mdx_eri4_sph(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
                         int64_t out_capacity, int64_t* out_offsets, void* stream) {
+  const NvtxRange nvtx_range("mdx_eri4_sph");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
@@ -599,6 +610,7 @@ mdx_status mdx_eri4_sph(mdx_ctx* c, const mdx_basis* basis, const int32_t* quart
 
 mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
                     double* out, int64_t out_capacity, int64_t* out_offsets, void* stream) {
+  const NvtxRange nvtx_range("mdx_eri3");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
@@ -616,6 +628,7 @@ mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, cons
 
 mdx_status mdx_batch_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,
                           void* stream) {
+  const NvtxRange nvtx_range("mdx_batch_eri4");
   if (!c || !out) return MDX_EINVAL;
   *out = nullptr;
   c->last_error.clear();
@@ -626,6 +639,7 @@ mdx_status mdx_batch_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* qua
 
 mdx_status mdx_batch_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
                           mdx_batch** out, void* stream) {
+  const NvtxRange nvtx_range("mdx_batch_eri3");
   if (!c || !out) return MDX_EINVAL;
   *out = nullptr;
   c->last_error.clear();
@@ -653,6 +667,7 @@ mdx_status mdx_batch_offsets(mdx_ctx* c, const mdx_batch* b, int64_t* out_offset
 
 mdx_status mdx_batch_run(mdx_ctx* c, mdx_batch* b, double* out, int64_t out_capacity, int32_t* n_launches,
                          void* stream) {
+  const NvtxRange nvtx_range("mdx_batch_run");
   if (!c || !b || !out) return MDX_EINVAL;
   if (b->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
   if (b->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
@@ -664,6 +679,7 @@ void mdx_batch_destroy(mdx_batch* b) { batch_free(b); }
 
 mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out_capacity, int64_t max_trial,
                               void* stream) {
+  const NvtxRange nvtx_range("mdx_batch_autotune");
   if (!c || !b || !out || max_trial < 1) return MDX_EINVAL;
   if (b->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
   if (b->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
@@ -679,14 +695,17 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
     // candidate shapes: team sizes x shared-memory budgets (teams per SM)
     // (classes whose default plan splits the ket columns into groups only vary
     // the team size and budget: their plans are expensive to build)
+    // plus the register kernel (one thread per quartet) where the class has one
     std::vector<PlanConfig> cands;
     if (r.plan->d.ngroups > 1) {
       for (int budget : {200 * 1024, 108 * 1024, 72 * 1024})
-        for (int T : {256, 512, 1024}) cands.push_back(PlanConfig{T, budget, 96 * 1024});
+        for (int T : {256, 512, 1024}) cands.push_back(PlanConfig{T, budget, 96 * 1024, 1});
     } else {
       for (int single : {96 * 1024, 40 * 1024})
-        for (int T : {0, 1, 4, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, single});
+        for (int T : {0, 1, 4, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, single, 1});
     }
+    if (reg_eligible(r.key.la, r.key.lb, r.key.lc, r.key.ld))
+      cands.push_back(PlanConfig{0, 200 * 1024, 96 * 1024, 2});
     float best_ms = 1e30f;
     PlanConfig best{};
     std::unique_ptr<Plan> best_plan;
@@ -695,7 +714,8 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
       std::unique_ptr<Plan> p(new Plan());
       std::string err;
       if (!build_plan(r.key, cfg, *p, err)) continue;
-      const std::pair<int, int> sig{p->d.T * 100000 + p->d.ngroups, p->d.team_doubles * 64 + p->d.teams_per_cta};
+      const std::pair<int, int> sig{p->d.reg ? -1 : p->d.T * 100000 + p->d.ngroups,
+                                    p->d.reg ? 0 : p->d.team_doubles * 64 + p->d.teams_per_cta};
       if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;   // same shape as one already timed
       seen.push_back(sig);
       mdx_status st = upload_plan(c, p.get(), s);
@@ -747,6 +767,7 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
 
 mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, int64_t n, double* Q_out,
                        void* stream) {
+  const NvtxRange nvtx_range("mdx_schwarz");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
@@ -912,6 +933,7 @@ extern "C" {
 
 mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
                         double tau, const double* D, double* K, void* stream) {
+  const NvtxRange nvtx_range("mdx_exchange");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
@@ -971,6 +993,7 @@ mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs
 mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q,
                              int64_t n_pairs, double tau, const double* D, double alpha, int32_t n_atoms,
                              double* grad, double* energy, void* stream) {
+  const NvtxRange nvtx_range("mdx_exchange_grad");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
@@ -1114,6 +1137,33 @@ mdx_status mdx_plan_info(mdx_ctx* c, int la, int lb, int lc, int ld, int Kb, int
   out->smem_bytes_per_team = p.d.team_doubles * 8;
   out->n_groups = p.d.ngroups;
   out->exec_fma = p.exec_fma;
+  out->register_kernel = p.d.reg;
+  out->pad = 0;
+  return MDX_OK;
+}
+
+mdx_status mdx_set_class_shape(mdx_ctx* c, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
+                               int team_threads, int smem_budget, int variant) {
+  if (!c) return MDX_EINVAL;
+  if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > MDX_LMAX || lb > MDX_LMAX || lc > MDX_LMAX || ld > MDX_LMAX ||
+      Kb < 1 || Kk < 1 || Kb > MDX_KMAX * MDX_KMAX || Kk > MDX_KMAX * MDX_KMAX)
+    return fail(c, MDX_EUNSUPPORTED, "class outside the supported range");
+  if (team_threads < 0 || smem_budget < 0 || smem_budget > 227 * 1024 || variant < 0 || variant > 2)
+    return fail(c, MDX_EINVAL, "invalid shape");
+  const ClassKey key{la, lb, lc, ld, Kb, Kk, one_centre ? 1 : 0};
+  PlanConfig cfg{};
+  cfg.T = team_threads;
+  if (smem_budget > 0) cfg.budget = smem_budget;
+  cfg.variant = variant;
+  Plan p;
+  std::string err;
+  if (!build_plan(key, cfg, p, err)) return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
+  c->tuned[key] = cfg;
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    c->retired.push_back(std::move(it->second));
+    c->plans.erase(it);
+  }
   return MDX_OK;
 }
 
@@ -1121,6 +1171,7 @@ mdx_status mdx_plan_info(mdx_ctx* c, int la, int lb, int lc, int ld, int Kb, int
 // ---------------------------------------------------------------- batched exchange
 mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, const double* const* D,
                              double* const* K, double tau, mdx_xbatch** out, void* stream) {
+  const NvtxRange nvtx_range("mdx_xbatch_create");
   if (!c || !out) return MDX_EINVAL;
   *out = nullptr;
   c->last_error.clear();
@@ -1414,6 +1465,7 @@ mdx_status mdx_xbatch_info(const mdx_xbatch* xb, int64_t* n_quartets, int64_t* n
 }
 
 mdx_status mdx_xbatch_run(mdx_ctx* c, mdx_xbatch* xb, int32_t persistent, int32_t* n_launches, void* stream) {
+  const NvtxRange nvtx_range("mdx_xbatch_run");
   if (!c || !xb || xb->ctx != c) return MDX_EINVAL;
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1454,6 +1506,7 @@ mdx_status mdx_xbatch_launch_info(const mdx_xbatch* xb, int32_t i, int32_t* lk, 
 }
 
 mdx_status mdx_xbatch_run_class(mdx_ctx* c, mdx_xbatch* xb, int32_t i, void* stream) {
+  const NvtxRange nvtx_range("mdx_xbatch_run_class");
   if (!c || !xb || xb->ctx != c || i < 0 || i >= (int32_t)xb->launches.size()) return MDX_EINVAL;
   cudaSetDevice(c->device);
   const cudaError_t e = launch_quartets(xb->launches[i], (cudaStream_t)stream);

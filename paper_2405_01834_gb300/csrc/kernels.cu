@@ -640,9 +640,35 @@ cudaError_t launch_persistent(const PersistLaunch& pl, int64_t smem_bytes, int g
   return cudaGetLastError();
 }
 
+cudaError_t launch_reg_part00(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part01(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part02(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part03(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part04(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part05(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part06(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part07(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part08(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part09(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part10(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part11(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+using RegPart = cudaError_t (*)(int, const QuartetLaunch&, cudaStream_t, bool*);
+static const RegPart kRegParts[] = {launch_reg_part00, launch_reg_part01, launch_reg_part02, launch_reg_part03,
+                                    launch_reg_part04, launch_reg_part05, launch_reg_part06, launch_reg_part07,
+                                    launch_reg_part08, launch_reg_part09, launch_reg_part10, launch_reg_part11};
+
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
   if (a.nq <= 0) return cudaSuccess;
   const PlanDev& P = a.plan;
+  if (P.reg && !a.grad) {
+    // one thread per quartet, registers only (store and digestion epilogues)
+    const int code = ((P.la * 7 + P.lb) * 7 + P.lc) * 7 + P.ld;
+    for (RegPart part : kRegParts) {
+      bool handled = false;
+      const cudaError_t e = part(code, a, s, &handled);
+      if (handled || e != cudaSuccess) return e;
+    }
+  }
   const int64_t grid = (a.nq + P.teams_per_cta - 1) / P.teams_per_cta;
   const int block = P.teams_per_cta * P.T;
   const size_t shm = (size_t)P.teams_per_cta * P.team_doubles * sizeof(double);

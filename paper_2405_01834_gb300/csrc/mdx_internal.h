@@ -51,10 +51,20 @@ inline int rec_size(int la, int lb) {        // padded to a multiple of 2 double
   return (s + 1) & ~1;
 }
 
-inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
-inline int tri(int n) { return n < 0 ? 0 : n * (n + 1) / 2; }
-inline int tet(int n) { return n < 0 ? 0 : n * (n + 1) * (n + 2) / 6; }
-inline int nherm(int l) { return tet(l + 1); }
+constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+constexpr int tri(int n) { return n < 0 ? 0 : n * (n + 1) / 2; }
+constexpr int tet(int n) { return n < 0 ? 0 : n * (n + 1) * (n + 2) / 6; }
+constexpr int nherm(int l) { return tet(l + 1); }
+
+// Register kernel (one thread per quartet, all intermediates in registers):
+// classes of total angular momentum <= 4 whose R table, [p|cd] block and
+// shellset hold at most 100 doubles together have one.
+constexpr int reg_footprint(int la, int lb, int lc, int ld) {
+  return nherm(la + lb + lc + ld) + nherm(la + lb) * ncart(lc) * ncart(ld) + ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
+}
+constexpr bool reg_eligible(int la, int lb, int lc, int ld) {
+  return la + lb + lc + ld <= 4 && reg_footprint(la, lb, lc, ld) <= 100;
+}
 
 // ----------------------------------------------------------------- programs
 // A "step" computes entries out = sum_{k<n} coef[c + k*s] * src[x + k*s]
@@ -107,6 +117,7 @@ struct PlanDev {
   int32_t ngroups, ncols_max;
   int32_t nb1, nb23;
   int32_t cache_R;                       // R computed once (single primitive quartet)
+  int32_t reg;                           // launch the register kernel (store / digestion launches)
   const Group* groups;
   const StepEntry* kprog;
   const StepEntry* b1;
@@ -130,7 +141,10 @@ struct PlanConfig {
   int T = 0;                 // threads per team (1..1024, a power of two)
   int budget = 200 * 1024;   // shared-memory bytes per team
   int single_max = 96 * 1024;  // largest workspace for which all ket columns form one group
-  bool operator==(const PlanConfig& o) const { return T == o.T && budget == o.budget && single_max == o.single_max; }
+  int variant = 0;           // 0: register kernel where the class has one, else team; 1: team; 2: register
+  bool operator==(const PlanConfig& o) const {
+    return T == o.T && budget == o.budget && single_max == o.single_max && variant == o.variant;
+  }
 };
 
 // Builds the plan of a class for the given shape.

@@ -23,6 +23,7 @@
 // Every step is emitted as a list of entries "out = sum_k coef[c+k*s] *
 // src[x+k*s]" over offsets in the team's shared-memory workspace; only
 // entries some output depends on are emitted.
+#include <array>
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -391,6 +392,33 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   for (int n = 0; n < P.L; ++n) fma_r += tet(P.L - n + 1) - 1;
   const double nrec = (P.cache_R || P.ngroups == 1) ? 1.0 : P.ngroups;
   plan.exec_fma = key.Kb * key.Kk * (fma_k + nrec * (fma_r + 8.0 * (P.L + 1))) + key.Kb * fma_b * P.Nk;
+
+  // register kernel (one thread per quartet) where the class has one
+  const bool has_reg = reg_eligible(key.la, key.lb, key.lc, key.ld);
+  if (cfg.variant == 2 && !has_reg) { err = "class has no register kernel"; return false; }
+  P.reg = (has_reg && cfg.variant != 1) ? 1 : 0;
+  if (P.reg) {
+    // its FP64 work: per primitive quartet Boys, R, the ket E products and
+    // X += E R; per bra primitive the bra E products and V += E X
+    auto comps = [](int l) {
+      std::vector<std::array<int, 3>> v;
+      for (int ax = l; ax >= 0; --ax)
+        for (int ay = l - ax; ay >= 0; --ay) v.push_back({ax, ay, l - ax - ay});
+      return v;
+    };
+    double ket = 0, bra = 0;
+    for (auto& c : comps(key.lc))
+      for (auto& d : comps(key.ld)) {
+        const int nx = c[0] + d[0] + 1, ny = c[1] + d[1] + 1, nz = c[2] + d[2] + 1;
+        ket += nx * ny * nz + nx * ny + (double)nherm(P.Lb) * nx * ny * nz;
+      }
+    for (auto& a : comps(key.la))
+      for (auto& b : comps(key.lb)) {
+        const int nx = a[0] + b[0] + 1, ny = a[1] + b[1] + 1, nz = a[2] + b[2] + 1;
+        bra += nx * ny * nz + nx * ny + (double)P.Nk * nx * ny * nz;
+      }
+    plan.exec_fma = key.Kb * key.Kk * (fma_r + 8.0 * (P.L + 1) + ket) + key.Kb * bra;
+  }
 
   if (!validate_plan(plan, err)) return false;
 

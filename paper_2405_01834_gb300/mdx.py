@@ -31,7 +31,8 @@ class _Basis(ctypes.Structure):
 
 class PlanStats(ctypes.Structure):
     _fields_ = [("team_threads", ctypes.c_int32), ("teams_per_cta", ctypes.c_int32),
-                ("smem_bytes_per_team", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("exec_fma", ctypes.c_double)]
+                ("smem_bytes_per_team", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("exec_fma", ctypes.c_double),
+                ("register_kernel", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def plan_info(la, lb, lc, ld, Kb=1, Kk=1, one_centre=False) -> PlanStats:
@@ -129,6 +130,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_xbatch_destroy.restype = None
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
     lib.mdx_plan_info.restype = I32
+    lib.mdx_set_class_shape.argtypes = [P] + [I32] * 10
+    lib.mdx_set_class_shape.restype = I32
     _lib = lib
     return lib
 
@@ -269,6 +272,19 @@ class Engine:
                                         e.data_ptr() if with_energy else None, _stream())
         self._check(st, "mdx_exchange_grad")
         return g, (e[0] if with_energy else None)
+
+    def plan_info(self, la, lb, lc, ld, Kb=1, Kk=1, one_centre=False) -> PlanStats:
+        """The shape this engine uses for a class (tuned or fixed shapes included)."""
+        st = PlanStats()
+        self._check(self.lib.mdx_plan_info(self.ctx, la, lb, lc, ld, Kb, Kk, int(one_centre), ctypes.byref(st)),
+                    "mdx_plan_info")
+        return st
+
+    def set_class_shape(self, la, lb, lc, ld, Kb=1, Kk=1, one_centre=False, team_threads=0, smem_budget=0,
+                        variant=0):
+        """Fix a class's shape (variant 0: default, 1: team kernel, 2: register kernel)."""
+        self._check(self.lib.mdx_set_class_shape(self.ctx, la, lb, lc, ld, Kb, Kk, int(one_centre), team_threads,
+                                                 smem_budget, variant), "mdx_set_class_shape")
 
     def last_quartet_count(self) -> int:
         return int(self.lib.mdx_last_quartet_count(self.ctx))
