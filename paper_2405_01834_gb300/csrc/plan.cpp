@@ -392,6 +392,7 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   for (int n = 0; n < P.L; ++n) fma_r += tet(P.L - n + 1) - 1;
   const double nrec = (P.cache_R || P.ngroups == 1) ? 1.0 : P.ngroups;
   plan.exec_fma = key.Kb * key.Kk * (fma_k + nrec * (fma_r + 8.0 * (P.L + 1))) + key.Kb * fma_b * P.Nk;
+  const double team_fma_per_prim = plan.exec_fma / ((double)key.Kb * key.Kk);
 
   // register kernel (one thread per quartet) where the class has one
   const bool has_reg = reg_eligible(key.la, key.lb, key.lc, key.ld);
@@ -428,6 +429,12 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   if (cfg.T > 0) {
     if (cfg.T > 1024 || (cfg.T & (cfg.T - 1))) { err = "team size must be a power of two <= 1024"; return false; }
     P.T = cfg.T;
+  } else if (key.Kb * key.Kk > 1) {
+    // contracted: the work per primitive quartet (Boys, R, ket steps) sets the
+    // team; about 40 FMAs per lane per primitive quartet, at most 128 lanes
+    // (GB300 sweeps of team sizes over contracted classes of L = 4..10)
+    P.T = 1;
+    while (P.T < 128 && 2 * P.T * 40.0 <= team_fma_per_prim) P.T *= 2;
   } else if (P.ngroups > 1) {
     P.T = 512;
   } else {
