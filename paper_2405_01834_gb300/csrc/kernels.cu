@@ -473,6 +473,9 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
     compute_R<CTA>(a, ws, tl, mask);
   }
   double* outq = a.D ? nullptr : a.out + a.qout[q];
+  // store epilogue: b23 of the last bra primitive writes the shellset to global
+  // memory itself (no OUT pass, no barrier after it)
+  const bool direct = !a.D && !a.grad;
   for (int g = 0; g < P.ngroups; ++g) {
     const Group grp = P.groups[g];
     const int ncols = grp.ncols;
@@ -484,8 +487,10 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
           team_sync<CTA>(mask);
           compute_R<CTA>(a, ws, tl, mask);
         }
-        run_step(P.kprog + grp.k1_off, grp.k1_n, ws, tl, T, false);
-        team_sync<CTA>(mask);
+        if (grp.k1_n > 0) {   // groups after the first of a z-pair reuse its A (uncontracted classes)
+          run_step(P.kprog + grp.k1_off, grp.k1_n, ws, tl, T, false);
+          team_sync<CTA>(mask);
+        }
         run_step(P.kprog + grp.k2_off, grp.k2_n, ws, tl, T, false);
         team_sync<CTA>(mask);
         run_step(P.kprog + grp.k3_off, grp.k3_n, ws, tl, T, pk > 0);
@@ -514,6 +519,8 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
       // b23: OUT += Ez (x) Ey (x) C1, per column; two Hermite z-indices v in
       // flight per lane (independent inner sums over u)
       {
+        const bool to_global = direct && pb == Kb - 1;
+        const uint16_t* cm = P.colmap + grp.col_off;
         const int tot = P.nb23 * ncols;
         for (int e = tl; e < tot; e += T) {
           const int ent = e / ncols, col = e - ent * ncols;
@@ -550,28 +557,31 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
             for (int iu = 0; iu < nu; ++iu) ia = fma(ey[iu * su], ra[iu * su], ia);
             acc = fma(ez[iv * sv], ia, acc);
           }
-          *o = acc;
+          if (to_global) {
+            if (active) outq[(int64_t)s.out * P.Nk + cm[col]] = acc;
+          } else {
+            *o = acc;
+          }
         }
       }
-      team_sync<CTA>(mask);
+      // Barrier before the next writer of what b23 reads: the bra record (reloaded
+      // per bra primitive unless the class has one primitive quartet) or OUT (read
+      // by other lanes in the digestion / gradient epilogue). C1 is overwritten by
+      // the next b1 only after the k-step barriers.
+      if (!P.cache_R || (!direct && pb == Kb - 1)) team_sync<CTA>(mask);
     }
     if (a.grad) {
       grad_group<CTA>(a, ws, grp, qp, tl, T, active, mask);
+      team_sync<CTA>(mask);
     } else if (a.D) {
       // exchange digestion of this group's columns (Sec. 6: K_bc = sum_ad [ab|cd] D_ad),
       // unique quartet (ij|kl) with i>=j, k>=l, ij>=kl and weight w; the host adds K^T at the end
       if (active) digest_group(a, ws, grp, qp, tl, T);
-    } else if (active) {
-      // store the group's columns: OUT[ab][col] -> out[ab*Nk + cd]
-      const uint16_t* cm = P.colmap + grp.col_off;
-      const int tot = P.Nb * ncols;
-      for (int e = tl; e < tot; e += T) {
-        const int ab = e / ncols, col = e - ab * ncols;
-        outq[(int64_t)ab * P.Nk + cm[col]] = ws[P.o_OUT + e];
-      }
+      team_sync<CTA>(mask);
     }
-    team_sync<CTA>(mask);
   }
+  // the records of the next quartet (persistent kernel) overwrite what b23 reads
+  if (direct) team_sync<CTA>(mask);
 }
 
 template <bool CTA>

@@ -64,21 +64,28 @@ struct Layout {                  // a set of rows, each a contiguous run of doub
 struct ColInfo { CartC c, d; int gcol; };
 
 // Builds the ket programs of one group of columns; returns false on overflow.
-// Offsets emitted are absolute in the team workspace.
+// Offsets emitted are absolute in the team workspace. The A blocks (k1
+// outputs) are laid out for the columns `a_cols` (default: the group's own),
+// so that groups of one z-pair can share one A computed by the first of them
+// (emit_k1 = false for the others).
 bool build_group_k(const PlanDev& P, const std::vector<ColInfo>& cols, int o_A, int o_B, int o_X,
                    std::vector<StepEntry>& k1, std::vector<StepEntry>& k2, std::vector<StepEntry>& k3,
-                   int& a_size, int& b_size, double& fma) {
+                   int& a_size, int& b_size, double& fma, const std::vector<ColInfo>* a_cols = nullptr,
+                   bool emit_k1 = true) {
   const int Lb = P.Lb, L = P.L;
   const int Tcd = etab_size(P.lc, P.ld);
   // B layout per column: rows (u,v), t' contiguous, full rows
   std::vector<Layout> BL(cols.size());
-  std::map<std::pair<int, int>, Layout> AL;    // per z-pair (cz,dz)
   for (size_t j = 0; j < cols.size(); ++j) {
-    const CartC& c = cols[j].c; const CartC& d = cols[j].d;
-    const int xx = c.x + d.x, yy = c.y + d.y;
+    const int xx = cols[j].c.x + cols[j].d.x;
     for (int u = 0; u <= Lb; ++u)
       for (int v = 0; u + v <= Lb; ++v) BL[j].need(u, v, Lb - u - v + xx);
     BL[j].finalize();
+  }
+  std::map<std::pair<int, int>, Layout> AL;    // per z-pair (cz,dz)
+  for (const ColInfo& ci : a_cols ? *a_cols : cols) {
+    const CartC& c = ci.c; const CartC& d = ci.d;
+    const int xx = c.x + d.x, yy = c.y + d.y;
     Layout& A = AL[{c.z, d.z}];
     for (int u = 0; u <= Lb; ++u)
       for (int v = 0; u + v <= Lb; ++v)
@@ -101,6 +108,7 @@ bool build_group_k(const PlanDev& P, const std::vector<ColInfo>& cols, int o_A, 
   };
   // k1: A_z[t',u',v] = sum_phi Ez'[cz,dz][phi] R[t',u',v+phi]
   for (auto& kv : AL) {
+    if (!emit_k1) break;
     const int cz = kv.first.first, dz = kv.first.second;
     const int coef = reck + 2 * Tcd + etab_off(P.lc, P.ld, cz, dz);
     for (auto& row : kv.second.rowlen) {
@@ -299,35 +307,46 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
 
   // try a single group holding every column
   std::vector<std::vector<ColInfo>> groups;
-  auto group_sizes = [&](const std::vector<ColInfo>& g, int& as, int& bs) {
+  // z-pair columns whose shared A a group uses (uncontracted classes: R, and so
+  // A, stays valid from one group to the next), and whether it computes that A
+  std::vector<const std::vector<ColInfo>*> gz;
+  std::vector<char> gfirst;
+  const bool share_a = key.Kb * key.Kk == 1;
+  auto group_sizes = [&](const std::vector<ColInfo>& g, int& as, int& bs, const std::vector<ColInfo>* zc) {
     std::vector<StepEntry> k1, k2, k3;
     double f = 0;
-    return build_group_k(P, g, 0, 0, 0, k1, k2, k3, as, bs, f);
+    return build_group_k(P, g, 0, 0, 0, k1, k2, k3, as, bs, f, zc);
   };
   {
     int as = 0, bs = 0;
-    bool ok = group_sizes(allcols, as, bs);
+    bool ok = group_sizes(allcols, as, bs, nullptr);
     const int td = team_doubles(as, bs, (int)allcols.size());
-    if (ok && td * 8 <= std::min(smem_budget_bytes, cfg.single_max)) groups.push_back(allcols);
+    if (ok && td * 8 <= std::min(smem_budget_bytes, cfg.single_max)) {
+      groups.push_back(allcols);
+      gz.push_back(nullptr);
+      gfirst.push_back(1);
+    }
   }
   int regmax = 0, cmax = 0;
+  std::map<std::pair<int, int>, std::vector<ColInfo>> byz;   // columns per z-pair (outlives gz)
   if (groups.empty()) {
     // one group per z-pair, columns split into chunks of at most `cap` so that
     // the largest region plus the widest group fit the budget together
-    std::map<std::pair<int, int>, std::vector<ColInfo>> byz;
     for (auto& c : allcols) byz[{c.c.z, c.d.z}].push_back(c);
     size_t cap = 0;
     for (auto& kv : byz) cap = std::max(cap, kv.second.size());
     while (true) {
-      groups.clear();
+      groups.clear(); gz.clear(); gfirst.clear();
       regmax = 0; cmax = 0;
       bool ok = true;
       for (auto& kv : byz) {
         std::vector<ColInfo>& cs = kv.second;
         for (size_t s0 = 0; s0 < cs.size(); s0 += cap) {
           groups.emplace_back(cs.begin() + s0, cs.begin() + std::min(cs.size(), s0 + cap));
+          gz.push_back(share_a ? &cs : nullptr);
+          gfirst.push_back(s0 == 0 || !share_a);
           int as = 0, bs = 0;
-          if (!group_sizes(groups.back(), as, bs)) ok = false;
+          if (!group_sizes(groups.back(), as, bs, gz.back())) ok = false;
           regmax = std::max(regmax, region_size(as, bs));
           cmax = std::max(cmax, (int)groups.back().size());
         }
@@ -339,7 +358,7 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
     }
   } else {
     int as = 0, bs = 0;
-    group_sizes(groups[0], as, bs);
+    group_sizes(groups[0], as, bs, nullptr);
     regmax = region_size(as, bs);
     cmax = (int)groups[0].size();
   }
@@ -360,12 +379,13 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   // emit the group programs with final offsets
   plan.groups.clear(); plan.kprog.clear(); plan.colmap.clear();
   double fma_k = 0;
-  for (auto& g : groups) {
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::vector<ColInfo>& g = groups[gi];
     std::vector<StepEntry> k1, k2, k3;
     int as = 0, bs = 0; double f = 0;
-    group_sizes(g, as, bs);
+    group_sizes(g, as, bs, gz[gi]);
     const int oB = P.o_A + as;
-    if (!build_group_k(P, g, P.o_A, oB, P.o_X, k1, k2, k3, as, bs, f)) {
+    if (!build_group_k(P, g, P.o_A, oB, P.o_X, k1, k2, k3, as, bs, f, gz[gi], gfirst[gi] != 0)) {
       err = "program offsets overflow";
       return false;
     }
