@@ -37,9 +37,9 @@ UNIT = "GFLOP/s"
 FP64_FLOP_PER_CLK_SM = 4.0
 CHUNK_BYTES = 2 << 30
 # DRAM bytes (read + write) per [ii|ii] quartet of the k_quartets launch, from the ncu capture summarised
-# in profiles/k_quartets_ii_16x16.md (256 quartets: 2.743 GB read + 3.876 GB written); scaled by the
+# in profiles/k_quartets_ii_16x16.md (256 quartets: 2.751 GB read + 3.862 GB written); scaled by the
 # quartets of a launch when the dominant class is [ii|ii]
-NCU_DRAM_BYTES_PER_II_QUARTET = (2.742647e9 + 3.875670e9) / 256
+NCU_DRAM_BYTES_PER_II_QUARTET = (2.751376e9 + 3.861786e9) / 256
 
 
 def parse():
@@ -55,10 +55,12 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the per-class team-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad", "ab"],
                     help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules; "
                          "df: per-class 3-center rates on the density-fitting cluster; grad: exchange energy "
-                         "and its nuclear gradient against the exchange build alone")
+                         "and its nuclear gradient against the exchange build alone; ab: the default kernels "
+                         "against the materialized-Hermite variant (dense [p|q], batched DGEMMs)")
+    ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
     ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
     ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
     ap.add_argument("--n-mol", type=int, default=64)
@@ -412,6 +414,44 @@ def grad_main(args):
     eng.close()
 
 
+def ab_main(args):
+    """A/B of the two designs on the class sweep: the axis-factored kernels (mdx_batch_run) against the
+    materialized-Hermite variant of the paper (mdx_batch_run_materialized: [p|q] matrices in HBM, both
+    transforms as batched DGEMMs on the FP64 tensor units), same prepared batch, grid --ab-grid^2 per class."""
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    stream = torch.cuda.current_stream()
+    rows, ta, tb = [], 0.0, 0.0
+    for l in [int(x) for x in args.classes.split(",") if x]:
+        b, q = inputs.class_sweep((l, l, l, l), n_bra=args.ab_grid, n_ket=args.ab_grid)
+        bt = eng.batch_eri4(mdx.DeviceBasis(b), q)
+        out_a = torch.empty(bt.total, dtype=torch.float64, device="cuda")
+        out_b = torch.empty(bt.total, dtype=torch.float64, device="cuda")
+        ms_a = _event_ms(torch, stream, lambda: bt.run(out_a), args.steps, args.warmup)
+        ms_b = _event_ms(torch, stream, lambda: bt.run_materialized(out_b), args.steps, args.warmup)
+        diff = float((out_a - out_b).abs().max() / out_a.abs().max())
+        f = model_flops(l, len(q))
+        rows.append({"class": CLASS_NAMES[l], "quartets": len(q),
+                     "axis_factored": {"ms": round(ms_a, 3), "quartets_per_s": round(len(q) / (ms_a * 1e-3), 1),
+                                       "model_gflops": round(f / (ms_a * 1e-3) * 1e-9, 1)},
+                     "materialized": {"ms": round(ms_b, 3), "quartets_per_s": round(len(q) / (ms_b * 1e-3), 1),
+                                      "model_gflops": round(f / (ms_b * 1e-3) * 1e-9, 1)},
+                     "speedup_of_axis_factored": round(ms_b / ms_a, 2), "max_rel_diff": diff})
+        ta += ms_a; tb += ms_b
+        bt.close()
+    eng.sync()
+    line = {"metric": "materialized-Hermite variant time / axis-factored time on the class sweep", "unit": "x",
+            "value": round(tb / ta, 3), "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "class sweep [ll|ll], %dx%d random uncontracted quartets per class" %
+                                   (args.ab_grid, args.ab_grid)},
+            "per_class": rows}
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def peak_fp64(torch, sm_mhz: float = 2070.0):
     """FP64 pipe peak of this GPU at the given SM clock (default: the GB300 maximum), FLOP/s."""
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
@@ -428,6 +468,8 @@ def main():
         return df_main(args)
     if args.workload == "grad":
         return grad_main(args)
+    if args.workload == "ab":
+        return ab_main(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:
@@ -586,8 +628,9 @@ def main():
 
 
 def e2e(eng, work, args, torch):
-    """One step through mdx_eri4 with host buffers: pinned basis/quartet arrays
-    copied in, integrals copied back to pinned host memory, chunk by chunk."""
+    """One step through mdx_eri4 with host buffers: pinned quartet arrays copied in, integrals copied back to
+    pinned host memory, chunk by chunk. Two device output buffers: the copy of one chunk's integrals to the host
+    (on a second stream) overlaps the evaluation of the next chunk."""
     from paper_2405_01834_gb300 import mdx
     host = []
     for l, b, q in work:
@@ -595,10 +638,14 @@ def e2e(eng, work, args, torch):
         cq = max(1, min(len(q), CHUNK_BYTES // per_q))
         host.append((l, b, torch.from_numpy(q).pin_memory(), cq))
     max_out = max(min(len(q), cq) * inputs.ncart(l) ** 4 for l, b, q, cq in host)
-    out_dev = torch.empty(max_out, dtype=torch.float64, device="cuda")
-    out_host = torch.empty(max_out, dtype=torch.float64).pin_memory()
+    out_dev = [torch.empty(max_out, dtype=torch.float64, device="cuda") for _ in range(2)]
+    out_host = [torch.empty(max_out, dtype=torch.float64).pin_memory() for _ in range(2)]
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    copied = [None, None]   # event: the host copy out of buffer k has finished
     h2d = d2h = 0
     tot_f = 0.0
+    k = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for l, b, qh, cq in host:
@@ -606,12 +653,21 @@ def e2e(eng, work, args, torch):
         h2d += sum(t.numel() * t.element_size() for t in (db.l, db.nprim, db.prim_off, db.ao_off, db.atom,
                                                           db.center, db.exps, db.coefs))
         for s in range(0, qh.shape[0], cq):
+            if copied[k] is not None:
+                comp.wait_event(copied[k])
             qd = qh[s:s + cq].to("cuda", non_blocking=True)
             h2d += qd.numel() * 4
-            v, off = eng.eri4(db, qd, out=out_dev)
+            v, off = eng.eri4(db, qd, out=out_dev[k])
             n = qd.shape[0] * inputs.ncart(l) ** 4
-            out_host[:n].copy_(v[:n], non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(comp)
+            with torch.cuda.stream(copy):
+                copy.wait_event(ready)
+                out_host[k][:n].copy_(v[:n], non_blocking=True)
+                copied[k] = torch.cuda.Event()
+                copied[k].record(copy)
             d2h += n * 8
+            k ^= 1
         tot_f += model_flops(l, qh.shape[0])
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0

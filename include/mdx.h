@@ -172,6 +172,16 @@ mdx_status mdx_batch_run(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t ou
 mdx_status mdx_batch_autotune(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t out_capacity,
                               int64_t max_trial, void* stream);
 
+/* The same batch through the materialized-Hermite variant of the paper
+ * (Sec. 4): per quartet the full matrix [p|q] = (-1)^{|q|} [p+q] is written
+ * to device memory and both transforms run as batched dense DGEMMs
+ * ([p|cd] = [p|q] E^cd, [ab|cd] = E^ab [p|cd]; cuBLAS, i.e. the FP64 tensor
+ * units). An A/B experiment against mdx_batch_run: same results, same output
+ * layout, uncontracted 4-center classes only (MDX_EUNSUPPORTED otherwise),
+ * synchronises the stream per class (not capturable). */
+mdx_status mdx_batch_run_materialized(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t out_capacity,
+                                      int32_t* n_launches, void* stream);
+
 /* Free a batch (NULL allowed). No work of the batch may still be running. */
 void mdx_batch_destroy(mdx_batch* batch);
 

@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("libmdx build failed:\n" + "\n".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -11,6 +11,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cublas_v2.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/mdx.h"
@@ -47,6 +48,7 @@ struct mdx_ctx {
   std::map<ClassKey, PlanConfig> tuned;   // shapes chosen by mdx_batch_autotune
   std::vector<std::unique_ptr<Plan>> retired;   // replaced plans, kept alive for batches that use them
   int64_t last_quartets = 0;
+  cublasHandle_t cublas = nullptr;        // materialized-Hermite path only, created on first use
 };
 
 namespace {
@@ -521,6 +523,7 @@ void mdx_destroy(mdx_ctx* c) {
   cudaFree(c->d_hdec);
   cudaFree(c->d_hdec_off);
   cudaFree(c->d_err);
+  if (c->cublas) cublasDestroy(c->cublas);
   delete c;
 }
 
@@ -673,6 +676,99 @@ mdx_status mdx_batch_run(mdx_ctx* c, mdx_batch* b, double* out, int64_t out_capa
   if (b->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
   cudaSetDevice(c->device);
   return batch_run(c, b, out, n_launches, (cudaStream_t)stream);
+}
+
+mdx_status mdx_batch_run_materialized(mdx_ctx* c, mdx_batch* B, double* out, int64_t out_capacity,
+                                      int32_t* n_launches, void* stream) {
+  const NvtxRange nvtx_range("mdx_batch_run_materialized");
+  if (!c || !B || !out) return MDX_EINVAL;
+  if (B->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
+  if (B->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  for (auto& r : B->ranges)
+    if (r.count > 0 && (r.key.Kb != 1 || r.key.Kk != 1 || r.key.onec))
+      return fail(c, MDX_EUNSUPPORTED, "materialized path: uncontracted 4-center classes only");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!c->cublas && cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) {
+    c->cublas = nullptr;
+    return fail(c, MDX_ECUDA, "cublasCreate failed");
+  }
+  if (cublasSetStream(c->cublas, s) != CUBLAS_STATUS_SUCCESS) return fail(c, MDX_ECUDA, "cublasSetStream failed");
+  int32_t nl = 0;
+  cudaError_t e = launch_pair_records(B->b0, B->b1, B->jobs, B->njobs, B->recs, B->recs_s, c->d_err, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+  if (B->njobs > 0) ++nl;
+  mdx_status st;
+  for (auto& r : B->ranges) {
+    if (r.count == 0) continue;
+    const ClassKey& k = r.key;
+    const int Lb = k.la + k.lb, Lk = k.lc + k.ld;
+    const int64_t Nb = ncart(k.la) * ncart(k.lb), Nk = ncart(k.lc) * ncart(k.ld);
+    const int64_t Hb = nherm(Lb), Hk = nherm(Lk);
+    // the class's bra and ket pairs, numbered compactly
+    std::vector<int2> hq;
+    hq.resize((size_t)r.count);
+    e = cudaMemcpyAsync(hq.data(), B->qp + r.begin, r.count * sizeof(int2), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "quartet download");
+    std::unordered_map<int32_t, int32_t> mb, mk;
+    std::vector<int32_t> ub, uk, qib((size_t)r.count), qik((size_t)r.count);
+    for (int64_t i = 0; i < r.count; ++i) {
+      auto ib = mb.emplace(hq[i].x, (int32_t)ub.size());
+      if (ib.second) ub.push_back(hq[i].x);
+      auto ik = mk.emplace(hq[i].y, (int32_t)uk.size());
+      if (ik.second) uk.push_back(hq[i].y);
+      qib[i] = ib.first->second;
+      qik[i] = ik.first->second;
+    }
+    int32_t *d_ub, *d_uk, *d_qib, *d_qik;
+    if ((st = upload(c, "mat_ub", ub, &d_ub, s)) != MDX_OK) return st;
+    if ((st = upload(c, "mat_uk", uk, &d_uk, s)) != MDX_OK) return st;
+    if ((st = upload(c, "mat_qib", qib, &d_qib, s)) != MDX_OK) return st;
+    if ((st = upload(c, "mat_qik", qik, &d_qik, s)) != MDX_OK) return st;
+    double *Eab, *Ecd;
+    if ((st = ensure(c, "mat_eab", (size_t)(ub.size() * Nb * Hb), &Eab, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "mat_ecd", (size_t)(uk.size() * Hk * Nk), &Ecd, s)) != MDX_OK) return st;
+    e = launch_mat_emat(B->recs, B->pair_rec, d_ub, (int64_t)ub.size(), k.la, k.lb, true, Eab, s);
+    if (e == cudaSuccess) e = launch_mat_emat(B->recs, B->pair_rec, d_uk, (int64_t)uk.size(), k.lc, k.ld, false, Ecd, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "E matrices");
+    nl += 2;
+    // chunks whose [p|q] and [p|cd] matrices fit a 2 GB workspace
+    const int64_t per_q = (Hb * Hk + Hb * Nk) * (int64_t)sizeof(double);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(r.count, (int64_t(2) << 30) / per_q));
+    double *PQ, *Tm;
+    const double** ptrs;
+    if ((st = ensure(c, "mat_pq", (size_t)(chunk * Hb * Hk), &PQ, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "mat_t", (size_t)(chunk * Hb * Nk), &Tm, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "mat_ptrs", (size_t)(6 * chunk), &ptrs, s)) != MDX_OK) return st;
+    const double** a1 = ptrs;
+    const double** b1 = ptrs + chunk;
+    double** c1 = (double**)(ptrs + 2 * chunk);
+    const double** a2 = ptrs + 3 * chunk;
+    const double** b2 = ptrs + 4 * chunk;
+    double** c2 = (double**)(ptrs + 5 * chunk);
+    const double one = 1.0, zero = 0.0;
+    for (int64_t q0 = 0; q0 < r.count; q0 += chunk) {
+      const int64_t nq = std::min(chunk, r.count - q0);
+      e = launch_mat_hermite(B->recs, B->pair_rec, B->qp + r.begin + q0, nq, Lb, Lk, c->d_boys, PQ, s);
+      if (e == cudaSuccess)
+        e = launch_mat_ptrs(nq, d_qib + q0, d_qik + q0, B->qoff + r.begin + q0, Eab, Nb * Hb, Ecd, Hk * Nk, PQ,
+                            Hb * Hk, Tm, Hb * Nk, out, a1, b1, c1, a2, b2, c2, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "materialized Hermite matrices");
+      nl += 2;
+      // row-major X[r x c] is column-major X^T: [p|cd]^T = (E^cd)^T [p|q]^T, then
+      // [ab|cd]^T = [p|cd]^T (E^ab)^T, both with the Cartesian ket index fastest
+      cublasStatus_t cs = cublasDgemmBatched(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, (int)Nk, (int)Hb, (int)Hk, &one,
+                                             a1, (int)Nk, b1, (int)Hk, &zero, c1, (int)Nk, (int)nq);
+      if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasDgemmBatched(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, (int)Nk, (int)Nb, (int)Hb, &one, a2, (int)Nk,
+                                b2, (int)Hb, &zero, c2, (int)Nk, (int)nq);
+      if (cs != CUBLAS_STATUS_SUCCESS) return fail(c, MDX_ECUDA, "cublasDgemmBatched failed");
+      nl += 2;
+    }
+  }
+  if (n_launches) *n_launches = nl;
+  return MDX_OK;
 }
 
 void mdx_batch_destroy(mdx_batch* b) { batch_free(b); }

@@ -129,6 +129,18 @@ struct SphLaunch {
 };
 cudaError_t launch_cart2sph(const SphLaunch& a, cudaStream_t s);
 
+// Materialized-Hermite path (A/B experiment): E matrices of listed pairs
+// (bra: [N_b x Nt(L)] rows ab; ket: [Nt(L) x N_k] rows q), [p|q] matrices of a
+// chunk of quartets, and the pointer arrays of the two batched products.
+cudaError_t launch_mat_emat(const double* recs, const int64_t* pair_rec, const int32_t* pairs, int64_t npairs,
+                            int la, int lb, bool bra, double* E, cudaStream_t s);
+cudaError_t launch_mat_hermite(const double* recs, const int64_t* pair_rec, const int2* qp, int64_t nq, int Lb,
+                               int Lk, const double* boys, double* PQ, cudaStream_t s);
+cudaError_t launch_mat_ptrs(int64_t nq, const int32_t* ib, const int32_t* ik, const int64_t* qoff,
+                            const double* Eab, int64_t sEab, const double* Ecd, int64_t sEcd, const double* PQ,
+                            int64_t sPQ, double* Tm, int64_t sT, double* out, const double** a1, const double** b1,
+                            double** c1, const double** a2, const double** b2, double** c2, cudaStream_t s);
+
 // Schwarz reduction: Q[p] = sqrt(max_ab |diag of shellset p|).
 cudaError_t launch_schwarz_reduce(const int64_t* off, const int32_t* nab, int64_t n, const double* vals,
                                   double* Q, cudaStream_t s);

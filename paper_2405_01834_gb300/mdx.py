@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_xbatch_destroy.restype = None
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
     lib.mdx_plan_info.restype = I32
+    lib.mdx_batch_run_materialized.argtypes = [P, P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), P]
+    lib.mdx_batch_run_materialized.restype = I32
     lib.mdx_set_class_shape.argtypes = [P] + [I32] * 10
     lib.mdx_set_class_shape.restype = I32
     _lib = lib
@@ -340,6 +342,14 @@ class Batch:
         nl = ctypes.c_int32()
         self.eng._check(self.eng.lib.mdx_batch_run(self.eng.ctx, self.h, out.data_ptr(), out.numel(),
                                                    ctypes.byref(nl), _stream()), "mdx_batch_run")
+        return nl.value
+
+    def run_materialized(self, out: torch.Tensor) -> int:
+        """The materialized-Hermite variant (dense [p|q] matrices, batched DGEMMs); uncontracted classes only."""
+        nl = ctypes.c_int32()
+        self.eng._check(self.eng.lib.mdx_batch_run_materialized(self.eng.ctx, self.h, out.data_ptr(), out.numel(),
+                                                                ctypes.byref(nl), _stream()),
+                        "mdx_batch_run_materialized")
         return nl.value
 
     def autotune(self, out: torch.Tensor, max_trial: int = 256):
