@@ -85,6 +85,18 @@ def workload(args):
     return out
 
 
+def chunk_quartets(l: int, n: int, sms: int) -> int:
+    """Quartets per launch: output within CHUNK_BYTES, and a whole number of waves of one team per SM
+    (the large classes run one CTA per SM, so a launch of k*SMs quartets has no partial last wave)."""
+    per_q = inputs.ncart(l) ** 4 * 8
+    cq = max(1, min(n, CHUNK_BYTES // per_q))
+    if n > cq >= 2 * sms:
+        down = cq - cq % sms
+        up = down + sms   # the nearer whole number of waves, up to 12.5 % over the byte budget
+        cq = up if (up - cq < cq - down and up * per_q <= CHUNK_BYTES * 1.125) else down
+    return min(cq, n)
+
+
 def model_flops(l, n):
     return flops.eri4_flops(l, l, l, l) * n
 
@@ -487,10 +499,10 @@ def main():
     # prepare: inputs resident on the device, quartet lists split into chunks
     prepared = []
     max_chunk = 0
+    sms = props.multi_processor_count
     for l, b, q in work:
         db = mdx.DeviceBasis(b)
-        per_q = inputs.ncart(l) ** 4 * 8
-        cq = max(1, min(len(q), CHUNK_BYTES // per_q))
+        cq = chunk_quartets(l, len(q), sms)
         batches = [eng.batch_eri4(db, q[s:s + cq]) for s in range(0, len(q), cq)]
         max_chunk = max(max_chunk, max(bt.total for bt in batches))
         prepared.append((l, db, q, batches))
@@ -508,8 +520,7 @@ def main():
         for i, (l, db, q, batches) in enumerate(prepared):
             for bt in batches:
                 bt.close()
-            per_q = inputs.ncart(l) ** 4 * 8
-            cq = max(1, min(len(q), CHUNK_BYTES // per_q))
+            cq = chunk_quartets(l, len(q), sms)
             prepared[i] = (l, db, q, [eng.batch_eri4(db, q[s:s + cq]) for s in range(0, len(q), cq)])
     stream = torch.cuda.current_stream()
 
@@ -633,10 +644,9 @@ def e2e(eng, work, args, torch):
     (on a second stream) overlaps the evaluation of the next chunk."""
     from paper_2405_01834_gb300 import mdx
     host = []
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     for l, b, q in work:
-        per_q = inputs.ncart(l) ** 4 * 8
-        cq = max(1, min(len(q), CHUNK_BYTES // per_q))
-        host.append((l, b, torch.from_numpy(q).pin_memory(), cq))
+        host.append((l, b, torch.from_numpy(q).pin_memory(), chunk_quartets(l, len(q), sms)))
     max_out = max(min(len(q), cq) * inputs.ncart(l) ** 4 for l, b, q, cq in host)
     out_dev = [torch.empty(max_out, dtype=torch.float64, device="cuda") for _ in range(2)]
     out_host = [torch.empty(max_out, dtype=torch.float64).pin_memory() for _ in range(2)]

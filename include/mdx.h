@@ -99,8 +99,13 @@ mdx_status mdx_sync(mdx_ctx* ctx, void* stream);
  *   shellset sizes in quartet order); out_offsets[n] is the total.
  * Returns MDX_ECAPACITY (writing nothing) if the total exceeds out_capacity.
  * Copies the quartet list and the shell l/nprim arrays to the host and
- * synchronises `stream` once to group quartets by class. n = 0 is allowed
- * and writes out_offsets[0] = 0. */
+ * synchronises `stream` to group quartets by class, then enqueues the kernels
+ * and returns without waiting for them (results are ready when `stream`
+ * reaches this point; errors their kernels record are returned by the next
+ * call or mdx_sync). Its per-call device arrays are context workspace, never
+ * cudaMalloc/cudaFree, so work on other streams is not stalled; calls of one
+ * context that overlap must be issued on one stream. n = 0 is allowed and
+ * writes out_offsets[0] = 0. */
 mdx_status mdx_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
                     double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
 

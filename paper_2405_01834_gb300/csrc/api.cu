@@ -220,6 +220,7 @@ struct mdx_batch {
   std::vector<int64_t> qorig;     // caller index of each class-sorted quartet
   double model_flops = 0.0;
   double exec_fma = 0.0;
+  bool owned = true;              // device arrays belong to the batch (else: context workspace of one call)
 };
 
 // Several molecules' exchange builds prepared together (one super basis, one
@@ -263,8 +264,10 @@ void xbatch_free(mdx_xbatch* x) {
 
 void batch_free(mdx_batch* b) {
   if (!b) return;
-  cudaFree(b->jobs); cudaFree(b->pair_rec); cudaFree(b->recs); cudaFree(b->recs_s);
-  cudaFree(b->qp); cudaFree(b->qoff); cudaFree(b->offsets);
+  if (b->owned) {
+    cudaFree(b->jobs); cudaFree(b->pair_rec); cudaFree(b->recs); cudaFree(b->recs_s);
+    cudaFree(b->qp); cudaFree(b->qoff); cudaFree(b->offsets);
+  }
   delete b;
 }
 
@@ -292,10 +295,14 @@ double model_flops_class(const ClassKey& k) {
 
 // Host preparation of a batch: primitive-pair jobs, class grouping, plans,
 // uploads. Synchronises `s` before returning (host vectors go out of scope).
+// call_ws: the device arrays live in context workspace (one-shot calls: no
+// cudaMalloc / cudaFree, whose implicit device-wide synchronisation would
+// stall other streams; consecutive calls on one stream reuse it in order).
 mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const HostBasis& h0,
                          const HostBasis& h1, const Batch& bt, const std::vector<int64_t>& offs, mdx_batch** out,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool call_ws = false) {
   std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> B(new mdx_batch(), batch_free);
+  B->owned = !call_ws;
   B->ctx = c;
   B->n = (int64_t)bt.qp.size();
   B->total = offs.back();
@@ -344,12 +351,22 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     B->exec_fma += plan->exec_fma * (double)kv.second.size();
   }
   B->njobs = (int64_t)jobs.size();
+  if (call_ws) {
+    if ((st = upload(c, "call_jobs", jobs, &B->jobs, s)) != MDX_OK) return st;
+    if ((st = upload(c, "call_pair_rec", pair_rec, &B->pair_rec, s)) != MDX_OK) return st;
+    if ((st = upload(c, "call_qp", qp_sorted, &B->qp, s)) != MDX_OK) return st;
+    if ((st = upload(c, "call_qoff", qoff_sorted, &B->qoff, s)) != MDX_OK) return st;
+    if ((st = upload(c, "call_offsets", offs, &B->offsets, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "call_recs", (size_t)std::max<int64_t>(roff, 1), &B->recs, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "call_recs_s", (size_t)std::max<int64_t>(roff, 1), &B->recs_s, s)) != MDX_OK) return st;
+  } else {
   if ((st = dev_upload(c, jobs, &B->jobs, s)) != MDX_OK) return st;
   if ((st = dev_upload(c, pair_rec, &B->pair_rec, s)) != MDX_OK) return st;
   if ((st = dev_upload(c, qp_sorted, &B->qp, s)) != MDX_OK) return st;
   if ((st = dev_upload(c, qoff_sorted, &B->qoff, s)) != MDX_OK) return st;
   if ((st = dev_upload(c, offs, &B->offsets, s)) != MDX_OK) return st;
-  if (roff > 0) {
+  }
+  if (roff > 0 && !call_ws) {
     if (cudaMalloc(&B->recs, roff * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&B->recs_s, roff * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
@@ -415,7 +432,7 @@ struct PairIndex {
 };
 
 mdx_status make_batch4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool call_ws = false) {
   HostBasis hb;
   mdx_status st = fetch_basis(c, basis, hb, s);
   if (st != MDX_OK) return st;
@@ -435,11 +452,11 @@ mdx_status make_batch4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quarte
     bt.qoff[q] = offs[q];
     offs[q + 1] = offs[q] + (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * ncart(hb.l[s4[2]]) * ncart(hb.l[s4[3]]);
   }
-  return batch_prepare(c, basis, nullptr, hb, hb, bt, offs, out, s);
+  return batch_prepare(c, basis, nullptr, hb, hb, bt, offs, out, s, call_ws);
 }
 
 mdx_status make_batch3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
-                       mdx_batch** out, cudaStream_t s) {
+                       mdx_batch** out, cudaStream_t s, bool call_ws = false) {
   HostBasis ha, ho;
   mdx_status st = fetch_basis(c, aux, ha, s);
   if (st != MDX_OK) return st;
@@ -460,20 +477,21 @@ mdx_status make_batch3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, c
     bt.qoff[q] = offs[q];
     offs[q + 1] = offs[q] + (int64_t)ncart(ha.l[t3[0]]) * ncart(ho.l[t3[1]]) * ncart(ho.l[t3[2]]);
   }
-  return batch_prepare(c, aux, orb, ha, ho, bt, offs, out, s);
+  return batch_prepare(c, aux, orb, ha, ho, bt, offs, out, s, call_ws);
 }
 
 // create, run into `out`, copy offsets, destroy (synchronous)
+// One-shot evaluation of a batch built in context workspace: reports errors
+// that earlier kernels recorded, enqueues the work and returns without
+// waiting for it (its own kernel errors surface at the next call or mdx_sync).
 mdx_status run_once(mdx_ctx* c, mdx_batch* B, double* out, int64_t cap, int64_t* out_offsets, cudaStream_t s) {
   std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
   if (B->total > cap) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  mdx_status st = check_device_error(c, s);
+  if (st != MDX_OK) return st;
   cudaError_t e = cudaMemcpyAsync(out_offsets, B->offsets, (B->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "offsets");
-  mdx_status st = batch_run(c, B, out, nullptr, s);
-  if (st != MDX_OK) return st;
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "batch run");
-  return check_device_error(c, s);
+  return batch_run(c, B, out, nullptr, s);
 }
 
 }  // namespace
@@ -548,7 +566,7 @@ mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets,
     return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
   }
   mdx_batch* B = nullptr;
-  mdx_status st = make_batch4(c, basis, quartets, n, &B, s);
+  mdx_status st = make_batch4(c, basis, quartets, n, &B, s, true);
   if (st != MDX_OK) return st;
   return run_once(c, B, out, out_capacity, out_offsets, s);
 }
@@ -624,7 +642,7 @@ mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, cons
     return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
   }
   mdx_batch* B = nullptr;
-  mdx_status st = make_batch3(c, aux, orb, triplets, n, &B, s);
+  mdx_status st = make_batch3(c, aux, orb, triplets, n, &B, s, true);
   if (st != MDX_OK) return st;
   return run_once(c, B, out, out_capacity, out_offsets, s);
 }

@@ -165,14 +165,12 @@ __device__ void compute_R(const QuartetLaunch& a, double* ws, int tl, unsigned m
   const PlanDev& P = a.plan;
   const int T = P.T;
   const int L = P.L;
-  double* scal = ws + P.o_scal;
   double* G = ws + P.o_G;
   const double* rb = ws + P.o_recb;
   const double* rk = ws + P.o_reck;
   // every lane needs P - Q for the R levels; the Boys lanes (m = tl, tl + T,
   // ... <= L) also derive rho, T and the prefactor (no barrier needed)
   const double PQx = rb[2] - rk[2], PQy = rb[3] - rk[3], PQz = rb[4] - rk[4];
-  if (tl == 0) { scal[0] = PQx; scal[1] = PQy; scal[2] = PQz; }
   if (tl <= L) {
     const double zp = rb[0], izp = rb[1], zq = rk[0], izq = rk[1];
     const double s = zp + zq;

@@ -112,7 +112,7 @@ struct PlanDev {
   int32_t L, Lb, Lk, Nb, Nk, hb;         // hb = Nt(Lb)
   int32_t T, teams_per_cta, team_doubles;
   int32_t recb, reck;                    // record sizes (doubles)
-  int32_t o_recb, o_reck, o_scal, o_G, o_R0, o_R1, o_A, o_B, o_X, o_C1, o_OUT;
+  int32_t o_recb, o_reck, o_scal, o_G, o_R0, o_R1, o_A, o_B, o_X, o_C1, o_OUT;   // o_scal: end of the records
   int32_t c1size;                        // C1 doubles per column
   int32_t ngroups, ncols_max;
   int32_t nb1, nb23;

@@ -231,8 +231,8 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   // fixed part of the workspace
   P.o_recb = 0;
   P.o_reck = P.recb;
-  P.o_scal = P.o_reck + P.reck;          // PQ[3], pad, Taylor c[8]
-  P.o_G = P.o_scal + 16;
+  P.o_scal = P.o_reck + P.reck;          // end of the records
+  P.o_G = P.o_scal;
   P.o_R0 = P.o_G + ((P.L + 2 + 1) & ~1);
   const int r0size = tet(P.L + 1);
   const int r1size = tet(P.L);
