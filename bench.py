@@ -640,8 +640,9 @@ def main():
 
 def e2e(eng, work, args, torch):
     """One step through mdx_eri4 with host buffers: pinned quartet arrays copied in, integrals copied back to
-    pinned host memory, chunk by chunk. Two device output buffers: the copy of one chunk's integrals to the host
-    (on a second stream) overlaps the evaluation of the next chunk."""
+    pinned host memory, chunk by chunk. Two device output buffers; the host copy of chunk i-1 is enqueued (on a
+    second stream) right after chunk i's kernels, so it runs while they compute. (Enqueued earlier, it would
+    sit in the copy engine ahead of mdx_eri4's small index downloads for chunk i and serialise the two.)"""
     from paper_2405_01834_gb300 import mdx
     host = []
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -653,9 +654,18 @@ def e2e(eng, work, args, torch):
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
     copied = [None, None]   # event: the host copy out of buffer k has finished
+    pending = None          # (buffer, doubles) computed but not yet copied out
     h2d = d2h = 0
     tot_f = 0.0
     k = 0
+
+    def copy_out(buf, n, ready):
+        with torch.cuda.stream(copy):
+            copy.wait_event(ready)
+            out_host[buf][:n].copy_(out_dev[buf][:n], non_blocking=True)
+            copied[buf] = torch.cuda.Event()
+            copied[buf].record(copy)
+
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for l, b, qh, cq in host:
@@ -667,18 +677,18 @@ def e2e(eng, work, args, torch):
                 comp.wait_event(copied[k])
             qd = qh[s:s + cq].to("cuda", non_blocking=True)
             h2d += qd.numel() * 4
-            v, off = eng.eri4(db, qd, out=out_dev[k])
+            eng.eri4(db, qd, out=out_dev[k])
+            done = torch.cuda.Event()   # this chunk's kernels, for its copy one iteration later
+            done.record(comp)
             n = qd.shape[0] * inputs.ncart(l) ** 4
-            ready = torch.cuda.Event()
-            ready.record(comp)
-            with torch.cuda.stream(copy):
-                copy.wait_event(ready)
-                out_host[k][:n].copy_(v[:n], non_blocking=True)
-                copied[k] = torch.cuda.Event()
-                copied[k].record(copy)
+            if pending is not None:
+                copy_out(*pending)
+            pending = (k, n, done)
             d2h += n * 8
             k ^= 1
         tot_f += model_flops(l, qh.shape[0])
+    if pending is not None:
+        copy_out(*pending)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"value": round(tot_f / dt * 1e-9, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
