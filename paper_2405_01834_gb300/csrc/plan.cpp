@@ -369,7 +369,9 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   P.o_X = o_region + reg;
   P.o_C1 = P.o_X + cmax * P.hb;
   P.o_OUT = P.o_C1 + cmax * P.c1size;
-  P.team_doubles = ((P.o_OUT + cmax * P.Nb) + 1) & ~1;
+  // odd: the workspaces of the teams of a CTA start on different shared-memory
+  // bank pairs, so lanes of different teams at the same offset do not conflict
+  P.team_doubles = (P.o_OUT + cmax * P.Nb) | 1;
   P.ncols_max = cmax;
   if (P.team_doubles >= 65536 || P.team_doubles * 8 > smem_budget_bytes) {
     err = "workspace exceeds the shared-memory budget";
