@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-    procs, objs = [], []
+    cmds, objs = [], []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         if src.endswith(".cu"):
@@ -55,10 +55,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 cmd.insert(1, "-Xptxas=-v")
         else:
             cmd = [nvcc, *common, "-x", "c++", "-c", src, "-o", obj]
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        cmds.append(cmd)
         objs.append(obj)
-    failed = []
-    for cmd, p in procs:
+    # at most one compiler per core at a time (the register-kernel units are large)
+    limit = max(1, os.cpu_count() or 1)
+    failed, running, pending = [], [], list(cmds)
+    while pending or running:
+        while pending and len(running) < limit:
+            cmd = pending.pop(0)
+            running.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        cmd, p = running.pop(0)
         out, _ = p.communicate()
         if verbose or p.returncode != 0:
             sys.stderr.write(out.decode(errors="replace"))

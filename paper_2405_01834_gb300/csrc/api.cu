@@ -818,7 +818,8 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
       for (int single : {96 * 1024, 40 * 1024})
         for (int T : {0, 1, 4, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, single, 1});
     }
-    if (reg_eligible(r.key.la, r.key.lb, r.key.lc, r.key.ld))
+    const ClassKey& rk = r.key;
+    if (reg_eligible(rk.la, rk.lb, rk.lc, rk.ld) || reg_xs_eligible(rk.la, rk.lb, rk.lc, rk.ld))
       cands.push_back(PlanConfig{0, 200 * 1024, 96 * 1024, 2});
     float best_ms = 1e30f;
     PlanConfig best{};

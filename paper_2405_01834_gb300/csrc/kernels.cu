@@ -660,10 +660,14 @@ cudaError_t launch_reg_part08(int code, const QuartetLaunch& a, cudaStream_t s, 
 cudaError_t launch_reg_part09(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
 cudaError_t launch_reg_part10(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
 cudaError_t launch_reg_part11(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part12(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part13(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
+cudaError_t launch_reg_part14(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled);
 using RegPart = cudaError_t (*)(int, const QuartetLaunch&, cudaStream_t, bool*);
 static const RegPart kRegParts[] = {launch_reg_part00, launch_reg_part01, launch_reg_part02, launch_reg_part03,
                                     launch_reg_part04, launch_reg_part05, launch_reg_part06, launch_reg_part07,
-                                    launch_reg_part08, launch_reg_part09, launch_reg_part10, launch_reg_part11};
+                                    launch_reg_part08, launch_reg_part09, launch_reg_part10, launch_reg_part11,
+                                    launch_reg_part12, launch_reg_part13, launch_reg_part14};
 
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
   if (a.nq <= 0) return cudaSuccess;

@@ -65,6 +65,36 @@ constexpr int reg_footprint(int la, int lb, int lc, int ld) {
 constexpr bool reg_eligible(int la, int lb, int lc, int ld) {
   return la + lb + lc + ld <= 4 && reg_footprint(la, lb, lc, ld) <= 100;
 }
+// Size of the unrolled register-kernel body of a class: the R recursion, the
+// ket transform (E products and FMAs per Cartesian ket pair and Hermite bra
+// index) and the bra transform.
+constexpr int reg_body_size(int la, int lb, int lc, int ld) {
+  int c = 2 * nherm(la + lb + lc + ld);
+  for (int cx = lc; cx >= 0; --cx)
+    for (int cy = lc - cx; cy >= 0; --cy)
+      for (int dx = ld; dx >= 0; --dx)
+        for (int dy = ld - dx; dy >= 0; --dy) {
+          const int n = (cx + dx + 1) * (cy + dy + 1) * (lc - cx - cy + ld - dx - dy + 1);
+          c += n + nherm(la + lb) * n;
+        }
+  for (int ax = la; ax >= 0; --ax)
+    for (int ay = la - ax; ay >= 0; --ay)
+      for (int bx = lb; bx >= 0; --bx)
+        for (int by = lb - bx; by >= 0; --by) {
+          const int n = (ax + bx + 1) * (ay + by + 1) * (la - ax - ay + lb - bx - by + 1);
+          c += n + ncart(lc) * ncart(ld) * n;
+        }
+  return c;
+}
+// Further classes of total angular momentum <= 6 have a variant with R in
+// registers and [p|cd] plus the shellset in shared memory (64 threads x their
+// doubles within 200 KB), as long as the unrolled body stays small enough to
+// compile quickly.
+constexpr bool reg_xs_eligible(int la, int lb, int lc, int ld) {
+  return !reg_eligible(la, lb, lc, ld) && la + lb + lc + ld <= 6 &&
+         (nherm(la + lb) + ncart(la) * ncart(lb)) * ncart(lc) * ncart(ld) * 64 * 8 <= 200 * 1024 &&
+         reg_body_size(la, lb, lc, ld) <= 1200;
+}
 
 // ----------------------------------------------------------------- programs
 // A "step" computes entries out = sum_{k<n} coef[c + k*s] * src[x + k*s]

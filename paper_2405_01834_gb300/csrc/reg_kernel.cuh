@@ -71,8 +71,25 @@ __device__ __forceinline__ void sfor(F&& f) {
   if constexpr (N > 0) sfor_impl(f, std::make_integer_sequence<int, N>{});
 }
 
-template <int LA, int LB, int LC, int LD, bool DIGEST>
-__global__ void __launch_bounds__(128) k_reg(const QuartetLaunch a) {
+// Per-thread array of N doubles: in registers (SH = false), or one column of a
+// block-wide shared-memory table (element i of thread t at p[i * kXsBlock]).
+constexpr int kXsBlock = 64;
+template <bool SH, int N>
+struct TArr {
+  double r[N];
+  __device__ __forceinline__ double& operator[](int i) { return r[i]; }
+};
+template <int N>
+struct TArr<true, N> {
+  double* p;
+  __device__ __forceinline__ double& operator[](int i) { return p[i * kXsBlock]; }
+};
+
+// XS = false: R, [p|cd] and the shellset in registers (classes with
+// reg_eligible). XS = true: R in registers, [p|cd] and the shellset in shared
+// memory (classes with reg_xs_eligible, total angular momentum <= 6).
+template <int LA, int LB, int LC, int LD, bool DIGEST, bool XS>
+__global__ void __launch_bounds__(XS ? kXsBlock : 128) k_reg(const QuartetLaunch a) {
   constexpr int Lb = LA + LB, Lk = LC + LD, L = Lb + Lk;
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int Nb = NA * NB, Nk = NC * ND;
@@ -80,6 +97,7 @@ __global__ void __launch_bounds__(128) k_reg(const QuartetLaunch a) {
   constexpr int RB = rec_size(LA, LB), RK = rec_size(LC, LD);
   constexpr int EB = etab_size(LA, LB), EK = etab_size(LC, LD);
 
+  extern __shared__ double xs_smem[];
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nq) return;
   const int2 qp = a.qpairs[q];
@@ -88,7 +106,12 @@ __global__ void __launch_bounds__(128) k_reg(const QuartetLaunch a) {
   const double* __restrict__ boys = a.boys;
   const int Kb = a.plan.Kb, Kk = a.plan.Kk;
 
-  double V[Nb * Nk];
+  TArr<XS, Nb * Nk> V;
+  TArr<XS, HB * Nk> X;
+  if constexpr (XS) {
+    V.p = xs_smem + threadIdx.x;
+    X.p = xs_smem + Nb * Nk * kXsBlock + threadIdx.x;
+  }
   sfor<Nb * Nk>([&](auto i) { V[i] = 0.0; });
 
   for (int pb = 0; pb < Kb; ++pb) {
@@ -97,7 +120,6 @@ __global__ void __launch_bounds__(128) k_reg(const QuartetLaunch a) {
     const double Px = __ldg(rb + 2), Py = __ldg(rb + 3), Pz = __ldg(rb + 4);
     // 2 pi^(5/2) / zp * c_a c_b K_ab (the ket part and 1/sqrt(zp+zq) per ket primitive)
     const double prefb = 34.986836655249725693 * izp * __ldg(rb + 5);
-    double X[HB * Nk];
     sfor<HB * Nk>([&](auto i) { X[i] = 0.0; });
 
     for (int pk = 0; pk < Kk; ++pk) {
@@ -282,11 +304,26 @@ __global__ void __launch_bounds__(128) k_reg(const QuartetLaunch a) {
 
 template <int LA, int LB, int LC, int LD>
 cudaError_t launch_reg_class(const QuartetLaunch& a, cudaStream_t s) {
-  const int bs = 128;
+  constexpr bool XS = !reg_eligible(LA, LB, LC, LD);
+  constexpr int bs = XS ? kXsBlock : 128;
+  constexpr int Nk = ncart(LC) * ncart(LD);
+  constexpr size_t shm = XS ? (size_t)(ncart(LA) * ncart(LB) * Nk + nherm(LA + LB) * Nk) * kXsBlock * sizeof(double) : 0;
   const int64_t grid = (a.nq + bs - 1) / bs;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  if (a.D) k_reg<LA, LB, LC, LD, true><<<(unsigned)grid, bs, 0, s>>>(a);
-  else k_reg<LA, LB, LC, LD, false><<<(unsigned)grid, bs, 0, s>>>(a);
+  if constexpr (shm > 48 * 1024) {
+    static bool attr = false;   // opt in to more than 48 KB of dynamic shared memory, once per instance
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_reg<LA, LB, LC, LD, true, XS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reg<LA, LB, LC, LD, false, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+  }
+  if (a.D) k_reg<LA, LB, LC, LD, true, XS><<<(unsigned)grid, bs, shm, s>>>(a);
+  else k_reg<LA, LB, LC, LD, false, XS><<<(unsigned)grid, bs, shm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -297,7 +334,8 @@ using RegLaunchFn = cudaError_t (*)(const QuartetLaunch&, cudaStream_t);
 template <int C>
 constexpr RegLaunchFn reg_fn() {
   constexpr int la = C / 343, lb = C / 49 % 7, lc = C / 7 % 7, ld = C % 7;
-  if constexpr (reg_eligible(la, lb, lc, ld)) return &launch_reg_class<la, lb, lc, ld>;
+  if constexpr (reg_eligible(la, lb, lc, ld) || reg_xs_eligible(la, lb, lc, ld))
+    return &launch_reg_class<la, lb, lc, ld>;
   else return nullptr;
 }
 template <int BASE, int... I>

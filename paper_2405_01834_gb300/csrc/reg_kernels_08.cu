@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 357..440, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 392..412, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part08(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 357 || code >= 441) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<357>(code, std::make_integer_sequence<int, 84>{});
+  if (code < 392 || code >= 413) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<392>(code, std::make_integer_sequence<int, 21>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 441..692, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 413..685, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part09(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 441 || code >= 693) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<441>(code, std::make_integer_sequence<int, 252>{});
+  if (code < 413 || code >= 686) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<413>(code, std::make_integer_sequence<int, 273>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

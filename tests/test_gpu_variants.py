@@ -99,3 +99,54 @@ def test_shape_setter_rejects():
     with pytest.raises(mdx.MdxError):
         eng.set_class_shape(1, 1, 1, 1, variant=5)
     eng.close()
+
+
+# classes of total angular momentum 5-6 (and L = 4 ones too large for registers alone):
+# R in registers, [p|cd] and the shellset in shared memory
+XS_CLASSES = [((3, 0, 1, 0), (1, 3, 2, 3)), ((1, 1, 1, 1), (2, 1, 1, 2)), ((2, 1, 1, 0), (1, 2, 3, 1)),
+              ((6, 0, 0, 0), (1, 1, 2, 2)), ((2, 0, 1, 1), (1, 2, 2, 1)), ((5, 0, 0, 0), (1, 1, 2, 2)),
+              ((1, 0, 0, 3), (2, 2, 1, 1)), ((3, 0, 0, 1), (1, 1, 2, 2)), ((4, 0, 1, 0), (1, 1, 1, 1))]
+
+
+@pytest.mark.parametrize("lq,K", XS_CLASSES)
+def test_shared_memory_register_variant(lq, K):
+    b, q = inputs.class_sweep(lq, n_bra=6, n_ket=5, seed=43, K=K)
+    ref, roff = oracle.eri4(b, q)
+    refl = oracle.eri4(b, q, precision=1)[0]
+    got = {}
+    for variant in (1, 2):
+        eng = mdx.Engine(0)
+        eng.set_class_shape(*lq, *_kb(K), variant=variant)
+        v, off = eng.eri4(mdx.DeviceBasis(b), q)
+        torch.cuda.synchronize()
+        eng.sync()
+        v, off = v.cpu().numpy(), off.cpu().numpy()
+        assert np.array_equal(off, roff)
+        parity.check(v[: off[-1]], ref, refl, "%s K=%s variant %d" % (lq, K, variant), off)
+        got[variant] = v[: off[-1]]
+        eng.close()
+    assert np.max(np.abs(got[1] - got[2])) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("la", [5, 6])
+def test_three_center_shared_memory_variant(la):
+    """[a|ss] and [a|ps] with contracted orbital pairs (K = 36 / 18) in the shared-memory variant."""
+    aux, orb = inputs.df_cluster(seed=1003, n_atoms=3)
+    rng = np.random.Generator(np.random.PCG64(70 + la))
+    A = rng.choice(np.where(aux.l == la)[0], 2, replace=False)
+    pairs = [(c, d) for c in range(orb.n_shells) for d in range(c + 1) if orb.l[c] + orb.l[d] <= 1]
+    P = np.array(pairs)[rng.choice(len(pairs), 6, replace=False)]
+    trip = np.array([(a, c, d) for a in A for c, d in P], dtype=np.int32)
+    eng = mdx.Engine(0)
+    for lc, ld in ((0, 0), (1, 0), (0, 1)):
+        kc = {0: 6, 1: 3}
+        try:
+            eng.set_class_shape(la, 0, lc, ld, 1, kc[lc] * kc[ld], one_centre=True, variant=2)
+        except mdx.MdxError:
+            pass    # [i|ps] is above the size limit of the variant: stays on the team kernel
+    v, off = eng.eri3(mdx.DeviceBasis(aux), mdx.DeviceBasis(orb), trip)
+    torch.cuda.synchronize()
+    eng.sync()
+    ref, roff = oracle.eri3(aux, orb, trip)
+    parity.check(v.cpu().numpy()[: roff[-1]], ref, oracle.eri3(aux, orb, trip, precision=1)[0], "3c xs la=%d" % la, roff)
+    eng.close()
