@@ -514,7 +514,8 @@ def main():
         # later chunks of the class use the choice when they are re-planned
         for l, db, q, batches in prepared:
             t0 = time.perf_counter()
-            batches[0].autotune(out, max_trial=max(304, min(len(q), 4096 // max(1, l))))
+            # trials large enough to fill the GPU with one-thread-per-quartet candidates at low l
+            batches[0].autotune(out, max_trial=max(304, min(len(q), 65536 // max(1, l) ** 3)))
             tuned[CLASS_NAMES[l]] = round(time.perf_counter() - t0, 2)
         # re-prepare so every chunk picks up the tuned plans
         for i, (l, db, q, batches) in enumerate(prepared):

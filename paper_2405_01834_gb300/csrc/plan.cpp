@@ -420,7 +420,7 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   const bool has_reg = reg_eligible(key.la, key.lb, key.lc, key.ld) || reg_xs_eligible(key.la, key.lb, key.lc, key.ld);
   if (cfg.variant == 2 && !has_reg) { err = "class has no register kernel"; return false; }
   // default: the register kernel (either variant) where the class has one; measured 1.6-4.4x faster than
-  // the best team shape on contracted and uncontracted classes of total angular momentum <= 6
+  // the team kernel on contracted and uncontracted classes of total angular momentum <= 6
   P.reg = (has_reg && cfg.variant != 1) ? 1 : 0;
   if (P.reg) {
     // its FP64 work: per primitive quartet Boys, R, the ket E products and
