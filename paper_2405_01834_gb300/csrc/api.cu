@@ -1220,7 +1220,29 @@ mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* 
         a.gpos = v.pos;
         a.gsign = v.sign;
         for (int k = 0; k < 4; ++k) a.lorig[k] = l0[k];
-        e = launch_quartets(a, s);
+        if (plan->d.reg) {
+          // register kernel: shifted shellsets to workspace (back to back), then the
+          // gradient contraction, in chunks of at most 1 GiB of shellsets
+          const int64_t per = (int64_t)plan->d.Nb * plan->d.Nk;
+          const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(a.nq, (int64_t(1) << 27) / per));
+          double* V;
+          if ((st = ensure(c, "g_shellsets", (size_t)(chunk * per), &V, s)) != MDX_OK) return st;
+          for (int64_t q0 = 0; q0 < a.nq && e == cudaSuccess; q0 += chunk) {
+            QuartetLaunch part = a;
+            part.qpairs = a.qpairs + q0;
+            part.nq = std::min(chunk, a.nq - q0);
+            QuartetLaunch st_part = part;
+            st_part.D = nullptr;
+            st_part.grad = nullptr;
+            st_part.energy = nullptr;
+            st_part.out = V;
+            st_part.qout = nullptr;
+            e = launch_quartets(st_part, s);
+            if (e == cudaSuccess) e = launch_grad_contract(part, V, s);
+          }
+        } else {
+          e = launch_quartets(a, s);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "gradient quartet launch");
       }
     }

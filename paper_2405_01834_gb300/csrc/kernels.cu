@@ -452,6 +452,85 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
   atomicAdd(gD + 0, -f * s0); atomicAdd(gD + 1, -f * s1); atomicAdd(gD + 2, -f * s2);
 }
 
+// Exchange-gradient contraction of shellsets already written to memory (the
+// register-kernel path of mdx_exchange_grad): the same sums as grad_group,
+// one warp per quartet, V = the launch's (shifted) shellset of quartet q at
+// V + q N_b N_k.
+__global__ void k_grad_contract(const QuartetLaunch a, const double* __restrict__ V) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= a.nq) return;
+  const PlanDev& P = a.plan;
+  const int2 qp = a.qpairs[q];
+  const int2 bp = a.pair_shells[qp.x], kp = a.pair_shells[qp.y];
+  const int si = bp.x, sj = bp.y, sk = kp.x, sl = kp.y;
+  const double w = (si == sj ? 0.5 : 1.0) * (sk == sl ? 0.5 : 1.0) * (qp.x == qp.y ? 0.5 : 1.0);
+  const int nb_s = d_ncart(P.lb), nd_s = d_ncart(P.ld);
+  const int64_t nao = a.nao;
+  const int64_t ai = a.ao_off[si], aj = a.ao_off[sj], ak = a.ao_off[sk], al = a.ao_off[sl];
+  const int pos = a.gpos, sg = a.gsign;
+  const int lsh = pos == 0 ? P.la : (pos == 1 ? P.lb : P.lc);
+  const int lorg = pos >= 0 ? a.lorig[pos] : 0;
+  const int Nk = P.Nk, tot = P.Nb * P.Nk;
+  const double* v0 = V + q * (int64_t)tot;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int e = lane; e < tot; e += 32) {
+    const int ab = e / Nk, cd = e - ab * Nk;
+    const double v = __ldg(v0 + e);
+    const int ia = ab / nb_s, ib = ab - ia * nb_s, ic = cd / nd_s, id = cd - ic * nd_s;
+    if (pos < 0) {
+      s0 = fma(v, dens_G(a.D, nao, ai + ia, aj + ib, ak + ic, al + id), s0);
+      continue;
+    }
+    const int sidx = pos == 0 ? ia : (pos == 1 ? ib : ic);
+    const uint32_t xyz = c_cart[lsh][sidx];
+    const int cmp[3] = {(int)(xyz & 0xff), (int)((xyz >> 8) & 0xff), (int)((xyz >> 16) & 0xff)};
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+      int o[3] = {cmp[0], cmp[1], cmp[2]};
+      double wt;
+      if (sg > 0) {
+        if (o[dir] == 0) continue;
+        o[dir] -= 1;
+        wt = 1.0;
+      } else {
+        o[dir] += 1;
+        wt = -(double)o[dir];
+      }
+      const int oidx = d_tri(lorg - o[0]) + o[2];
+      const int ja = pos == 0 ? oidx : ia, jb = pos == 1 ? oidx : ib, jc = pos == 2 ? oidx : ic;
+      const double t = wt * v * dens_G(a.D, nao, ai + ja, aj + jb, ak + jc, al + id);
+      if (dir == 0) s0 += t; else if (dir == 1) s1 += t; else s2 += t;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  }
+  if (lane != 0) return;
+  const double f = a.alpha * 4.0 * w;
+  if (pos < 0) {
+    atomicAdd(a.energy, f * s0);
+    return;
+  }
+  const int sh = pos == 0 ? si : (pos == 1 ? sj : sk);
+  double* gA = a.grad + 3 * (int64_t)a.atom[sh];
+  double* gD = a.grad + 3 * (int64_t)a.atom[sl];
+  atomicAdd(gA + 0, f * s0); atomicAdd(gA + 1, f * s1); atomicAdd(gA + 2, f * s2);
+  atomicAdd(gD + 0, -f * s0); atomicAdd(gD + 1, -f * s1); atomicAdd(gD + 2, -f * s2);
+}
+
+cudaError_t launch_grad_contract(const QuartetLaunch& a, const double* V, cudaStream_t s) {
+  if (a.nq <= 0) return cudaSuccess;
+  const int64_t threads = a.nq * 32;
+  const int bs = 256;
+  const int64_t grid = (threads + bs - 1) / bs;
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  k_grad_contract<<<(unsigned)grid, bs, 0, s>>>(a, V);
+  return cudaGetLastError();
+}
+
 // The work of one team on one shell quartet q (all groups, all primitives,
 // store / digestion / gradient epilogue). Inactive teams run the same control
 // flow on a shadow quartet (so that barriers match) and write nothing global.
@@ -470,7 +549,8 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
     team_sync<CTA>(mask);
     compute_R<CTA>(a, ws, tl, mask);
   }
-  double* outq = a.D ? nullptr : a.out + a.qout[q];
+  // qout == nullptr: shellsets back to back, N_b N_k doubles each
+  double* outq = a.D ? nullptr : a.out + (a.qout ? a.qout[q] : q * (int64_t)P.Nb * P.Nk);
   // store epilogue: b23 of the last bra primitive writes the shellset to global
   // memory itself (no OUT pass, no barrier after it)
   const bool direct = !a.D && !a.grad;

@@ -90,6 +90,8 @@ cudaError_t launch_persistent(const PersistLaunch& pl, int64_t smem_bytes, int g
 const void* persistent_kernel_ptr();
 
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s);
+// Gradient epilogue over shellsets already in memory (V + q N_b N_k for quartet q of launch a).
+cudaError_t launch_grad_contract(const QuartetLaunch& a, const double* V, cudaStream_t s);
 
 // Exchange support: per shell-pair block max |D| (float), screening of unique
 // quartets into class buckets, K <- K + K^T.

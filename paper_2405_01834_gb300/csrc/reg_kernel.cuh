@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(XS ? kXsBlock : 128) k_reg(const QuartetLaunch
   }
 
   if constexpr (!DIGEST) {
-    double* o = a.out + a.qout[q];
+    double* o = a.out + (a.qout ? a.qout[q] : q * (int64_t)(Nb * Nk));   // no offsets: back to back
     sfor<Nb * Nk>([&](auto i) { o[i] = V[i]; });
   } else {
     // Exchange digestion of the unique quartet (ij|kl) with weight w, as in
