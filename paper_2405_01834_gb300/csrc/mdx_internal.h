@@ -67,8 +67,9 @@ constexpr bool reg_eligible(int la, int lb, int lc, int ld) {
 }
 // Size of the unrolled register-kernel body of a class: the R recursion, the
 // ket transform (E products and FMAs per Cartesian ket pair and Hermite bra
-// index) and the bra transform.
-constexpr int reg_body_size(int la, int lb, int lc, int ld) {
+// index) and, with_bra, the bra transform (the shared-memory variant runs the
+// bra transform and the epilogues as runtime loops).
+constexpr int reg_body_size(int la, int lb, int lc, int ld, bool with_bra = true) {
   int c = 2 * nherm(la + lb + lc + ld);
   for (int cx = lc; cx >= 0; --cx)
     for (int cy = lc - cx; cy >= 0; --cy)
@@ -77,6 +78,7 @@ constexpr int reg_body_size(int la, int lb, int lc, int ld) {
           const int n = (cx + dx + 1) * (cy + dy + 1) * (lc - cx - cy + ld - dx - dy + 1);
           c += n + nherm(la + lb) * n;
         }
+  if (!with_bra) return c;
   for (int ax = la; ax >= 0; --ax)
     for (int ay = la - ax; ay >= 0; --ay)
       for (int bx = lb; bx >= 0; --bx)
@@ -93,7 +95,7 @@ constexpr int reg_body_size(int la, int lb, int lc, int ld) {
 constexpr bool reg_xs_eligible(int la, int lb, int lc, int ld) {
   return !reg_eligible(la, lb, lc, ld) && la + lb + lc + ld <= 6 &&
          (nherm(la + lb) + ncart(la) * ncart(lb)) * ncart(lc) * ncart(ld) * 64 * 8 <= 200 * 1024 &&
-         reg_body_size(la, lb, lc, ld) <= 1200;
+         reg_body_size(la, lb, lc, ld, false) <= 1000;
 }
 
 // ----------------------------------------------------------------- programs

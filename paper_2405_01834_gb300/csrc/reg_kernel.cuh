@@ -229,39 +229,72 @@ __global__ void __launch_bounds__(XS ? kXsBlock : 128) k_reg(const QuartetLaunch
       });
     }
     // bra transform: V[ab][cd] += sum_{t,u,v} Ex Ey Ez X[tuv][cd]
-    sfor<NA>([&](auto ia) {
-      sfor<NB>([&](auto ib) {
-        constexpr int ax = cx(LA, ia), ay = cy(LA, ia), az = cz(LA, ia);
-        constexpr int bx = cx(LB, ib), by = cy(LB, ib), bz = cz(LB, ib);
-        constexpr int nx = ax + bx + 1, ny = ay + by + 1, nz = az + bz + 1;
-        const double* Ex = rb + kRecHeader + etab_off(LB, ax, bx);
-        const double* Ey = rb + kRecHeader + EB + etab_off(LB, ay, by);
-        const double* Ez = rb + kRecHeader + 2 * EB + etab_off(LB, az, bz);
-        double E[nx * ny * nz];
-        sfor<nx>([&](auto t) {
-          const double vx = __ldg(Ex + t);
-          sfor<ny>([&](auto u) {
-            const double vxy = vx * __ldg(Ey + u);
-            sfor<nz>([&](auto v) { E[(t * ny + u) * nz + v] = vxy * __ldg(Ez + v); });
-          });
-        });
-        sfor<Nk>([&](auto cd) {
-          constexpr int o = (ia * NB + ib) * Nk + cd;
-          double acc = V[o];
+    if constexpr (XS) {
+      // [p|cd] and the shellset are in shared memory: runtime loops over ab and
+      // (t,u,v), the ket pairs cd unrolled (keeps the unrolled body small)
+      for (int ia = 0; ia < NA; ++ia) {
+        const int ax = cx(LA, ia), ay = cy(LA, ia), az = LA - ax - ay;
+        for (int ib = 0; ib < NB; ++ib) {
+          const int bx = cx(LB, ib), by = cy(LB, ib), bz = LB - bx - by;
+          const double* Ex = rb + kRecHeader + etab_off(LB, ax, bx);
+          const double* Ey = rb + kRecHeader + EB + etab_off(LB, ay, by);
+          const double* Ez = rb + kRecHeader + 2 * EB + etab_off(LB, az, bz);
+          double acc[Nk];
+          sfor<Nk>([&](auto cd) { acc[cd] = 0.0; });
+          for (int t = 0; t <= ax + bx; ++t) {
+            const double vx = __ldg(Ex + t);
+            for (int u = 0; u <= ay + by; ++u) {
+              const double vxy = vx * __ldg(Ey + u);
+              for (int v = 0; v <= az + bz; ++v) {
+                const double e = vxy * __ldg(Ez + v);
+                const int h = hidx(Lb, t, u, v) * Nk;
+                sfor<Nk>([&](auto cd) { acc[cd] = fma(e, X[h + cd], acc[cd]); });
+              }
+            }
+          }
+          const int o = (ia * NB + ib) * Nk;
+          sfor<Nk>([&](auto cd) { V[o + cd] += acc[cd]; });
+        }
+      }
+    } else {
+      sfor<NA>([&](auto ia) {
+        sfor<NB>([&](auto ib) {
+          constexpr int ax = cx(LA, ia), ay = cy(LA, ia), az = cz(LA, ia);
+          constexpr int bx = cx(LB, ib), by = cy(LB, ib), bz = cz(LB, ib);
+          constexpr int nx = ax + bx + 1, ny = ay + by + 1, nz = az + bz + 1;
+          const double* Ex = rb + kRecHeader + etab_off(LB, ax, bx);
+          const double* Ey = rb + kRecHeader + EB + etab_off(LB, ay, by);
+          const double* Ez = rb + kRecHeader + 2 * EB + etab_off(LB, az, bz);
+          double E[nx * ny * nz];
           sfor<nx>([&](auto t) {
+            const double vx = __ldg(Ex + t);
             sfor<ny>([&](auto u) {
-              sfor<nz>([&](auto v) { acc = fma(E[(t * ny + u) * nz + v], X[hidx(Lb, t, u, v) * Nk + cd], acc); });
+              const double vxy = vx * __ldg(Ey + u);
+              sfor<nz>([&](auto v) { E[(t * ny + u) * nz + v] = vxy * __ldg(Ez + v); });
             });
           });
-          V[o] = acc;
+          sfor<Nk>([&](auto cd) {
+            constexpr int o = (ia * NB + ib) * Nk + cd;
+            double acc = V[o];
+            sfor<nx>([&](auto t) {
+              sfor<ny>([&](auto u) {
+                sfor<nz>([&](auto v) { acc = fma(E[(t * ny + u) * nz + v], X[hidx(Lb, t, u, v) * Nk + cd], acc); });
+              });
+            });
+            V[o] = acc;
+          });
         });
       });
-    });
+    }
   }
 
   if constexpr (!DIGEST) {
     double* o = a.out + (a.qout ? a.qout[q] : q * (int64_t)(Nb * Nk));   // no offsets: back to back
-    sfor<Nb * Nk>([&](auto i) { o[i] = V[i]; });
+    if constexpr (XS) {
+      for (int i = 0; i < Nb * Nk; ++i) o[i] = V[i];
+    } else {
+      sfor<Nb * Nk>([&](auto i) { o[i] = V[i]; });
+    }
   } else {
     // Exchange digestion of the unique quartet (ij|kl) with weight w, as in
     // the team kernel: K_ik += w D_jl V, K_il += w D_jk V, K_jk += w D_il V,
@@ -274,31 +307,72 @@ __global__ void __launch_bounds__(XS ? kXsBlock : 128) k_reg(const QuartetLaunch
     const double* __restrict__ D = mol >= 0 ? a.mol_D[mol] : a.D;
     double* K = mol >= 0 ? a.mol_K[mol] : a.K;
     const int64_t ai = a.ao_off[si], aj = a.ao_off[sj], ak = a.ao_off[sk], al = a.ao_off[sl];
-    auto Vat = [&](auto x, auto b, auto c, auto d) -> double { return V[((x * NB + b) * NC + c) * ND + d]; };
-    sfor<NA>([&](auto x) {
-      sfor<NC>([&](auto c) {   // K_ik
-        double s1 = 0.0;
-        sfor<NB>([&](auto b) { sfor<ND>([&](auto d) { s1 = fma(__ldg(D + (aj + b) * nao + al + d), Vat(x, b, c, d), s1); }); });
-        atomicAdd(K + (ai + x) * nao + ak + c, w * s1);
+    if constexpr (XS) {
+      // the shellset is in shared memory: runtime loops
+      auto Vr = [&](int x, int b, int c, int d) -> double { return V[((x * NB + b) * NC + c) * ND + d]; };
+      for (int x = 0; x < NA; ++x) {
+        for (int c = 0; c < NC; ++c) {   // K_ik
+          double s1 = 0.0;
+          for (int b = 0; b < NB; ++b)
+            for (int d = 0; d < ND; ++d) s1 = fma(__ldg(D + (aj + b) * nao + al + d), Vr(x, b, c, d), s1);
+          atomicAdd(K + (ai + x) * nao + ak + c, w * s1);
+        }
+        for (int d = 0; d < ND; ++d) {   // K_il
+          double s2 = 0.0;
+          for (int b = 0; b < NB; ++b)
+            for (int c = 0; c < NC; ++c) s2 = fma(__ldg(D + (aj + b) * nao + ak + c), Vr(x, b, c, d), s2);
+          atomicAdd(K + (ai + x) * nao + al + d, w * s2);
+        }
+      }
+      for (int x = 0; x < NB; ++x) {
+        for (int c = 0; c < NC; ++c) {   // K_jk
+          double s3 = 0.0;
+          for (int y = 0; y < NA; ++y)
+            for (int d = 0; d < ND; ++d) s3 = fma(__ldg(D + (ai + y) * nao + al + d), Vr(y, x, c, d), s3);
+          atomicAdd(K + (aj + x) * nao + ak + c, w * s3);
+        }
+        for (int d = 0; d < ND; ++d) {   // K_jl
+          double s4 = 0.0;
+          for (int y = 0; y < NA; ++y)
+            for (int c = 0; c < NC; ++c) s4 = fma(__ldg(D + (ai + y) * nao + ak + c), Vr(y, x, c, d), s4);
+          atomicAdd(K + (aj + x) * nao + al + d, w * s4);
+        }
+      }
+    } else {
+      auto Vat = [&](auto x, auto b, auto c, auto d) -> double { return V[((x * NB + b) * NC + c) * ND + d]; };
+      sfor<NA>([&](auto x) {
+        sfor<NC>([&](auto c) {   // K_ik
+          double s1 = 0.0;
+          sfor<NB>([&](auto b) {
+            sfor<ND>([&](auto d) { s1 = fma(__ldg(D + (aj + b) * nao + al + d), Vat(x, b, c, d), s1); });
+          });
+          atomicAdd(K + (ai + x) * nao + ak + c, w * s1);
+        });
+        sfor<ND>([&](auto d) {   // K_il
+          double s2 = 0.0;
+          sfor<NB>([&](auto b) {
+            sfor<NC>([&](auto c) { s2 = fma(__ldg(D + (aj + b) * nao + ak + c), Vat(x, b, c, d), s2); });
+          });
+          atomicAdd(K + (ai + x) * nao + al + d, w * s2);
+        });
       });
-      sfor<ND>([&](auto d) {   // K_il
-        double s2 = 0.0;
-        sfor<NB>([&](auto b) { sfor<NC>([&](auto c) { s2 = fma(__ldg(D + (aj + b) * nao + ak + c), Vat(x, b, c, d), s2); }); });
-        atomicAdd(K + (ai + x) * nao + al + d, w * s2);
+      sfor<NB>([&](auto x) {
+        sfor<NC>([&](auto c) {   // K_jk
+          double s3 = 0.0;
+          sfor<NA>([&](auto y) {
+            sfor<ND>([&](auto d) { s3 = fma(__ldg(D + (ai + y) * nao + al + d), Vat(y, x, c, d), s3); });
+          });
+          atomicAdd(K + (aj + x) * nao + ak + c, w * s3);
+        });
+        sfor<ND>([&](auto d) {   // K_jl
+          double s4 = 0.0;
+          sfor<NA>([&](auto y) {
+            sfor<NC>([&](auto c) { s4 = fma(__ldg(D + (ai + y) * nao + ak + c), Vat(y, x, c, d), s4); });
+          });
+          atomicAdd(K + (aj + x) * nao + al + d, w * s4);
+        });
       });
-    });
-    sfor<NB>([&](auto x) {
-      sfor<NC>([&](auto c) {   // K_jk
-        double s3 = 0.0;
-        sfor<NA>([&](auto y) { sfor<ND>([&](auto d) { s3 = fma(__ldg(D + (ai + y) * nao + al + d), Vat(y, x, c, d), s3); }); });
-        atomicAdd(K + (aj + x) * nao + ak + c, w * s3);
-      });
-      sfor<ND>([&](auto d) {   // K_jl
-        double s4 = 0.0;
-        sfor<NA>([&](auto y) { sfor<NC>([&](auto c) { s4 = fma(__ldg(D + (ai + y) * nao + ak + c), Vat(y, x, c, d), s4); }); });
-        atomicAdd(K + (aj + x) * nao + al + d, w * s4);
-      });
-    });
+    }
   }
 }
 
@@ -307,7 +381,8 @@ cudaError_t launch_reg_class(const QuartetLaunch& a, cudaStream_t s) {
   constexpr bool XS = !reg_eligible(LA, LB, LC, LD);
   constexpr int bs = XS ? kXsBlock : 128;
   constexpr int Nk = ncart(LC) * ncart(LD);
-  constexpr size_t shm = XS ? (size_t)(ncart(LA) * ncart(LB) * Nk + nherm(LA + LB) * Nk) * kXsBlock * sizeof(double) : 0;
+  constexpr size_t shm =
+      XS ? (size_t)(ncart(LA) * ncart(LB) * Nk + nherm(LA + LB) * Nk) * kXsBlock * sizeof(double) : 0;
   const int64_t grid = (a.nq + bs - 1) / bs;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
   if constexpr (shm > 48 * 1024) {

@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 0..15, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 0..48, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part00(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 0 || code >= 16) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<0>(code, std::make_integer_sequence<int, 16>{});
+  if (code < 0 || code >= 49) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<0>(code, std::make_integer_sequence<int, 49>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

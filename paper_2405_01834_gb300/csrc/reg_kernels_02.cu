@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 49..69, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 98..153, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part02(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 49 || code >= 70) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<49>(code, std::make_integer_sequence<int, 21>{});
+  if (code < 98 || code >= 154) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<98>(code, std::make_integer_sequence<int, 56>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

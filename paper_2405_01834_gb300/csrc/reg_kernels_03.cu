@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 70..104, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 154..209, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part03(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 70 || code >= 105) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<70>(code, std::make_integer_sequence<int, 35>{});
+  if (code < 154 || code >= 210) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<154>(code, std::make_integer_sequence<int, 56>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

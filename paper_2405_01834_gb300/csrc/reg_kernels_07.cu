@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 350..391, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 455..538, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part07(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 350 || code >= 392) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<350>(code, std::make_integer_sequence<int, 42>{});
+  if (code < 455 || code >= 539) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<455>(code, std::make_integer_sequence<int, 84>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 413..685, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 700..783, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part09(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 413 || code >= 686) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<413>(code, std::make_integer_sequence<int, 273>{});
+  if (code < 700 || code >= 784) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<700>(code, std::make_integer_sequence<int, 84>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 686..706, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 784..1035, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part10(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 686 || code >= 707) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<686>(code, std::make_integer_sequence<int, 21>{});
+  if (code < 784 || code >= 1036) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<784>(code, std::make_integer_sequence<int, 252>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

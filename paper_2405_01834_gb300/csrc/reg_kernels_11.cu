@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 707..1028, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 1036..1091, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part11(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 707 || code >= 1029) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<707>(code, std::make_integer_sequence<int, 322>{});
+  if (code < 1036 || code >= 1092) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<1036>(code, std::make_integer_sequence<int, 56>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

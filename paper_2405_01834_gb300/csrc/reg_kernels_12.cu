@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 1029..1077, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 1092..1378, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part12(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 1029 || code >= 1078) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<1029>(code, std::make_integer_sequence<int, 49>{});
+  if (code < 1092 || code >= 1379) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<1092>(code, std::make_integer_sequence<int, 287>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 1078..2057, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 1379..1721, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part13(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 1078 || code >= 2058) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<1078>(code, std::make_integer_sequence<int, 980>{});
+  if (code < 1379 || code >= 1722) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<1379>(code, std::make_integer_sequence<int, 343>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

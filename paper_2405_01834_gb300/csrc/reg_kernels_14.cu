@@ -1,4 +1,4 @@
-// Register-kernel instances for class codes 2058..2400, code = ((la*7 + lb)*7 + lc)*7 + ld
+// Register-kernel instances for class codes 1722..2400, code = ((la*7 + lb)*7 + lc)*7 + ld
 // (see reg_kernel.cuh; split over several files so that they compile in parallel).
 #include "reg_kernel.cuh"
 
@@ -6,8 +6,8 @@ namespace mdx {
 
 cudaError_t launch_reg_part14(int code, const QuartetLaunch& a, cudaStream_t s, bool* handled) {
   *handled = false;
-  if (code < 2058 || code >= 2401) return cudaSuccess;
-  const reg::RegLaunchFn f = reg::reg_pick<2058>(code, std::make_integer_sequence<int, 343>{});
+  if (code < 1722 || code >= 2401) return cudaSuccess;
+  const reg::RegLaunchFn f = reg::reg_pick<1722>(code, std::make_integer_sequence<int, 679>{});
   if (!f) return cudaSuccess;
   *handled = true;
   return f(a, s);

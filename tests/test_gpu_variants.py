@@ -105,7 +105,9 @@ def test_shape_setter_rejects():
 # R in registers, [p|cd] and the shellset in shared memory
 XS_CLASSES = [((3, 0, 1, 0), (1, 3, 2, 3)), ((1, 1, 1, 1), (2, 1, 1, 2)), ((2, 1, 1, 0), (1, 2, 3, 1)),
               ((6, 0, 0, 0), (1, 1, 2, 2)), ((2, 0, 1, 1), (1, 2, 2, 1)), ((5, 0, 0, 0), (1, 1, 2, 2)),
-              ((1, 0, 0, 3), (2, 2, 1, 1)), ((3, 0, 0, 1), (1, 1, 2, 2)), ((4, 0, 1, 0), (1, 1, 1, 1))]
+              ((1, 0, 0, 3), (2, 2, 1, 1)), ((3, 0, 0, 1), (1, 1, 2, 2)), ((4, 0, 1, 0), (1, 1, 1, 1)),
+              ((3, 0, 1, 1), (1, 2, 2, 1)), ((5, 0, 1, 0), (1, 1, 2, 2)), ((2, 2, 1, 0), (1, 1, 2, 1)),
+              ((2, 1, 1, 1), (1, 1, 1, 2))]
 
 
 @pytest.mark.parametrize("lq,K", XS_CLASSES)
