@@ -74,6 +74,7 @@ __device__ __forceinline__ void sfor(F&& f) {
 // Per-thread array of N doubles: in registers (SH = false), or one column of a
 // block-wide shared-memory table (element i of thread t at p[i * kXsBlock]).
 constexpr int kXsBlock = 64;
+constexpr int kRegMaxDevices = 64;
 template <bool SH, int N>
 struct TArr {
   double r[N];
@@ -386,15 +387,20 @@ cudaError_t launch_reg_class(const QuartetLaunch& a, cudaStream_t s) {
   const int64_t grid = (a.nq + bs - 1) / bs;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
   if constexpr (shm > 48 * 1024) {
-    static bool attr = false;   // opt in to more than 48 KB of dynamic shared memory, once per instance
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_reg<LA, LB, LC, LD, true, XS>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    // opt in to more than 48 KB of dynamic shared memory, once per instance and device
+    static bool attr[kRegMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kRegMaxDevices) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+      e = cudaFuncSetAttribute(k_reg<LA, LB, LC, LD, true, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)shm);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_reg<LA, LB, LC, LD, false, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)shm);
       if (e != cudaSuccess) return e;
-      attr = true;
+      attr[dev] = true;
     }
   }
   if (a.D) k_reg<LA, LB, LC, LD, true, XS><<<(unsigned)grid, bs, shm, s>>>(a);
