@@ -40,8 +40,8 @@ struct mdx_ctx {
   int device = 0;
   std::string last_error;
   double* d_boys = nullptr;
-  uint32_t* d_hdec = nullptr;
-  int32_t* d_hdec_off = nullptr;
+  uint32_t* d_rprog = nullptr;
+  int32_t* d_rprog_off = nullptr;
   int* d_err = nullptr;
   std::map<ClassKey, std::unique_ptr<Plan>> plans;
   std::map<std::string, DevBuf> bufs;
@@ -396,8 +396,8 @@ mdx_status batch_run(mdx_ctx* c, mdx_batch* B, double* out, int32_t* nlaunch, cu
     a.recs = B->recs;
     a.recs_signed = B->recs_s;
     a.boys = c->d_boys;
-    a.hdec = c->d_hdec;
-    a.hdec_off = c->d_hdec_off;
+    a.rprog = c->d_rprog;
+    a.rprog_off = c->d_rprog_off;
     a.out = out;
     a.err = c->d_err;
     e = launch_quartets(a, s);
@@ -511,19 +511,14 @@ mdx_status mdx_create(mdx_ctx** ctx, int device) {
   if (cudaMalloc(&c->d_boys, tab.size() * sizeof(double)) != cudaSuccess) return MDX_ENOMEM;
   if (cudaMemcpy(c->d_boys, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return MDX_ECUDA;
-  // Hermite index decode: for total order N, entry e of the [t][u][v] simplex layout
+  // R-level programs of the team kernel (Eq. r), one word per Hermite entry
   std::vector<uint32_t> dec;
   std::vector<int32_t> doff;
-  for (int N = 0; N <= kLtot; ++N) {
-    doff.push_back((int32_t)dec.size());
-    for (int t = 0; t <= N; ++t)
-      for (int u = 0; t + u <= N; ++u)
-        for (int v = 0; t + u + v <= N; ++v) dec.push_back((uint32_t)t | ((uint32_t)u << 8) | ((uint32_t)v << 16));
-  }
-  if (cudaMalloc(&c->d_hdec, dec.size() * sizeof(uint32_t)) != cudaSuccess) return MDX_ENOMEM;
-  if (cudaMalloc(&c->d_hdec_off, doff.size() * sizeof(int32_t)) != cudaSuccess) return MDX_ENOMEM;
-  if (cudaMemcpy(c->d_hdec, dec.data(), dec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(c->d_hdec_off, doff.data(), doff.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+  build_rlevel_programs(dec, doff);
+  if (cudaMalloc(&c->d_rprog, dec.size() * sizeof(uint32_t)) != cudaSuccess) return MDX_ENOMEM;
+  if (cudaMalloc(&c->d_rprog_off, doff.size() * sizeof(int32_t)) != cudaSuccess) return MDX_ENOMEM;
+  if (cudaMemcpy(c->d_rprog, dec.data(), dec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_rprog_off, doff.data(), doff.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
     return MDX_ECUDA;
   if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) return MDX_ENOMEM;
   if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) return MDX_ECUDA;
@@ -538,8 +533,8 @@ void mdx_destroy(mdx_ctx* c) {
   for (auto& p : c->retired) if (p->dev_blob) cudaFree(p->dev_blob);
   for (auto& kv : c->bufs) if (kv.second.p) cudaFree(kv.second.p);
   cudaFree(c->d_boys);
-  cudaFree(c->d_hdec);
-  cudaFree(c->d_hdec_off);
+  cudaFree(c->d_rprog);
+  cudaFree(c->d_rprog_off);
   cudaFree(c->d_err);
   if (c->cublas) cublasDestroy(c->cublas);
   delete c;
@@ -844,8 +839,8 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
       a.recs = b->recs;
       a.recs_signed = b->recs_s;
       a.boys = c->d_boys;
-      a.hdec = c->d_hdec;
-      a.hdec_off = c->d_hdec_off;
+      a.rprog = c->d_rprog;
+      a.rprog_off = c->d_rprog_off;
       a.out = out;
       a.err = c->d_err;
       float ms = 1e30f;
@@ -1036,8 +1031,8 @@ QuartetLaunch base_launch(mdx_ctx* c, Plan* plan, const int2* qp, int64_t nq, co
   a.recs = recs;
   a.recs_signed = recs_s;
   a.boys = c->d_boys;
-  a.hdec = c->d_hdec;
-  a.hdec_off = c->d_hdec_off;
+  a.rprog = c->d_rprog;
+  a.rprog_off = c->d_rprog_off;
   a.err = c->d_err;
   return a;
 }

@@ -26,6 +26,8 @@ namespace mdx {
 // integers 0..63 as doubles, to multiply by small integers without an
 // int->double conversion on the FP64 pipe
 __constant__ double c_dint[64];
+// the same small integers in global memory, for per-lane (divergent) reads through L1
+__device__ double g_dint[64];
 // sqrt(pi)/2 * (2m-1)!! / 2^m: F_m(T) = c_gh[m] T^(-m-1/2) for large T
 __constant__ double c_gh[kBoysOrders];
 // Cartesian components of shells l <= 7 in library order, packed x | y << 8 | z << 16
@@ -140,12 +142,8 @@ __device__ __forceinline__ void team_sync(unsigned mask) {
   else __syncwarp(mask);
 }
 
-// offset of row (t,u) in a [t][u][v] simplex layout of total order N
 __device__ __forceinline__ int d_tet(int n) { return n < 0 ? 0 : n * (n + 1) * (n + 2) / 6; }
 __device__ __forceinline__ int d_tri(int n) { return n < 0 ? 0 : n * (n + 1) / 2; }
-__device__ __forceinline__ int d_roff(int N, int t, int u) {
-  return d_tet(N + 1) - d_tet(N - t + 1) + d_tri(N - t + 1) - d_tri(N - t - u + 1);
-}
 
 __device__ __forceinline__ double ipow(double x, int m) {
   double r = 1.0;
@@ -227,27 +225,18 @@ __device__ void compute_R(const QuartetLaunch& a, double* ws, int tl, unsigned m
     const int N = L - n;
     double* dst = (n & 1) ? R1 : R0;
     const double* src = (n & 1) ? R0 : R1;
-    const uint32_t* dec = a.hdec + a.hdec_off[N];
+    const uint32_t* prog = a.rprog + a.rprog_off[N];
     const int cnt = d_tet(N + 1);
     const double g = G[n];
+    // one branch-free program word per entry (build_rlevel_programs): the two
+    // sources in the previous level, the axis of X_PQ and the coefficient
     for (int e = tl; e < cnt; e += T) {
-      const uint32_t w = __ldg(dec + e);
-      const int t = w & 0xff, u = (w >> 8) & 0xff, v = (w >> 16) & 0xff;
-      double val;
-      if (v > 0) {
-        const int o = d_roff(N - 1, t, u) + v - 1;
-        val = PQz * src[o];
-        if (v > 1) val = fma(c_dint[v - 1], src[o - 1], val);
-      } else if (u > 0) {
-        val = PQy * src[d_roff(N - 1, t, u - 1)];
-        if (u > 1) val = fma(c_dint[u - 1], src[d_roff(N - 1, t, u - 2)], val);
-      } else if (t > 0) {
-        val = PQx * src[d_roff(N - 1, t - 1, 0)];
-        if (t > 1) val = fma(c_dint[t - 1], src[d_roff(N - 1, t - 2, 0)], val);
-      } else {
-        val = g;
-      }
-      dst[d_roff(N, t, u) + v] = val;
+      const uint32_t w = __ldg(prog + e);
+      const int ax = (w >> 24) & 3;
+      const double pq = ax == 0 ? PQx : (ax == 1 ? PQy : PQz);
+      double val = pq * src[w & 0xfff];
+      val = fma(__ldg(g_dint + (w >> 26)), src[(w >> 12) & 0xfff], val);
+      dst[e] = e == 0 ? g : val;
     }
     team_sync<CTA>(mask);
   }
@@ -965,6 +954,7 @@ cudaError_t kernel_attributes_init() {
   double dint[64];
   for (int i = 0; i < 64; ++i) dint[i] = (double)i;
   cudaError_t e = cudaMemcpyToSymbol(c_dint, dint, sizeof(dint));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dint, dint, sizeof(dint));
   if (e != cudaSuccess) return e;
   double gh[kBoysOrders];
   // sqrt(pi)/2 * (2m-1)!! / 2^m

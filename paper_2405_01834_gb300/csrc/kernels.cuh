@@ -40,8 +40,8 @@ struct QuartetLaunch {
   const double* recs;
   const double* recs_signed;
   const double* boys;
-  const uint32_t* hdec;      // Hermite index decode table
-  const int32_t* hdec_off;   // start of each total order N in hdec
+  const uint32_t* rprog;     // R-level programs (one word per Hermite entry, build_rlevel_programs)
+  const int32_t* rprog_off;  // start of each total order N in rprog
   double* out;
   int* err;
   // exchange digestion (out unused when D != nullptr): K_ik += w sum_jl D_jl (ij|kl)

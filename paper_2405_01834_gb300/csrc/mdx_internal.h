@@ -179,6 +179,15 @@ struct PlanConfig {
   }
 };
 
+// R-level programs (Eq. r) for the team kernel: for every total order N, one
+// word per entry (t,u,v) of the [t][u][v] simplex of order N, in layout order:
+// bits 0-11 the offset of [t',u',v'] = [tuv] - 1_axis and bits 12-23 the
+// offset of [tuv] - 2_axis in the order N-1 layout of the previous level,
+// bits 24-25 the axis (0 x, 1 y, 2 z; entry 0 is [000]), bits 26-31 the
+// coefficient (index along the axis - 1; 0 where there is no second term).
+// off[N] is the first word of order N.
+void build_rlevel_programs(std::vector<uint32_t>& prog, std::vector<int32_t>& off);
+
 // Builds the plan of a class for the given shape.
 bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::string& err);
 

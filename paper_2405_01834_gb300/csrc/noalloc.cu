@@ -39,8 +39,8 @@ struct DevState {
   bool ready = false;
   unsigned char* base = nullptr;   // device address of g_scratch on this device
   double* boys = nullptr;
-  uint32_t* hdec = nullptr;
-  int32_t* hdec_off = nullptr;
+  uint32_t* rprog = nullptr;
+  int32_t* rprog_off = nullptr;
   int* err = nullptr;
   size_t fixed = 0;                // bytes used by the tables above
 };
@@ -60,26 +60,22 @@ mdx_status setup(int dev, DevState& st) {
   if (kernel_attributes_init() != cudaSuccess) { cudaGetLastError(); return MDX_ECUDA; }
   unsigned char* base = (unsigned char*)p;
   const std::vector<double> tab = build_boys_table();
+  // R-level programs of the team kernel (Eq. r), one word per Hermite entry
   std::vector<uint32_t> dec;
   std::vector<int32_t> doff;
-  for (int N = 0; N <= kLtot; ++N) {
-    doff.push_back((int32_t)dec.size());
-    for (int t = 0; t <= N; ++t)
-      for (int u = 0; t + u <= N; ++u)
-        for (int v = 0; t + u + v <= N; ++v) dec.push_back((uint32_t)t | ((uint32_t)u << 8) | ((uint32_t)v << 16));
-  }
+  build_rlevel_programs(dec, doff);
   size_t o = 0;
   st.err = (int*)(base + o);
   o += 256;
   st.boys = (double*)(base + o);
   o += align256(tab.size() * sizeof(double));
-  st.hdec = (uint32_t*)(base + o);
+  st.rprog = (uint32_t*)(base + o);
   o += align256(dec.size() * sizeof(uint32_t));
-  st.hdec_off = (int32_t*)(base + o);
+  st.rprog_off = (int32_t*)(base + o);
   o += align256(doff.size() * sizeof(int32_t));
   if (cudaMemcpy(st.boys, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(st.hdec, dec.data(), dec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(st.hdec_off, doff.data(), doff.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(st.rprog, dec.data(), dec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(st.rprog_off, doff.data(), doff.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     return MDX_ECUDA;
   }
@@ -240,8 +236,8 @@ extern "C" mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* qu
     a.recs = recs;
     a.recs_signed = recs_s;
     a.boys = st.boys;
-    a.hdec = st.hdec;
-    a.hdec_off = st.hdec_off;
+    a.rprog = st.rprog;
+    a.rprog_off = st.rprog_off;
     a.out = out;
     a.err = st.err;
     e = launch_quartets(a, s);

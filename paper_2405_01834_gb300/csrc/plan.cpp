@@ -210,6 +210,36 @@ bool validate_plan(const Plan& plan, std::string& err) {
 
 }  // namespace
 
+void build_rlevel_programs(std::vector<uint32_t>& prog, std::vector<int32_t>& off) {
+  prog.clear();
+  off.clear();
+  for (int N = 0; N <= kLtot; ++N) {
+    off.push_back((int32_t)prog.size());
+    for (int t = 0; t <= N; ++t)
+      for (int u = 0; t + u <= N; ++u)
+        for (int v = 0; t + u + v <= N; ++v) {
+          // [tuv]^(n) = X_PQ [tuv - 1]^(n+1) + (i - 1) [tuv - 2]^(n+1) along the last raised axis
+          int axis, i, s1, s2;
+          if (v > 0) {
+            axis = 2; i = v;
+            s1 = roff(N - 1, t, u) + v - 1;
+            s2 = v > 1 ? roff(N - 1, t, u) + v - 2 : s1;
+          } else if (u > 0) {
+            axis = 1; i = u;
+            s1 = roff(N - 1, t, u - 1);
+            s2 = u > 1 ? roff(N - 1, t, u - 2) : s1;
+          } else if (t > 0) {
+            axis = 0; i = t;
+            s1 = roff(N - 1, t - 1, 0);
+            s2 = t > 1 ? roff(N - 1, t - 2, 0) : s1;
+          } else {
+            axis = 0; i = 1; s1 = 0; s2 = 0;
+          }
+          prog.push_back((uint32_t)s1 | ((uint32_t)s2 << 12) | ((uint32_t)axis << 24) | ((uint32_t)(i - 1) << 26));
+        }
+  }
+}
+
 bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::string& err) {
   const int smem_budget_bytes = std::min(cfg.budget, 220 * 1024);
   PlanDev& P = plan.d;
