@@ -485,10 +485,10 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
     P.T = cfg.T;
   } else if (key.Kb * key.Kk > 1) {
     // contracted: the work per primitive quartet (Boys, R, ket steps) sets the
-    // team; about 40 FMAs per lane per primitive quartet, at most 128 lanes
-    // (GB300 sweeps of team sizes over contracted classes of L = 4..10)
+    // team; about 30 FMAs per lane per primitive quartet, at most 128 lanes
+    // (GB300 sweeps of team sizes over contracted classes of L = 6..10)
     P.T = 1;
-    while (P.T < 128 && 2 * P.T * 40.0 <= team_fma_per_prim) P.T *= 2;
+    while (P.T < 128 && 2 * P.T * 30.0 <= team_fma_per_prim) P.T *= 2;
   } else if (P.ngroups > 1) {
     P.T = 512;
   } else {
