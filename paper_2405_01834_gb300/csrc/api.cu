@@ -334,6 +334,7 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     ClassKey key{HB.l[bp.i], bp.j >= 0 ? HB.l[bp.j] : 0, HK.l[kp.i], HK.l[kp.j],
                  HB.nprim[bp.i] * (bp.j >= 0 ? HB.nprim[bp.j] : 1), HK.nprim[kp.i] * HK.nprim[kp.j],
                  bp.j < 0 ? 1 : 0};
+    key.store = 1;   // batches only store shellsets
     classes[key].push_back((int64_t)q);
   }
   std::vector<int2> qp_sorted;
@@ -1290,11 +1291,15 @@ mdx_status mdx_set_class_shape(mdx_ctx* c, int la, int lb, int lc, int ld, int K
   Plan p;
   std::string err;
   if (!build_plan(key, cfg, p, err)) return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
-  c->tuned[key] = cfg;
-  auto it = c->plans.find(key);
-  if (it != c->plans.end()) {
-    c->retired.push_back(std::move(it->second));
-    c->plans.erase(it);
+  for (int store = 0; store <= 1; ++store) {   // the general plan and the store-only plan of the class
+    ClassKey k2 = key;
+    k2.store = store;
+    c->tuned[k2] = cfg;
+    auto it = c->plans.find(k2);
+    if (it != c->plans.end()) {
+      c->retired.push_back(std::move(it->second));
+      c->plans.erase(it);
+    }
   }
   return MDX_OK;
 }

@@ -741,6 +741,7 @@ static const RegPart kRegParts[] = {launch_reg_part00, launch_reg_part01, launch
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
   if (a.nq <= 0) return cudaSuccess;
   const PlanDev& P = a.plan;
+  if (!P.has_out && (a.D || a.grad)) return cudaErrorInvalidValue;   // store-only plan in an epilogue launch
   if (P.reg && !a.grad) {
     // one thread per quartet, registers only (store and digestion epilogues)
     const int code = ((P.la * 7 + P.lb) * 7 + P.lc) * 7 + P.ld;

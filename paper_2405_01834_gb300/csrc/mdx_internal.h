@@ -131,9 +131,10 @@ struct Group {
 
 struct ClassKey {
   int la, lb, lc, ld, Kb, Kk, onec;
+  int store = 0;   // 1: plan for the store epilogue only (no OUT region when Kb = 1)
   bool operator<(const ClassKey& o) const {
-    const int a[7] = {la, lb, lc, ld, Kb, Kk, onec}, b[7] = {o.la, o.lb, o.lc, o.ld, o.Kb, o.Kk, o.onec};
-    for (int i = 0; i < 7; ++i) if (a[i] != b[i]) return a[i] < b[i];
+    const int a[8] = {la, lb, lc, ld, Kb, Kk, onec, store}, b[8] = {o.la, o.lb, o.lc, o.ld, o.Kb, o.Kk, o.onec, o.store};
+    for (int i = 0; i < 8; ++i) if (a[i] != b[i]) return a[i] < b[i];
     return false;
   }
 };
@@ -150,6 +151,7 @@ struct PlanDev {
   int32_t nb1, nb23;
   int32_t cache_R;                       // R computed once (single primitive quartet)
   int32_t reg;                           // launch the register kernel (store / digestion launches)
+  int32_t has_out;                       // OUT region present (0: store-only plan, b23 writes global memory)
   const Group* groups;
   const StepEntry* kprog;
   const StepEntry* b1;

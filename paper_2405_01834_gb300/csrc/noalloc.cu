@@ -165,7 +165,7 @@ extern "C" mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* qu
   std::map<ClassKey, std::vector<int64_t>> classes;
   for (int64_t q = 0; q < n; ++q) {
     const int2 b = pairs[qp[q].x], k = pairs[qp[q].y];
-    classes[ClassKey{hl[b.x], hl[b.y], hl[k.x], hl[k.y], hk[b.x] * hk[b.y], hk[k.x] * hk[k.y], 0}].push_back(q);
+    classes[ClassKey{hl[b.x], hl[b.y], hl[k.x], hl[k.y], hk[b.x] * hk[b.y], hk[k.x] * hk[k.y], 0, 1}].push_back(q);
   }
   std::vector<int2> qp_sorted;
   std::vector<int64_t> qoff_sorted;

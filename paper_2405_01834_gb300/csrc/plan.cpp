@@ -201,7 +201,10 @@ bool validate_plan(const Plan& plan, std::string& err) {
     if (s.out >= P.Nb || !in(0, P.c1size, s.src + rowmax + umax) || umax > s.r - vmax ||
         !in(P.o_recb, P.o_recb + P.recb, s.ey + (long)(s.nu - 1) * s.su) ||
         !in(P.o_recb, P.o_recb + P.recb, s.ez + (long)(s.nv - 1) * s.sv) ||
-        cr + ncm * P.c1size > orr || orr + ncm * P.Nb > W) { err = "b23 entry out of range"; return false; }
+        cr + ncm * P.c1size > orr || orr + (P.has_out ? ncm * P.Nb : 0) > W) {
+      err = "b23 entry out of range";
+      return false;
+    }
   }
   if (P.o_R1 + tet(P.L) > P.o_X || P.o_R0 + tet(P.L + 1) > P.o_R1 || P.o_G + P.L + 1 > P.o_R0 ||
       P.o_reck + P.reck > P.o_scal) { err = "fixed regions overlap"; return false; }
@@ -328,10 +331,13 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   for (size_t ic = 0; ic < cc.size(); ++ic)
     for (size_t id = 0; id < cd.size(); ++id) allcols.push_back({cc[ic], cd[id], (int)(ic * cd.size() + id)});
 
+  // store-only plans of uncontracted-bra classes need no OUT region: b23 writes the shellset to global memory
+  P.has_out = (key.store && key.Kb == 1) ? 0 : 1;
+  const int out_per_col = P.has_out ? P.Nb : 0;
   auto region_size = [&](int a_size, int b_size) { return std::max(r1size, a_size + b_size); };
   auto team_doubles = [&](int a_size, int b_size, int ncols) {
     int reg = (region_size(a_size, b_size) + 1) & ~1;
-    int tot = o_region + reg + ncols * P.hb + ncols * P.c1size + ncols * P.Nb;
+    int tot = o_region + reg + ncols * P.hb + ncols * P.c1size + ncols * out_per_col;
     return (tot + 1) & ~1;
   };
 
@@ -363,16 +369,19 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
     // one group per z-pair, columns split into chunks of at most `cap` so that
     // the largest region plus the widest group fit the budget together
     for (auto& c : allcols) byz[{c.c.z, c.d.z}].push_back(c);
-    size_t cap = 0;
-    for (auto& kv : byz) cap = std::max(cap, kv.second.size());
-    while (true) {
+    size_t maxcap = 0;
+    for (auto& kv : byz) maxcap = std::max(maxcap, kv.second.size());
+    // groups of at most `cap` columns, a z-pair's columns split into chunks of nearly equal size
+    auto try_cap = [&](size_t cap) {
       groups.clear(); gz.clear(); gfirst.clear();
       regmax = 0; cmax = 0;
       bool ok = true;
       for (auto& kv : byz) {
         std::vector<ColInfo>& cs = kv.second;
-        for (size_t s0 = 0; s0 < cs.size(); s0 += cap) {
-          groups.emplace_back(cs.begin() + s0, cs.begin() + std::min(cs.size(), s0 + cap));
+        const size_t nchunk = (cs.size() + cap - 1) / cap;
+        const size_t len = (cs.size() + nchunk - 1) / nchunk;
+        for (size_t s0 = 0; s0 < cs.size(); s0 += len) {
+          groups.emplace_back(cs.begin() + s0, cs.begin() + std::min(cs.size(), s0 + len));
           gz.push_back(share_a ? &cs : nullptr);
           gfirst.push_back(s0 == 0 || !share_a);
           int as = 0, bs = 0;
@@ -381,10 +390,18 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
           cmax = std::max(cmax, (int)groups.back().size());
         }
       }
-      const int td = o_region + ((regmax + 1) & ~1) + cmax * (P.hb + P.c1size + P.Nb);
-      if (ok && td * 8 <= smem_budget_bytes) break;
-      if (cap == 1) { err = "class does not fit the shared-memory budget"; return false; }
-      cap = (cap + 1) / 2;
+      const int td = o_region + ((regmax + 1) & ~1) + cmax * (P.hb + P.c1size + out_per_col);
+      return ok && td * 8 <= smem_budget_bytes;
+    };
+    // the largest cap that fits (binary search; the workspace grows with the cap)
+    if (!try_cap(maxcap)) {
+      size_t lo = 0, hi = maxcap;   // try_cap(hi) fails; lo is the largest known fit (0: none yet)
+      while (hi - lo > 1) {
+        const size_t mid = (lo + hi) / 2;
+        if (try_cap(mid)) lo = mid; else hi = mid;
+      }
+      if (lo == 0) { err = "class does not fit the shared-memory budget"; return false; }
+      try_cap(lo);
     }
   } else {
     int as = 0, bs = 0;
@@ -401,7 +418,7 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   P.o_OUT = P.o_C1 + cmax * P.c1size;
   // odd: the workspaces of the teams of a CTA start on different shared-memory
   // bank pairs, so lanes of different teams at the same offset do not conflict
-  P.team_doubles = (P.o_OUT + cmax * P.Nb) | 1;
+  P.team_doubles = (P.o_OUT + cmax * out_per_col) | 1;
   P.ncols_max = cmax;
   if (P.team_doubles >= 65536 || P.team_doubles * 8 > smem_budget_bytes) {
     err = "workspace exceeds the shared-memory budget";
