@@ -237,9 +237,11 @@ mdx_status mdx_exchange_grad(mdx_ctx* ctx, const mdx_basis* basis, const int32_t
 /* ---- batched exchange of many molecules ---------------------------------
  * Exchange matrices K_m = sum_jl D_m,jl (ij|kl) of n_mol independent molecules
  * (uneven sizes, mixed classes and contraction degrees) prepared once and run
- * as either one launch per integral class across all molecules or one
- * persistent launch whose CTAs pull work items (a class's quartets for one
- * block of teams, heaviest first) from a queue with a single atomicAdd each.
+ * as one launch per integral class across all molecules, as one persistent
+ * launch whose CTAs pull work items (a class's quartets for one block of
+ * teams of the class's own team size, heaviest first) from a queue with a
+ * single atomicAdd each, or as the register-kernel classes launched one by
+ * one followed by one persistent launch over the remaining classes.
  * bases: host array of n_mol basis descriptors (device arrays, ao_off
  * required); D, K: host arrays of n_mol device pointers ([nao_m][nao_m]
  * row-major; D read, K overwritten by run). Every shell pair of every
@@ -256,8 +258,11 @@ mdx_status mdx_xbatch_create(mdx_ctx* ctx, int32_t n_mol, const mdx_basis* bases
 mdx_status mdx_xbatch_info(const mdx_xbatch* xbatch, int64_t* n_quartets, int64_t* n_items,
                            int32_t* n_class_launches, double* model_flops);
 
-/* Enqueue K_m <- 0, the integral kernels with fused digestion (persistent = 1:
- * one persistent launch; 0: one launch per class) and K_m <- K_m + K_m^T.
+/* Enqueue K_m <- 0, the integral kernels with fused digestion and
+ * K_m <- K_m + K_m^T. persistent = 0: one launch per class; 1: one persistent
+ * launch over all classes (team kernel only); 2: one launch per class that
+ * has a register kernel, then one persistent launch over the other classes.
+ * Other values give MDX_EINVAL.
  * No host synchronisation and no allocation: the enqueued work can be
  * captured in a CUDA graph and replayed. n_launches (may be NULL) receives
  * the kernels enqueued. */

@@ -229,7 +229,8 @@ struct mdx_xbatch {
   mdx_ctx* ctx = nullptr;
   int32_t nmol = 0;
   int64_t max_nao = 0, nq = 0, nitems = 0, smem = 0;
-  int grid = 0;
+  int64_t nitems_team = 0, smem_team = 0;   // the queue without the register-kernel classes
+  int grid = 0, grid_team = 0;
   double model_flops = 0.0;
   mdx_basis sb{};
   int32_t *l = nullptr, *nprim = nullptr, *prim_off = nullptr, *ao_off = nullptr;
@@ -245,8 +246,10 @@ struct mdx_xbatch {
   std::vector<QuartetLaunch> launches, plaunches;
   std::vector<ClassKey> lkey;          // class of each per-class launch
   std::vector<double> lflops;          // its Table-1 model FLOPs
+  std::vector<int32_t> reg_launches;   // per-class launches that run a register kernel
   QuartetLaunch* d_plaunches = nullptr;
   WorkItem* items = nullptr;
+  WorkItem* items_team = nullptr;
   unsigned long long* counter = nullptr;
 };
 
@@ -258,7 +261,8 @@ void xbatch_free(mdx_xbatch* x) {
   cudaFree(x->center); cudaFree(x->exps); cudaFree(x->coefs);
   cudaFree(x->molD); cudaFree(x->molK); cudaFree(x->molnao);
   cudaFree(x->pshell); cudaFree(x->pmol); cudaFree(x->prec); cudaFree(x->recs); cudaFree(x->recs_s);
-  cudaFree(x->quart); cudaFree(x->d_plaunches); cudaFree(x->items); cudaFree(x->counter);
+  cudaFree(x->quart); cudaFree(x->d_plaunches); cudaFree(x->items); cudaFree(x->items_team);
+  cudaFree(x->counter);
   delete x;
 }
 
@@ -1507,7 +1511,8 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
     // one launch descriptor per non-empty bucket, plus the persistent work items
     std::vector<WorkItem> items;
     std::vector<double> cost;
-    int64_t smem = 0;
+    std::vector<char> item_reg;   // the item's class has a register kernel
+    int64_t smem = 0, smem_team = 0;
     for (int cp = 0; cp < nclass; ++cp)
       for (int cq = 0; cq <= cp; ++cq) {
         const int64_t b = (int64_t)cp * (cp + 1) / 2 + cq;
@@ -1528,60 +1533,83 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
         X->lkey.push_back(key);
         X->lflops.push_back(model_flops_class(key) * (double)counts[b]);
         X->model_flops += X->lflops.back();
-        // persistent shape: teams of T threads filling the 512-thread block, at most
-        // kPersistSmem of shared memory per block so that two blocks share an SM
-        const int64_t tb = (int64_t)plan->d.team_doubles * 8;
-        int tpb = std::max(1, std::min<int>(kPersistBlock / plan->d.T, (int)(kPersistSmem / tb)));
-        int p2 = 1;
-        while (p2 * 2 <= tpb) p2 *= 2;
-        tpb = p2;
+        // persistent shape: the class's own team size T, as many teams as fit the block's
+        // threads and kPersistSmem of shared memory (two blocks per SM), in whole warps (the
+        // kernel's barriers are warp-uniform); a plan whose teams do not fill one warp is
+        // rebuilt with at least 32 threads per team and a smaller budget
         Plan* pp = plan;
-        if (kPersistBlock / tpb != plan->d.T || tb * tpb > kPersistSmem) {
+        auto shape = [](const PlanDev& d) {
+          if (d.T > kPersistBlock) return 0;
+          int tpb = (int)std::min<int64_t>(kPersistBlock / d.T, kPersistSmem / ((int64_t)d.team_doubles * 8));
+          if (d.T < 32) tpb -= tpb % (32 / d.T);
+          return tpb;
+        };
+        int tpb = shape(plan->d);
+        if (tpb < 1) {
           std::unique_ptr<Plan> np2(new Plan());
           std::string err;
           PlanConfig cfg{};
           auto tc = c->tuned.find(key);
           if (tc != c->tuned.end()) cfg = tc->second;
-          cfg.T = kPersistBlock / tpb;
-          cfg.budget = std::min<int>(cfg.budget, (int)(kPersistSmem / tpb));
-          if (!build_plan(key, cfg, *np2, err)) {        // fall back to one full-size team per block
-            cfg = PlanConfig{};
+          cfg.T = std::min(std::max(plan->d.T, 32), kPersistBlock);
+          cfg.budget = std::min<int>(cfg.budget, (int)kPersistSmem);
+          cfg.single_max = std::min(cfg.single_max, cfg.budget);
+          cfg.variant = 1;
+          bool ok = build_plan(key, cfg, *np2, err) && shape(np2->d) >= 1;
+          if (!ok && cfg.T != kPersistBlock) {   // one block-wide team
             cfg.T = kPersistBlock;
-            tpb = 1;
-            if (!build_plan(key, cfg, *np2, err)) return fail(c, MDX_EUNSUPPORTED, "persistent planner: " + err);
+            ok = build_plan(key, cfg, *np2, err) && shape(np2->d) >= 1;
           }
-          if ((int64_t)np2->d.team_doubles * 8 * tpb > 226 * 1024) return fail(c, MDX_EUNSUPPORTED, "persistent shape");
+          if (!ok) return fail(c, MDX_EUNSUPPORTED, "persistent planner: " + err);
           if ((st = upload_plan(c, np2.get(), s)) != MDX_OK) return st;
           pp = np2.get();
+          tpb = shape(pp->d);
           c->retired.push_back(std::move(np2));
         }
         QuartetLaunch ap = a;
         ap.plan = pp->d;
+        ap.plan.teams_per_cta = tpb;
         X->plaunches.push_back(ap);
-        smem = std::max<int64_t>(smem, (int64_t)pp->d.team_doubles * 8 * tpb);
+        const bool reg_class = plan->d.reg != 0;
+        const int64_t need = (int64_t)pp->d.team_doubles * 8 * tpb;
+        smem = std::max(smem, need);
+        if (!reg_class) smem_team = std::max(smem_team, need);
         const int per_item = tpb * kPersistRounds;
         for (int64_t q0 = 0; q0 < (int64_t)counts[b]; q0 += per_item) {
           const int cnt = (int)std::min<int64_t>(per_item, (int64_t)counts[b] - q0);
           items.push_back(WorkItem{(int32_t)(X->plaunches.size() - 1), cnt, q0});
           cost.push_back(pp->exec_fma * cnt);
+          item_reg.push_back(reg_class);
         }
+        if (reg_class) X->reg_launches.push_back((int32_t)(X->launches.size() - 1));
       }
     // heaviest items first (the queue hands them out in order)
     std::vector<size_t> order(items.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-    std::vector<WorkItem> sorted;
-    for (size_t i : order) sorted.push_back(items[i]);
+    // all items (mode 1), and the items of the classes without a register kernel (mode 2)
+    std::vector<WorkItem> sorted, sorted_team;
+    for (size_t i : order) {
+      sorted.push_back(items[i]);
+      if (!item_reg[i]) sorted_team.push_back(items[i]);
+    }
     X->nitems = (int64_t)sorted.size();
+    X->nitems_team = (int64_t)sorted_team.size();
     X->smem = smem;
+    X->smem_team = smem_team;
     if ((st = dev_upload(c, X->plaunches, &X->d_plaunches, s)) != MDX_OK) return st;
     if ((st = dev_upload(c, sorted, &X->items, s)) != MDX_OK) return st;
+    if (!sorted_team.empty() && (st = dev_upload(c, sorted_team, &X->items_team, s)) != MDX_OK) return st;
     if (cudaMalloc(&X->counter, sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); return fail(c, MDX_ENOMEM, "counter"); }
-    int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, persistent_kernel_ptr(), kPersistBlock, (size_t)std::max<int64_t>(smem, 1));
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    X->grid = std::max(1, bps) * std::max(1, sms);
+    auto grid_for = [&](int64_t shm) {
+      int bps = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, persistent_kernel_ptr(), kPersistBlock, (size_t)std::max<int64_t>(shm, 1));
+      return std::max(1, bps) * std::max(1, sms);
+    };
+    X->grid = grid_for(smem);
+    X->grid_team = grid_for(smem_team);
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "batched exchange set-up");
@@ -1603,18 +1631,31 @@ mdx_status mdx_xbatch_info(const mdx_xbatch* xb, int64_t* n_quartets, int64_t* n
 
 mdx_status mdx_xbatch_run(mdx_ctx* c, mdx_xbatch* xb, int32_t persistent, int32_t* n_launches, void* stream) {
   const NvtxRange nvtx_range("mdx_xbatch_run");
-  if (!c || !xb || xb->ctx != c) return MDX_EINVAL;
+  if (!c || !xb || xb->ctx != c || persistent < 0 || persistent > 2) return MDX_EINVAL;
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   int32_t nl = 0;
   cudaError_t e = launch_multi_k(xb->molK, xb->molnao, xb->nmol, xb->max_nao, true, s);
   ++nl;
   if (e == cudaSuccess && xb->nq > 0) {
-    if (persistent) {
+    if (persistent == 1) {
       e = cudaMemsetAsync(xb->counter, 0, sizeof(unsigned long long), s);
       PersistLaunch pl{xb->d_plaunches, xb->items, xb->nitems, xb->counter};
       if (e == cudaSuccess) e = launch_persistent(pl, xb->smem, xb->grid, s);
       ++nl;
+    } else if (persistent == 2) {
+      // register-kernel classes one launch each, then one persistent launch for the rest
+      for (int32_t i : xb->reg_launches) {
+        e = launch_quartets(xb->launches[i], s);
+        if (e != cudaSuccess) break;
+        ++nl;
+      }
+      if (e == cudaSuccess && xb->nitems_team > 0) {
+        e = cudaMemsetAsync(xb->counter, 0, sizeof(unsigned long long), s);
+        PersistLaunch pl{xb->d_plaunches, xb->items_team, xb->nitems_team, xb->counter};
+        if (e == cudaSuccess) e = launch_persistent(pl, xb->smem_team, xb->grid_team, s);
+        ++nl;
+      }
     } else {
       for (const QuartetLaunch& a : xb->launches) {
         e = launch_quartets(a, s);

@@ -136,10 +136,18 @@ cudaError_t launch_pair_records(const BasisDev& b0, const BasisDev& b1, const Pr
 }
 
 // ----------------------------------------------------------------- quartets
+// Barrier of one team. Warp teams (T <= 32): `mask` holds the lanes of this
+// warp that take part. Teams of whole warps (CTA = true): `mask` is 0 when the
+// team is the whole block, else (barrier id << 16) | team threads for a named
+// barrier of its own (several teams in one block, persistent kernel).
 template <bool CTA>
 __device__ __forceinline__ void team_sync(unsigned mask) {
-  if (CTA) __syncthreads();
-  else __syncwarp(mask);
+  if (CTA) {
+    if (mask == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(mask >> 16), "r"(mask & 0xffffu) : "memory");
+  } else {
+    __syncwarp(mask);
+  }
 }
 
 __device__ __forceinline__ int d_tet(int n) { return n < 0 ? 0 : n * (n + 1) * (n + 2) / 6; }
@@ -423,10 +431,11 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
   }
   // reduce over the lanes of the team (whole warps for CTA teams, aligned lane groups otherwise)
   const int width = T < 32 ? T : 32;
+  const unsigned lanes = CTA ? 0xffffffffu : mask;
   for (int off = width / 2; off > 0; off >>= 1) {
-    s0 += __shfl_xor_sync(mask, s0, off);
-    s1 += __shfl_xor_sync(mask, s1, off);
-    s2 += __shfl_xor_sync(mask, s2, off);
+    s0 += __shfl_xor_sync(lanes, s0, off);
+    s1 += __shfl_xor_sync(lanes, s1, off);
+    s2 += __shfl_xor_sync(lanes, s2, off);
   }
   if (!active || (threadIdx.x & (width - 1)) != 0) return;
   const double f = a.alpha * 4.0 * w;
@@ -659,8 +668,9 @@ __global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaun
   const int team = threadIdx.x / T;
   const int tl = threadIdx.x - team * T;
   double* ws = smem + (size_t)team * P.team_doubles;
-  // lanes of this warp that exist (a partial last warp when the CTA is not a multiple of 32)
-  unsigned mask = 0xffffffffu;
+  // lanes of this warp that exist (a partial last warp when the CTA is not a multiple of 32);
+  // a CTA team is the whole block
+  unsigned mask = CTA ? 0u : 0xffffffffu;
   if (!CTA) {
     const int wbase = threadIdx.x & ~31;
     const int live = blockDim.x - wbase;
@@ -674,8 +684,10 @@ __global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaun
 
 // Persistent kernel over a queue of work items from many launches (classes,
 // molecules): each CTA takes the next item with one atomicAdd (no waiting on
-// other CTAs), adopts that item's plan (teams of T threads, T x teams = the
-// block size, CTA-wide barriers) and runs its quartets.
+// other CTAs), adopts that item's plan and runs its quartets in teams_per_cta
+// teams of T threads (the class's own team size; threads past the last team
+// wait for the next item). Warp teams synchronise per warp, teams of whole
+// warps on a named barrier of their own, so teams never wait for each other.
 __global__ void __launch_bounds__(kPersistBlock) k_persistent(const PersistLaunch pl) {
   extern __shared__ __align__(16) double smem[];
   __shared__ long long s_item;
@@ -697,14 +709,18 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(const PersistLaunc
     __syncthreads();
     const QuartetLaunch& a = s_launch;
     const int T = a.plan.T;
-    const int tpb = kPersistBlock / T;
+    const int tpb = a.plan.teams_per_cta;   // T x tpb <= blockDim.x, whole warps (host-checked)
     const int team = threadIdx.x / T;
+    if (team >= tpb) continue;   // idle warps: straight to the next item's barrier
     const int tl = threadIdx.x - team * T;
     double* ws = smem + (size_t)team * a.plan.team_doubles;
+    // barriers 1..tpb of T threads each for teams of whole warps; whole warps of teams otherwise
+    const unsigned mask = T > 32 ? ((unsigned)(team + 1) << 16) | (unsigned)T : 0xffffffffu;
     for (int64_t sub = 0; sub < w.count; sub += tpb) {   // an item holds a few rounds of teams
       const bool active = team < w.count - sub;
       const int64_t q = w.begin + sub + (active ? team : 0);
-      quartet_body<true>(a, ws, q, active, tl, 0xffffffffu);
+      if (T > 32) quartet_body<true>(a, ws, q, active, tl, mask);
+      else quartet_body<false>(a, ws, q, active, tl, mask);
     }
   }
 }

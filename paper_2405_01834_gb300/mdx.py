@@ -420,7 +420,8 @@ def exchange_energy(eng: Engine, basis: DeviceBasis, coords: torch.Tensor, D: to
 
 
 class ExchangeBatch:
-    """Exchange matrices of several molecules: one launch per class or one persistent launch."""
+    """Exchange matrices of several molecules: one launch per class, one persistent launch,
+    or the register-kernel classes per class plus one persistent launch for the rest."""
 
     def __init__(self, eng: Engine, bases, Ds, tau: float):
         self.eng = eng
@@ -441,8 +442,10 @@ class ExchangeBatch:
         self.n_quartets, self.n_items, self.n_class_launches = nq.value, ni.value, nl.value
         self.model_flops = mf.value
 
-    def run(self, persistent: bool = True) -> int:
-        """Enqueue on the current stream (capturable); returns kernels launched. Results in self.Ks."""
+    def run(self, persistent: int = 1) -> int:
+        """Enqueue on the current stream (capturable); returns kernels launched. Results in self.Ks.
+        persistent: 0 one launch per class, 1 one persistent launch, 2 register-kernel classes
+        per class and one persistent launch for the others (True/False mean 1/0)."""
         nl = ctypes.c_int32()
         self.eng._check(self.eng.lib.mdx_xbatch_run(self.eng.ctx, self.h, int(persistent), ctypes.byref(nl),
                                                     _stream()), "mdx_xbatch_run")

@@ -1,5 +1,6 @@
-"""Batched exchange of several uneven molecules: per-class launches and one persistent
-launch (optionally replayed from a CUDA graph) against per-molecule mdx_exchange and the oracle."""
+"""Batched exchange of several uneven molecules: per-class launches, one persistent launch
+and the hybrid of both (optionally replayed from a CUDA graph) against per-molecule
+mdx_exchange and the oracle."""
 import numpy as np
 import pytest
 import torch
@@ -27,7 +28,11 @@ def _pairs(b):
     return np.array([(i, j) for i in range(b.n_shells) for j in range(i + 1)], dtype=np.int32)
 
 
-@pytest.mark.parametrize("persistent", [False, True])
+def _register_launches(eng, xb):
+    return sum(eng.plan_info(*xb.launch_info(i)[0]).register_kernel != 0 for i in range(xb.n_class_launches))
+
+
+@pytest.mark.parametrize("persistent", [0, 1, 2])
 def test_batched_exchange_matches_single(eng, persistent):
     mols = _molecules()
     bases = [mdx.DeviceBasis(b) for b in mols]
@@ -36,7 +41,9 @@ def test_batched_exchange_matches_single(eng, persistent):
     n = xb.run(persistent=persistent)
     torch.cuda.synchronize()
     eng.sync()
-    assert n == (3 if persistent else 2 + xb.n_class_launches)
+    n_reg = _register_launches(eng, xb)
+    assert 0 < n_reg < xb.n_class_launches
+    assert n == {0: 2 + xb.n_class_launches, 1: 3, 2: 3 + n_reg}[persistent]
     tot = 0
     for i, (b, db) in enumerate(zip(mols, bases)):
         p = _pairs(b)
@@ -53,12 +60,13 @@ def test_batched_exchange_matches_single(eng, persistent):
     xb.close()
 
 
-def test_persistent_launch_in_cuda_graph(eng):
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_persistent_launch_in_cuda_graph(eng, persistent):
     mols = _molecules()[:4]
     bases = [mdx.DeviceBasis(b) for b in mols]
     Ds = [torch.from_numpy(inputs.density(b.nao, 30 + i)) for i, b in enumerate(mols)]
     xb = eng.xbatch(bases, Ds, tau=1e-12)
-    xb.run(persistent=True)
+    xb.run(persistent=persistent)
     torch.cuda.synchronize()
     ref = [K.clone() for K in xb.Ks]
     for K in xb.Ks:
@@ -68,7 +76,7 @@ def test_persistent_launch_in_cuda_graph(eng):
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s):
-            xb.run(persistent=True)
+            xb.run(persistent=persistent)
     torch.cuda.synchronize()
     for _ in range(2):
         for K in xb.Ks:
