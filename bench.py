@@ -39,7 +39,7 @@ CHUNK_BYTES = 2 << 30
 # DRAM bytes (read + write) per [ii|ii] quartet of the k_quartets launch, from the ncu capture summarised
 # in profiles/k_quartets_ii_16x16.md (256 quartets: 2.739 GB read + 3.838 GB written); scaled by the
 # quartets of a launch when the dominant class is [ii|ii]
-NCU_DRAM_BYTES_PER_II_QUARTET = (2.739075e9 + 3.838031e9) / 256
+NCU_DRAM_BYTES_PER_II_QUARTET = (2.739450e9 + 3.838610e9) / 256
 
 
 def parse():

@@ -136,14 +136,16 @@ cudaError_t launch_pair_records(const BasisDev& b0, const BasisDev& b1, const Pr
 }
 
 // ----------------------------------------------------------------- quartets
-// Barrier of one team. Warp teams (T <= 32): `mask` holds the lanes of this
-// warp that take part. Teams of whole warps (CTA = true): `mask` is 0 when the
-// team is the whole block, else (barrier id << 16) | team threads for a named
-// barrier of its own (several teams in one block, persistent kernel).
+// Barrier of one team. CTA = false (k_quartets with T <= 32): `mask` holds
+// the lanes of this warp that take part. CTA = true: `mask` is 0 when the team
+// is the whole block; all ones for teams that fill whole warps of T <= 32
+// threads (warp barrier); else (barrier id << 16) | team threads for a named
+// barrier of the team's own (several teams of whole warps in one block).
 template <bool CTA>
 __device__ __forceinline__ void team_sync(unsigned mask) {
   if (CTA) {
     if (mask == 0) __syncthreads();
+    else if (mask == 0xffffffffu) __syncwarp();
     else asm volatile("bar.sync %0, %1;" ::"r"(mask >> 16), "r"(mask & 0xffffu) : "memory");
   } else {
     __syncwarp(mask);
@@ -714,13 +716,13 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(const PersistLaunc
     if (team >= tpb) continue;   // idle warps: straight to the next item's barrier
     const int tl = threadIdx.x - team * T;
     double* ws = smem + (size_t)team * a.plan.team_doubles;
-    // barriers 1..tpb of T threads each for teams of whole warps; whole warps of teams otherwise
+    // barriers 1..tpb of T threads each for teams of whole warps; a warp barrier for
+    // warps of teams of T <= 32 (one body for both, so that one set of registers serves)
     const unsigned mask = T > 32 ? ((unsigned)(team + 1) << 16) | (unsigned)T : 0xffffffffu;
     for (int64_t sub = 0; sub < w.count; sub += tpb) {   // an item holds a few rounds of teams
       const bool active = team < w.count - sub;
       const int64_t q = w.begin + sub + (active ? team : 0);
-      if (T > 32) quartet_body<true>(a, ws, q, active, tl, mask);
-      else quartet_body<false>(a, ws, q, active, tl, mask);
+      quartet_body<true>(a, ws, q, active, tl, mask);
     }
   }
 }
