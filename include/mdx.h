@@ -210,7 +210,10 @@ mdx_status mdx_schwarz(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pair
  * D: [nao][nao] row-major, symmetric (device). K: [nao][nao] (device),
  *   overwritten. nao = max over shells of ao_off + ncart(l); basis->ao_off is
  *   required. Synchronises `stream` (screening counts) and on return K is
- *   complete. Pairs absent from the list contribute nothing. */
+ *   complete. Pairs absent from the list contribute nothing. The per-class
+ *   integral launches are spread over `stream` and three internal streams of
+ *   the context, each ordered after the work already queued on `stream`, and
+ *   `stream` waits for all of them before K <- K + K^T. */
 mdx_status mdx_exchange(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
                         double tau, const double* D, double* K, void* stream);
 
@@ -229,7 +232,8 @@ mdx_status mdx_exchange(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pai
  * basis->atom is required (atom of each shell, 0 <= atom < n_atoms).
  * grad: [n_atoms][3] doubles (device), overwritten with dE_x/dR (hartree/bohr
  * for normalised inputs). energy: one double (device) receiving E_x, or NULL.
- * Synchronises `stream`; results are complete on return. */
+ * The launches are spread over `stream` and the context's internal streams as
+ * in mdx_exchange. Synchronises `stream`; results are complete on return. */
 mdx_status mdx_exchange_grad(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, const double* Q,
                              int64_t n_pairs, double tau, const double* D, double alpha, int32_t n_atoms,
                              double* grad, double* energy, void* stream);

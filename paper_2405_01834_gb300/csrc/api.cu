@@ -49,6 +49,10 @@ struct mdx_ctx {
   std::vector<std::unique_ptr<Plan>> retired;   // replaced plans, kept alive for batches that use them
   int64_t last_quartets = 0;
   cublasHandle_t cublas = nullptr;        // materialized-Hermite path only, created on first use
+  // auxiliary streams for independent per-class launches (created on first use)
+  static constexpr int kAux = 3;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
 };
 
 namespace {
@@ -287,6 +291,48 @@ mdx_status dev_upload(mdx_ctx* c, const std::vector<T>& v, T** out, cudaStream_t
   if (e != cudaSuccess) return cuda_fail(c, e, "batch upload");
   return MDX_OK;
 }
+
+// Independent launches (one per class, each summing into K or the gradient
+// with atomics) spread over the caller's stream and the context's auxiliary
+// streams, so that launches too small to fill the GPU overlap. fork() makes
+// every auxiliary stream wait for the work enqueued on the caller's stream so
+// far (plan uploads included); pick() takes the stream with the least work
+// assigned; join() makes the caller's stream wait for all of them.
+struct Fanout {
+  mdx_ctx* c;
+  cudaStream_t s;
+  double load[mdx_ctx::kAux + 1] = {};
+  cudaStream_t stream(int i) const { return i == 0 ? s : c->aux[i - 1]; }
+  cudaError_t fork() {
+    if (!c->ev_fork) {
+      for (int i = 0; i < mdx_ctx::kAux; ++i) {
+        cudaError_t e = c->aux[i] ? cudaSuccess : cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !c->ev_join[i]) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+      }
+      const cudaError_t e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaEventRecord(c->ev_fork, s);
+    for (int i = 0; i < mdx_ctx::kAux && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->aux[i], c->ev_fork, 0);
+    return e;
+  }
+  int pick(double work) {
+    int best = 0;
+    for (int i = 1; i <= mdx_ctx::kAux; ++i)
+      if (load[i] < load[best]) best = i;
+    load[best] += work;
+    return best;
+  }
+  cudaError_t join() {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < mdx_ctx::kAux && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(c->ev_join[i], c->aux[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[i], 0);
+    }
+    return e;
+  }
+};
 
 double model_flops_class(const ClassKey& k) {
   auto nh = [](int l) { return (double)nherm(l); };
@@ -542,6 +588,11 @@ void mdx_destroy(mdx_ctx* c) {
   cudaFree(c->d_rprog_off);
   cudaFree(c->d_err);
   if (c->cublas) cublasDestroy(c->cublas);
+  for (int i = 0; i < mdx_ctx::kAux; ++i) {
+    if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 
@@ -1080,6 +1131,8 @@ mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs
     if ((st = ensure(c, "x_recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
     e = launch_pair_records(to_dev(basis), to_dev(basis), d_jobs, (int64_t)jobs.size(), d_recs, d_recs_s, c->d_err, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+    // all plans first (their uploads go to s before the fork), heaviest launch first
+    std::vector<std::pair<double, QuartetLaunch>> jobs_k;
     const int nclass = (int)X.classes.size();
     for (int cp = 0; cp < nclass; ++cp)
       for (int cq = 0; cq <= cp; ++cq) {
@@ -1095,9 +1148,19 @@ mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs
         a.nao = (int32_t)X.nao;
         a.ao_off = basis->ao_off;
         a.pair_shells = X.d_pshell;
-        e = launch_quartets(a, s);
-        if (e != cudaSuccess) return cuda_fail(c, e, "exchange quartet launch");
+        jobs_k.emplace_back(model_flops_class(key) * (double)X.counts[b], a);
       }
+    std::stable_sort(jobs_k.begin(), jobs_k.end(),
+                     [](const std::pair<double, QuartetLaunch>& x, const std::pair<double, QuartetLaunch>& y) {
+                       return x.first > y.first;
+                     });
+    Fanout fan{c, s};
+    e = fan.fork();
+    for (size_t i = 0; i < jobs_k.size() && e == cudaSuccess; ++i)
+      e = launch_quartets(jobs_k[i].second, fan.stream(fan.pick(jobs_k[i].first)));
+    const cudaError_t ej = fan.join();
+    if (e == cudaSuccess) e = ej;
+    if (e != cudaSuccess) return cuda_fail(c, e, "exchange quartet launch");
   }
   e = launch_symmetrize(K, (int32_t)X.nao, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1192,6 +1255,15 @@ mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* 
   // per bucket: centre A (+/-), B (+/-), C (+/-) and, if asked, the energy
   struct Var { int bra, ket, pos, sign; };
   const Var vars[7] = {{1, 0, 0, 1}, {2, 0, 0, -1}, {3, 0, 1, 1}, {4, 0, 1, -1}, {0, 1, 2, 1}, {0, 2, 2, -1}, {0, 0, -1, 0}};
+  // all plans first (their uploads go to s before the fork), then the launches
+  // spread over the streams, heaviest first
+  struct GradJob {
+    QuartetLaunch a;
+    double work;
+    int64_t per, chunk;   // register path: doubles per shellset, shellsets per chunk (0: team kernel)
+  };
+  std::vector<GradJob> gjobs;
+  int64_t ws_doubles = 0;
   const int nclass = (int)X.classes.size();
   for (int cp = 0; cp < nclass; ++cp)
     for (int cq = 0; cq <= cp; ++cq) {
@@ -1220,32 +1292,52 @@ mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* 
         a.gpos = v.pos;
         a.gsign = v.sign;
         for (int k = 0; k < 4; ++k) a.lorig[k] = l0[k];
+        GradJob g{a, model_flops_class(key) * (double)a.nq, 0, 0};
         if (plan->d.reg) {
           // register kernel: shifted shellsets to workspace (back to back), then the
           // gradient contraction, in chunks of at most 1 GiB of shellsets
-          const int64_t per = (int64_t)plan->d.Nb * plan->d.Nk;
-          const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(a.nq, (int64_t(1) << 27) / per));
-          double* V;
-          if ((st = ensure(c, "g_shellsets", (size_t)(chunk * per), &V, s)) != MDX_OK) return st;
-          for (int64_t q0 = 0; q0 < a.nq && e == cudaSuccess; q0 += chunk) {
-            QuartetLaunch part = a;
-            part.qpairs = a.qpairs + q0;
-            part.nq = std::min(chunk, a.nq - q0);
-            QuartetLaunch st_part = part;
-            st_part.D = nullptr;
-            st_part.grad = nullptr;
-            st_part.energy = nullptr;
-            st_part.out = V;
-            st_part.qout = nullptr;
-            e = launch_quartets(st_part, s);
-            if (e == cudaSuccess) e = launch_grad_contract(part, V, s);
-          }
-        } else {
-          e = launch_quartets(a, s);
+          g.per = (int64_t)plan->d.Nb * plan->d.Nk;
+          g.chunk = std::max<int64_t>(1, std::min<int64_t>(a.nq, (int64_t(1) << 27) / g.per));
+          ws_doubles = std::max(ws_doubles, g.chunk * g.per);
         }
-        if (e != cudaSuccess) return cuda_fail(c, e, "gradient quartet launch");
+        gjobs.push_back(g);
       }
     }
+  // one shellset workspace per stream
+  static const char* const kWsName[mdx_ctx::kAux + 1] = {"g_shellsets0", "g_shellsets1", "g_shellsets2",
+                                                          "g_shellsets3"};
+  double* ws[mdx_ctx::kAux + 1] = {};
+  if (ws_doubles > 0)
+    for (int i = 0; i <= mdx_ctx::kAux; ++i)
+      if ((st = ensure(c, kWsName[i], (size_t)ws_doubles, &ws[i], s)) != MDX_OK) return st;
+  std::stable_sort(gjobs.begin(), gjobs.end(), [](const GradJob& x, const GradJob& y) { return x.work > y.work; });
+  Fanout fan{c, s};
+  e = fan.fork();
+  for (size_t j = 0; j < gjobs.size() && e == cudaSuccess; ++j) {
+    const GradJob& g = gjobs[j];
+    const int si = fan.pick(g.work);
+    const cudaStream_t gs = fan.stream(si);
+    if (g.chunk == 0) {
+      e = launch_quartets(g.a, gs);
+      continue;
+    }
+    for (int64_t q0 = 0; q0 < g.a.nq && e == cudaSuccess; q0 += g.chunk) {
+      QuartetLaunch part = g.a;
+      part.qpairs = g.a.qpairs + q0;
+      part.nq = std::min(g.chunk, g.a.nq - q0);
+      QuartetLaunch st_part = part;
+      st_part.D = nullptr;
+      st_part.grad = nullptr;
+      st_part.energy = nullptr;
+      st_part.out = ws[si];
+      st_part.qout = nullptr;
+      e = launch_quartets(st_part, gs);
+      if (e == cudaSuccess) e = launch_grad_contract(part, ws[si], gs);
+    }
+  }
+  const cudaError_t ej = fan.join();
+  if (e == cudaSuccess) e = ej;
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient quartet launch");
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "exchange gradient");
   return check_device_error(c, s);
