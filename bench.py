@@ -624,7 +624,8 @@ def main():
             "quartets_per_s": round(whole_job_rate(sum(len(q) for _, _, q, _ in prepared), world, ms_step), 1),
             "model_frac_of_peak": round(value / world / peak_gflops, 4),
             "exec_gflops": round(world * total_exec / (ms_step * 1e-3) * 1e-9, 3),
-            "per_class": per_class, "roofline": roofline, "autotune_s": tuned or None, "gpu_launches": launches // args.steps if args.steps else 0,
+            "per_class": per_class, "roofline": roofline, "autotune_s": tuned or None, "gpu_launches": launches,
+            "gpu_launches_per_step": launches // args.steps if args.steps else 0,
             "clocks": clocks}
 
     # ---- end to end through the public call with host buffers (rank 0 timing only)
