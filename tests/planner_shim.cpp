@@ -1,0 +1,89 @@
+// Host-only test shim: builds the engine's planner (csrc/plan.cpp) with the
+// host compiler and hands its step programs to Python, so that the CPU test
+// suite can run them in an emulator of the team kernel and compare the
+// result with the oracle. Test infrastructure: nothing in the library or the
+// benchmark links this file.
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mdx_internal.h"
+
+namespace {
+mdx::Plan g_plan;
+std::vector<uint32_t> g_rprog;
+std::vector<int32_t> g_roff;
+
+template <typename T>
+int64_t copy_out(const std::vector<T>& v, void* dst, int64_t cap) {
+  const int64_t bytes = (int64_t)(v.size() * sizeof(T));
+  if (dst && cap >= bytes && bytes > 0) std::memcpy(dst, v.data(), (size_t)bytes);
+  return bytes;
+}
+}  // namespace
+
+extern "C" {
+
+// Plan one class (team kernel programs). Returns 0 on success, else 1 with a
+// message in err.
+int shim_build(int la, int lb, int lc, int ld, int Kb, int Kk, int onec, int store, int T, int budget,
+               int single_max, char* err, int errcap) {
+  mdx::ClassKey key{la, lb, lc, ld, Kb, Kk, onec, store};
+  mdx::PlanConfig cfg;
+  cfg.T = T;
+  if (budget > 0) cfg.budget = budget;
+  if (single_max > 0) cfg.single_max = single_max;
+  cfg.variant = 1;
+  g_plan = mdx::Plan();
+  std::string e;
+  if (!mdx::build_plan(key, cfg, g_plan, e)) {
+    if (err && errcap > 0) {
+      std::strncpy(err, e.c_str(), (size_t)errcap - 1);
+      err[errcap - 1] = 0;
+    }
+    return 1;
+  }
+  return 0;
+}
+
+// The scalar fields of the last plan, in the order the Python side names them.
+int shim_scalars(int32_t* out, int cap) {
+  const mdx::PlanDev& P = g_plan.d;
+  const int32_t v[] = {P.la, P.lb, P.lc, P.ld, P.Kb, P.Kk, P.onec, P.L, P.Lb, P.Lk, P.Nb, P.Nk, P.hb,
+                       P.T, P.teams_per_cta, P.team_doubles, P.recb, P.reck, P.o_recb, P.o_reck, P.o_scal,
+                       P.o_G, P.o_R0, P.o_R1, P.o_A, P.o_B, P.o_X, P.o_C1, P.o_OUT, P.c1size, P.ngroups,
+                       P.ncols_max, P.nb1, P.nb23, P.cache_R, P.has_out};
+  const int n = (int)(sizeof(v) / sizeof(v[0]));
+  if (out && cap >= n) std::memcpy(out, v, sizeof(v));
+  return n;
+}
+
+// Raw program arrays of the last plan: 0 groups, 1 ket steps, 2 b1, 3 b23,
+// 4 column map. Returns the byte size; copies when cap suffices.
+int64_t shim_array(int which, void* dst, int64_t cap) {
+  switch (which) {
+    case 0: return copy_out(g_plan.groups, dst, cap);
+    case 1: return copy_out(g_plan.kprog, dst, cap);
+    case 2: return copy_out(g_plan.b1, dst, cap);
+    case 3: return copy_out(g_plan.b23, dst, cap);
+    case 4: return copy_out(g_plan.colmap, dst, cap);
+    default: return -1;
+  }
+}
+
+// R-level programs: which = 0 the words, 1 the start of each total order.
+int64_t shim_rprog(int which, void* dst, int64_t cap) {
+  if (g_rprog.empty()) mdx::build_rlevel_programs(g_rprog, g_roff);
+  return which == 0 ? copy_out(g_rprog, dst, cap) : copy_out(g_roff, dst, cap);
+}
+
+int shim_sizes(int32_t* out) {
+  out[0] = (int32_t)sizeof(mdx::StepEntry);
+  out[1] = (int32_t)sizeof(mdx::B23Entry);
+  out[2] = (int32_t)sizeof(mdx::Group);
+  out[3] = mdx::kRecHeader;
+  return 0;
+}
+
+}  // extern "C"

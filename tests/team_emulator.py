@@ -1,0 +1,352 @@
+"""CPU emulator of the team kernel's step programs (test infrastructure).
+
+The team kernel is a generic interpreter: everything class-specific lives in
+the programs that the host planner emits (R levels of Eq. r, the ket steps
+k1/k2/k3 of Eq. ket-from-hermite, the bra steps b1/b23 of Eq.
+bra-from-hermite, the column map). This module builds those programs with the
+library's own planner (compiled here with the host compiler through
+`planner_shim.cpp`) and executes them on one flat float64 workspace with the
+semantics the kernel gives each entry, so that the CPU suite can check every
+class's programs against the oracle without a GPU.
+
+Everything else the kernel takes as input is formed here from the paper's
+definitions, not from the library: primitive-pair records (zeta_p, P, the
+prefactor c_a c_b exp(-zeta_a zeta_b |AB|^2 / zeta_p) and per-axis E tables
+with E_00^0 = 1, Eqs. E2rr1/E2rr2 or E1rr, taken from the oracle's E routines)
+and the Boys values (the oracle's F_m). The ket records carry the (-1)^t of
+Eq. pq, as the kernel expects.
+
+Within a step the kernel runs all entries in parallel; the emulator gathers
+every operand before it writes, and `check_hazards` asserts that no entry of a
+step reads or writes what another entry of the same step writes.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2405_01834_gb300", "csrc")
+SHIM_SRC = os.path.join(HERE, "planner_shim.cpp")
+BUILD = os.path.join(HERE, "_build")
+SHIM_LIB = os.path.join(BUILD, "libplanner_shim.so")
+
+SCALARS = ("la lb lc ld Kb Kk onec L Lb Lk Nb Nk hb T teams_per_cta team_doubles recb reck o_recb o_reck o_scal "
+           "o_G o_R0 o_R1 o_A o_B o_X o_C1 o_OUT c1size ngroups ncols_max nb1 nb23 cache_R has_out").split()
+STEP = np.dtype([("out", "<u2"), ("src", "<u2"), ("coef", "<u2"), ("n", "u1"), ("stride", "u1")])
+B23 = np.dtype([("out", "<u2"), ("src", "<u2"), ("ey", "<u2"), ("ez", "<u2"), ("u0", "u1"), ("nu", "u1"),
+                ("su", "u1"), ("v0", "u1"), ("nv", "u1"), ("sv", "u1"), ("r", "u1"), ("pad", "u1")])
+GROUP = np.dtype([(n, "<i4") for n in ("k1_off", "k1_n", "k2_off", "k2_n", "k3_off", "k3_n", "ncols", "col_off",
+                                       "o_B", "pad")])
+REC_HEADER = 8
+TWO_PI_52 = 2.0 * math.pi ** 2.5
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _build_shim() -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    deps = [SHIM_SRC, os.path.join(CSRC, "plan.cpp"), os.path.join(CSRC, "mdx_internal.h")]
+    if not os.path.exists(SHIM_LIB) or any(os.path.getmtime(d) > os.path.getmtime(SHIM_LIB) for d in deps):
+        tmp = SHIM_LIB + ".tmp%d" % os.getpid()
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, SHIM_SRC,
+                        os.path.join(CSRC, "plan.cpp"), "-o", tmp], check=True)
+        os.replace(tmp, SHIM_LIB)
+    return SHIM_LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(_build_shim())
+            lib.shim_build.argtypes = [ctypes.c_int] * 11 + [ctypes.c_char_p, ctypes.c_int]
+            lib.shim_build.restype = ctypes.c_int
+            lib.shim_scalars.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.shim_scalars.restype = ctypes.c_int
+            lib.shim_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
+            lib.shim_array.restype = ctypes.c_int64
+            lib.shim_rprog.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
+            lib.shim_rprog.restype = ctypes.c_int64
+            lib.shim_sizes.argtypes = [ctypes.c_void_p]
+            sizes = np.zeros(4, dtype=np.int32)
+            lib.shim_sizes(sizes.ctypes.data)
+            assert (sizes[0], sizes[1], sizes[2], sizes[3]) == (STEP.itemsize, B23.itemsize, GROUP.itemsize,
+                                                                REC_HEADER), sizes
+            _lib = lib
+    return _lib
+
+
+def _array(lib, fn, which, dtype):
+    nbytes = fn(which, None, 0)
+    buf = np.zeros(max(nbytes, 0), dtype=np.uint8)
+    if nbytes > 0:
+        fn(which, buf.ctypes.data, nbytes)
+    return buf.view(dtype)
+
+
+@dataclass
+class Plan:
+    s: dict
+    groups: np.ndarray
+    kprog: np.ndarray
+    b1: np.ndarray
+    b23: np.ndarray
+    colmap: np.ndarray
+    rprog: np.ndarray
+    roff: np.ndarray
+
+
+class PlanError(RuntimeError):
+    pass
+
+
+def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, single_max=0) -> Plan:
+    """The planner's team-kernel programs for one class and shape."""
+    lib = _load()
+    err = ctypes.create_string_buffer(256)
+    if lib.shim_build(la, lb, lc, ld, Kb, Kk, int(onec), int(store), T, budget, single_max, err, 256):
+        raise PlanError(err.value.decode())
+    sc = np.zeros(64, dtype=np.int32)
+    n = lib.shim_scalars(sc.ctypes.data, 64)
+    assert n == len(SCALARS)
+    s = {k: int(v) for k, v in zip(SCALARS, sc[:n])}
+    return Plan(s, _array(lib, lib.shim_array, 0, GROUP), _array(lib, lib.shim_array, 1, STEP),
+                _array(lib, lib.shim_array, 2, STEP), _array(lib, lib.shim_array, 3, B23),
+                _array(lib, lib.shim_array, 4, np.uint16), _array(lib, lib.shim_rprog, 0, np.uint32),
+                _array(lib, lib.shim_rprog, 1, np.int32))
+
+
+# ----------------------------------------------------------------- records
+def _etab_blocks(la, lb):
+    """(a, b, offset) of each (a, b) block of a per-axis table, t contiguous, a-major."""
+    o = 0
+    for a in range(la + 1):
+        for b in range(lb + 1):
+            yield a, b, o
+            o += a + b + 1
+
+
+def rec_size(la, lb):
+    tab = sum(a + b + 1 for a in range(la + 1) for b in range(lb + 1))
+    return (REC_HEADER + 3 * tab + 1) & ~1
+
+
+def pair_record(la, lb, za, zb, ca, cb, A, B, signed):
+    """Primitive-pair record: header [zeta_p, 1/zeta_p, P, prefactor, 0, 0], then
+    the x, y, z tables (E)_{ab}^t scaled to E_00^0 = 1 (Eqs. E2rr1/E2rr2);
+    signed: (-1)^t folded in (Eq. pq). lb = -1: one-centre bra (Eq. E1rr)."""
+    one = lb < 0
+    lb = max(lb, 0)
+    A = np.asarray(A, dtype=np.float64)
+    B = A if one else np.asarray(B, dtype=np.float64)
+    p = za + (0.0 if one else zb)
+    P = A if one else (za * A + zb * B) / p
+    pref = ca * (1.0 if one else cb * math.exp(-za * zb * float(np.sum((A - B) ** 2)) / p))
+    tabs = []
+    for ax in range(3):
+        if one:
+            E1 = oracle.e1c(la, za)
+            E = np.zeros((la + 1, 1, la + 1))
+            E[:, 0, :] = E1 / E1[0, 0]
+        else:
+            E = oracle.e2c(la, lb, za, zb, float(A[ax]), float(B[ax]))
+            E = E / E[0, 0, 0]
+        t = []
+        for a, b, _ in _etab_blocks(la, lb):
+            blk = E[a, b, :a + b + 1].copy()
+            if signed:
+                blk[1::2] *= -1.0
+            t.append(blk)
+        tabs.append(np.concatenate(t))
+    rec = np.zeros(rec_size(la, lb))
+    rec[:REC_HEADER] = [p, 1.0 / p, P[0], P[1], P[2], pref, 0.0, 0.0]
+    body = np.concatenate(tabs)
+    rec[REC_HEADER:REC_HEADER + len(body)] = body
+    return rec
+
+
+def shell_pair_records(basis, i, j, signed):
+    """Records of all primitive pairs of shells (i, j) of `basis`; j = None: one-centre."""
+    li = int(basis.l[i])
+    pi = range(int(basis.prim_off[i]), int(basis.prim_off[i] + basis.nprim[i]))
+    if j is None:
+        return [pair_record(li, -1, basis.exps[a], 0.0, basis.coefs[a], 1.0, basis.center[i], None, signed)
+                for a in pi]
+    lj = int(basis.l[j])
+    pj = range(int(basis.prim_off[j]), int(basis.prim_off[j] + basis.nprim[j]))
+    return [pair_record(li, lj, basis.exps[a], basis.exps[b], basis.coefs[a], basis.coefs[b], basis.center[i],
+                        basis.center[j], signed) for a in pi for b in pj]
+
+
+# ----------------------------------------------------------------- hazards
+def check_hazards(pl: Plan):
+    """No entry of a ket step reads or writes what another entry of that step
+    writes, and every access stays inside the team workspace."""
+    W = pl.s["team_doubles"]
+    for g in pl.groups:
+        for off, n in ((g["k1_off"], g["k1_n"]), (g["k2_off"], g["k2_n"]), (g["k3_off"], g["k3_n"])):
+            ent = pl.kprog[off:off + n]
+            outs = ent["out"].astype(np.int64)
+            assert len(np.unique(outs)) == len(outs), "two entries of one step write the same word"
+            n_max = int(ent["n"].max()) if n else 0
+            reads = set()
+            for k in range(n_max):
+                live = ent["n"] > k
+                reads |= set((ent["coef"][live].astype(np.int64) + k * ent["stride"][live]).tolist())
+                reads |= set((ent["src"][live].astype(np.int64) + k * ent["stride"][live]).tolist())
+            assert not (reads & set(outs.tolist())), "a step reads a word another entry of it writes"
+            assert outs.max(initial=0) < W and max(reads, default=0) < W
+
+
+# ----------------------------------------------------------------- execution
+def _run_step(ws, ent, acc):
+    if len(ent) == 0:
+        return
+    out = ent["out"].astype(np.int64)
+    coef = ent["coef"].astype(np.int64)
+    src = ent["src"].astype(np.int64)
+    st = ent["stride"].astype(np.int64)
+    n = ent["n"].astype(np.int64)
+    v = ws[out].copy() if acc else np.zeros(len(ent))
+    for k in range(int(n.max())):
+        live = n > k
+        v[live] += ws[coef[live] + k * st[live]] * ws[src[live] + k * st[live]]
+    ws[out] = v
+
+
+def rlevel_programs():
+    """The planner's R-level program words and the start of each total order."""
+    lib = _load()
+    return _array(lib, lib.shim_rprog, 0, np.uint32), _array(lib, lib.shim_rprog, 1, np.int32)
+
+
+def _level(rprog, roff, N, src, g):
+    """Entries of total order N of one R level from the previous level `src`."""
+    cnt = (N + 1) * (N + 2) * (N + 3) // 6
+    w = rprog[roff[N]:roff[N] + cnt].astype(np.int64)
+    ax = (w >> 24) & 3
+    s1 = w & 0xFFF
+    s2 = (w >> 12) & 0xFFF
+    c = (w >> 26).astype(np.float64)
+    val = g[1][ax] * src[s1] + c * src[s2]
+    val[0] = g[0]
+    return val
+
+
+def hermite_R(rprog, roff, L, G, PQ):
+    """[tuv]^(0) of total order <= L from the seeds G[m] = [000]^(m) by the
+    program words alone, in the layout (t, u, v) -> roff(L, t, u) + v."""
+    PQ = np.asarray(PQ, dtype=np.float64)
+    cur = np.array([G[L]])
+    for nn in range(L - 1, -1, -1):
+        cur = _level(rprog, roff, L - nn, cur, (G[nn], PQ))
+    return cur
+
+
+def simplex_offset(N, t, u):
+    """Start of row (t, u) of a [t][u][v] simplex of total order N."""
+    tet = lambda n: 0 if n < 0 else n * (n + 1) * (n + 2) // 6
+    tri = lambda n: 0 if n < 0 else n * (n + 1) // 2
+    return tet(N + 1) - tet(N - t + 1) + tri(N - t + 1) - tri(N - t - u + 1)
+
+
+def _compute_R(pl: Plan, ws):
+    s = pl.s
+    L = s["L"]
+    rb = ws[s["o_recb"]:s["o_recb"] + REC_HEADER]
+    rk = ws[s["o_reck"]:s["o_reck"] + REC_HEADER]
+    PQ = rb[2:5] - rk[2:5]
+    zp, zq = rb[0], rk[0]
+    rho = zp * zq / (zp + zq)
+    Tb = rho * float(PQ @ PQ)
+    pref = TWO_PI_52 / (zp * zq * math.sqrt(zp + zq)) * rb[5] * rk[5]
+    F = oracle.boys(L, Tb)
+    G = np.array([(-2.0 * rho) ** m * pref * F[m] for m in range(L + 1)])
+    ws[s["o_G"]:s["o_G"] + L + 1] = G
+    o0, o1 = s["o_R0"], s["o_R1"]
+    if L == 0:
+        ws[o0] = G[0]
+        return
+    ws[o1 if L & 1 else o0] = G[L]
+    # levels alternate between the R0 and R1 regions of the workspace, as in the kernel
+    for nn in range(L - 1, -1, -1):
+        N = L - nn
+        dst, src = (o1, o0) if nn & 1 else (o0, o1)
+        val = _level(pl.rprog, pl.roff, N, ws[src:], (G[nn], PQ))
+        ws[dst:dst + len(val)] = val
+
+
+def emulate(pl: Plan, bra_recs, ket_recs_signed) -> np.ndarray:
+    """Run one quartet through the plan's programs (store epilogue); returns
+    the shellset [Nb][Nk] (row-major, bra Cartesian pair major)."""
+    s = pl.s
+    Nb, Nk, hb, c1size = s["Nb"], s["Nk"], s["hb"], s["c1size"]
+    assert len(bra_recs) == s["Kb"] and len(ket_recs_signed) == s["Kk"]
+    ws = np.zeros(s["team_doubles"])
+    out = np.full(Nb * Nk, np.nan)
+    ob, ok = s["o_recb"], s["o_reck"]
+
+    def load_bra(r):
+        ws[ob:ob + s["recb"]] = r[:s["recb"]]
+
+    def load_ket(r):
+        ws[ok:ok + s["reck"]] = r[:s["reck"]]
+
+    if s["cache_R"]:
+        load_bra(bra_recs[0])
+        load_ket(ket_recs_signed[0])
+        _compute_R(pl, ws)
+    b1 = pl.b1
+    b23 = pl.b23
+    for g in pl.groups:
+        ncols = int(g["ncols"])
+        cols = np.arange(ncols)
+        cm = pl.colmap[g["col_off"]:g["col_off"] + ncols].astype(np.int64)
+        for pb in range(s["Kb"]):
+            if not s["cache_R"]:
+                load_bra(bra_recs[pb])
+            for pk in range(s["Kk"]):
+                if not s["cache_R"]:
+                    load_ket(ket_recs_signed[pk])
+                    _compute_R(pl, ws)
+                if g["k1_n"] > 0:
+                    _run_step(ws, pl.kprog[g["k1_off"]:g["k1_off"] + g["k1_n"]], False)
+                _run_step(ws, pl.kprog[g["k2_off"]:g["k2_off"] + g["k2_n"]], False)
+                _run_step(ws, pl.kprog[g["k3_off"]:g["k3_off"] + g["k3_n"]], pk > 0)
+            # b1: C1[col][out] = sum_k E[coef + k st] X[col][src + k st]
+            for e in b1:
+                k = np.arange(int(e["n"])) * int(e["stride"])
+                c = ws[int(e["coef"]) + k]
+                x = ws[s["o_X"] + cols[:, None] * hb + int(e["src"]) + k[None, :]]
+                ws[s["o_C1"] + cols * c1size + int(e["out"])] = x @ c
+            # b23: OUT[out][col] (+)= sum_v Ez[v] sum_u Ey[u] C1[col][row(v) + u]
+            to_global = pb == s["Kb"] - 1
+            for e in b23:
+                r1 = int(e["r"]) + 1
+                iu = np.arange(int(e["nu"])) * int(e["su"])
+                ey = ws[int(e["ey"]) + iu]
+                acc = np.zeros(ncols)
+                for iv in range(int(e["nv"])):
+                    va = int(e["v0"]) + iv * int(e["sv"])
+                    row = int(e["src"]) + int(e["u0"]) + va * r1 - va * (va - 1) // 2
+                    c1 = ws[s["o_C1"] + cols[:, None] * c1size + row + iu[None, :]]
+                    acc += ws[int(e["ez"]) + iv * int(e["sv"])] * (c1 @ ey)
+                o = s["o_OUT"] + int(e["out"]) * ncols + cols
+                if pb > 0:
+                    acc = ws[o] + acc
+                if to_global:
+                    out[int(e["out"]) * Nk + cm] = acc
+                else:
+                    ws[o] = acc
+    return out.reshape(Nb, Nk)

@@ -1,0 +1,176 @@
+"""Host logic on the CPU: the planner's step programs, run in an emulator of the
+team kernel (tests/team_emulator.py), reproduce the oracle's shellsets.
+
+The team kernel executes whatever programs the host planner emits for a class
+(R levels, ket steps k1/k2/k3, bra steps b1/b23, column map) with fixed
+per-entry semantics. Running those programs here checks, without a GPU, that
+for every class shape the planner produces (one group or many, z-pair groups
+sharing one k1 output, contracted classes, one-centre bras, store-only plans)
+the programs compute [ab|cd] of Eqs. ket-from-hermite and bra-from-hermite and
+that no entry of a step depends on another entry of the same step.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+import team_emulator as te
+from paper_2405_01834_gb300 import inputs
+
+
+def _basis_4c(lq, K, seed, n=2):
+    """n x n quartets of class lq: random bra and ket pairs in a 1.5-bohr box
+    (overlapping shells, so integrals are O(1)), exponents log-uniform [0.2, 4]."""
+    b, q = inputs.class_sweep(lq, n_bra=n, n_ket=n, seed=seed, box=1.5, zlo=0.2, zhi=4.0, K=K)
+    return b, q
+
+
+def _emulate_4c(pl, b, q):
+    out = []
+    for a, bb, c, d in q:
+        br = te.shell_pair_records(b, a, bb, signed=False)
+        kr = te.shell_pair_records(b, c, d, signed=True)
+        out.append(te.emulate(pl, br, kr).reshape(-1))
+    return np.concatenate(out)
+
+
+def _check_4c(lq, K=(1, 1, 1, 1), seed=11, n=2, **shape):
+    b, q = _basis_4c(lq, K, seed, n)
+    pl = te.plan(*lq, K[0] * K[1], K[2] * K[3], **shape)
+    te.check_hazards(pl)
+    got = _emulate_4c(pl, b, q)
+    ref, off = oracle.eri4(b, q)
+    assert np.max(np.abs(ref)) > 1e-3   # the inputs give integrals of a meaningful size
+    ld, _ = oracle.eri4(b, q, precision=1)
+    parity.check(got, ref, ld, what="emulated %s K=%s %s" % (lq, K, shape), offsets=off)
+    return pl
+
+
+def test_rlevel_programs_reproduce_hermite_integrals():
+    """The R-level program words (Eq. r), run alone, give the oracle's
+    [tuv]^(0) for every total order the engine uses (L <= 25: l = 6 gradients)."""
+    rprog, roff = te.rlevel_programs()
+    rng = np.random.default_rng(3)
+    for L in list(range(0, 26)):
+        rho = float(rng.uniform(0.3, 2.0))
+        PQ = rng.uniform(-1.0, 1.0, 3)
+        T = rho * float(PQ @ PQ)
+        F = oracle.boys(L, T)
+        G = np.array([(-2.0 * rho) ** m * F[m] for m in range(L + 1)])
+        R = te.hermite_R(rprog, roff, L, G, PQ)
+        ref = oracle.rtable(L, rho, PQ)
+        scale = np.max(np.abs(ref))
+        for t in range(L + 1):
+            for u in range(L + 1 - t):
+                o = te.simplex_offset(L, t, u)
+                got = R[o:o + L + 1 - t - u]
+                np.testing.assert_allclose(got, ref[t, u, :L + 1 - t - u], rtol=0, atol=1e-12 * scale,
+                                           err_msg="L=%d t=%d u=%d" % (L, t, u))
+
+
+@pytest.mark.parametrize("lq", [q for q in itertools.product(range(3), repeat=4)])
+def test_uncontracted_low_l(lq):
+    """Every class with all l <= 2, one primitive per shell."""
+    _check_4c(lq, seed=100 + sum(x * 3 ** i for i, x in enumerate(lq)))
+
+
+@pytest.mark.parametrize("lq", [(3, 3, 3, 3), (4, 3, 2, 1), (1, 2, 3, 4), (0, 4, 4, 0), (4, 4, 4, 4),
+                                (5, 4, 3, 2), (6, 6, 1, 0), (6, 6, 6, 6)])
+def test_uncontracted_high_l(lq):
+    """Higher l, including [gg|gg] and [ii|ii] (workspace split into many column groups)."""
+    pl = _check_4c(lq, seed=7, n=1 if sum(lq) >= 20 else 2)
+    if sum(lq) >= 16:
+        assert pl.s["ngroups"] > 1
+
+
+@pytest.mark.parametrize("lq,K", [((0, 0, 0, 0), (6, 6, 6, 6)), ((1, 0, 1, 0), (3, 6, 3, 6)),
+                                  ((1, 1, 1, 1), (3, 2, 2, 1)), ((2, 1, 0, 0), (1, 3, 6, 6)),
+                                  ((2, 2, 2, 2), (2, 2, 1, 2)), ((3, 1, 2, 0), (1, 3, 2, 6)),
+                                  ((3, 3, 2, 2), (2, 1, 1, 2))])
+def test_contracted(lq, K):
+    """Contracted shells: primitive loops over bra and ket pairs, R per primitive quartet."""
+    pl = _check_4c(lq, K=K, seed=21)
+    assert pl.s["cache_R"] == 0
+
+
+@pytest.mark.parametrize("lq,K,store", [((1, 1, 1, 1), (1, 1, 1, 1), True), ((2, 2, 2, 2), (1, 1, 1, 1), True),
+                                        ((3, 2, 3, 2), (1, 1, 1, 1), True), ((2, 1, 2, 1), (1, 1, 2, 3), True),
+                                        ((2, 1, 2, 1), (2, 1, 1, 1), True)])
+def test_store_only_plans(lq, K, store):
+    """Store plans: no OUT region when the bra has one primitive pair (b23 writes the shellset)."""
+    pl = _check_4c(lq, K=K, seed=31, store=store)
+    assert pl.s["has_out"] == (0 if K[0] * K[1] == 1 else 1)
+
+
+@pytest.mark.parametrize("lq,K,single_max,budget", [((2, 2, 2, 2), (1, 1, 1, 1), 4000, 0),
+                                                    ((2, 2, 2, 2), (1, 1, 1, 1), 4000, 8 * 1024),
+                                                    ((3, 2, 2, 2), (1, 1, 1, 1), 4000, 12 * 1024),
+                                                    ((2, 2, 2, 1), (2, 1, 2, 1), 4000, 8 * 1024),
+                                                    ((3, 3, 3, 3), (1, 1, 1, 1), 4000, 24 * 1024)])
+def test_forced_column_groups(lq, K, single_max, budget):
+    """Small workspace caps force one group per ket z-pair (split into chunks);
+    uncontracted classes share one k1 output between the groups of a z-pair."""
+    pl = _check_4c(lq, K=K, seed=41, single_max=single_max, budget=budget)
+    assert pl.s["ngroups"] > 1
+    if K == (1, 1, 1, 1) and budget:
+        assert np.any(pl.groups["k1_n"] == 0)   # some group reuses its z-pair's A
+    if K != (1, 1, 1, 1):
+        assert np.all(pl.groups["k1_n"] > 0)    # contracted: every group recomputes A
+
+
+def _basis_3c(la, lc, ld, Ka, Kc, Kd, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    aux, orb = inputs.BasisBuilder(), inputs.BasisBuilder()
+    for _ in range(2):
+        inputs.random_shell(rng, aux, la, rng.uniform(0, 1.5, 3), Ka, 0.2, 4.0)
+        inputs.random_shell(rng, orb, lc, rng.uniform(0, 1.5, 3), Kc, 0.2, 4.0)
+        inputs.random_shell(rng, orb, ld, rng.uniform(0, 1.5, 3), Kd, 0.2, 4.0)
+    trip = np.array([[a, 2 * k, 2 * k + 1] for a in range(2) for k in range(2)], dtype=np.int32)
+    return aux.build(), orb.build(), trip
+
+
+@pytest.mark.parametrize("la,lc,ld,K", [(0, 0, 0, (1, 1, 1)), (1, 1, 0, (1, 3, 1)), (2, 1, 1, (1, 1, 1)),
+                                        (3, 2, 1, (1, 1, 1)), (4, 0, 0, (1, 6, 6)), (5, 1, 0, (1, 3, 6)),
+                                        (6, 2, 2, (1, 1, 1)), (6, 3, 3, (1, 1, 1)), (2, 2, 0, (2, 1, 1))])
+def test_three_center(la, lc, ld, K):
+    """[a|cd] with a one-centre bra (Eq. E1rr; the bra steps skip the zero
+    parity terms with stride-2 entries)."""
+    aux, orb, trip = _basis_3c(la, lc, ld, *K, seed=51 + la)
+    pl = te.plan(la, 0, lc, ld, K[0], K[1] * K[2], onec=True)
+    te.check_hazards(pl)
+    got = []
+    for a, c, d in trip:
+        br = te.shell_pair_records(aux, a, None, signed=False)
+        kr = te.shell_pair_records(orb, c, d, signed=True)
+        got.append(te.emulate(pl, br, kr).reshape(-1))
+    got = np.concatenate(got)
+    ref, off = oracle.eri3(aux, orb, trip)
+    assert np.max(np.abs(ref)) > 1e-3
+    ld_ref, _ = oracle.eri3(aux, orb, trip, precision=1)
+    parity.check(got, ref, ld_ref, what="emulated [%d|%d%d]" % (la, lc, ld), offsets=off)
+
+
+def test_emulator_detects_a_corrupted_program():
+    """The comparison is sensitive: one ket-step entry pointed at the wrong E
+    coefficient, or one bra entry with a shortened sum, makes the result differ."""
+    lq = (2, 1, 2, 1)
+    b, q = _basis_4c(lq, (1, 1, 1, 1), 61)
+    ref, off = oracle.eri4(b, q)
+    pl = te.plan(*lq)
+    g = pl.groups[0]
+    k3 = pl.kprog[g["k3_off"]:g["k3_off"] + g["k3_n"]]
+    i = int(np.argmax(k3["n"]))
+    bad = pl.kprog.copy()
+    bad[g["k3_off"] + i]["coef"] += 1
+    pl_bad = te.Plan(pl.s, pl.groups, bad, pl.b1, pl.b23, pl.colmap, pl.rprog, pl.roff)
+    with pytest.raises(AssertionError):
+        parity.check(_emulate_4c(pl_bad, b, q), ref, what="corrupted k3")
+    b23 = pl.b23.copy()
+    j = int(np.argmax(b23["nu"]))
+    b23[j]["nu"] -= 1
+    pl_bad = te.Plan(pl.s, pl.groups, pl.kprog, pl.b1, b23, pl.colmap, pl.rprog, pl.roff)
+    with pytest.raises(AssertionError):
+        parity.check(_emulate_4c(pl_bad, b, q), ref, what="corrupted b23")
+    parity.check(_emulate_4c(pl, b, q), ref, what="intact")
