@@ -230,6 +230,9 @@ mdx_status mdx_exchange(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pai
  * the kernel with G = D_ik (x) D_jl + D_il (x) D_jk; the fourth centre follows
  * from translational invariance.
  * basis->atom is required (atom of each shell, 0 <= atom < n_atoms).
+ * Shells must have l <= MDX_LMAX - 1 (the raised classes reach l + 1);
+ * MDX_EUNSUPPORTED otherwise (after the screening, before any integral
+ * launch; grad is then left untouched).
  * grad: [n_atoms][3] doubles (device), overwritten with dE_x/dR (hartree/bohr
  * for normalised inputs). energy: one double (device) receiving E_x, or NULL.
  * The launches are spread over `stream` and the context's internal streams as

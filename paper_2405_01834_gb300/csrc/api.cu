@@ -1184,6 +1184,10 @@ mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* 
   if (st != MDX_OK) return st;
   const HostBasis& hb = X.hb;
   const int32_t n = hb.n;
+  // the derivative raises a shell's l by one, and the planner and kernels stop at MDX_LMAX
+  for (int i = 0; i < n; ++i)
+    if (hb.l[i] >= MDX_LMAX)
+      return fail(c, MDX_EUNSUPPORTED, "exchange gradient: shell angular momentum above MDX_LMAX - 1");
   cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)n_atoms * 3 * sizeof(double), s);
   if (e == cudaSuccess && energy) e = cudaMemsetAsync(energy, 0, sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "gradient clear");
