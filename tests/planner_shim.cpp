@@ -1,7 +1,8 @@
-// Host-only test shim: builds the engine's planner (csrc/plan.cpp) with the
-// host compiler and hands its step programs to Python, so that the CPU test
-// suite can run them in an emulator of the team kernel and compare the
-// result with the oracle. Test infrastructure: nothing in the library or the
+// Host-only test shim: builds the engine's host-side table and program
+// generators (csrc/plan.cpp, boys_table.cpp, solid.cpp) with the host
+// compiler and hands their output to Python, so that the CPU test suite can
+// run the planner's programs in an emulator of the team kernel and check the
+// tables against the oracle. Test infrastructure: nothing in the library or the
 // benchmark links this file.
 #include <cstdint>
 #include <cstring>
@@ -76,6 +77,24 @@ int64_t shim_array(int which, void* dst, int64_t cap) {
 int64_t shim_rprog(int which, void* dst, int64_t cap) {
   if (g_rprog.empty()) mdx::build_rlevel_programs(g_rprog, g_roff);
   return which == 0 ? copy_out(g_rprog, dst, cap) : copy_out(g_roff, dst, cap);
+}
+
+// The device's Boys interpolation table ([grid point][m][k], F_{m+k}(T0)/k!)
+// and its shape: dims = {grid points, orders, terms}, inv_h = 1/h.
+int64_t shim_boys(double* dst, int64_t cap, int32_t* dims, double* inv_h) {
+  const std::vector<double> t = mdx::build_boys_table();
+  dims[0] = mdx::kBoysNgrid;
+  dims[1] = mdx::kBoysOrders;
+  dims[2] = mdx::kBoysTerms;
+  *inv_h = mdx::kBoysInvH;
+  return copy_out(t, dst, cap * (int64_t)sizeof(double)) / (int64_t)sizeof(double);
+}
+
+// The library's real-solid-harmonic table of one l: [2l+1][ncart(l)].
+int64_t shim_solid(int l, double* dst, int64_t cap) {
+  const std::vector<std::vector<double>> t = mdx::build_solid_tables(mdx::kLmax);
+  if (l < 0 || l > mdx::kLmax) return -1;
+  return copy_out(t[(size_t)l], dst, cap * (int64_t)sizeof(double)) / (int64_t)sizeof(double);
 }
 
 int shim_sizes(int32_t* out) {

@@ -56,11 +56,12 @@ _lib = None
 
 def _build_shim() -> str:
     os.makedirs(BUILD, exist_ok=True)
-    deps = [SHIM_SRC, os.path.join(CSRC, "plan.cpp"), os.path.join(CSRC, "mdx_internal.h")]
+    srcs = [os.path.join(CSRC, f) for f in ("plan.cpp", "boys_table.cpp", "solid.cpp")]
+    deps = [SHIM_SRC, os.path.join(CSRC, "mdx_internal.h")] + srcs
     if not os.path.exists(SHIM_LIB) or any(os.path.getmtime(d) > os.path.getmtime(SHIM_LIB) for d in deps):
         tmp = SHIM_LIB + ".tmp%d" % os.getpid()
-        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, SHIM_SRC,
-                        os.path.join(CSRC, "plan.cpp"), "-o", tmp], check=True)
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, SHIM_SRC, *srcs, "-o", tmp],
+                       check=True)
         os.replace(tmp, SHIM_LIB)
     return SHIM_LIB
 
@@ -79,6 +80,10 @@ def _load():
             lib.shim_rprog.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
             lib.shim_rprog.restype = ctypes.c_int64
             lib.shim_sizes.argtypes = [ctypes.c_void_p]
+            lib.shim_boys.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            lib.shim_boys.restype = ctypes.c_int64
+            lib.shim_solid.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
+            lib.shim_solid.restype = ctypes.c_int64
             sizes = np.zeros(4, dtype=np.int32)
             lib.shim_sizes(sizes.ctypes.data)
             assert (sizes[0], sizes[1], sizes[2], sizes[3]) == (STEP.itemsize, B23.itemsize, GROUP.itemsize,
@@ -125,6 +130,39 @@ def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, sin
                 _array(lib, lib.shim_array, 2, STEP), _array(lib, lib.shim_array, 3, B23),
                 _array(lib, lib.shim_array, 4, np.uint16), _array(lib, lib.shim_rprog, 0, np.uint32),
                 _array(lib, lib.shim_rprog, 1, np.int32))
+
+
+def boys_table():
+    """The library's Boys table as [grid][m][k] and the grid's 1/h."""
+    lib = _load()
+    dims = np.zeros(3, dtype=np.int32)
+    inv_h = ctypes.c_double(0.0)
+    n = lib.shim_boys(None, 0, dims.ctypes.data, ctypes.byref(inv_h))
+    tab = np.zeros(n)
+    lib.shim_boys(tab.ctypes.data, n, dims.ctypes.data, ctypes.byref(inv_h))
+    return tab.reshape(int(dims[0]), int(dims[1]), int(dims[2])), inv_h.value
+
+
+def boys_interpolate(tab, inv_h, m, T):
+    """F_m(T) as the kernel forms it inside the table: nearest grid point
+    T0 = i h (round to nearest), then Horner's rule in -d = T0 - T over the
+    row's coefficients F_{m+k}(T0)/k!."""
+    i = int(math.floor(T * inv_h + 0.5))
+    nd = i / inv_h - T
+    c = tab[i, m]
+    f = c[-1]
+    for k in range(len(c) - 2, -1, -1):
+        f = f * nd + c[k]
+    return f
+
+
+def solid_table(l):
+    """The library's real solid harmonics of one l: [2l+1][ncart(l)]."""
+    lib = _load()
+    nc = (l + 1) * (l + 2) // 2
+    out = np.zeros((2 * l + 1) * nc)
+    assert lib.shim_solid(l, out.ctypes.data, len(out)) == len(out)
+    return out.reshape(2 * l + 1, nc)
 
 
 # ----------------------------------------------------------------- records

@@ -174,3 +174,30 @@ def test_emulator_detects_a_corrupted_program():
     with pytest.raises(AssertionError):
         parity.check(_emulate_4c(pl_bad, b, q), ref, what="corrupted b23")
     parity.check(_emulate_4c(pl, b, q), ref, what="intact")
+
+
+def test_boys_table_interpolation():
+    """The library's Boys table, evaluated the way the kernel does (nearest grid
+    point, 8-term Taylor series by Horner's rule), against the oracle's
+    long-double F_m for every order the engine uses (m <= 25) across the
+    tabulated range T < 100."""
+    tab, inv_h = te.boys_table()
+    assert tab.shape[1] >= 26
+    rng = np.random.default_rng(5)
+    Ts = np.concatenate([[0.0, 1e-12, 0.03125, 1.0 / 32 - 1e-13, 99.96875, 99.99999],
+                         rng.uniform(0.0, 100.0, 300), rng.uniform(0.0, 2.0, 100)])
+    worst = 0.0
+    for T in Ts:
+        ref = oracle.boys(25, float(T), precision=1)
+        for m in range(26):
+            got = te.boys_interpolate(tab, inv_h, m, float(T))
+            worst = max(worst, abs(got - ref[m]) / ref[m])
+    # Taylor truncation <= (1/32)^8/8! relative; the rest is FP64 rounding of the Horner steps
+    assert worst <= 4e-16, worst
+
+
+@pytest.mark.parametrize("l", range(7))
+def test_solid_harmonic_tables(l):
+    """The library's solid-harmonic coefficients (built by recurrences in l)
+    equal the oracle's explicit closed form."""
+    np.testing.assert_allclose(te.solid_table(l), oracle.solid_coefs(l), rtol=0, atol=1e-13)
