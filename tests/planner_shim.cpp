@@ -60,6 +60,10 @@ int shim_scalars(int32_t* out, int cap) {
   return n;
 }
 
+// FP64 FMAs per shellset the planner reports for the last plan (the count
+// behind the executed-FLOP rates).
+double shim_exec_fma() { return g_plan.exec_fma; }
+
 // Raw program arrays of the last plan: 0 groups, 1 ket steps, 2 b1, 3 b23,
 // 4 column map. Returns the byte size; copies when cap suffices.
 int64_t shim_array(int which, void* dst, int64_t cap) {

@@ -84,6 +84,8 @@ def _load():
             lib.shim_boys.restype = ctypes.c_int64
             lib.shim_solid.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
             lib.shim_solid.restype = ctypes.c_int64
+            lib.shim_exec_fma.argtypes = []
+            lib.shim_exec_fma.restype = ctypes.c_double
             sizes = np.zeros(4, dtype=np.int32)
             lib.shim_sizes(sizes.ctypes.data)
             assert (sizes[0], sizes[1], sizes[2], sizes[3]) == (STEP.itemsize, B23.itemsize, GROUP.itemsize,
@@ -110,6 +112,7 @@ class Plan:
     colmap: np.ndarray
     rprog: np.ndarray
     roff: np.ndarray
+    exec_fma: float = 0.0   # FP64 FMAs per shellset as the planner reports them
 
 
 class PlanError(RuntimeError):
@@ -129,7 +132,7 @@ def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, sin
     return Plan(s, _array(lib, lib.shim_array, 0, GROUP), _array(lib, lib.shim_array, 1, STEP),
                 _array(lib, lib.shim_array, 2, STEP), _array(lib, lib.shim_array, 3, B23),
                 _array(lib, lib.shim_array, 4, np.uint16), _array(lib, lib.shim_rprog, 0, np.uint32),
-                _array(lib, lib.shim_rprog, 1, np.int32))
+                _array(lib, lib.shim_rprog, 1, np.int32), float(lib.shim_exec_fma()))
 
 
 def boys_table():
@@ -248,9 +251,10 @@ def check_hazards(pl: Plan):
 
 
 # ----------------------------------------------------------------- execution
-def _run_step(ws, ent, acc):
+def _run_step(ws, ent, acc, count):
     if len(ent) == 0:
         return
+    count["fma"] += int(ent["n"].astype(np.int64).sum())
     out = ent["out"].astype(np.int64)
     coef = ent["coef"].astype(np.int64)
     src = ent["src"].astype(np.int64)
@@ -299,9 +303,12 @@ def simplex_offset(N, t, u):
     return tet(N + 1) - tet(N - t + 1) + tri(N - t + 1) - tri(N - t - u + 1)
 
 
-def _compute_R(pl: Plan, ws):
+def _compute_R(pl: Plan, ws, count):
     s = pl.s
     L = s["L"]
+    # the kernel's count: 8 per Boys order (Horner and the power of -2 rho),
+    # one per R entry below the top of each level
+    count["fma"] += 8 * (L + 1) + sum((L - nn + 1) * (L - nn + 2) * (L - nn + 3) // 6 - 1 for nn in range(L))
     rb = ws[s["o_recb"]:s["o_recb"] + REC_HEADER]
     rk = ws[s["o_reck"]:s["o_reck"] + REC_HEADER]
     PQ = rb[2:5] - rk[2:5]
@@ -325,9 +332,13 @@ def _compute_R(pl: Plan, ws):
         ws[dst:dst + len(val)] = val
 
 
-def emulate(pl: Plan, bra_recs, ket_recs_signed) -> np.ndarray:
+def emulate(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
     """Run one quartet through the plan's programs (store epilogue); returns
-    the shellset [Nb][Nk] (row-major, bra Cartesian pair major)."""
+    the shellset [Nb][Nk] (row-major, bra Cartesian pair major). `count`, a
+    dict, receives the FP64 FMAs the programs execute ("fma")."""
+    if count is None:
+        count = {}
+    count.setdefault("fma", 0)
     s = pl.s
     Nb, Nk, hb, c1size = s["Nb"], s["Nk"], s["hb"], s["c1size"]
     assert len(bra_recs) == s["Kb"] and len(ket_recs_signed) == s["Kk"]
@@ -344,7 +355,7 @@ def emulate(pl: Plan, bra_recs, ket_recs_signed) -> np.ndarray:
     if s["cache_R"]:
         load_bra(bra_recs[0])
         load_ket(ket_recs_signed[0])
-        _compute_R(pl, ws)
+        _compute_R(pl, ws, count)
     b1 = pl.b1
     b23 = pl.b23
     for g in pl.groups:
@@ -357,12 +368,14 @@ def emulate(pl: Plan, bra_recs, ket_recs_signed) -> np.ndarray:
             for pk in range(s["Kk"]):
                 if not s["cache_R"]:
                     load_ket(ket_recs_signed[pk])
-                    _compute_R(pl, ws)
+                    _compute_R(pl, ws, count)
                 if g["k1_n"] > 0:
-                    _run_step(ws, pl.kprog[g["k1_off"]:g["k1_off"] + g["k1_n"]], False)
-                _run_step(ws, pl.kprog[g["k2_off"]:g["k2_off"] + g["k2_n"]], False)
-                _run_step(ws, pl.kprog[g["k3_off"]:g["k3_off"] + g["k3_n"]], pk > 0)
+                    _run_step(ws, pl.kprog[g["k1_off"]:g["k1_off"] + g["k1_n"]], False, count)
+                _run_step(ws, pl.kprog[g["k2_off"]:g["k2_off"] + g["k2_n"]], False, count)
+                _run_step(ws, pl.kprog[g["k3_off"]:g["k3_off"] + g["k3_n"]], pk > 0, count)
             # b1: C1[col][out] = sum_k E[coef + k st] X[col][src + k st]
+            count["fma"] += int(b1["n"].astype(np.int64).sum()) * ncols
+            count["fma"] += int((b23["nv"].astype(np.int64) * (b23["nu"].astype(np.int64) + 1)).sum()) * ncols
             for e in b1:
                 k = np.arange(int(e["n"])) * int(e["stride"])
                 c = ws[int(e["coef"]) + k]

@@ -201,3 +201,22 @@ def test_solid_harmonic_tables(l):
     """The library's solid-harmonic coefficients (built by recurrences in l)
     equal the oracle's explicit closed form."""
     np.testing.assert_allclose(te.solid_table(l), oracle.solid_coefs(l), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("lq,K,shape", [((1, 1, 1, 1), (1, 1, 1, 1), {}), ((2, 2, 2, 2), (1, 1, 1, 1), {}),
+                                        ((3, 3, 3, 3), (1, 1, 1, 1), {}), ((4, 4, 4, 4), (1, 1, 1, 1), {}),
+                                        ((2, 1, 2, 1), (2, 3, 1, 2), {}),
+                                        ((2, 2, 2, 1), (2, 1, 2, 1), {"single_max": 4000, "budget": 8 * 1024}),
+                                        ((3, 2, 2, 2), (1, 1, 1, 1), {"single_max": 4000, "budget": 12 * 1024})])
+def test_planner_fma_count_matches_programs(lq, K, shape):
+    """The FP64 FMA count per shellset the planner reports (the numerator of
+    the benchmark's executed-FLOP rates) equals the FMAs its programs execute
+    when run: Boys and R per primitive quartet (per group when R is not
+    cached), the ket steps per primitive quartet and the bra steps per bra
+    primitive pair and column."""
+    b, q = _basis_4c(lq, K, 71, n=1)
+    pl = te.plan(*lq, K[0] * K[1], K[2] * K[3], **shape)
+    count = {}
+    a, bb, c, d = q[0]
+    te.emulate(pl, te.shell_pair_records(b, a, bb, False), te.shell_pair_records(b, c, d, True), count)
+    assert count["fma"] == pl.exec_fma, (count["fma"], pl.exec_fma)
