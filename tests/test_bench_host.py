@@ -1,0 +1,33 @@
+"""Host logic of the benchmark (no GPU): how a class's quartets are split into
+launches, and the work model behind its rates."""
+import pytest
+
+import bench
+from paper_2405_01834_gb300 import flops, inputs
+
+
+@pytest.mark.parametrize("l", range(1, 7))
+@pytest.mark.parametrize("sms", [152, 148])
+def test_chunks_cover_the_class_in_whole_waves(l, sms):
+    """Chunks of one class cover all 50,176 quartets; each chunk's output fits
+    the buffer (up to the stated 12.5 % allowance); a class that needs several
+    chunks of at least two waves gets whole waves of the SM count."""
+    n = 224 * 224
+    cq = bench.chunk_quartets(l, n, sms)
+    per_q = inputs.ncart(l) ** 4 * 8
+    assert 1 <= cq <= n
+    assert cq * per_q <= bench.CHUNK_BYTES * 1.125 or cq == 1
+    starts = list(range(0, n, cq))
+    assert sum(min(cq, n - s) for s in starts) == n
+    if n > cq and cq >= 2 * sms:
+        assert cq % sms == 0
+
+
+def test_model_flops_is_the_table1_model():
+    for l in range(1, 7):
+        assert bench.model_flops(l, 3) == 3 * flops.eri4_flops(l, l, l, l)
+
+
+def test_whole_job_rate_is_weak_scaling():
+    assert bench.whole_job_rate(100.0, 1, 1000.0) == pytest.approx(100.0)
+    assert bench.whole_job_rate(100.0, 4, 2000.0) == pytest.approx(200.0)
