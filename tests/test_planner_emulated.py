@@ -88,9 +88,11 @@ def test_uncontracted_high_l(lq):
 @pytest.mark.parametrize("lq,K", [((0, 0, 0, 0), (6, 6, 6, 6)), ((1, 0, 1, 0), (3, 6, 3, 6)),
                                   ((1, 1, 1, 1), (3, 2, 2, 1)), ((2, 1, 0, 0), (1, 3, 6, 6)),
                                   ((2, 2, 2, 2), (2, 2, 1, 2)), ((3, 1, 2, 0), (1, 3, 2, 6)),
-                                  ((3, 3, 2, 2), (2, 1, 1, 2))])
+                                  ((3, 3, 2, 2), (2, 1, 1, 2)), ((0, 0, 0, 0), (32, 32, 1, 2)),
+                                  ((1, 1, 0, 0), (32, 4, 2, 2))])
 def test_contracted(lq, K):
-    """Contracted shells: primitive loops over bra and ket pairs, R per primitive quartet."""
+    """Contracted shells: primitive loops over bra and ket pairs, R per primitive
+    quartet; up to the largest contraction degree the engine accepts (32)."""
     pl = _check_4c(lq, K=K, seed=21)
     assert pl.s["cache_R"] == 0
 
