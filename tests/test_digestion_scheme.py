@@ -90,3 +90,74 @@ def test_unique_quartet_energy_sum():
     assert abs(S - ref) <= 1e-13 * abs(ref)
     K = np.einsum("ijkl,jl->ik", full, D)
     assert abs(float(np.sum(D * K)) - ref) <= 1e-13 * abs(ref)
+
+
+def _cart(l):
+    return [(ax, ay, l - ax - ay) for ax in range(l, -1, -1) for ay in range(l - ax, -1, -1)]
+
+
+def test_shifted_class_gradient_scheme():
+    """The GPU's gradient scheme: per unique quartet and each of its first three
+    shells, the class with that shell raised (l+1, coefficients 2 zeta c) and
+    lowered (l-1), contracted with G = D_ik D_jl + D_il D_jk at the unshifted
+    component (raised element a' feeds a' - 1_x with weight +1, lowered element
+    a' feeds a' + 1_x with weight -(a'_x + 1)); the fourth shell's atom takes
+    minus the sum (translational invariance). Against the oracle's gradient,
+    which differentiates all four centres explicitly."""
+    b = inputs.small_molecule(seed=23, n_atoms=3, shells=(0, 1, 2), K=2)
+    D = inputs.density(b.nao, 8, occ_fraction=0.4)
+    ref = oracle.exchange_grad(b, D)
+    ns = b.n_shells
+    # extended basis: shell s, its raised partner ns + s, its lowered partner 2 ns + s (an s shell
+    # gets a placeholder s shell there, never used)
+    bb = inputs.BasisBuilder()
+    for v in range(3):
+        for s in range(ns):
+            p0, n = int(b.prim_off[s]), int(b.nprim[s])
+            z, c = b.exps[p0:p0 + n], b.coefs[p0:p0 + n]
+            l = int(b.l[s])
+            if v == 0:
+                bb.add_shell(l, b.center[s], z, c)
+            elif v == 1:
+                bb.add_shell(l + 1, b.center[s], z, 2.0 * z * c)
+            else:
+                bb.add_shell(max(l - 1, 0), b.center[s], z, c)
+    ext = bb.build()
+    sl = _blocks(b)
+    g = np.zeros((b.n_atoms, 3))
+    jobs = []
+    for (i, j), (k, l), same in _unique(ns):
+        w = (0.5 if i == j else 1.0) * (0.5 if k == l else 1.0) * (0.5 if same else 1.0)
+        for pos in range(3):
+            for sign in (1, -1):
+                sh = (i, j, k)[pos]
+                if sign < 0 and b.l[sh] == 0:
+                    continue
+                q = [i, j, k, l]
+                q[pos] = sh + (ns if sign > 0 else 2 * ns)
+                jobs.append((q, (i, j, k, l), w, pos, sign))
+    vals, off = oracle.eri4(ext, np.array([j[0] for j in jobs], dtype=np.int32))
+    for n, (q, (i, j, k, l), w, pos, sign) in enumerate(jobs):
+        ls = [int(ext.l[x]) for x in q]
+        V = vals[off[n]:off[n + 1]].reshape([inputs.ncart(x) for x in ls])
+        G = np.einsum("ac,bd->abcd", D[sl[i], sl[k]], D[sl[j], sl[l]]) + \
+            np.einsum("ad,bc->abcd", D[sl[i], sl[l]], D[sl[j], sl[k]])
+        lorg = int(b.l[(i, j, k)[pos]])
+        orig_index = {c: idx for idx, c in enumerate(_cart(lorg))}
+        for sidx, comp in enumerate(_cart(ls[pos])):
+            Vs = np.take(V, sidx, axis=pos)
+            for x in range(3):
+                o = list(comp)
+                if sign > 0:
+                    if o[x] == 0:
+                        continue
+                    o[x] -= 1
+                    wt = 1.0
+                else:
+                    o[x] += 1
+                    wt = -float(o[x])
+                Gs = np.take(G, orig_index[tuple(o)], axis=pos)
+                t = 4.0 * w * wt * float(np.sum(Vs * Gs))
+                g[b.atom[(i, j, k)[pos]], x] += t
+                g[b.atom[l], x] -= t
+    np.testing.assert_allclose(g, ref, rtol=0, atol=1e-11 * np.max(np.abs(ref)))
