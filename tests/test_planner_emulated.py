@@ -133,14 +133,15 @@ def _basis_3c(la, lc, ld, Ka, Kc, Kd, seed):
     return aux.build(), orb.build(), trip
 
 
+@pytest.mark.parametrize("store", [False, True])
 @pytest.mark.parametrize("la,lc,ld,K", [(0, 0, 0, (1, 1, 1)), (1, 1, 0, (1, 3, 1)), (2, 1, 1, (1, 1, 1)),
                                         (3, 2, 1, (1, 1, 1)), (4, 0, 0, (1, 6, 6)), (5, 1, 0, (1, 3, 6)),
                                         (6, 2, 2, (1, 1, 1)), (6, 3, 3, (1, 1, 1)), (2, 2, 0, (2, 1, 1))])
-def test_three_center(la, lc, ld, K):
+def test_three_center(la, lc, ld, K, store):
     """[a|cd] with a one-centre bra (Eq. E1rr; the bra steps skip the zero
-    parity terms with stride-2 entries)."""
+    parity terms with stride-2 entries), with and without the OUT region."""
     aux, orb, trip = _basis_3c(la, lc, ld, *K, seed=51 + la)
-    pl = te.plan(la, 0, lc, ld, K[0], K[1] * K[2], onec=True)
+    pl = te.plan(la, 0, lc, ld, K[0], K[1] * K[2], onec=True, store=store)
     te.check_hazards(pl)
     got = []
     for a, c, d in trip:
