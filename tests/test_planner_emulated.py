@@ -223,3 +223,29 @@ def test_planner_fma_count_matches_programs(lq, K, shape):
     a, bb, c, d = q[0]
     te.emulate(pl, te.shell_pair_records(b, a, bb, False), te.shell_pair_records(b, c, d, True), count)
     assert count["fma"] == pl.exec_fma, (count["fma"], pl.exec_fma)
+
+
+def test_random_shapes():
+    """Seeded random classes (l <= 3), contraction degrees, shared-memory budgets,
+    single-group caps and store flags: the shapes the autotuner may ask for.
+    Every plan the planner accepts computes the oracle's shellset."""
+    rng = np.random.default_rng(2024)
+    done = 0
+    while done < 60:
+        lq = tuple(int(x) for x in rng.integers(0, 4, 4))
+        K = tuple(int(rng.choice([1, 1, 1, 2, 3])) for _ in range(4))
+        budget = int(rng.choice([0, 8, 12, 16, 24, 32, 64, 128, 200])) * 1024
+        single_max = int(rng.choice([0, 2000, 4000, 16000, 48000]))
+        store = bool(rng.integers(0, 2))
+        try:
+            pl = te.plan(*lq, K[0] * K[1], K[2] * K[3], store=store, budget=budget, single_max=single_max)
+        except te.PlanError:
+            continue   # a budget too small for the class: the planner refuses, which is its contract
+        te.check_hazards(pl)
+        b, q = _basis_4c(lq, K, int(rng.integers(0, 10 ** 6)), n=1)
+        got = _emulate_4c(pl, b, q)
+        ref, off = oracle.eri4(b, q)
+        ld, _ = oracle.eri4(b, q, precision=1)
+        parity.check(got, ref, ld, what="random shape %s K=%s b=%d s=%d store=%d" % (lq, K, budget, single_max, store),
+                     offsets=off)
+        done += 1
