@@ -191,7 +191,10 @@ mdx_status mdx_batch_run_materialized(mdx_ctx* ctx, mdx_batch* batch, double* ou
 void mdx_batch_destroy(mdx_batch* batch);
 
 /* Schwarz factors Q_ij = sqrt(max_ab |(ab|ab)|) over the Cartesian
- * components a of shell i and b of shell j, for n shell pairs.
+ * components a of shell i and b of shell j, for n shell pairs. The paper
+ * screens shell pairs before batching (Sec. 3, memory order of the batches)
+ * without defining the bound; this is the standard Cauchy-Schwarz factor,
+ * |(ab|cd)| <= Q_ab Q_cd, used by mdx_exchange's screening.
  * pairs: [n][2] int32 shell indices. Q_out: [n] doubles (device), written.
  * Synchronises `stream` once (class grouping). */
 mdx_status mdx_schwarz(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, int64_t n,
