@@ -178,7 +178,7 @@ mdx_status mdx_batch_autotune(mdx_ctx* ctx, mdx_batch* batch, double* out, int64
                               int64_t max_trial, void* stream);
 
 /* The same batch through the materialized-Hermite variant of the paper
- * (Sec. 4): per quartet the full matrix [p|q] = (-1)^{|q|} [p+q] is written
+ * (V2, Sec. 3): per quartet the full matrix [p|q] = (-1)^{|q|} [p+q] is written
  * to device memory and both transforms run as batched dense DGEMMs
  * ([p|cd] = [p|q] E^cd, [ab|cd] = E^ab [p|cd]; cuBLAS, i.e. the FP64 tensor
  * units). An A/B experiment against mdx_batch_run: same results, same output
@@ -339,12 +339,14 @@ typedef struct {
   int32_t pad;
 } mdx_plan_stats;
 
-/* register_kernel: small classes (total angular momentum <= 4, whose Hermite
- * table R, [p|cd] block and shellset hold at most 100 doubles together) also
- * have a kernel with one
- * thread per quartet and every intermediate in registers (the paper's
- * smallest variant, Sec. 4); it is the default for them, and the autotuner
- * times it against the team shapes. Gradient launches always use teams. */
+/* register_kernel: small classes have a kernel with one thread per quartet
+ * (the paper's smallest variant V0, Sec. 3): total angular momentum <= 4 with
+ * the Hermite table R, the [p|cd] block and the shellset in at most 100
+ * registers' worth of doubles, and further classes of total angular momentum
+ * <= 6 with R in registers and [p|cd] plus the shellset in shared memory. It
+ * is the default for them, and the autotuner times it against the team
+ * shapes. In gradient launches it evaluates the shifted shellsets into
+ * workspace, and a separate kernel contracts them with D (x) D. */
 mdx_status mdx_plan_info(mdx_ctx* ctx, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
                          mdx_plan_stats* out);
 

@@ -1,4 +1,4 @@
-// Materialized-Hermite path (the paper's third GPU variant, Sec. 4: the
+// Materialized-Hermite path (the paper's third GPU variant V2, Sec. 3: the
 // Hermite integral matrix [p|q] is written to memory and both transforms are
 // dense matrix products), kept as an A/B experiment against the
 // axis-factored team and register kernels.

@@ -1,6 +1,6 @@
 // Register-resident quartet kernel for small classes: one thread per shell
 // quartet, every intermediate of Sec. 2 in registers (the paper's smallest
-// GPU variant, Sec. 4, where a thread owns a whole shellset).
+// GPU variant V0, Sec. 3, where a thread owns a whole shellset).
 //
 // Per thread, for every bra primitive pair and every ket primitive pair:
 // Boys seeds [0]^(m) = (-2 rho)^m pref F_m(T) (Eq. 0m), the Hermite integrals

@@ -1,5 +1,5 @@
 """The materialized-Hermite variant (dense [p|q] matrices and batched DGEMMs, the
-paper's Sec. 4 third variant) against the oracle and the default kernels."""
+paper's Sec. 3 third variant) against the oracle and the default kernels."""
 import numpy as np
 import pytest
 import torch
