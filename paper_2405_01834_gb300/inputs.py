@@ -144,7 +144,7 @@ def unique_quartets(n_shells: int) -> np.ndarray:
     return np.array(out, dtype=np.int32).reshape(-1, 4)
 
 
-# ---------------------------------------------------------------- config 1
+# ---------------------------------------------------------------- small molecules
 def small_molecule(seed: int = 1001, n_atoms: int = 6, box: float = 6.0, K: int = 3,
                    shells=(0, 1, 2), zlo: float = 0.1, zhi: float = 10.0) -> Basis:
     """Atoms uniform in a box, each with s,p,d Cartesian shells of contraction K.
@@ -162,7 +162,7 @@ def small_molecule(seed: int = 1001, n_atoms: int = 6, box: float = 6.0, K: int 
     return bb.build()
 
 
-# ---------------------------------------------------------------- config 2
+# ---------------------------------------------------------------- per-class quartet grids
 def class_sweep(lq, n_bra: int = 224, n_ket: int = 224, seed: int = 1002, box: float = 10.0,
                 zlo: float = 0.05, zhi: float = 50.0, K=(1, 1, 1, 1)):
     """Random quartets of one class (la,lb|lc,ld): an n_bra x n_ket grid of
@@ -194,7 +194,7 @@ def class_sweep(lq, n_bra: int = 224, n_ket: int = 224, seed: int = 1002, box: f
 SWEEP_CLASSES = [(1, 1, 1, 1), (2, 2, 2, 2), (3, 3, 3, 3), (4, 4, 4, 4), (5, 5, 5, 5), (6, 6, 6, 6)]
 
 
-# ---------------------------------------------------------------- clusters (configs 3-5)
+# ---------------------------------------------------------------- clusters
 def cluster(rng, n_atoms: int, min_sep: float = 2.8, density_radius: float = 2.2) -> np.ndarray:
     """Seeded sequential random insertion of atoms in a sphere at >= min_sep bohr."""
     R = density_radius * n_atoms ** (1.0 / 3.0) + min_sep
@@ -237,7 +237,7 @@ def _add_element_shells(rng, bb: BasisBuilder, atom: int, xyz, recipe, zmin: flo
 
 
 def df_cluster(seed: int = 1003, n_atoms: int = 100):
-    """Config-3 shape: orbital basis 4s3p2d1f (K 6/3/1/1) and auxiliary basis
+    """Density-fitting cluster: orbital basis 4s3p2d1f (K 6/3/1/1) and auxiliary basis
     s..i (K=1, even-tempered ratio 2.5) on a random cluster. Returns (aux, orb)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     xyz = cluster(rng, n_atoms)
@@ -251,7 +251,7 @@ def df_cluster(seed: int = 1003, n_atoms: int = 100):
 
 def molecule(seed: int, n_atoms: int, heavy_fraction: float = 0.5) -> Basis:
     """Compact cluster molecule, heavy atoms 5s4p3d2f1g and H-like 4s3p2d1f,
-    shells renormalised (configs 4-5 shape)."""
+    shells renormalised (the molecules of the batched-exchange and gradient workloads)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     xyz = cluster(rng, n_atoms)
     heavy = rng.uniform(0, 1, n_atoms) < heavy_fraction
@@ -264,7 +264,7 @@ def molecule(seed: int, n_atoms: int, heavy_fraction: float = 0.5) -> Basis:
 
 
 def molecule_batch(seed: int = 1004, n_mol: int = 64, lo: int = 10, hi: int = 120):
-    """Config-4 shape: n_mol molecules with seeded atom counts uniform in [lo, hi]."""
+    """Batch of uneven molecules: n_mol molecules with seeded atom counts uniform in [lo, hi]."""
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = rng.integers(lo, hi + 1, n_mol)
     return [molecule(seed * 1000 + i, int(s)) for i, s in enumerate(sizes)]

@@ -1,4 +1,4 @@
-"""Config-3 shape at full size: 100-atom cluster, orbital 4s3p2d1f (K 6/3/1/1), auxiliary s..i.
+"""Density-fitting cluster at full size: 100 atoms, orbital 4s3p2d1f (K 6/3/1/1), auxiliary s..i.
 Schwarz factors of all 500,500 orbital shell pairs on the GPU (checked on a sample against the
 oracle), pairs screened at Q >= 1e-12, then a seeded sample of [a|cd] triplets over the kept
 pairs and every auxiliary class compared with the oracle."""

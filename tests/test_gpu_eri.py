@@ -29,20 +29,20 @@ def _gpu4(eng, basis, q):
 
 
 def test_small_molecule_all_unique_quartets(eng):
-    """Config-1 shape: 6 atoms with s,p,d shells, K = 3, every unique quartet."""
+    """Small molecule: 6 atoms with s,p,d shells, K = 3, every unique quartet."""
     b = inputs.small_molecule()
     q = inputs.unique_quartets(b.n_shells)
     assert len(q) == 14706
     v, off = _gpu4(eng, b, q)
     ref, roff = oracle.eri4(b, q)
     assert np.array_equal(off, roff)
-    r = parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "config-1", off)
+    r = parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "small molecule", off)
     print(r)
 
 
 @pytest.mark.parametrize("l", [0, 1, 2, 3, 4, 5, 6])
 def test_class_sweep_grid(eng, l):
-    """Config-2 shape at a size the oracle finishes in seconds: a 5 x 3 grid of
+    """Per-class random quartet grid at a size the oracle finishes in seconds: a 5 x 3 grid of
     random bra/ket pairs of class [ll|ll], K = 1, exponents in [0.05, 50]."""
     nb, nk = (5, 3) if l < 6 else (3, 2)
     b, q = inputs.class_sweep((l, l, l, l), n_bra=nb, n_ket=nk, seed=77)

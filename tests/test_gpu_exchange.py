@@ -35,7 +35,7 @@ def _run(eng, b, D, tau, seed_shuffle=None):
 
 
 def test_exchange_small_molecule_no_screening(eng):
-    """Config-1 shape on 3 atoms (s,p,d, K=3), random symmetric D, every unique quartet."""
+    """Small molecule of 3 atoms (s,p,d, K=3), random symmetric D, every unique quartet."""
     b = inputs.small_molecule(n_atoms=3)
     D = inputs.random_symmetric(b.nao, 5)
     K, nq, npair = _run(eng, b, D, 0.0, seed_shuffle=1)
@@ -46,7 +46,7 @@ def test_exchange_small_molecule_no_screening(eng):
 
 
 def test_exchange_high_l_molecule(eng):
-    """Heavy/light clusters with f and g shells and K = 6 s shells (config 4-5 shape), D = C C^T."""
+    """Heavy/light clusters with f and g shells and K = 6 s shells (the batched-exchange molecules), D = C C^T."""
     b = inputs.molecule(seed=21, n_atoms=3)
     D = inputs.density(b.nao, 4)
     K, nq, npair = _run(eng, b, D, 0.0)

@@ -54,7 +54,7 @@ def _energy(eng, b, D):
 
 def test_gradient_against_finite_differences(eng):
     """Central differences (h = 1e-4 bohr) of the GPU forward energy, every atom and axis of a
-    contracted heavy/light molecule (configs 4-5 shape)."""
+    contracted heavy/light molecule (the batched-exchange and gradient molecules)."""
     b = inputs.molecule(seed=61, n_atoms=3)
     D = inputs.density(b.nao, 11)
     g, E = _grad(eng, b, D)
@@ -89,7 +89,7 @@ def test_autograd_function(eng):
 
 
 def test_gradient_ten_atom_cluster_fd_eight_atoms(eng):
-    """Config-5 shape at reduced size: a 10-atom heavy/light cluster (quadruple-zeta-like shells,
+    """The 400-atom gradient workload at reduced size: a 10-atom heavy/light cluster (quadruple-zeta-like shells,
     Schwarz x density screening at 1e-11); dE_x/dR against central differences of the GPU forward
     energy on 8 seeded atoms (one seeded axis each), and translational invariance."""
     b = inputs.molecule(seed=1005, n_atoms=10)
