@@ -461,3 +461,31 @@ def test_h2_sto3g_textbook_integrals():
         i, j, k, l = (idx[ch] for ch in key if ch in "12")
         v, _ = oracle.eri4(b, np.array([[i, j, k, l]], dtype=np.int32))
         assert abs(v[0] - float(vals[0])) <= 0.5e-4, (key, v[0], vals[0])
+
+
+def test_eri3_is_eri4_with_a_constant_function():
+    """A Gaussian of exponent 0 is the constant 1, so [a|cd] (Eq. def-acd, one-centre
+    E of Eq. E1rr) equals [a b|cd] with b an s function of exponent 0 and coefficient
+    1 placed anywhere (two-centre E of Eqs. E2rr1/E2rr2)."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    aux, orb = inputs.BasisBuilder(), inputs.BasisBuilder()
+    for la in range(5):
+        inputs.random_shell(rng, aux, la, rng.uniform(0, 2, 3), 2, 0.3, 3.0)
+    for l in (0, 1, 2):
+        inputs.random_shell(rng, orb, l, rng.uniform(0, 2, 3), 2, 0.3, 3.0)
+    A, O = aux.build(), orb.build()
+    t = np.array([[a, c, d] for a in range(A.n_shells) for c in range(O.n_shells) for d in range(O.n_shells)],
+                 dtype=np.int32)
+    v3, _ = oracle.eri3(A, O, t)
+    bb = inputs.BasisBuilder()
+    for B_, shells in ((A, range(A.n_shells)), (None, [None]), (O, range(O.n_shells))):
+        for s in shells:
+            if B_ is None:
+                bb.add_shell(0, [0.3, -0.2, 0.1], np.array([0.0]), np.array([1.0]))
+                continue
+            p0, n = int(B_.prim_off[s]), int(B_.nprim[s])
+            bb.add_shell(int(B_.l[s]), B_.center[s], B_.exps[p0:p0 + n], B_.coefs[p0:p0 + n])
+    unit = A.n_shells
+    q = np.array([[a, unit, unit + 1 + c, unit + 1 + d] for a, c, d in t], dtype=np.int32)
+    v4, _ = oracle.eri4(bb.build(), q)
+    np.testing.assert_allclose(v3, v4, rtol=0, atol=1e-13 * np.max(np.abs(v3)))
