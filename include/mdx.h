@@ -28,6 +28,10 @@
  *    shell index, bounded wait expired) are recorded in a device error word of
  *    the context and returned by the next mdx_sync() or by the next call.
  *    mdx_last_error() gives a one-line description of the last failure.
+ *  - A context is not thread-safe: calls on one context must not run
+ *    concurrently from several host threads (use one context per thread).
+ *    mdx_eri4_noalloc, which takes no context, serialises its host work on
+ *    an internal lock.
  */
 #ifndef MDX_H
 #define MDX_H
