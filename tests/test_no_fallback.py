@@ -1,0 +1,28 @@
+"""The product path has no CPU fallback: without a CUDA device the engine
+refuses to start, and nothing in the package or its C sources reaches the
+oracle (test infrastructure only)."""
+import glob
+import os
+import re
+
+import pytest
+import torch
+
+from paper_2405_01834_gb300 import mdx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the behaviour without a CUDA device")
+def test_engine_refuses_without_a_gpu():
+    with pytest.raises(mdx.MdxError, match="no CPU path"):
+        mdx.Engine(0)
+
+
+def test_package_never_reaches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2405_01834_gb300")
+    files = glob.glob(os.path.join(pkg, "*.py")) + glob.glob(os.path.join(pkg, "csrc", "*"))
+    files += [os.path.join(ROOT, "include", "mdx.h")]
+    pat = re.compile(r"\bimport\s+oracle\b|\bfrom\s+oracle\b|mdx_oracle|libmdx_oracle|orc_[a-z0-9_]+\s*\(")
+    offenders = [f for f in files if os.path.isfile(f) and pat.search(open(f, errors="replace").read())]
+    assert not offenders, offenders
