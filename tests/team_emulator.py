@@ -401,3 +401,44 @@ def emulate(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
                 else:
                     ws[o] = acc
     return out.reshape(Nb, Nk)
+
+
+# ----------------------------------------------------------------- lane efficiency
+def lane_efficiency(pl: Plan):
+    """Share of FP64 lane slots that do useful work when a team runs the plan's
+    ket steps and its b23 step, under the kernel's lane assignment: in a ket
+    step lane tl runs entries tl and tl + T side by side (2 chains), then moves
+    on by 2T; in b23 lane tl runs (entry, column) items tl, tl + T, ... with
+    the column fastest. A warp instruction costs as many slots as the longest
+    chain of its 32 lanes needs. Returns (ket, b23) as fractions."""
+    T = pl.s["T"]
+    width = min(T, 32)
+
+    def warp_share(work_per_lane_round):
+        W = work_per_lane_round.reshape(work_per_lane_round.shape[0], -1, width)
+        used = W.sum()
+        slots = (W.max(axis=2) * width).sum()
+        return used, slots
+
+    ku = ks = bu = bs = 0
+    w23 = pl.b23["nv"].astype(np.int64) * (pl.b23["nu"].astype(np.int64) + 1)
+    for g in pl.groups:
+        for off, n in ((g["k1_off"], g["k1_n"]), (g["k2_off"], g["k2_n"]), (g["k3_off"], g["k3_n"])):
+            if n == 0:
+                continue
+            nn = pl.kprog["n"][off:off + n].astype(np.int64)
+            rounds = (n + 2 * T - 1) // (2 * T)
+            pad = np.zeros(rounds * 2 * T, dtype=np.int64)
+            pad[:n] = nn
+            u, s_ = warp_share(pad.reshape(rounds, 2, T).sum(axis=1))
+            ku += u
+            ks += s_
+        ncols = int(g["ncols"])
+        n = len(pl.b23) * ncols
+        rounds = (n + T - 1) // T
+        pad = np.zeros(rounds * T, dtype=np.int64)
+        pad[:n] = w23[np.arange(n) // ncols]
+        u, s_ = warp_share(pad.reshape(rounds, T))
+        bu += u
+        bs += s_
+    return ku / ks, bu / bs

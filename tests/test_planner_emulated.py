@@ -249,3 +249,13 @@ def test_random_shapes():
         parity.check(got, ref, ld, what="random shape %s K=%s b=%d s=%d store=%d" % (lq, K, budget, single_max, store),
                      offsets=off)
         done += 1
+
+
+@pytest.mark.parametrize("lq,k_min,b23_min", [((3, 3, 3, 3), 0.95, 0.85), ((4, 4, 4, 4), 0.97, 0.90),
+                                              ((5, 5, 5, 5), 0.98, 0.90), ((6, 6, 6, 6), 0.98, 0.90)])
+def test_planner_lane_efficiency(lq, k_min, b23_min):
+    """Regression guard on the plans' shape: the share of FP64 lane slots doing
+    useful work in the ket steps and in b23 (sorted entries, columns fastest),
+    for the uncontracted [ll|ll] classes the benchmark times."""
+    k, b23 = te.lane_efficiency(te.plan(*lq, store=True))
+    assert k >= k_min and b23 >= b23_min, (k, b23)
