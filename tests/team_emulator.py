@@ -274,7 +274,10 @@ def rlevel_programs():
 
 
 def _level(rprog, roff, N, src, g):
-    """Entries of total order N of one R level from the previous level `src`."""
+    """Entries of total order N of one R level from the previous level `src`:
+    PQ[axis] * src[first source] + k * src[second source], with k the word's
+    coefficient field (the kernel looks k up in a table of small integers as
+    doubles) and entry 0 the Boys seed g[0]."""
     cnt = (N + 1) * (N + 2) * (N + 3) // 6
     w = rprog[roff[N]:roff[N] + cnt].astype(np.int64)
     ax = (w >> 24) & 3
