@@ -10,6 +10,7 @@ the programs compute [ab|cd] of Eqs. ket-from-hermite and bra-from-hermite and
 that no entry of a step depends on another entry of the same step.
 """
 import itertools
+import math
 
 import numpy as np
 import pytest
@@ -259,3 +260,20 @@ def test_planner_lane_efficiency(lq, k_min, b23_min):
     for the uncontracted [ll|ll] classes the benchmark times."""
     k, b23 = te.lane_efficiency(te.plan(*lq, store=True))
     assert k >= k_min and b23 >= b23_min, (k, b23)
+
+
+def test_boys_asymptotic_form_above_the_table():
+    """Above the table (T >= 100) the kernel uses F_m(T) = c_m T^-(m+1/2) with
+    c_0 = sqrt(pi)/2 and c_(m+1) = c_m (2m+1)/2, dropping the exp(-T) terms;
+    against the oracle's long-double F_m the dropped part is below 1e-17
+    relative for m <= 25, so only rounding remains."""
+    c = [math.sqrt(math.pi) / 2.0]
+    for m in range(25):
+        c.append(c[-1] * (2 * m + 1) / 2.0)
+    worst = 0.0
+    for T in (100.0, 100.5, 137.25, 400.0, 1e3, 1e4):
+        ref = oracle.boys(25, T, precision=1)
+        for m in range(26):
+            got = c[m] * T ** (-(m + 0.5))
+            worst = max(worst, abs(got - ref[m]) / ref[m])
+    assert worst <= 2e-15, worst
