@@ -118,8 +118,9 @@ def whole_job_rate(units_per_rank: float, world: int, ms_step: float) -> float:
 
 
 # ------------------------------------------------------------------ oracle arm
-def run_oracle(work, frac, seed=2024):
-    """Time the oracle on a seeded sample of each class; returns (model flops, seconds, quartets, sample text)."""
+def run_oracle(work, frac, seed=2024, nthreads=0):
+    """Time the oracle on a seeded sample of each class (nthreads = 0: all host cores); returns
+    (model flops, seconds, quartets, per-class results)."""
     import oracle
     oracle.build()
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -130,7 +131,7 @@ def run_oracle(work, frac, seed=2024):
         m = max(1, int(round(frac * len(q))))
         idx = np.sort(rng.choice(len(q), m, replace=False))
         t0 = time.perf_counter()
-        oracle.eri4(b, q[idx])
+        oracle.eri4(b, q[idx], nthreads=nthreads)
         dt = time.perf_counter() - t0
         f = model_flops(l, m)
         tot_f += f; tot_t += dt; tot_q += m
@@ -638,6 +639,10 @@ def main():
         line["cpu_baseline"] = {"value": round(f / t * 1e-9, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                                 "sample": "seeded %.2f%% of each class (%d quartets), oracle as committed" % (
                                     100 * args.cpu_sample, nq), "per_class": per}
+        f1, t1, nq1, _ = run_oracle(work, args.cpu_sample / 10, seed=7, nthreads=1)
+        line["cpu_baseline"]["one_core"] = {"value": round(f1 / t1 * 1e-9, 4), "unit": UNIT, "cores": 1,
+                                            "sample": "seeded %.3f%% of each class (%d quartets)" % (
+                                                10 * args.cpu_sample, nq1)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     eng.close()
