@@ -1,14 +1,14 @@
 """GPU parity: the CUDA engine (through the C ABI) against the CPU oracle.
 
 Inputs are seeded and synthetic (paper_2405_01834_gb300.inputs); the oracle
-is the plain CPU McMurchie-Davidson code in oracle/. Tolerance: tests/parity.py.
+is the plain CPU McMurchie-Davidson code in oracle/. Tolerance: oracle/parity.py.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
-import parity
+from oracle import parity
 from paper_2405_01834_gb300 import inputs, mdx
 
 pytestmark = pytest.mark.gpu
@@ -36,7 +36,7 @@ def test_small_molecule_all_unique_quartets(eng):
     v, off = _gpu4(eng, b, q)
     ref, roff = oracle.eri4(b, q)
     assert np.array_equal(off, roff)
-    r = parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "small molecule", off)
+    r = parity.check(v[: off[-1]], ref, off, "small molecule", parity.Eri4Evaluator(b, q))
     print(r)
 
 
@@ -49,7 +49,7 @@ def test_class_sweep_grid(eng, l):
     v, off = _gpu4(eng, b, q)
     ref, roff = oracle.eri4(b, q)
     assert np.array_equal(off, roff)
-    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "sweep l=%d" % l, off)
+    print(parity.check(v[: off[-1]], ref, off, "sweep l=%d" % l, parity.Eri4Evaluator(b, q)))
 
 
 MIXED = [(0, 1, 2, 3), (3, 2, 1, 0), (6, 0, 0, 0), (0, 0, 0, 6), (2, 6, 1, 4), (5, 0, 4, 1), (1, 3, 6, 2),
@@ -63,7 +63,7 @@ def test_mixed_classes_contracted(eng, lq):
     b, q = inputs.class_sweep(lq, n_bra=3, n_ket=2, seed=5, K=K)
     v, off = _gpu4(eng, b, q)
     ref, _ = oracle.eri4(b, q)
-    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "mixed %s" % (lq,), off)
+    print(parity.check(v[: off[-1]], ref, off, "mixed %s" % (lq,), parity.Eri4Evaluator(b, q)))
 
 
 def test_random_quartets_many_classes(eng):
@@ -82,7 +82,7 @@ def test_random_quartets_many_classes(eng):
     q = q[L <= 14]
     v, off = _gpu4(eng, b, q)
     ref, _ = oracle.eri4(b, q)
-    parity.check(v[: off[-1]], ref, oracle.eri4(b, q, precision=1)[0], "random", off)
+    print(parity.check(v[: off[-1]], ref, off, "random", parity.Eri4Evaluator(b, q)))
 
 
 def test_empty_and_single(eng):
@@ -92,8 +92,8 @@ def test_empty_and_single(eng):
     assert off.cpu().numpy().tolist() == [0]
     q = np.array([[2, 2, 2, 2]], dtype=np.int32)
     v, off = eng.eri4(db, q)
-    ref, _ = oracle.eri4(b, q)
-    parity.check(v.cpu().numpy()[: int(off[-1])], ref, None, "single")
+    ref, roff = oracle.eri4(b, q)
+    print(parity.check(v.cpu().numpy()[: int(off[-1])], ref, roff, "single", parity.Eri4Evaluator(b, q)))
 
 
 def test_errors_are_reported(eng):
@@ -111,8 +111,8 @@ def test_errors_are_reported(eng):
     # the context stays usable (two atoms: no shellset that vanishes by symmetry)
     b2 = inputs.small_molecule(n_atoms=2)
     v, off = eng.eri4(mdx.DeviceBasis(b2), np.array([[0, 4, 2, 3]], dtype=np.int32))
-    ref, _ = oracle.eri4(b2, [[0, 4, 2, 3]])
-    parity.check(v.cpu().numpy()[: int(off[-1])], ref, None, "after errors")
+    ref, roff = oracle.eri4(b2, [[0, 4, 2, 3]])
+    print(parity.check(v.cpu().numpy()[: int(off[-1])], ref, roff, "after errors", parity.Eri4Evaluator(b2, [[0, 4, 2, 3]])))
 
 
 @pytest.mark.parametrize("la", [0, 1, 2, 3, 4, 5, 6])
@@ -128,8 +128,7 @@ def test_three_center(eng, la):
     torch.cuda.synchronize()
     ref, roff = oracle.eri3(aux_all, orb, t)
     assert np.array_equal(off.cpu().numpy(), roff)
-    parity.check(v.cpu().numpy()[: roff[-1]], ref, oracle.eri3(aux_all, orb, t, precision=1)[0], "3c la=%d" % la,
-                 roff)
+    print(parity.check(v.cpu().numpy()[: roff[-1]], ref, roff, "3c la=%d" % la, parity.Eri3Evaluator(aux_all, orb, t)))
 
 
 def test_prepared_batch_runs_repeatably(eng):
@@ -177,7 +176,7 @@ def test_autotuned_batch_matches(eng):
     torch.cuda.synchronize()
     eng.sync()
     ref, _ = oracle.eri4(b, q)
-    parity.check(w.cpu().numpy(), ref, oracle.eri4(b, q, precision=1)[0], "autotuned", off.cpu().numpy())
+    print(parity.check(w.cpu().numpy(), ref, off.cpu().numpy(), "autotuned", parity.Eri4Evaluator(b, q)))
     bt.close()
 
 
@@ -191,4 +190,59 @@ def test_solid_harmonic_eri4(eng, lq):
     torch.cuda.synchronize()
     ref, roff = oracle.eri4_sph(b, q)
     assert np.array_equal(off.cpu().numpy(), roff)
-    parity.check(v.cpu().numpy()[: roff[-1]], ref, None, "solid %s" % (lq,))
+    print(parity.check(v.cpu().numpy()[: roff[-1]], ref, roff, "solid %s" % (lq,)))
+
+
+def test_bound_screens_quartets(eng):
+    """mdx_eri4's bound input: quartets with bound < tau are written as zeros without evaluation, the
+    others are the unscreened values bit for bit; bound = NULL and tau = 0 keep every quartet."""
+    b = inputs.small_molecule(n_atoms=3)
+    db = mdx.DeviceBasis(b)
+    q = inputs.unique_quartets(b.n_shells)[::7]
+    pairs = np.array([(i, j) for i in range(b.n_shells) for j in range(i + 1)], dtype=np.int32)
+    Q = eng.schwarz(db, pairs).cpu().numpy()
+    pid = {(int(i), int(j)): n for n, (i, j) in enumerate(pairs)}
+    key = lambda i, j: pid[(max(i, j), min(i, j))]
+    bound = np.array([Q[key(a, bb)] * Q[key(c, d)] for a, bb, c, d in q])
+    v0, off0 = eng.eri4(db, q)
+    tau = float(np.quantile(bound, 0.4))
+    v1, off1 = eng.eri4(db, q, bound=bound, tau=tau)
+    v2, off2 = eng.eri4(db, q, bound=bound, tau=0.0)
+    torch.cuda.synchronize()
+    assert torch.equal(off0, off1) and torch.equal(off0, off2)
+    off = off0.cpu().numpy()
+    v0, v1, v2 = v0.cpu().numpy(), v1.cpu().numpy(), v2.cpu().numpy()
+    assert np.array_equal(v0[: off[-1]], v2[: off[-1]])
+    dropped = bound < tau
+    assert 0 < dropped.sum() < len(q)
+    for n in range(len(q)):
+        a, z = off[n], off[n + 1]
+        if dropped[n]:
+            assert np.all(v1[a:z] == 0.0)
+            # the bound holds: the dropped integrals are below it
+            assert np.max(np.abs(v0[a:z])) <= bound[n] * (1 + 1e-12)
+        else:
+            assert np.array_equal(v1[a:z], v0[a:z])
+    with pytest.raises(mdx.MdxError, match="EINVAL"):
+        eng.eri4(db, q, bound=bound, tau=-1.0)
+
+
+def test_bound_screens_triplets(eng):
+    """mdx_eri3's bound input, as mdx_eri4's."""
+    aux, orb = inputs.df_cluster(seed=11, n_atoms=2)
+    t = np.array([[a, c, d] for a in range(0, aux.n_shells, 3) for c in range(orb.n_shells) for d in range(c + 1)][:300],
+                 dtype=np.int32)
+    rng = np.random.Generator(np.random.PCG64(4))
+    bound = rng.uniform(0, 1, len(t))
+    daux, dorb = mdx.DeviceBasis(aux), mdx.DeviceBasis(orb)
+    v0, off = eng.eri3(daux, dorb, t)
+    v1, _ = eng.eri3(daux, dorb, t, bound=bound, tau=0.5)
+    torch.cuda.synchronize()
+    off = off.cpu().numpy()
+    v0, v1 = v0.cpu().numpy(), v1.cpu().numpy()
+    for n in range(len(t)):
+        a, z = off[n], off[n + 1]
+        if bound[n] < 0.5:
+            assert np.all(v1[a:z] == 0.0)
+        else:
+            assert np.array_equal(v1[a:z], v0[a:z])

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-import parity
+from oracle import parity
 import team_emulator as te
 from paper_2405_01834_gb300 import inputs
 
@@ -44,8 +44,7 @@ def _check_4c(lq, K=(1, 1, 1, 1), seed=11, n=2, **shape):
     got = _emulate_4c(pl, b, q)
     ref, off = oracle.eri4(b, q)
     assert np.max(np.abs(ref)) > 1e-3   # the inputs give integrals of a meaningful size
-    ld, _ = oracle.eri4(b, q, precision=1)
-    parity.check(got, ref, ld, what="emulated %s K=%s %s" % (lq, K, shape), offsets=off)
+    parity.check(got, ref, off, what="emulated %s K=%s %s" % (lq, K, shape), evaluate=parity.Eri4Evaluator(b, q))
     return pl
 
 
@@ -152,8 +151,7 @@ def test_three_center(la, lc, ld, K, store):
     got = np.concatenate(got)
     ref, off = oracle.eri3(aux, orb, trip)
     assert np.max(np.abs(ref)) > 1e-3
-    ld_ref, _ = oracle.eri3(aux, orb, trip, precision=1)
-    parity.check(got, ref, ld_ref, what="emulated [%d|%d%d]" % (la, lc, ld), offsets=off)
+    parity.check(got, ref, off, what="emulated [%d|%d%d]" % (la, lc, ld), evaluate=parity.Eri3Evaluator(aux, orb, trip))
 
 
 def test_emulator_detects_a_corrupted_program():
@@ -170,14 +168,14 @@ def test_emulator_detects_a_corrupted_program():
     bad[g["k3_off"] + i]["coef"] += 1
     pl_bad = te.Plan(pl.s, pl.groups, bad, pl.b1, pl.b23, pl.colmap, pl.rprog, pl.roff)
     with pytest.raises(AssertionError):
-        parity.check(_emulate_4c(pl_bad, b, q), ref, what="corrupted k3")
+        parity.check(_emulate_4c(pl_bad, b, q), ref, off, what="corrupted k3", evaluate=parity.Eri4Evaluator(b, q))
     b23 = pl.b23.copy()
     j = int(np.argmax(b23["nu"]))
     b23[j]["nu"] -= 1
     pl_bad = te.Plan(pl.s, pl.groups, pl.kprog, pl.b1, b23, pl.colmap, pl.rprog, pl.roff)
     with pytest.raises(AssertionError):
-        parity.check(_emulate_4c(pl_bad, b, q), ref, what="corrupted b23")
-    parity.check(_emulate_4c(pl, b, q), ref, what="intact")
+        parity.check(_emulate_4c(pl_bad, b, q), ref, off, what="corrupted b23", evaluate=parity.Eri4Evaluator(b, q))
+    parity.check(_emulate_4c(pl, b, q), ref, off, what="intact", evaluate=parity.Eri4Evaluator(b, q))
 
 
 def test_boys_table_interpolation():
@@ -246,9 +244,8 @@ def test_random_shapes():
         b, q = _basis_4c(lq, K, int(rng.integers(0, 10 ** 6)), n=1)
         got = _emulate_4c(pl, b, q)
         ref, off = oracle.eri4(b, q)
-        ld, _ = oracle.eri4(b, q, precision=1)
-        parity.check(got, ref, ld, what="random shape %s K=%s b=%d s=%d store=%d" % (lq, K, budget, single_max, store),
-                     offsets=off)
+        parity.check(got, ref, off, what="random shape %s K=%s b=%d s=%d store=%d" % (lq, K, budget, single_max, store),
+                     evaluate=parity.Eri4Evaluator(b, q))
         done += 1
 
 
