@@ -7,9 +7,13 @@ quartets) of random uncontracted bra and ket shell pairs (centres uniform in
 a 10-bohr box, exponents log-uniform in [0.05, 50]); outputs are written to a
 reused device buffer in chunks (the [ii|ii] class alone is 247 GB).
 
-Metric: model FP64 GFLOP/s (the paper's Table 1 work model for contracted
-Cartesian shellsets) and shell quartets per second, per class and for the
-whole sweep, with the fraction of the GB300 FP64 peak.
+Metric: FP64 GFLOP/s and shell quartets per second, per class and for the
+whole sweep, with the fraction of the GB300 FP64 peak. `value` counts the work
+in the paper's Table 1 FLOP model (contracted Cartesian shellsets), the unit
+both arms share; the kernels execute several times fewer FP64 operations
+(axis-factored transforms), so the roofline fraction is taken on the FP64
+multiply-adds they do execute, against the FP64 peak measured in the same run
+(scalar DFMA and the FP64 tensor instruction, the larger of the two).
 """
 from __future__ import annotations
 
@@ -30,16 +34,16 @@ sys.path.insert(0, ROOT)
 from paper_2405_01834_gb300 import flops, inputs  # noqa: E402
 
 CLASS_NAMES = {1: "[pp|pp]", 2: "[dd|dd]", 3: "[ff|ff]", 4: "[gg|gg]", 5: "[hh|hh]", 6: "[ii|ii]"}
-METRIC = "FP64 GFLOP/s (model) and shell-quartets/s per class; % of GB300 FP64 peak"
-UNIT = "GFLOP/s"
-# GB300 FP64 pipe: 2 DFMA per clock per SM (measured with a DFMA throughput
-# probe: 1203 GFLOP/s at ~1.98 GHz), 152 SMs, 2070 MHz maximum SM clock.
+METRIC = "FP64 GFLOP/s and shell-quartets/s per (la,lb,lc,ld) class; % of GB300 FP64 peak"
+UNIT = "GFLOP/s (Table-1 model FLOPs)"
+# GB300 FP64 pipe: 2 FP64 multiply-adds per clock per SM, 152 SMs; used only for the derived
+# peak that is reported beside the measured one
 FP64_FLOP_PER_CLK_SM = 4.0
 CHUNK_BYTES = 2 << 30
-# DRAM bytes (read + write) per [ii|ii] quartet of the k_quartets launch, from the ncu capture summarised
-# in profiles/k_quartets_ii_16x16.md (256 quartets: 2.739 GB read + 3.838 GB written); scaled by the
-# quartets of a launch when the dominant class is [ii|ii]
-NCU_DRAM_BYTES_PER_II_QUARTET = (2.739450e9 + 3.838610e9) / 256
+# DRAM bytes (read + write) per [ii|ii] quartet of one k_quartets launch of the benchmark (456 quartets),
+# from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of that launch; None: not captured
+# for the current kernel
+NCU_DRAM_BYTES_PER_II_QUARTET = None
 
 
 def parse():
@@ -55,11 +59,12 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the per-class team-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad", "ab"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad", "ab", "peak"],
                     help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules; "
                          "df: per-class 3-center rates on the density-fitting cluster; grad: exchange energy "
                          "and its nuclear gradient against the exchange build alone; ab: the default kernels "
-                         "against the materialized-Hermite variant (dense [p|q], batched DGEMMs)")
+                         "against the materialized-Hermite variant (dense [p|q], batched DGEMMs); "
+                         "peak: measured FP64 throughput, scalar DFMA vs the FP64 tensor instruction")
     ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
     ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
     ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
@@ -101,6 +106,12 @@ def model_flops(l, n):
     return flops.eri4_flops(l, l, l, l) * n
 
 
+def autotune_trial(l: int, n: int) -> int:
+    """Quartets the autotuner times per candidate shape: enough to fill the GPU with one-thread-per-
+    quartet candidates at low l."""
+    return max(304, min(n, 65536 // max(1, l) ** 3))
+
+
 def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
     """Slowest rank's step time (every rank runs its own replica of the workload)."""
     if world <= 1:
@@ -118,9 +129,10 @@ def whole_job_rate(units_per_rank: float, world: int, ms_step: float) -> float:
 
 
 # ------------------------------------------------------------------ oracle arm
-def run_oracle(work, frac, seed=2024, nthreads=0):
+def run_oracle(work, frac, seed=2024, nthreads=0, keep=None):
     """Time the oracle on a seeded sample of each class (nthreads = 0: all host cores); returns
-    (model flops, seconds, quartets, per-class results)."""
+    (model flops, seconds, quartets, per-class results). keep: dict that receives, per class l, the
+    sampled quartet indices and the oracle's shellsets and offsets."""
     import oracle
     oracle.build()
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -131,8 +143,10 @@ def run_oracle(work, frac, seed=2024, nthreads=0):
         m = max(1, int(round(frac * len(q))))
         idx = np.sort(rng.choice(len(q), m, replace=False))
         t0 = time.perf_counter()
-        oracle.eri4(b, q[idx], nthreads=nthreads)
+        vals, off = oracle.eri4(b, q[idx], nthreads=nthreads)
         dt = time.perf_counter() - t0
+        if keep is not None:
+            keep[l] = (idx, vals, off)
         f = model_flops(l, m)
         tot_f += f; tot_t += dt; tot_q += m
         per[CLASS_NAMES[l]] = {"quartets": m, "s": round(dt, 4), "model_gflops": round(f / dt * 1e-9, 4)}
@@ -353,6 +367,7 @@ def df_main(args):
     lo = np.asarray(orb.l); la_aux = np.asarray(aux.l)
     rng = np.random.Generator(np.random.PCG64(1003))
     stream = torch.cuda.current_stream()
+    peak = max(mdx.fp64_peak(0, 3), mdx.fp64_peak(1, 3)) * 1e9   # FP64 FLOP/s, measured
     rows, tot_ms, tot_flops, full_s, full_trip = [], 0.0, 0.0, 0.0, 0
     for la in range(int(la_aux.max()) + 1):
         a_sh = np.where(la_aux == la)[0]
@@ -377,7 +392,7 @@ def df_main(args):
                 rows.append({"class": "[%d|%d%d]" % (la, lc, ld), "K_cd": Kc * Kd, "triplets": n,
                              "ms": round(ms, 4), "triplets_per_s": round(n / (ms * 1e-3), 1),
                              "model_gflops": round(f / (ms * 1e-3) * 1e-9, 2),
-                             "executed_frac": round(2 * bt.exec_fma / (ms * 1e-3) / peak_fp64(torch), 4),
+                             "executed_frac": round(2 * bt.exec_fma / (ms * 1e-3) / peak, 4),
                              "full_tensor_triplets": full})
                 tot_ms += ms; tot_flops += f
                 full_s += full / (n / (ms * 1e-3)); full_trip += full
@@ -392,6 +407,7 @@ def df_main(args):
                        "orbital_pairs": int(len(pairs)), "kept_pairs": int(len(kept)),
                        "aux_shells": int(aux.n_shells)},
             "full_tensor": {"triplets": int(full_trip), "estimated_s": round(full_s, 3)},
+            "fp64_peak_gflops": round(peak * 1e-9, 1),
             "per_class": rows}
     print(json.dumps(line), flush=True)
     eng.close()
@@ -471,10 +487,30 @@ def ab_main(args):
     eng.close()
 
 
-def peak_fp64(torch, sm_mhz: float = 2070.0):
-    """FP64 pipe peak of this GPU at the given SM clock (default: the GB300 maximum), FLOP/s."""
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    return FP64_FLOP_PER_CLK_SM * props.multi_processor_count * sm_mhz * 1e6
+def peak_main(args):
+    """FP64 throughput of this GPU: scalar DFMA against the FP64 tensor instruction (DMMA) in its three
+    shapes (mdx_fp64_peak), with the SM clocks sampled meanwhile. The engine's transforms use DFMA
+    because DMMA retires FP64 multiply-adds at about the same rate on this part (and needs dense tiles)."""
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    mdx.fp64_peak(0, 1)   # warm-up
+    clk = ClockSampler(0)
+    clk.start()
+    names = {0: "dfma", 1: "dmma_m8n8k4", 2: "dmma_m16n8k4", 3: "dmma_m16n8k16"}
+    res = {names[k]: round(max(mdx.fp64_peak(k, 5) for _ in range(max(1, args.steps))), 1) for k in range(4)}
+    clocks = clk.stop()
+    props = torch.cuda.get_device_properties(0)
+    mhz = (clocks or {}).get("sm_mhz") or 0.0
+    line = {"metric": "FP64 throughput: scalar DFMA vs the FP64 tensor instruction", "unit": "GFLOP/s",
+            "value": max(res.values()), "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "config": {"workload": "register-resident FP64 multiply-add loops, 4 x 256 threads "
+                                                        "per SM, %d SMs" % props.multi_processor_count},
+            "per_kind": res,
+            "per_sm_per_clock": ({k: round(v * 1e9 / (props.multi_processor_count * mhz * 1e6), 3)
+                                  for k, v in res.items()} if mhz else None),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -489,6 +525,8 @@ def main():
         return grad_main(args)
     if args.workload == "ab":
         return ab_main(args)
+    if args.workload == "peak":
+        return peak_main(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:
@@ -522,7 +560,7 @@ def main():
         for l, db, q, batches in prepared:
             t0 = time.perf_counter()
             # trials large enough to fill the GPU with one-thread-per-quartet candidates at low l
-            batches[0].autotune(out, max_trial=max(304, min(len(q), 65536 // max(1, l) ** 3)))
+            batches[0].autotune(out, max_trial=autotune_trial(l, len(q)))
             tuned[CLASS_NAMES[l]] = round(time.perf_counter() - t0, 2)
         # re-prepare so every chunk picks up the tuned plans
         for i, (l, db, q, batches) in enumerate(prepared):
@@ -559,6 +597,10 @@ def main():
     barrier()
     clk = ClockSampler(dev)
     clk.start()
+    # the FP64 peak of this GPU, measured now (clocks sampled with the timed region): scalar DFMA and
+    # the FP64 tensor instruction (m8n8k4); the roofline takes the larger
+    probe = {"dfma": mdx.fp64_peak(0, 3), "dmma_m8n8k4": mdx.fp64_peak(1, 3)}
+    barrier()
     per_class_ms = {l: [] for l, *_ in prepared}
     per_launch_ms = {l: [] for l, *_ in prepared}
     step_ms = []
@@ -581,7 +623,8 @@ def main():
     ms_step = max_over_ranks(sum(step_ms) / len(step_ms), world, "cuda")
 
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak_gflops = FP64_FLOP_PER_CLK_SM * props.multi_processor_count * sm_max * 1e-3
+    derived_gflops = FP64_FLOP_PER_CLK_SM * props.multi_processor_count * sm_max * 1e-3
+    peak_gflops = max(probe.values())
     total_flops = sum(model_flops(l, len(q)) for l, _, q, _ in prepared)
     total_exec = sum(2.0 * bt.exec_fma for *_, batches in prepared for bt in batches)
     value = whole_job_rate(total_flops, world, ms_step) * 1e-9
@@ -593,30 +636,35 @@ def main():
         ex = sum(2.0 * bt.exec_fma for bt in batches)
         per_class[CLASS_NAMES[l]] = {
             "quartets": len(q), "ms": round(ms, 3), "quartets_per_s": round(len(q) / (ms * 1e-3), 1),
-            "model_gflops": round(f / (ms * 1e-3) * 1e-9, 2),
-            "model_frac_of_peak": round(f / (ms * 1e-3) * 1e-9 / peak_gflops, 4),
             "exec_gflops": round(ex / (ms * 1e-3) * 1e-9, 2),
             "exec_frac_of_peak": round(ex / (ms * 1e-3) * 1e-9 / peak_gflops, 4),
+            "model_gflops": round(f / (ms * 1e-3) * 1e-9, 2),
+            "model_over_executed_flops": round(f / ex, 2),
             "launches_per_step": 2 * len(batches)}
         if ms > dom_ms:
             dom_ms, dom_l = ms, l
-    # roofline of the dominant class's launches (pair records + quartet kernel per chunk)
+    # roofline of the dominant class's launches (pair records + quartet kernel per chunk): the FP64
+    # multiply-adds its planner counts (x2) per launch over the launch's CUDA-event time
     l = dom_l
     _, _, q, batches = next(p for p in prepared if p[0] == l)
     lm = per_launch_ms[l]
     avg_launch_ms = sum(lm) / len(lm)
-    per_launch_flops = model_flops(l, len(q)) / len(batches)
-    achieved = per_launch_flops / (avg_launch_ms * 1e-3) * 1e-12
     per_launch_exec = sum(2.0 * bt.exec_fma for bt in batches) / len(batches)
+    per_launch_model = model_flops(l, len(q)) / len(batches)
+    achieved = per_launch_exec / (avg_launch_ms * 1e-3) * 1e-12
+    traffic = None
+    if NCU_DRAM_BYTES_PER_II_QUARTET is not None and l == 6:
+        traffic = round(NCU_DRAM_BYTES_PER_II_QUARTET * len(q) / len(batches))
     roofline = {"bound": "alu", "kernel": "k_quartets %s" % CLASS_NAMES[l], "achieved": round(achieved, 4),
                 "peak": round(peak_gflops * 1e-3, 4), "unit": "TFLOP/s", "frac": round(achieved / (peak_gflops * 1e-3), 4),
-                "traffic": (round(NCU_DRAM_BYTES_PER_II_QUARTET * len(q) / len(batches)) if l == 6 else None),
-                "traffic_unit": "bytes per launch (ncu capture of 256 quartets, scaled)",
-                "model_flops_per_launch": per_launch_flops,
-                "executed_tflops": round(per_launch_exec / (avg_launch_ms * 1e-3) * 1e-12, 4),
-                "executed_frac": round(per_launch_exec / (avg_launch_ms * 1e-3) * 1e-12 / (peak_gflops * 1e-3), 4),
-                "peak_basis": "FP64 pipe: 2 DFMA/clk/SM x %d SMs x %.0f MHz (derived; DFMA probe measured 1.203 "
-                              "TFLOP/s)" % (props.multi_processor_count, sm_max)}
+                "traffic": traffic, "traffic_unit": "DRAM bytes read + written per launch (ncu)",
+                "algorithmic_flops_per_launch": per_launch_exec,
+                "peak_basis": "FP64, measured in this run: max of scalar DFMA %.1f and DMMA m8n8k4 %.1f GFLOP/s "
+                              "(mdx_fp64_peak); derived 2 FMA/clk/SM x %d SMs x %.0f MHz = %.1f GFLOP/s" % (
+                                  probe["dfma"], probe["dmma_m8n8k4"], props.multi_processor_count, sm_max,
+                                  derived_gflops),
+                "model_tflops": round(per_launch_model / (avg_launch_ms * 1e-3) * 1e-12, 4),
+                "model_flops_per_launch": per_launch_model}
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
@@ -625,8 +673,9 @@ def main():
                                    "class, Cartesian, FP64" % (args.n_bra, args.n_ket), "classes": args.classes,
                        "l2": "256 MB buffer written between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "quartets_per_s": round(whole_job_rate(sum(len(q) for _, _, q, _ in prepared), world, ms_step), 1),
-            "model_frac_of_peak": round(value / world / peak_gflops, 4),
             "exec_gflops": round(world * total_exec / (ms_step * 1e-3) * 1e-9, 3),
+            "exec_frac_of_peak": round(total_exec / (ms_step * 1e-3) * 1e-9 / peak_gflops, 4),
+            "fp64_peak_gflops": {k: round(v, 1) for k, v in probe.items()},
             "per_class": per_class, "roofline": roofline, "autotune_s": tuned or None, "gpu_launches": launches,
             "gpu_launches_per_step": launches // args.steps if args.steps else 0,
             "clocks": clocks}
@@ -635,10 +684,12 @@ def main():
     if not args.no_e2e:
         line["e2e"] = e2e(eng, work, args, torch)
     if rank == 0 and not args.no_cpu:
-        f, t, nq, per = run_oracle(work, args.cpu_sample)
+        kept = {}
+        f, t, nq, per = run_oracle(work, args.cpu_sample, keep=kept)
         line["cpu_baseline"] = {"value": round(f / t * 1e-9, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                                 "sample": "seeded %.2f%% of each class (%d quartets), oracle as committed" % (
                                     100 * args.cpu_sample, nq), "per_class": per}
+        line["parity"] = sample_parity(prepared, kept, out, torch)
         f1, t1, nq1, _ = run_oracle(work, args.cpu_sample / 10, seed=7, nthreads=1)
         line["cpu_baseline"]["one_core"] = {"value": round(f1 / t1 * 1e-9, 4), "unit": UNIT, "cores": 1,
                                             "sample": "seeded %.3f%% of each class (%d quartets)" % (
@@ -649,6 +700,41 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def sample_parity(prepared, kept, out, torch):
+    """The oracle's CPU-baseline sample of each class against the GPU shellsets of the same quartets, from
+    the timed launch configuration (the class's prepared batches, run once more): the parity record of the
+    benchmark (rule: oracle/parity.py)."""
+    from oracle import parity
+    rec, worst_abs, worst_rel, n_cancel, n_el = {}, 0.0, 0.0, 0, 0
+    for l, db, q, batches in prepared:
+        if l not in kept:
+            continue
+        idx, ref, off = kept[l]
+        per_q = inputs.ncart(l) ** 4
+        got = np.zeros(len(idx) * per_q)
+        lo = 0
+        for bt in batches:
+            bt.run(out)
+            torch.cuda.synchronize()
+            hi = lo + bt.n
+            sel = np.where((idx >= lo) & (idx < hi))[0]
+            if len(sel):
+                rows = torch.as_tensor(idx[sel] - lo, device="cuda")
+                vals = out[: bt.n * per_q].view(bt.n, per_q).index_select(0, rows).cpu().numpy()
+                for k, n in enumerate(sel):
+                    got[n * per_q:(n + 1) * per_q] = vals[k]
+            lo = hi
+        r = parity.check(got, ref, off, "bench sample %s" % CLASS_NAMES[l], parity.Eri4Evaluator(db.host, q[idx]))
+        rec[CLASS_NAMES[l]] = {k: r[k] for k in ("elements", "max_abs_over_scale", "max_rel", "n_cancel")}
+        worst_abs = max(worst_abs, r["max_abs_over_scale"])
+        worst_rel = max(worst_rel, r["max_rel"])
+        n_cancel += r["n_cancel"]
+        n_el += r["elements"]
+    return {"rule": "abs <= 1e-12 max|shellset|, rel <= 1e-10 above 1e-10, cancellation exception counted "
+                    "(oracle/parity.py)", "elements": n_el, "max_abs_over_scale": worst_abs, "max_rel": worst_rel,
+            "n_cancel": n_cancel, "per_class": rec}
 
 
 def e2e(eng, work, args, torch):

@@ -96,6 +96,13 @@ mdx_status mdx_sync(mdx_ctx* ctx, void* stream);
 
 /* 4-center integrals [ab|cd] (Eq. def-abcd) for n shell quartets.
  * quartets: [n][4] int32 shell indices (a, b, c, d) into `basis`.
+ * bound: [n] doubles (device) or NULL. bound[q] is an upper bound on
+ *   |(ab|cd)| over the shellset of quartet q, e.g. the Schwarz product
+ *   Q_ab Q_cd of mdx_schwarz (the paper screens quartets before batching,
+ *   Sec. 3, without fixing the bound). A quartet with bound[q] < tau is not
+ *   evaluated: its shellset is written as zeros, its output slot and offset
+ *   are unchanged. bound = NULL evaluates every quartet and ignores tau.
+ * tau: screening threshold (>= 0 when bound is given, else MDX_EINVAL).
  * out: receives, for quartet q, the contracted shellset in row-major
  *   [a][b][c][d] order (d fastest) at out + out_offsets[q]; out has room for
  *   out_capacity doubles.
@@ -110,8 +117,8 @@ mdx_status mdx_sync(mdx_ctx* ctx, void* stream);
  * cudaMalloc/cudaFree, so work on other streams is not stalled; calls of one
  * context that overlap must be issued on one stream. n = 0 is allowed and
  * writes out_offsets[0] = 0. */
-mdx_status mdx_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
-                    double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
+mdx_status mdx_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, const double* bound, int64_t n,
+                    double tau, double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
 
 /* mdx_eri4 over real solid harmonics (the paper's basis, Eqs. solid2herm):
  * shell of angular momentum l contributes 2l+1 functions S_lm, m = -l..l,
@@ -129,9 +136,13 @@ mdx_status mdx_eri4_sph(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* qua
  * from `orb`. triplets: [n][3] int32 (a, c, d). Output per triplet in
  * row-major [a][c][d] order at out + out_offsets[q]. The bra is a single
  * Gaussian (zeta_p = zeta_a, P = A) with the 1-center E coefficients of
- * Eq. E1rr. Same capacity, offset and synchronisation rules as mdx_eri4. */
+ * Eq. E1rr. bound / tau: per-triplet bounds on |(a|cd)| (e.g. Q_a Q_cd) and
+ * the threshold below which a triplet is written as zeros without being
+ * evaluated, as in mdx_eri4 (bound = NULL: none). Same capacity, offset and
+ * synchronisation rules as mdx_eri4. */
 mdx_status mdx_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
-                    int64_t n, double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
+                    const double* bound, int64_t n, double tau, double* out, int64_t out_capacity,
+                    int64_t* out_offsets, void* stream);
 
 /* ---- prepared batches --------------------------------------------------
  * A batch separates the host-side preparation of a call (index download,
@@ -143,8 +154,9 @@ mdx_status mdx_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, co
  * destroyed; the batch keeps its own copies of the index data. */
 typedef struct mdx_batch mdx_batch;
 
-/* Prepare the quartets of mdx_eri4 (same arguments). Synchronises `stream`.
- * n must be >= 1. */
+/* Prepare the quartets of mdx_eri4 (same arguments, without screening
+ * bounds: a batch evaluates every quartet it is given). Synchronises
+ * `stream`. n must be >= 1. */
 mdx_status mdx_batch_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
                           mdx_batch** batch, void* stream);
 
@@ -210,19 +222,40 @@ mdx_status mdx_schwarz(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pair
  *   (order inside a pair is free); Q: [n_pairs] Schwarz factors of the pairs
  *   (e.g. from mdx_schwarz), same order.
  * Unique quartets (ij|kl) of the pair list are screened on the GPU with
- *   Q_ij Q_kl max(|D_ik|, |D_il|, |D_jk|, |D_jl|) >= tau  (max over shell
- *   blocks; tau = 0 keeps every quartet); each kept quartet is evaluated once
+ *   Q_ij Q_kl max(|D_ik|, |D_il|, |D_jk|, |D_jl|) >= tau  (FP64; max over
+ *   shell blocks; tau = 0 keeps every quartet). Pairs are sorted by Q within
+ *   their class, so each bra pair stops testing a ket class at the first
+ *   pair whose Q cannot pass; the cost follows the kept quartets, not the
+ *   square of the pair count. The block maxima form one N_shells x N_shells
+ *   table of doubles in context workspace. Each kept quartet is evaluated once
  *   and digested into four K blocks inside the integral kernel (the integrals
  *   never reach device memory), with FP64 atomics; finally K <- K + K^T.
  * D: [nao][nao] row-major, symmetric (device). K: [nao][nao] (device),
  *   overwritten. nao = max over shells of ao_off + ncart(l); basis->ao_off is
- *   required. Synchronises `stream` (screening counts) and on return K is
+ *   required.
+ * energy: one double (device) receiving the exchange energy
+ *   E_x = alpha sum_ik D_ik K_ik = alpha sum_ijkl D_ik D_jl (ij|kl) of the
+ *   screened K (alpha = -1 for a closed-shell D = C C^T), or NULL. Synchronises `stream` (screening counts) and on return K is
  *   complete. Pairs absent from the list contribute nothing. The per-class
  *   integral launches are spread over `stream` and three internal streams of
  *   the context, each ordered after the work already queued on `stream`, and
  *   `stream` waits for all of them before K <- K + K^T. */
 mdx_status mdx_exchange(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
-                        double tau, const double* D, double* K, void* stream);
+                        double tau, const double* D, double* K, double alpha, double* energy, void* stream);
+
+/* The screening step of mdx_exchange on its own: the unique quartets
+ * (ij|kl) of the pair list kept by Q_ij Q_kl max(|D_ik|,|D_il|,|D_jk|,|D_jl|)
+ * >= tau (FP64, that product order; maxima over shell blocks of D).
+ * *n_kept (host) receives their number; model_flops (host, may be NULL) the
+ * paper's Table-1 work model summed over them (as mdx_batch_info counts it).
+ * kept: [kept_capacity][2] int32 (device) or NULL for counting only;
+ * receives each kept quartet as two indices into `pairs` (bra pair, ket
+ * pair), grouped by class pair, in no particular order within a group.
+ * MDX_ECAPACITY (with *n_kept set) when the list exceeds kept_capacity.
+ * Pairs, Q, D and tau as in mdx_exchange. Synchronises `stream`. */
+mdx_status mdx_exchange_screen(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, const double* Q,
+                               int64_t n_pairs, double tau, const double* D, int32_t* kept, int64_t kept_capacity,
+                               int64_t* n_kept, double* model_flops, void* stream);
 
 /* Nuclear gradient of the exchange energy E_x = alpha S, S = sum_ijkl D_ik D_jl
  * (ij|kl), with D held fixed (alpha = -1 for a closed-shell D = C C^T; the
@@ -308,7 +341,8 @@ int64_t mdx_last_quartet_count(const mdx_ctx* ctx);
  * steady-state loops that cannot afford cudaMalloc's implicit device
  * synchronisation. (The paper has no counterpart; this is a property of the
  * engine, not of the method.)
- * Same arguments and results as mdx_eri4, minus the context: it runs on the
+ * Same arguments and results as mdx_eri4 without screening bounds (every
+ * quartet is evaluated) and minus the context: it runs on the
  * current CUDA device. All device scratch (Boys and Hermite decode tables,
  * primitive-pair records, quartet lists, class step programs) lives in one
  * file-scope 32 MiB __device__ array that every GPU loading the library holds
@@ -322,6 +356,19 @@ int64_t mdx_last_quartet_count(const mdx_ctx* ctx);
  * text is kept (no context): the status code is the report. */
 mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
                             int64_t out_capacity, int64_t* out_offsets, void* stream);
+
+/* FP64 throughput of the current CUDA device, measured: the denominator of
+ * the engine's roofline (the integral kernels are bound by the FP64 pipe).
+ * The paper has no counterpart: it is a measurement utility of the engine.
+ * kind 0: scalar FP64 fused multiply-add (DFMA), 8 independent chains per
+ * thread; 1, 2, 3: the FP64 tensor-core instruction (mma.sync .f64) in the
+ * shapes m8n8k4, m16n8k4 and m16n8k16, 4 independent accumulators per warp.
+ * Register-resident loops over 4 blocks of 256 threads per SM; one warm-up
+ * launch, then `reps` launches of about 50 ms timed with CUDA events on
+ * `stream`. *gflops receives 2 x multiply-adds / second / 1e9. Synchronises
+ * `stream`; allocates nothing. MDX_EINVAL for a kind outside 0..3, reps < 1
+ * or a NULL gflops; MDX_ECUDA if a CUDA call fails. */
+mdx_status mdx_fp64_peak(int kind, int reps, double* gflops, void* stream);
 
 /* Shape the engine chooses for one integral class (no GPU needed; ctx may be
  * NULL). The class is (la lb | lc ld) with Kb = K_a K_b and Kk = K_c K_d

@@ -199,8 +199,10 @@ struct PairHash {
 // Quartets given as (bra pair, ket pair) over a pair list.
 struct Batch {
   std::vector<PairKey> pairs;
-  std::vector<int2> qp;          // per quartet (bra pair idx, ket pair idx)
-  std::vector<int64_t> qoff;     // output offset per quartet
+  std::vector<int2> qp;          // per evaluated quartet (bra pair idx, ket pair idx)
+  std::vector<int64_t> qoff;     // output offset per evaluated quartet
+  std::vector<int64_t> qcaller;  // caller index per evaluated quartet
+  std::vector<int64_t> zero;     // (offset, doubles) of every screened-out quartet, written as zeros
 };
 
 }  // namespace
@@ -219,6 +221,8 @@ struct mdx_batch {
   int2* qp = nullptr;
   int64_t* qoff = nullptr;
   int64_t* offsets = nullptr;     // [n+1] in caller order
+  int64_t* zero = nullptr;        // [nzero][2] (offset, doubles) of screened-out shellsets
+  int64_t nzero = 0;
   struct Range { Plan* plan; int64_t begin, count; ClassKey key; };
   std::vector<Range> ranges;
   std::vector<int64_t> qorig;     // caller index of each class-sorted quartet
@@ -274,7 +278,7 @@ void batch_free(mdx_batch* b) {
   if (!b) return;
   if (b->owned) {
     cudaFree(b->jobs); cudaFree(b->pair_rec); cudaFree(b->recs); cudaFree(b->recs_s);
-    cudaFree(b->qp); cudaFree(b->qoff); cudaFree(b->offsets);
+    cudaFree(b->qp); cudaFree(b->qoff); cudaFree(b->offsets); cudaFree(b->zero);
   }
   delete b;
 }
@@ -354,8 +358,9 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
   std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> B(new mdx_batch(), batch_free);
   B->owned = !call_ws;
   B->ctx = c;
-  B->n = (int64_t)bt.qp.size();
+  B->n = (int64_t)offs.size() - 1;
   B->total = offs.back();
+  B->nzero = (int64_t)bt.zero.size() / 2;
   B->b0 = to_dev(b0);
   B->b1 = to_dev(b1 ? b1 : b0);
   const HostBasis* hb[2] = {&h0, &h1};
@@ -394,7 +399,11 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
   mdx_status st;
   for (auto& kv : classes) {
     const int64_t b = (int64_t)qp_sorted.size();
-    for (int64_t q : kv.second) { qp_sorted.push_back(bt.qp[q]); qoff_sorted.push_back(bt.qoff[q]); B->qorig.push_back(q); }
+    for (int64_t q : kv.second) {
+      qp_sorted.push_back(bt.qp[q]);
+      qoff_sorted.push_back(bt.qoff[q]);
+      B->qorig.push_back(bt.qcaller.empty() ? q : bt.qcaller[q]);
+    }
     Plan* plan;
     if ((st = get_plan(c, kv.first, &plan, s)) != MDX_OK) return st;
     B->ranges.push_back({plan, b, (int64_t)kv.second.size(), kv.first});
@@ -408,6 +417,7 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     if ((st = upload(c, "call_qp", qp_sorted, &B->qp, s)) != MDX_OK) return st;
     if ((st = upload(c, "call_qoff", qoff_sorted, &B->qoff, s)) != MDX_OK) return st;
     if ((st = upload(c, "call_offsets", offs, &B->offsets, s)) != MDX_OK) return st;
+    if (!bt.zero.empty() && (st = upload(c, "call_zero", bt.zero, &B->zero, s)) != MDX_OK) return st;
     if ((st = ensure(c, "call_recs", (size_t)std::max<int64_t>(roff, 1), &B->recs, s)) != MDX_OK) return st;
     if ((st = ensure(c, "call_recs_s", (size_t)std::max<int64_t>(roff, 1), &B->recs_s, s)) != MDX_OK) return st;
   } else {
@@ -416,6 +426,7 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
   if ((st = dev_upload(c, qp_sorted, &B->qp, s)) != MDX_OK) return st;
   if ((st = dev_upload(c, qoff_sorted, &B->qoff, s)) != MDX_OK) return st;
   if ((st = dev_upload(c, offs, &B->offsets, s)) != MDX_OK) return st;
+  if ((st = dev_upload(c, bt.zero, &B->zero, s)) != MDX_OK) return st;
   }
   if (roff > 0 && !call_ws) {
     if (cudaMalloc(&B->recs, roff * sizeof(double)) != cudaSuccess ||
@@ -437,6 +448,11 @@ mdx_status batch_run(mdx_ctx* c, mdx_batch* B, double* out, int32_t* nlaunch, cu
   cudaError_t e = launch_pair_records(B->b0, B->b1, B->jobs, B->njobs, B->recs, B->recs_s, c->d_err, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
   if (B->njobs > 0) ++nl;
+  if (B->nzero > 0) {
+    e = launch_zero_ranges(B->zero, B->nzero, out, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "screened-out shellsets");
+    ++nl;
+  }
   for (auto& r : B->ranges) {
     QuartetLaunch a{};
     a.plan = r.plan->d;
@@ -482,51 +498,88 @@ struct PairIndex {
   }
 };
 
+// Per-quartet screening bounds (NULL: none) downloaded to the host; a quartet
+// with bound < tau is not evaluated (its shellset is written as zeros).
+mdx_status read_bounds(mdx_ctx* c, const double* bound, int64_t n, std::vector<double>& h, cudaStream_t s) {
+  h.clear();
+  if (!bound) return MDX_OK;
+  h.resize((size_t)n);
+  cudaError_t e = cudaMemcpyAsync(h.data(), bound, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bound download");
+  return MDX_OK;
+}
+
+// Adds quartet q (output offs[q], `size` doubles) to the batch, or to its
+// zero-filled list when its bound is below tau.
+void batch_add(Batch& bt, int64_t q, int2 qp, int64_t off, int64_t size, const std::vector<double>& hbound,
+               double tau) {
+  if (!hbound.empty() && hbound[(size_t)q] < tau) {
+    bt.zero.push_back(off);
+    bt.zero.push_back(size);
+    return;
+  }
+  bt.qp.push_back(qp);
+  bt.qoff.push_back(off);
+  bt.qcaller.push_back(q);
+}
+
 mdx_status make_batch4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,
-                       cudaStream_t s, bool call_ws = false) {
+                       cudaStream_t s, bool call_ws = false, const double* bound = nullptr, double tau = 0.0) {
   HostBasis hb;
   mdx_status st = fetch_basis(c, basis, hb, s);
   if (st != MDX_OK) return st;
   std::vector<int32_t> hq;
   if ((st = read_quartets(c, quartets, n, 4, hq, s)) != MDX_OK) return st;
+  std::vector<double> hbound;
+  if ((st = read_bounds(c, bound, n, hbound, s)) != MDX_OK) return st;
   Batch bt;
   PairIndex pix(bt);
   std::vector<int64_t> offs((size_t)n + 1);
   offs[0] = 0;
-  bt.qp.resize(n);
-  bt.qoff.resize(n);
+  bt.qp.reserve(n);
+  bt.qoff.reserve(n);
+  bt.qcaller.reserve(n);
   for (int64_t q = 0; q < n; ++q) {
     const int32_t* s4 = &hq[(size_t)q * 4];
     for (int k = 0; k < 4; ++k)
       if (s4[k] < 0 || s4[k] >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
-    bt.qp[q] = make_int2(pix(s4[0], s4[1], 0), pix(s4[2], s4[3], 0));
-    bt.qoff[q] = offs[q];
-    offs[q + 1] = offs[q] + (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * ncart(hb.l[s4[2]]) * ncart(hb.l[s4[3]]);
+    const int64_t size = (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * ncart(hb.l[s4[2]]) * ncart(hb.l[s4[3]]);
+    offs[q + 1] = offs[q] + size;
+    const int2 qp = hbound.empty() || hbound[(size_t)q] >= tau
+                        ? make_int2(pix(s4[0], s4[1], 0), pix(s4[2], s4[3], 0)) : make_int2(0, 0);
+    batch_add(bt, q, qp, offs[q], size, hbound, tau);
   }
   return batch_prepare(c, basis, nullptr, hb, hb, bt, offs, out, s, call_ws);
 }
 
 mdx_status make_batch3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
-                       mdx_batch** out, cudaStream_t s, bool call_ws = false) {
+                       mdx_batch** out, cudaStream_t s, bool call_ws = false, const double* bound = nullptr,
+                       double tau = 0.0) {
   HostBasis ha, ho;
   mdx_status st = fetch_basis(c, aux, ha, s);
   if (st != MDX_OK) return st;
   if ((st = fetch_basis(c, orb, ho, s)) != MDX_OK) return st;
   std::vector<int32_t> ht;
   if ((st = read_quartets(c, triplets, n, 3, ht, s)) != MDX_OK) return st;
+  std::vector<double> hbound;
+  if ((st = read_bounds(c, bound, n, hbound, s)) != MDX_OK) return st;
   Batch bt;
   PairIndex pix(bt);
   std::vector<int64_t> offs((size_t)n + 1);
   offs[0] = 0;
-  bt.qp.resize(n);
-  bt.qoff.resize(n);
+  bt.qp.reserve(n);
+  bt.qoff.reserve(n);
+  bt.qcaller.reserve(n);
   for (int64_t q = 0; q < n; ++q) {
     const int32_t* t3 = &ht[(size_t)q * 3];
     if (t3[0] < 0 || t3[0] >= ha.n || t3[1] < 0 || t3[1] >= ho.n || t3[2] < 0 || t3[2] >= ho.n)
       return fail(c, MDX_EINVAL, "shell index out of range");
-    bt.qp[q] = make_int2(pix(t3[0], -1, 0), pix(t3[1], t3[2], 1));
-    bt.qoff[q] = offs[q];
-    offs[q + 1] = offs[q] + (int64_t)ncart(ha.l[t3[0]]) * ncart(ho.l[t3[1]]) * ncart(ho.l[t3[2]]);
+    const int64_t size = (int64_t)ncart(ha.l[t3[0]]) * ncart(ho.l[t3[1]]) * ncart(ho.l[t3[2]]);
+    offs[q + 1] = offs[q] + size;
+    const int2 qp = hbound.empty() || hbound[(size_t)q] >= tau
+                        ? make_int2(pix(t3[0], -1, 0), pix(t3[1], t3[2], 1)) : make_int2(0, 0);
+    batch_add(bt, q, qp, offs[q], size, hbound, tau);
   }
   return batch_prepare(c, aux, orb, ha, ho, bt, offs, out, s, call_ws);
 }
@@ -604,20 +657,21 @@ mdx_status mdx_sync(mdx_ctx* c, void* stream) {
   return check_device_error(c, (cudaStream_t)stream);
 }
 
-mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
-                    int64_t out_capacity, int64_t* out_offsets, void* stream) {
+mdx_status mdx_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, const double* bound, int64_t n,
+                    double tau, double* out, int64_t out_capacity, int64_t* out_offsets, void* stream) {
   const NvtxRange nvtx_range("mdx_eri4");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (n < 0 || !out_offsets || (n > 0 && (!quartets || !out))) return fail(c, MDX_EINVAL, "invalid arguments");
+  if (bound && !(tau >= 0.0)) return fail(c, MDX_EINVAL, "tau must be >= 0");
   if (n == 0) {
     cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
     return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
   }
   mdx_batch* B = nullptr;
-  mdx_status st = make_batch4(c, basis, quartets, n, &B, s, true);
+  mdx_status st = make_batch4(c, basis, quartets, n, &B, s, true, bound, tau);
   if (st != MDX_OK) return st;
   return run_once(c, B, out, out_capacity, out_offsets, s);
 }
@@ -680,20 +734,22 @@ mdx_status mdx_eri4_sph(mdx_ctx* c, const mdx_basis* basis, const int32_t* quart
   return check_device_error(c, s);
 }
 
-mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
-                    double* out, int64_t out_capacity, int64_t* out_offsets, void* stream) {
+mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
+                    const double* bound, int64_t n, double tau, double* out, int64_t out_capacity,
+                    int64_t* out_offsets, void* stream) {
   const NvtxRange nvtx_range("mdx_eri3");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (n < 0 || !out_offsets || (n > 0 && (!triplets || !out))) return fail(c, MDX_EINVAL, "invalid arguments");
+  if (bound && !(tau >= 0.0)) return fail(c, MDX_EINVAL, "tau must be >= 0");
   if (n == 0) {
     cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
     return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
   }
   mdx_batch* B = nullptr;
-  mdx_status st = make_batch3(c, aux, orb, triplets, n, &B, s, true);
+  mdx_status st = make_batch3(c, aux, orb, triplets, n, &B, s, true, bound, tau);
   if (st != MDX_OK) return st;
   return run_once(c, B, out, out_capacity, out_offsets, s);
 }
@@ -982,23 +1038,26 @@ mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs,
 namespace {
 
 // Shared front end of the exchange build and its gradient: canonical distinct
-// pairs sorted by pair class, density-block maxima, Schwarz x density screening
-// of the unique quartets into (bra class, ket class) buckets on the GPU.
+// pairs sorted by pair class and, within a class, by decreasing Schwarz
+// factor; density-block maxima; Schwarz x density screening of the unique
+// quartets into (bra class, ket class) buckets on the GPU (FP64 throughout).
 struct XPrep {
   HostBasis hb;
   std::vector<int32_t> ao;
   int64_t nao = 0, np = 0, nq = 0;
-  struct P4 { int32_t i, j; double q; int li, lj, K; };
+  struct P4 { int32_t i, j; double q; int li, lj, K; int64_t orig; };
   std::vector<P4> pl;
   std::vector<std::array<int, 3>> classes;
   std::vector<unsigned long long> counts;
   std::vector<int64_t> boff;
   int2* d_pshell = nullptr;
   int2* d_quart = nullptr;
+  int64_t* d_orig = nullptr;   // caller index of each sorted pair
 };
 
+// fill = false: counts only (X.d_quart stays unset).
 mdx_status exchange_screen(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
-                           double tau, const double* D, XPrep& X, cudaStream_t s) {
+                           double tau, const double* D, XPrep& X, cudaStream_t s, bool fill = true) {
   if (!basis || !basis->ao_off) return fail(c, MDX_EINVAL, "basis needs ao_off");
   mdx_status st = fetch_basis(c, basis, X.hb, s);
   if (st != MDX_OK) return st;
@@ -1011,6 +1070,7 @@ mdx_status exchange_screen(mdx_ctx* c, const mdx_basis* basis, const int32_t* pa
   X.nao = 0;
   for (int i = 0; i < hb.n; ++i) X.nao = std::max<int64_t>(X.nao, (int64_t)X.ao[i] + ncart(hb.l[i]));
   if (X.nao > 2000000000 / 2) return fail(c, MDX_EUNSUPPORTED, "too many AOs");
+  if (n_pairs > 0x7fffffff) return fail(c, MDX_EUNSUPPORTED, "too many shell pairs");
   X.np = n_pairs;
   if (n_pairs == 0 || hb.n == 0) return MDX_OK;
   std::vector<int32_t> hp;
@@ -1024,37 +1084,80 @@ mdx_status exchange_screen(mdx_ctx* c, const mdx_basis* basis, const int32_t* pa
   for (int64_t p = 0; p < n_pairs; ++p) {
     int32_t i = hp[2 * p], j = hp[2 * p + 1];
     if (i < 0 || i >= hb.n || j < 0 || j >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
+    if (!(hq[p] >= 0.0)) return fail(c, MDX_EINVAL, "Schwarz factors must be >= 0");
     if (i < j) std::swap(i, j);
     if (!seen.emplace((int64_t)i * hb.n + j, 1).second) return fail(c, MDX_EINVAL, "shell pair listed twice");
-    X.pl[p] = XPrep::P4{i, j, hq[p], hb.l[i], hb.l[j], hb.nprim[i] * hb.nprim[j]};
+    X.pl[p] = XPrep::P4{i, j, hq[p], hb.l[i], hb.l[j], hb.nprim[i] * hb.nprim[j], p};
   }
   std::stable_sort(X.pl.begin(), X.pl.end(), [](const XPrep::P4& a, const XPrep::P4& b) {
     if (a.li != b.li) return a.li < b.li;
     if (a.lj != b.lj) return a.lj < b.lj;
-    return a.K < b.K;
+    if (a.K != b.K) return a.K < b.K;
+    return a.q > b.q;
   });
+  // one molecule: each class is one segment, listed in pair order (already Q-descending)
   std::vector<int2> pshell(n_pairs);
-  std::vector<int32_t> pclass(n_pairs);
-  std::vector<float> qf(n_pairs);
+  std::vector<int32_t> pclass(n_pairs), order(n_pairs), seg_class, mol_seg{0, 0}, shell_first{0, hb.n};
+  std::vector<int64_t> pos(n_pairs), seg_begin, orig(n_pairs), dmax_off{0};
+  std::vector<double> qd(n_pairs);
   for (int64_t p = 0; p < n_pairs; ++p) {
     std::array<int, 3> k{X.pl[p].li, X.pl[p].lj, X.pl[p].K};
-    if (X.classes.empty() || X.classes.back() != k) X.classes.push_back(k);
+    if (X.classes.empty() || X.classes.back() != k) {
+      X.classes.push_back(k);
+      seg_begin.push_back(p);
+      seg_class.push_back((int32_t)X.classes.size() - 1);
+    }
     pclass[p] = (int32_t)X.classes.size() - 1;
     pshell[p] = make_int2(X.pl[p].i, X.pl[p].j);
-    qf[p] = (float)X.pl[p].q;
+    qd[p] = X.pl[p].q;
+    order[p] = (int32_t)p;
+    pos[p] = p;
+    orig[p] = X.pl[p].orig;
   }
+  seg_begin.push_back(n_pairs);
+  mol_seg[1] = (int32_t)seg_class.size();
   const int nclass = (int)X.classes.size();
   const int64_t nbucket = (int64_t)nclass * (nclass + 1) / 2;
-  int32_t* d_pclass; float *d_q, *d_dmax; unsigned long long* d_counts; int64_t* d_boff;
+  int32_t *d_pclass, *d_order, *d_segc, *d_molseg, *d_sfirst;
+  int64_t *d_pos, *d_segb, *d_doff, *d_boff;
+  double *d_q, *d_dmax, *d_rowmax;
+  unsigned long long* d_counts;
   if ((st = upload(c, "x_pshell", pshell, &X.d_pshell, s)) != MDX_OK) return st;
   if ((st = upload(c, "x_pclass", pclass, &d_pclass, s)) != MDX_OK) return st;
-  if ((st = upload(c, "x_q", qf, &d_q, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_q", qd, &d_q, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_order", order, &d_order, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_pos", pos, &d_pos, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_orig", orig, &X.d_orig, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_segb", seg_begin, &d_segb, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_segc", seg_class, &d_segc, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_molseg", mol_seg, &d_molseg, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_sfirst", shell_first, &d_sfirst, s)) != MDX_OK) return st;
+  if ((st = upload(c, "x_doff", dmax_off, &d_doff, s)) != MDX_OK) return st;
+  // the N_shells x N_shells table of density-block maxima (8 bytes per shell pair)
   if ((st = ensure(c, "x_dmax", (size_t)hb.n * hb.n, &d_dmax, s)) != MDX_OK) return st;
+  if ((st = ensure(c, "x_rowmax", (size_t)hb.n, &d_rowmax, s)) != MDX_OK) return st;
   if ((st = ensure(c, "x_counts", (size_t)nbucket, &d_counts, s)) != MDX_OK) return st;
   e = launch_dmax(D, (int32_t)X.nao, basis->ao_off, basis->l, hb.n, d_dmax, hb.n, s);
+  if (e == cudaSuccess) e = launch_rowmax(d_dmax, hb.n, d_rowmax, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
-  ScreenArgs sa{n_pairs, X.d_pshell, d_pclass, d_q, d_dmax, hb.n, nclass, (float)tau, d_counts, nullptr, nullptr,
-                nullptr};
+  ScreenArgs sa{};
+  sa.npairs = n_pairs;
+  sa.pair_shells = X.d_pshell;
+  sa.Q = d_q;
+  sa.pair_class = d_pclass;
+  sa.pos = d_pos;
+  sa.order = d_order;
+  sa.seg_begin = d_segb;
+  sa.seg_class = d_segc;
+  sa.mol_seg = d_molseg;
+  sa.pair_mol = nullptr;
+  sa.shell_first = d_sfirst;
+  sa.dmax_off = d_doff;
+  sa.dmax = d_dmax;
+  sa.rowmax = d_rowmax;
+  sa.nclass = nclass;
+  sa.tau = tau;
+  sa.counts = d_counts;
   if (e == cudaSuccess) e = launch_screen(sa, false, s);
   X.counts.assign(nbucket, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(X.counts.data(), d_counts, nbucket * sizeof(unsigned long long),
@@ -1065,7 +1168,7 @@ mdx_status exchange_screen(mdx_ctx* c, const mdx_basis* basis, const int32_t* pa
   for (int64_t b = 0; b < nbucket; ++b) X.boff[b + 1] = X.boff[b] + (int64_t)X.counts[b];
   X.nq = X.boff[nbucket];
   c->last_quartets = X.nq;
-  if (X.nq > 0) {
+  if (X.nq > 0 && fill) {
     if ((st = upload(c, "x_boff", X.boff, &d_boff, s)) != MDX_OK) return st;
     if ((st = ensure(c, "x_quart", (size_t)X.nq, &X.d_quart, s)) != MDX_OK) return st;
     e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
@@ -1098,7 +1201,7 @@ QuartetLaunch base_launch(mdx_ctx* c, Plan* plan, const int2* qp, int64_t nq, co
 extern "C" {
 
 mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q, int64_t n_pairs,
-                        double tau, const double* D, double* K, void* stream) {
+                        double tau, const double* D, double* K, double alpha, double* energy, void* stream) {
   const NvtxRange nvtx_range("mdx_exchange");
   if (!c) return MDX_EINVAL;
   c->last_error.clear();
@@ -1110,6 +1213,7 @@ mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs
   mdx_status st = exchange_screen(c, basis, pairs, Q, n_pairs, tau, D, X, s);
   if (st != MDX_OK) return st;
   cudaError_t e = cudaMemsetAsync(K, 0, (size_t)X.nao * X.nao * sizeof(double), s);
+  if (e == cudaSuccess && energy) e = cudaMemsetAsync(energy, 0, sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "K clear");
   if (X.nq > 0) {
     const HostBasis& hb = X.hb;
@@ -1163,8 +1267,51 @@ mdx_status mdx_exchange(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs
     if (e != cudaSuccess) return cuda_fail(c, e, "exchange quartet launch");
   }
   e = launch_symmetrize(K, (int32_t)X.nao, s);
+  // E_x = alpha sum_ik D_ik K_ik = alpha sum_ijkl D_ik D_jl (ij|kl)
+  if (e == cudaSuccess && energy) e = launch_dot_energy(D, K, X.nao * X.nao, alpha, energy, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "exchange");
+  return check_device_error(c, s);
+}
+
+mdx_status mdx_exchange_screen(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs, const double* Q,
+                               int64_t n_pairs, double tau, const double* D, int32_t* kept, int64_t kept_capacity,
+                               int64_t* n_kept, double* model_flops, void* stream) {
+  const NvtxRange nvtx_range("mdx_exchange_screen");
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_pairs < 0 || !D || !n_kept || (n_pairs > 0 && (!pairs || !Q)) || !(tau >= 0.0) || kept_capacity < 0 ||
+      (kept_capacity > 0 && !kept))
+    return fail(c, MDX_EINVAL, "invalid arguments");
+  *n_kept = 0;
+  if (model_flops) *model_flops = 0.0;
+  XPrep X;
+  // count first; list only when the caller asked for it and it fits
+  mdx_status st = exchange_screen(c, basis, pairs, Q, n_pairs, tau, D, X, s, false);
+  if (st != MDX_OK) return st;
+  *n_kept = X.nq;
+  if (model_flops) {
+    double f = 0.0;
+    const int nclass = (int)X.classes.size();
+    for (int cp = 0; cp < nclass; ++cp)
+      for (int cq = 0; cq <= cp; ++cq) {
+        const int64_t b = (int64_t)cp * (cp + 1) / 2 + cq;
+        const ClassKey key{X.classes[cp][0], X.classes[cp][1], X.classes[cq][0], X.classes[cq][1], X.classes[cp][2],
+                           X.classes[cq][2], 0};
+        f += model_flops_class(key) * (double)X.counts[b];
+      }
+    *model_flops = f;
+  }
+  if (!kept || X.nq == 0) return check_device_error(c, s);
+  if (X.nq > kept_capacity) return fail(c, MDX_ECAPACITY, "kept-quartet capacity too small");
+  XPrep X2;
+  if ((st = exchange_screen(c, basis, pairs, Q, n_pairs, tau, D, X2, s, true)) != MDX_OK) return st;
+  if (X2.nq != X.nq) return fail(c, MDX_EDEVICE, "screening counts differ between passes");
+  cudaError_t e = launch_map_pairs(X2.d_quart, X2.nq, X2.d_orig, kept, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange screening");
   return check_device_error(c, s);
 }
 
@@ -1491,14 +1638,12 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
   std::vector<std::array<int, 3>> classes;
   std::vector<int2> pshell(np);
   std::vector<int32_t> pclass_raw(np), pmol(np);
-  std::vector<int64_t> pfirst(np);
   for (int64_t p = 0; p < np; ++p) {
     std::array<int, 3> k{pl[p].li, pl[p].lj, pl[p].K};
     auto it = cid.find(k);
     if (it == cid.end()) it = cid.emplace(k, 0).first;
     pshell[p] = make_int2(pl[p].i, pl[p].j);
     pmol[p] = pl[p].m;
-    pfirst[p] = (p > 0 && pl[p - 1].m == pl[p].m) ? pfirst[p - 1] : p;
   }
   // class ids ordered like the in-molecule sort, so class(q) <= class(p) for q <= p in a molecule
   { int k = 0; for (auto& kv : cid) { kv.second = k++; classes.push_back(kv.first); } }
@@ -1507,9 +1652,9 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
   const int64_t nbucket = (int64_t)nclass * (nclass + 1) / 2;
   if ((st = dev_upload(c, pshell, &X->pshell, s)) != MDX_OK) return st;
   if ((st = dev_upload(c, pmol, &X->pmol, s)) != MDX_OK) return st;
-  int32_t* d_pclass; int64_t* d_pfirst;
+  int32_t* d_pclass;
   if ((st = upload(c, "xb_pclass", pclass_raw, &d_pclass, s)) != MDX_OK) return st;
-  if ((st = upload(c, "xb_pfirst", pfirst, &d_pfirst, s)) != MDX_OK) return st;
+  if (np > 0x7fffffff) return fail(c, MDX_EUNSUPPORTED, "too many shell pairs");
   // Schwarz factors and primitive-pair records of every pair (records stay with the batch)
   std::vector<int64_t> prec(np);
   std::vector<PrimPairJob> jobs;
@@ -1570,22 +1715,67 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
     e = cudaMemcpyAsync(hQ.data(), d_Q, np * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "Schwarz");
-    std::vector<float> qf(np);
-    for (int64_t p = 0; p < np; ++p) qf[p] = (float)hQ[p];
-    float* d_qf;
-    if ((st = upload(c, "xb_qf", qf, &d_qf, s)) != MDX_OK) return st;
-    // density-block maxima of every molecule (block diagonal of one n_tot x n_tot table)
-    float* d_dmax;
-    if ((st = ensure(c, "xb_dmax", (size_t)ntot * ntot, &d_dmax, s)) != MDX_OK) return st;
+    // segments of one molecule and one class (contiguous in pair order), each listed by decreasing Q
+    std::vector<int32_t> order(np), seg_class, mol_seg(n_mol + 1, 0);
+    std::vector<int64_t> pos(np), seg_begin;
+    for (int64_t p = 0; p < np; ++p) {
+      if (p == 0 || pl[p].m != pl[p - 1].m || pclass_raw[p] != pclass_raw[p - 1]) {
+        seg_begin.push_back(p);
+        seg_class.push_back(pclass_raw[p]);
+        for (int m = pl[p].m + 1; m <= n_mol; ++m) mol_seg[m] = (int32_t)seg_class.size();
+      }
+      order[p] = (int32_t)p;
+    }
+    seg_begin.push_back(np);
+    for (size_t g = 0; g + 1 < seg_begin.size(); ++g)
+      std::stable_sort(order.begin() + seg_begin[g], order.begin() + seg_begin[g + 1],
+                       [&](int32_t x, int32_t y) { return hQ[x] > hQ[y]; });
+    for (int64_t i = 0; i < np; ++i) pos[order[i]] = i;
+    // density-block maxima: one [n_m][n_m] table per molecule, back to back
+    std::vector<int64_t> dmax_off(n_mol + 1, 0);
+    for (int m = 0; m < n_mol; ++m) {
+      const int64_t nm = shell_first[m + 1] - shell_first[m];
+      dmax_off[m + 1] = dmax_off[m] + nm * nm;
+    }
+    int32_t *d_order, *d_segc, *d_molseg, *d_sfirst;
+    int64_t *d_pos, *d_segb, *d_dmoff;
+    double *d_dmax, *d_rowmax;
+    if ((st = upload(c, "xb_order", order, &d_order, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_pos", pos, &d_pos, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_segb", seg_begin, &d_segb, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_segc", seg_class, &d_segc, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_molseg", mol_seg, &d_molseg, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_sfirst", shell_first, &d_sfirst, s)) != MDX_OK) return st;
+    if ((st = upload(c, "xb_dmoff", dmax_off, &d_dmoff, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "xb_dmax", (size_t)std::max<int64_t>(dmax_off[n_mol], 1), &d_dmax, s)) != MDX_OK) return st;
+    if ((st = ensure(c, "xb_rowmax", (size_t)std::max<int32_t>(ntot, 1), &d_rowmax, s)) != MDX_OK) return st;
     for (int m = 0; m < n_mol; ++m) {
       const int32_t f = shell_first[m], nm = shell_first[m + 1] - f;
-      e = launch_dmax(D[m], mol_nao[m], X->ao_off + f, X->l + f, nm, d_dmax + (int64_t)f * ntot + f, ntot, s);
+      e = launch_dmax(D[m], mol_nao[m], X->ao_off + f, X->l + f, nm, d_dmax + dmax_off[m], nm, s);
+      if (e == cudaSuccess) e = launch_rowmax(d_dmax + dmax_off[m], nm, d_rowmax + f, s);
       if (e != cudaSuccess) return cuda_fail(c, e, "density maxima");
     }
     unsigned long long* d_counts;
     if ((st = ensure(c, "xb_counts", (size_t)nbucket, &d_counts, s)) != MDX_OK) return st;
     e = cudaMemsetAsync(d_counts, 0, nbucket * sizeof(unsigned long long), s);
-    ScreenArgs sa{np, X->pshell, d_pclass, d_qf, d_dmax, ntot, nclass, (float)tau, d_counts, nullptr, nullptr, d_pfirst};
+    ScreenArgs sa{};
+    sa.npairs = np;
+    sa.pair_shells = X->pshell;
+    sa.Q = d_Q;
+    sa.pair_class = d_pclass;
+    sa.pos = d_pos;
+    sa.order = d_order;
+    sa.seg_begin = d_segb;
+    sa.seg_class = d_segc;
+    sa.mol_seg = d_molseg;
+    sa.pair_mol = X->pmol;
+    sa.shell_first = d_sfirst;
+    sa.dmax_off = d_dmoff;
+    sa.dmax = d_dmax;
+    sa.rowmax = d_rowmax;
+    sa.nclass = nclass;
+    sa.tau = tau;
+    sa.counts = d_counts;
     if (e == cudaSuccess) e = launch_screen(sa, false, s);
     std::vector<unsigned long long> counts(nbucket);
     if (e == cudaSuccess) e = cudaMemcpyAsync(counts.data(), d_counts, nbucket * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
@@ -1680,12 +1870,12 @@ mdx_status mdx_xbatch_create(mdx_ctx* c, int32_t n_mol, const mdx_basis* bases, 
         if (reg_class) X->reg_launches.push_back((int32_t)(X->launches.size() - 1));
       }
     // heaviest items first (the queue hands them out in order)
-    std::vector<size_t> order(items.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<size_t> iorder(items.size());
+    for (size_t i = 0; i < iorder.size(); ++i) iorder[i] = i;
+    std::stable_sort(iorder.begin(), iorder.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
     // all items (mode 1), and the items of the classes without a register kernel (mode 2)
     std::vector<WorkItem> sorted, sorted_team;
-    for (size_t i : order) {
+    for (size_t i : iorder) {
       sorted.push_back(items[i]);
       if (!item_reg[i]) sorted_team.push_back(items[i]);
     }

@@ -778,9 +778,24 @@ cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Screened-out shellsets: one block per range (grid-strided), threads over its doubles.
+__global__ void k_zero_ranges(const int64_t* __restrict__ ranges, int64_t n, double* __restrict__ out) {
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const int64_t off = ranges[2 * r], len = ranges[2 * r + 1];
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) out[off + i] = 0.0;
+  }
+}
+
+cudaError_t launch_zero_ranges(const int64_t* ranges, int64_t n, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(n, 65536);
+  k_zero_ranges<<<grid, 256, 0, s>>>(ranges, n, out);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- exchange support
 __global__ void k_dmax(const double* __restrict__ D, int32_t nao, const int32_t* __restrict__ ao_off,
-                       const int32_t* __restrict__ l, int32_t n, float* __restrict__ dmax, int64_t ld) {
+                       const int32_t* __restrict__ l, int32_t n, double* __restrict__ dmax, int64_t ld) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)n * n) return;
   const int x = (int)(g / n), y = (int)(g - (int64_t)x * n);
@@ -789,43 +804,128 @@ __global__ void k_dmax(const double* __restrict__ D, int32_t nao, const int32_t*
   double m = 0.0;
   for (int r = 0; r < nr; ++r)
     for (int c = 0; c < nc; ++c) m = fmax(m, fabs(D[(r0 + r) * nao + c0 + c]));
-  dmax[(int64_t)x * ld + y] = (float)m;
+  dmax[(int64_t)x * ld + y] = m;
 }
 
 cudaError_t launch_dmax(const double* D, int32_t nao, const int32_t* ao_off, const int32_t* l, int32_t n_shells,
-                        float* dmax, int64_t ld, cudaStream_t s) {
+                        double* dmax, int64_t ld, cudaStream_t s) {
   const int64_t tot = (int64_t)n_shells * n_shells;
   if (tot <= 0) return cudaSuccess;
   k_dmax<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, nao, ao_off, l, n_shells, dmax, ld);
   return cudaGetLastError();
 }
 
-// Unique quartets (p, q), q <= p, kept when Q_p Q_q max(|D_ik|,|D_il|,|D_jk|,|D_jl|) >= tau
-// (Schwarz bound times the largest density block the quartet touches).
-// Counting pass: per-bucket totals; fill pass: write (p, q) into its bucket.
-__global__ void k_screen(const ScreenArgs a, bool fill) {
+__global__ void k_rowmax(const double* __restrict__ dmax, int32_t n, double* __restrict__ rowmax) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* r = dmax + (int64_t)i * n;
+  double m = 0.0;
+  for (int k = 0; k < n; ++k) m = fmax(m, r[k]);
+  rowmax[i] = m;
+}
+
+cudaError_t launch_rowmax(const double* dmax, int32_t n, double* rowmax, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_rowmax<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(dmax, n, rowmax);
+  return cudaGetLastError();
+}
+
+// One block per bra pair p (see ScreenArgs). Counting pass: per-bucket totals;
+// fill pass: (p, q) written into its bucket. One atomic per warp and step:
+// the kept lanes of a warp take consecutive slots.
+__global__ void __launch_bounds__(256) k_screen(const ScreenArgs a, bool fill) {
   const int64_t p = blockIdx.x;
   if (p >= a.npairs) return;
   const int2 ij = a.pair_shells[p];
-  const float qp = a.Q[p];
+  const double qp = a.Q[p];
   const int cp = a.pair_class[p];
-  const float* di = a.dmax + (int64_t)ij.x * a.n_shells;
-  const float* dj = a.dmax + (int64_t)ij.y * a.n_shells;
-  const int64_t brow = (int64_t)cp * (cp + 1) / 2;
-  const int64_t q0 = a.pair_first ? a.pair_first[p] : 0;   // quartets stay inside one molecule
-  for (int64_t q = q0 + threadIdx.x; q <= p; q += blockDim.x) {
-    const int2 kl = a.pair_shells[q];
-    const float dm = fmaxf(fmaxf(di[kl.x], di[kl.y]), fmaxf(dj[kl.x], dj[kl.y]));
-    if (qp * a.Q[q] * dm < a.tau) continue;
-    const int64_t b = brow + a.pair_class[q];
-    const unsigned long long slot = atomicAdd(a.counts + b, 1ull);
-    if (fill) a.out[a.bucket_off[b] + (int64_t)slot] = make_int2((int)p, (int)q);
+  const int m = a.pair_mol ? a.pair_mol[p] : 0;
+  const int f = a.shell_first[m], nm = a.shell_first[m + 1] - f;
+  const double* dm = a.dmax + a.dmax_off[m];
+  const double* di = dm + (int64_t)(ij.x - f) * nm;
+  const double* dj = dm + (int64_t)(ij.y - f) * nm;
+  const double dr = fmax(a.rowmax[ij.x], a.rowmax[ij.y]);
+  const double tau = a.tau;
+  const int lane = threadIdx.x & 31;
+  const unsigned lower = (1u << lane) - 1u;
+  for (int g = a.mol_seg[m]; g < a.mol_seg[m + 1]; ++g) {
+    const int cq = a.seg_class[g];
+    if (cq > cp) break;
+    const int64_t b0 = a.seg_begin[g];
+    const int64_t e0 = cq == cp ? a.pos[p] + 1 : a.seg_begin[g + 1];
+    // first position whose Q_p Q_q rowmax falls below tau (Q decreasing along the segment)
+    int64_t lo = b0, hi = e0;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (qp * a.Q[a.order[mid]] * dr >= tau) lo = mid + 1; else hi = mid;
+    }
+    const int64_t cut = lo;
+    const int64_t bucket = (int64_t)cp * (cp + 1) / 2 + cq;
+    for (int64_t base = b0; base < cut; base += blockDim.x) {
+      const int64_t i = base + threadIdx.x;
+      bool keep = false;
+      int q = 0;
+      if (i < cut) {
+        q = a.order[i];
+        const int2 kl = a.pair_shells[q];
+        const double d = fmax(fmax(di[kl.x - f], di[kl.y - f]), fmax(dj[kl.x - f], dj[kl.y - f]));
+        keep = qp * a.Q[q] * d >= tau;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      if (!mask) continue;
+      const int leader = __ffs(mask) - 1;
+      unsigned long long slot = 0;
+      if (lane == leader) slot = atomicAdd(a.counts + bucket, (unsigned long long)__popc(mask));
+      slot = __shfl_sync(0xffffffffu, slot, leader);
+      if (fill && keep) a.out[a.bucket_off[bucket] + (int64_t)slot + __popc(mask & lower)] = make_int2((int)p, q);
+    }
   }
 }
 
 cudaError_t launch_screen(const ScreenArgs& a, bool fill, cudaStream_t s) {
   if (a.npairs <= 0) return cudaSuccess;
+  if (a.npairs > 0x7fffffff) return cudaErrorInvalidValue;
   k_screen<<<(unsigned)a.npairs, 256, 0, s>>>(a, fill);
+  return cudaGetLastError();
+}
+
+__global__ void k_map_pairs(const int2* __restrict__ qp, int64_t n, const int64_t* __restrict__ orig,
+                            int32_t* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int2 v = qp[k];
+  out[2 * k] = (int32_t)orig[v.x];
+  out[2 * k + 1] = (int32_t)orig[v.y];
+}
+
+cudaError_t launch_map_pairs(const int2* qp, int64_t n, const int64_t* orig, int32_t* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_map_pairs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(qp, n, orig, out);
+  return cudaGetLastError();
+}
+
+// energy += alpha sum_i D[i] K[i] over n doubles (block sums, one atomic per block)
+__global__ void __launch_bounds__(256) k_dot_energy(const double* __restrict__ D, const double* __restrict__ K,
+                                                    int64_t n, double alpha, double* energy) {
+  __shared__ double part[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(D[i], K[i], acc);
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    atomicAdd(energy, alpha * t);
+  }
+}
+
+cudaError_t launch_dot_energy(const double* D, const double* K, int64_t n, double alpha, double* energy,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 2048);
+  k_dot_energy<<<grid, 256, 0, s>>>(D, K, n, alpha, energy);
   return cudaGetLastError();
 }
 

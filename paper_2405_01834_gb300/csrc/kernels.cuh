@@ -90,29 +90,52 @@ cudaError_t launch_persistent(const PersistLaunch& pl, int64_t smem_bytes, int g
 const void* persistent_kernel_ptr();
 
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s);
+// Writes zeros over n output ranges given as (offset, doubles) pairs (screened-out shellsets).
+cudaError_t launch_zero_ranges(const int64_t* ranges, int64_t n, double* out, cudaStream_t s);
 // Gradient epilogue over shellsets already in memory (V + q N_b N_k for quartet q of launch a).
 cudaError_t launch_grad_contract(const QuartetLaunch& a, const double* V, cudaStream_t s);
 
-// Exchange support: per shell-pair block max |D| (float), screening of unique
-// quartets into class buckets, K <- K + K^T.
+// Exchange support: per shell-pair block max |D| (FP64), per-shell row maxima
+// of that table, screening of unique quartets into class buckets, K <- K + K^T.
 cudaError_t launch_dmax(const double* D, int32_t nao, const int32_t* ao_off, const int32_t* l, int32_t n_shells,
-                        float* dmax, int64_t ld, cudaStream_t s);
+                        double* dmax, int64_t ld, cudaStream_t s);
+// rowmax[i] = max_k dmax[i * n + k] for the n shells of one table
+cudaError_t launch_rowmax(const double* dmax, int32_t n, double* rowmax, cudaStream_t s);
+// Unique quartets (p, q) of a pair list kept when Q_p Q_q max(|D_ik|,|D_il|,|D_jk|,|D_jl|) >= tau,
+// evaluated in FP64 exactly in that order. Pairs are grouped into segments of one molecule and one
+// pair class, each listed in `order` by decreasing Q; q runs over the segments of p's molecule whose
+// class is <= p's class (in its own segment up to p's position), so every unordered pair of pairs is
+// tested once. A binary search stops each segment where Q_p Q_q rowmax < tau (every later q of the
+// descending segment fails too, since the product is monotone in Q_q and the block maximum is at most
+// the row maximum).
 struct ScreenArgs {
   int64_t npairs;
-  const int2* pair_shells;   // sorted by pair class
-  const int32_t* pair_class; // class index of each pair (non-decreasing)
-  const float* Q;            // Schwarz factor per pair
-  const float* dmax;         // [n_shells][n_shells]
-  int32_t n_shells;
+  const int2* pair_shells;     // per pair (i, j)
+  const double* Q;             // Schwarz factor per pair
+  const int32_t* pair_class;   // class index per pair
+  const int64_t* pos;          // position of each pair in `order`
+  const int32_t* order;        // pair indices, segment by segment, Q decreasing within a segment
+  const int64_t* seg_begin;    // [nseg + 1] first position of each segment in `order`
+  const int32_t* seg_class;    // class of each segment (increasing within a molecule)
+  const int32_t* mol_seg;      // [nmol + 1] first segment of each molecule
+  const int32_t* pair_mol;     // molecule of each pair (NULL: one molecule)
+  const int32_t* shell_first;  // [nmol + 1] first shell of each molecule
+  const int64_t* dmax_off;     // [nmol] start of each molecule's [n_m][n_m] table in dmax
+  const double* dmax;
+  const double* rowmax;        // per shell (global shell numbering)
   int32_t nclass;
-  float tau;
-  unsigned long long* counts;  // [nclass*(nclass+1)/2]
+  double tau;
+  unsigned long long* counts;  // [nclass*(nclass+1)/2] bucket (cp, cq), cp >= cq, at cp*(cp+1)/2 + cq
   const int64_t* bucket_off;   // fill pass: start of each bucket
   int2* out;                   // fill pass: (p, q) per surviving quartet
-  const int64_t* pair_first;   // first pair of p's molecule (NULL: one molecule)
 };
 cudaError_t launch_screen(const ScreenArgs& a, bool fill, cudaStream_t s);
+// out[2k], out[2k+1] = orig[qp[k].x], orig[qp[k].y] (sorted pair indices back to caller indices)
+cudaError_t launch_map_pairs(const int2* qp, int64_t n, const int64_t* orig, int32_t* out, cudaStream_t s);
 cudaError_t launch_symmetrize(double* K, int32_t nao, cudaStream_t s);
+// *energy += alpha sum_i D[i] K[i] over n doubles (the caller zeroes *energy)
+cudaError_t launch_dot_energy(const double* D, const double* K, int64_t n, double alpha, double* energy,
+                              cudaStream_t s);
 // K <- 0 (zero = true) or K <- K + K^T (zero = false) for nmol molecules; K and nao are device arrays
 cudaError_t launch_multi_k(double* const* K, const int32_t* nao, int32_t nmol, int64_t max_nao, bool zero,
                            cudaStream_t s);

@@ -209,23 +209,32 @@ extern "C" mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* qu
   }
   if (o > kScratchBytes) return MDX_ESCRATCH;   // request larger than the fixed scratch
 
+  // From the first copy into the scratch on, every return waits for the
+  // stream: work already queued may still read the shared array (and the host
+  // vectors it is copied from), and the next call, on any stream, rewrites it
+  // as soon as the lock is released.
+  auto drained = [s](mdx_status code) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return code;
+  };
   for (const Region& r : regs)
     if (r.src && r.bytes) {
       e = cudaMemcpyAsync(st.base + r.off, r.src, r.bytes, cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) return MDX_ECUDA;
+      if (e != cudaSuccess) return drained(MDX_ECUDA);
     }
   // the error word is the only scratch that must start at zero; everything
   // else is fully written before it is read
   e = cudaMemsetAsync(st.err, 0, sizeof(int), s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out_offsets, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return MDX_ECUDA;
+  if (e != cudaSuccess) return drained(MDX_ECUDA);
   const BasisDev bd{basis->l, basis->nprim, basis->prim_off, basis->center, basis->exps, basis->coefs};
   double* recs = (double*)(st.base + o_recs);
   double* recs_s = (double*)(st.base + o_recs_s);
   e = launch_pair_records(bd, bd, (const PrimPairJob*)(st.base + o_jobs), (int64_t)jobs.size(), recs, recs_s,
                           st.err, s);
-  if (e != cudaSuccess) return MDX_ECUDA;
+  if (e != cudaSuccess) return drained(MDX_ECUDA);
   for (size_t c = 0; c < ranges.size(); ++c) {
     QuartetLaunch a{};
     a.plan = pdev[c];
@@ -241,12 +250,12 @@ extern "C" mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* qu
     a.out = out;
     a.err = st.err;
     e = launch_quartets(a, s);
-    if (e != cudaSuccess) return MDX_ECUDA;
+    if (e != cudaSuccess) return drained(MDX_ECUDA);
   }
   int h = 0;
   e = cudaMemcpyAsync(&h, st.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host arrays above are released on return
-  if (e != cudaSuccess) return MDX_ECUDA;
+  if (e != cudaSuccess) return drained(MDX_ECUDA);
   if (h == kDevTimeout) return MDX_ETIMEOUT;
   if (h != kDevOk) return MDX_EDEVICE;
   return MDX_OK;

@@ -45,16 +45,39 @@ def plan_info(la, lb, lc, ld, Kb=1, Kk=1, one_centre=False) -> PlanStats:
     return st
 
 
+def _check_out(out: torch.Tensor, what: str):
+    """Output buffers cross the ABI as a pointer and a capacity in doubles: only a contiguous
+    float64 CUDA tensor has that meaning (anything else would be written past its end)."""
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous():
+        raise MdxError("%s: out must be a contiguous float64 CUDA tensor" % what)
+
+
+def _opt_ptr(t):
+    return None if t is None else t.data_ptr()
+
+
 def eri4_noalloc(basis: "DeviceBasis", quartets, out: torch.Tensor):
     """mdx_eri4_noalloc on the current device: [ab|cd] into the caller's `out`
     with no device allocation by the library (for callers whose device memory
     is owned by their own pool). Returns (status, offsets[n+1])."""
     lib = load()
+    _check_out(out, "mdx_eri4_noalloc")
     q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
     offs = torch.empty(q.shape[0] + 1, dtype=torch.int64, device="cuda")
     st = lib.mdx_eri4_noalloc(ctypes.byref(basis.desc), q.data_ptr(), q.shape[0], out.data_ptr(), out.numel(),
                               offs.data_ptr(), _stream())
     return st, offs
+
+
+def fp64_peak(kind: int = 0, reps: int = 3) -> float:
+    """Measured FP64 throughput (GFLOP/s) of the current device: kind 0 DFMA,
+    1/2/3 the f64 mma.sync shapes m8n8k4 / m16n8k4 / m16n8k16 (mdx_fp64_peak)."""
+    lib = load()
+    g = ctypes.c_double()
+    st = lib.mdx_fp64_peak(int(kind), int(reps), ctypes.byref(g), _stream())
+    if st != 0:
+        raise MdxError("mdx_fp64_peak(%d): %s" % (kind, STATUS.get(st, st)))
+    return g.value
 
 
 def library_path() -> str:
@@ -81,11 +104,12 @@ def load(build_if_missing: bool = True):
     lib.mdx_last_error.restype = ctypes.c_char_p
     lib.mdx_sync.argtypes = [P, P]
     lib.mdx_sync.restype = I32
-    lib.mdx_eri4.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
+    lib.mdx_eri4.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, I64, P, P]
     lib.mdx_eri4.restype = I32
     lib.mdx_eri4_sph.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
     lib.mdx_eri4_sph.restype = I32
-    lib.mdx_eri3.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
+    lib.mdx_eri3.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, I64,
+                             P, P]
     lib.mdx_eri3.restype = I32
     lib.mdx_schwarz.argtypes = [P, ctypes.POINTER(_Basis), P, I64, P, P]
     lib.mdx_schwarz.restype = I32
@@ -105,11 +129,15 @@ def load(build_if_missing: bool = True):
     lib.mdx_batch_autotune.restype = I32
     lib.mdx_batch_destroy.argtypes = [P]
     lib.mdx_batch_destroy.restype = None
-    lib.mdx_exchange.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, P, P]
+    lib.mdx_exchange.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, P, ctypes.c_double, P,
+                                 P]
     lib.mdx_exchange.restype = I32
     lib.mdx_exchange_grad.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, ctypes.c_double,
                                       ctypes.c_int32, P, P, P]
     lib.mdx_exchange_grad.restype = I32
+    lib.mdx_exchange_screen.argtypes = [P, ctypes.POINTER(_Basis), P, P, I64, ctypes.c_double, P, P, I64,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), P]
+    lib.mdx_exchange_screen.restype = I32
     lib.mdx_last_quartet_count.argtypes = [P]
     lib.mdx_last_quartet_count.restype = I64
     lib.mdx_eri4_noalloc.argtypes = [ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
@@ -134,6 +162,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_batch_run_materialized.restype = I32
     lib.mdx_set_class_shape.argtypes = [P] + [I32] * 10
     lib.mdx_set_class_shape.restype = I32
+    lib.mdx_fp64_peak.argtypes = [I32, I32, ctypes.POINTER(ctypes.c_double), P]
+    lib.mdx_fp64_peak.restype = I32
     _lib = lib
     return lib
 
@@ -202,18 +232,25 @@ class Engine:
         self._check(self.lib.mdx_sync(self.ctx, _stream()), "mdx_sync")
 
     # ----------------------------------------------------------------
-    def eri4(self, basis: DeviceBasis, quartets, out: torch.Tensor = None):
-        """[ab|cd] for quartets [n,4] (device int32). Returns (values, offsets[n+1])."""
+    def eri4(self, basis: DeviceBasis, quartets, out: torch.Tensor = None, bound=None, tau: float = 0.0):
+        """[ab|cd] for quartets [n,4] (device int32). Returns (values, offsets[n+1]).
+        bound: optional [n] upper bounds on |(ab|cd)| (e.g. Q_ab Q_cd); quartets with bound < tau are
+        written as zeros without being evaluated."""
         q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
         n = q.shape[0]
+        if bound is not None:
+            bound = torch.as_tensor(bound, dtype=torch.float64, device="cuda").contiguous()
+            if bound.numel() != n:
+                raise MdxError("mdx_eri4: bound needs one value per quartet")
         if out is None:
             qn = np.clip(q.cpu().numpy().astype(np.int64), 0, len(basis.nc) - 1)   # the ABI validates indices
             nc = basis.nc
             tot = int(np.sum(nc[qn[:, 0]] * nc[qn[:, 1]] * nc[qn[:, 2]] * nc[qn[:, 3]])) if n else 0
             out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        _check_out(out, "mdx_eri4")
         offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
-        st = self.lib.mdx_eri4(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), n, out.data_ptr(), out.numel(),
-                               offs.data_ptr(), _stream())
+        st = self.lib.mdx_eri4(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), _opt_ptr(bound), n, float(tau),
+                               out.data_ptr(), out.numel(), offs.data_ptr(), _stream())
         self._check(st, "mdx_eri4")
         return out, offs
 
@@ -226,38 +263,70 @@ class Engine:
             ns = 2 * basis.host.l.astype(np.int64) + 1
             tot = int(np.sum(ns[qn[:, 0]] * ns[qn[:, 1]] * ns[qn[:, 2]] * ns[qn[:, 3]])) if n else 0
             out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        _check_out(out, "mdx_eri4_sph")
         offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
         st = self.lib.mdx_eri4_sph(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), n, out.data_ptr(), out.numel(),
                                    offs.data_ptr(), _stream())
         self._check(st, "mdx_eri4_sph")
         return out, offs
 
-    def eri3(self, aux: DeviceBasis, orb: DeviceBasis, triplets, out: torch.Tensor = None):
-        """[a|cd] for triplets [n,3] = (aux shell, orb shell, orb shell). Returns (values, offsets)."""
+    def eri3(self, aux: DeviceBasis, orb: DeviceBasis, triplets, out: torch.Tensor = None, bound=None,
+             tau: float = 0.0):
+        """[a|cd] for triplets [n,3] = (aux shell, orb shell, orb shell). Returns (values, offsets).
+        bound / tau: optional per-triplet bounds and threshold, as in eri4."""
         t = torch.as_tensor(triplets, dtype=torch.int32, device="cuda").contiguous()
         n = t.shape[0]
+        if bound is not None:
+            bound = torch.as_tensor(bound, dtype=torch.float64, device="cuda").contiguous()
+            if bound.numel() != n:
+                raise MdxError("mdx_eri3: bound needs one value per triplet")
         if out is None:
             tn = t.cpu().numpy().astype(np.int64)
             tn[:, 0] = np.clip(tn[:, 0], 0, len(aux.nc) - 1)
             tn[:, 1:] = np.clip(tn[:, 1:], 0, len(orb.nc) - 1)
             tot = int(np.sum(aux.nc[tn[:, 0]] * orb.nc[tn[:, 1]] * orb.nc[tn[:, 2]])) if n else 0
             out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        _check_out(out, "mdx_eri3")
         offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
-        st = self.lib.mdx_eri3(self.ctx, ctypes.byref(aux.desc), ctypes.byref(orb.desc), t.data_ptr(), n,
-                               out.data_ptr(), out.numel(), offs.data_ptr(), _stream())
+        st = self.lib.mdx_eri3(self.ctx, ctypes.byref(aux.desc), ctypes.byref(orb.desc), t.data_ptr(), _opt_ptr(bound),
+                               n, float(tau), out.data_ptr(), out.numel(), offs.data_ptr(), _stream())
         self._check(st, "mdx_eri3")
         return out, offs
 
-    def exchange(self, basis: DeviceBasis, pairs, Q, D: torch.Tensor, tau: float = 0.0) -> torch.Tensor:
-        """K_ik = sum_jl D_jl (ij|kl) over the screened unique quartets of the pair list."""
+    def exchange(self, basis: DeviceBasis, pairs, Q, D: torch.Tensor, tau: float = 0.0, alpha: float = None):
+        """K_ik = sum_jl D_jl (ij|kl) over the screened unique quartets of the pair list. With alpha given,
+        returns (K, E_x) with E_x = alpha sum_ik D_ik K_ik computed by the library (device scalar)."""
         p = torch.as_tensor(pairs, dtype=torch.int32, device="cuda").contiguous()
         q = torch.as_tensor(Q, dtype=torch.float64, device="cuda").contiguous()
         D = D.to(device="cuda", dtype=torch.float64).contiguous()
         K = torch.empty_like(D)
+        e = torch.zeros(1, dtype=torch.float64, device="cuda") if alpha is not None else None
         st = self.lib.mdx_exchange(self.ctx, ctypes.byref(basis.desc), p.data_ptr(), q.data_ptr(), p.shape[0],
-                                   float(tau), D.data_ptr(), K.data_ptr(), _stream())
+                                   float(tau), D.data_ptr(), K.data_ptr(), float(alpha or 0.0), _opt_ptr(e),
+                                   _stream())
         self._check(st, "mdx_exchange")
-        return K
+        return K if alpha is None else (K, e[0])
+
+    def exchange_screen(self, basis: DeviceBasis, pairs, Q, D: torch.Tensor, tau: float = 0.0,
+                        list_quartets: bool = True):
+        """The screening of mdx_exchange alone: (kept [n,2] indices into `pairs` or None, n_kept,
+        Table-1 model FLOPs of the kept shellsets)."""
+        p = torch.as_tensor(pairs, dtype=torch.int32, device="cuda").contiguous()
+        q = torch.as_tensor(Q, dtype=torch.float64, device="cuda").contiguous()
+        D = D.to(device="cuda", dtype=torch.float64).contiguous()
+        n, mf = ctypes.c_int64(), ctypes.c_double()
+        st = self.lib.mdx_exchange_screen(self.ctx, ctypes.byref(basis.desc), p.data_ptr(), q.data_ptr(),
+                                          p.shape[0], float(tau), D.data_ptr(), None, 0, ctypes.byref(n),
+                                          ctypes.byref(mf), _stream())
+        self._check(st, "mdx_exchange_screen")
+        if not list_quartets:
+            return None, n.value, mf.value
+        kept = torch.empty((max(n.value, 1), 2), dtype=torch.int32, device="cuda")
+        st = self.lib.mdx_exchange_screen(self.ctx, ctypes.byref(basis.desc), p.data_ptr(), q.data_ptr(),
+                                          p.shape[0], float(tau), D.data_ptr(), kept.data_ptr(), kept.shape[0],
+                                          ctypes.byref(n), ctypes.byref(mf), _stream())
+        self._check(st, "mdx_exchange_screen")
+        return kept[: n.value], n.value, mf.value
 
     def exchange_grad(self, basis: DeviceBasis, pairs, Q, D: torch.Tensor, tau: float = 0.0, alpha: float = -1.0,
                       n_atoms: int = None, with_energy: bool = True):
@@ -339,6 +408,7 @@ class Batch:
 
     def run(self, out: torch.Tensor) -> int:
         """Enqueue on the current stream; returns the number of kernels launched."""
+        _check_out(out, "mdx_batch_run")
         nl = ctypes.c_int32()
         self.eng._check(self.eng.lib.mdx_batch_run(self.eng.ctx, self.h, out.data_ptr(), out.numel(),
                                                    ctypes.byref(nl), _stream()), "mdx_batch_run")
@@ -346,6 +416,7 @@ class Batch:
 
     def run_materialized(self, out: torch.Tensor) -> int:
         """The materialized-Hermite variant (dense [p|q] matrices, batched DGEMMs); uncontracted classes only."""
+        _check_out(out, "mdx_batch_run_materialized")
         nl = ctypes.c_int32()
         self.eng._check(self.eng.lib.mdx_batch_run_materialized(self.eng.ctx, self.h, out.data_ptr(), out.numel(),
                                                                 ctypes.byref(nl), _stream()),
@@ -354,6 +425,7 @@ class Batch:
 
     def autotune(self, out: torch.Tensor, max_trial: int = 256):
         """Pick the fastest team shape per class on this GPU (kept by the engine)."""
+        _check_out(out, "mdx_batch_autotune")
         self.eng._check(self.eng.lib.mdx_batch_autotune(self.eng.ctx, self.h, out.data_ptr(), out.numel(), max_trial,
                                                         _stream()), "mdx_batch_autotune")
 
@@ -370,10 +442,12 @@ class Batch:
 
 
 def basis_with_centers(basis: DeviceBasis, coords: torch.Tensor) -> DeviceBasis:
-    """A copy of `basis` whose shell centres are coords[atom of shell] (coords: [n_atoms, 3], device)."""
+    """A copy of `basis` whose shell centres are coords[atom of shell] (coords: [n_atoms, 3], any device
+    and floating dtype; the centres are copied to the basis's device in float64)."""
     nb = DeviceBasis.__new__(DeviceBasis)
     nb.__dict__.update(basis.__dict__)
-    nb.center = coords.detach().to(dtype=torch.float64)[basis.atom.long()].contiguous()
+    c = coords.detach().to(device=basis.center.device, dtype=torch.float64)
+    nb.center = c[basis.atom.long()].contiguous()
     nb.desc = _Basis(basis.desc.n_shells, basis.desc.n_prims, basis.l.data_ptr(), basis.nprim.data_ptr(),
                      basis.prim_off.data_ptr(), basis.ao_off.data_ptr(), basis.atom.data_ptr(), nb.center.data_ptr(),
                      basis.exps.data_ptr(), basis.coefs.data_ptr())
@@ -382,20 +456,26 @@ def basis_with_centers(basis: DeviceBasis, coords: torch.Tensor) -> DeviceBasis:
 
 class ExchangeEnergy(torch.autograd.Function):
     """E_x = alpha sum_ijkl D_ik D_jl (ij|kl) as a differentiable function of the
-    atom coordinates and of D. Forward: mdx_exchange (E_x = alpha sum D o K).
-    Backward: mdx_exchange_grad for the coordinates (derivative integrals
-    contracted with D (x) D inside the kernel) and 2 alpha K for D (symmetric D)."""
+    atom coordinates and of a symmetric D. Forward: mdx_exchange, which returns
+    K and E_x = alpha sum D o K. Backward: mdx_exchange_grad for the coordinates
+    (derivative integrals contracted with D (x) D inside the kernel) and
+    2 alpha K for D (the derivative for symmetric D; a D that is not symmetric
+    is rejected in forward, since the library's K assumes symmetry)."""
 
     @staticmethod
     def forward(ctx, coords, D, eng, basis, pairs, tau, alpha):
         db = basis_with_centers(basis, coords)
         Q = eng.schwarz(db, pairs)
         Dd = D.detach().to(device="cuda", dtype=torch.float64).contiguous()
-        K = eng.exchange(db, pairs, Q, Dd, tau)
+        if Dd.dim() != 2 or Dd.shape[0] != Dd.shape[1] or not torch.equal(Dd, Dd.T):
+            raise MdxError("ExchangeEnergy: D must be a symmetric square matrix")
+        K, E = eng.exchange(db, pairs, Q, Dd, tau, alpha=alpha)
         ctx.eng, ctx.db, ctx.pairs, ctx.tau, ctx.alpha = eng, db, pairs, tau, alpha
         ctx.n_atoms = coords.shape[0]
+        ctx.coords_like = (coords.device, coords.dtype)
+        ctx.D_like = (D.device, D.dtype)
         ctx.save_for_backward(Dd, K, Q)
-        return alpha * torch.sum(Dd * K)
+        return E.to(device=D.device, dtype=D.dtype)
 
     @staticmethod
     def backward(ctx, gE):
@@ -404,9 +484,11 @@ class ExchangeEnergy(torch.autograd.Function):
         if ctx.needs_input_grad[0]:
             g, _ = ctx.eng.exchange_grad(ctx.db, ctx.pairs, Q, Dd, tau=ctx.tau, alpha=ctx.alpha, n_atoms=ctx.n_atoms,
                                          with_energy=False)
-            gcoords = gE * g
+            dev, dt = ctx.coords_like
+            gcoords = (gE.to(device=g.device, dtype=g.dtype) * g).to(device=dev, dtype=dt)
         if ctx.needs_input_grad[1]:
-            gD = gE * 2.0 * ctx.alpha * K
+            dev, dt = ctx.D_like
+            gD = (gE.to(device=K.device, dtype=K.dtype) * 2.0 * ctx.alpha * K).to(device=dev, dtype=dt)
         return gcoords, gD, None, None, None, None, None
 
 

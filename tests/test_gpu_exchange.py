@@ -76,3 +76,59 @@ def test_exchange_rejects_duplicate_pairs(eng):
     pairs = np.array([[1, 0], [0, 1]], dtype=np.int32)
     with pytest.raises(mdx.MdxError, match="EINVAL"):
         eng.exchange(db, pairs, torch.ones(2, dtype=torch.float64), torch.eye(b.nao, dtype=torch.float64))
+
+
+def test_exchange_energy_from_the_library(eng):
+    """mdx_exchange's energy output: E_x = alpha sum D o K, against the oracle's."""
+    b = inputs.molecule(seed=23, n_atoms=3)
+    D = inputs.density(b.nao, 9)
+    db = mdx.DeviceBasis(b)
+    pairs = _pairs(b)
+    Q = eng.schwarz(db, pairs)
+    K, E = eng.exchange(db, pairs, Q, torch.from_numpy(D), 0.0, alpha=-1.0)
+    Eref = -oracle.exchange_energy(b, D)
+    assert abs(float(E) - Eref) <= 1e-12 * abs(Eref)
+    assert abs(float(E) + float(torch.sum(torch.from_numpy(D).cuda() * K))) <= 1e-13 * abs(Eref)
+
+
+def _rule_kept(b, pairs, Q, D, tau):
+    """Plain restatement of the screening rule over every unordered pair of pairs (FP64)."""
+    nc = (b.l + 1) * (b.l + 2) // 2
+    n = b.n_shells
+    dmax = np.zeros((n, n))
+    for i in range(n):
+        for k in range(n):
+            dmax[i, k] = np.max(np.abs(D[b.ao_off[i]:b.ao_off[i] + nc[i], b.ao_off[k]:b.ao_off[k] + nc[k]]))
+    kept = set()
+    for p in range(len(pairs)):
+        i, j = pairs[p]
+        for q in range(p + 1):
+            k, l = pairs[q]
+            d = max(max(dmax[i, k], dmax[i, l]), max(dmax[j, k], dmax[j, l]))
+            if Q[p] * Q[q] * d >= tau:
+                kept.add(frozenset((p, q)))
+    return kept
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-9, 1e-6])
+def test_screening_kept_set_matches_the_rule(eng, tau):
+    """The quartets the GPU screening keeps (mdx_exchange_screen) are exactly those of a plain
+    restatement of the rule, in any pair order and orientation; the count per class agrees too."""
+    b = inputs.molecule(seed=24, n_atoms=3)
+    D = inputs.density(b.nao, 3)
+    db = mdx.DeviceBasis(b)
+    rng = np.random.Generator(np.random.PCG64(8))
+    pairs = _pairs(b)[rng.permutation(b.n_shells * (b.n_shells + 1) // 2)]
+    flip = rng.uniform(size=len(pairs)) < 0.5
+    pairs[flip] = pairs[flip][:, ::-1]
+    Q = eng.schwarz(db, pairs)
+    kept, n, mf = eng.exchange_screen(db, pairs, Q, torch.from_numpy(D), tau)
+    got = {frozenset((int(x), int(y))) for x, y in kept.cpu().numpy()}
+    assert len(got) == n == kept.shape[0]
+    ref = _rule_kept(b, pairs, Q.cpu().numpy(), D, tau)
+    assert got == ref
+    assert mf > 0
+    if tau > 0:
+        assert n < len(pairs) * (len(pairs) + 1) // 2
+    _, n2, _ = eng.exchange_screen(db, pairs, Q, torch.from_numpy(D), tau, list_quartets=False)
+    assert n2 == n

@@ -122,3 +122,27 @@ def test_gradient_ten_atom_cluster_fd_eight_atoms(eng):
         fd = (vals[0] - vals[1]) / (2 * h)
         # screening at tau moves E by far less than the FD resolution here
         assert abs(g[A, x] - fd) <= 1e-6 * max(1.0, abs(fd)), (A, x, g[A, x], fd)
+
+
+def test_autograd_with_cpu_coordinates(eng):
+    """Coordinates on the host in float32: the centres go to the device in float64, and the gradient
+    comes back on the host in float32."""
+    b = inputs.small_molecule(seed=72, n_atoms=2, shells=(0, 1), K=2)
+    D = torch.from_numpy(inputs.density(b.nao, 13)).cuda()
+    coords = torch.from_numpy(b.atoms).to(torch.float32).requires_grad_(True)
+    db = mdx.DeviceBasis(b)
+    E = mdx.exchange_energy(eng, db, coords, D, alpha=-1.0)
+    (gc,) = torch.autograd.grad(E, (coords,))
+    assert gc.device.type == "cpu" and gc.dtype == torch.float32
+    bf = inputs.small_molecule(seed=72, n_atoms=2, shells=(0, 1), K=2)
+    bf.center = coords.detach().double().numpy()[bf.atom]
+    ref = -oracle.exchange_grad(bf, D.cpu().numpy())
+    np.testing.assert_allclose(gc.numpy(), ref, rtol=0, atol=1e-6 * np.max(np.abs(ref)))
+
+
+def test_autograd_rejects_asymmetric_density(eng):
+    b = inputs.small_molecule(seed=73, n_atoms=2, shells=(0, 1), K=1)
+    D = torch.from_numpy(inputs.density(b.nao, 14)).cuda()
+    D[0, 1] += 1e-3
+    with pytest.raises(mdx.MdxError, match="symmetric"):
+        mdx.exchange_energy(eng, mdx.DeviceBasis(b), torch.from_numpy(b.atoms).cuda(), D)

@@ -26,3 +26,15 @@ def test_package_never_reaches_the_oracle():
     pat = re.compile(r"\bimport\s+oracle\b|\bfrom\s+oracle\b|mdx_oracle|libmdx_oracle|orc_[a-z0-9_]+\s*\(")
     offenders = [f for f in files if os.path.isfile(f) and pat.search(open(f, errors="replace").read())]
     assert not offenders, offenders
+
+
+def test_output_buffers_are_checked_before_any_launch():
+    """An output crosses the ABI as a pointer and a capacity in doubles, so the binding accepts only
+    contiguous float64 CUDA tensors: a float32, host or strided tensor is refused before the library
+    is called (it would be written past its end)."""
+    for bad in (torch.empty(16, dtype=torch.float32), torch.empty(16, dtype=torch.float64),
+                torch.empty(32, dtype=torch.float64)[::2]):
+        with pytest.raises(mdx.MdxError, match="contiguous float64 CUDA"):
+            mdx._check_out(bad, "test")
+    with pytest.raises(mdx.MdxError, match="contiguous float64 CUDA"):
+        mdx.eri4_noalloc(None, [[0, 0, 0, 0]], torch.empty(8, dtype=torch.float32))
