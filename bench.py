@@ -59,12 +59,13 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the per-class team-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad", "ab", "peak"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad", "ab", "peak", "sph"],
                     help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules; "
                          "df: per-class 3-center rates on the density-fitting cluster; grad: exchange energy "
                          "and its nuclear gradient against the exchange build alone; ab: the default kernels "
                          "against the materialized-Hermite variant (dense [p|q], batched DGEMMs); "
-                         "peak: measured FP64 throughput, scalar DFMA vs the FP64 tensor instruction")
+                         "peak: measured FP64 throughput, scalar DFMA vs the FP64 tensor instruction; sph: "
+                         "solid-harmonic rates per class of the paper's Tab. nps4")
     ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
     ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
     ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
@@ -487,6 +488,75 @@ def ab_main(args):
     eng.close()
 
 
+# The paper's solid-harmonic 4-center rates on one V100 (shellsets/s, Tab. nps4), class [l1 l2|l3 l4] by its
+# four angular momenta, columns {K_bra, K_ket} = {1,1}, {1,5}, {5,5}: context for the solid-harmonic workload
+PAPER_NPS4_V100 = {
+    (0, 0, 0, 0): (4.53e9, 2.98e9, 9.11e8), (1, 0, 1, 0): (2.10e9, 1.23e9, 3.31e8),
+    (2, 0, 2, 0): (1.01e9, 5.17e8, 1.27e8), (3, 0, 3, 0): (1.28e8, 8.19e7, 1.75e7),
+    (4, 0, 4, 0): (8.31e7, 3.62e7, 7.52e6), (5, 0, 5, 0): (1.80e7, 7.19e6, 1.56e6),
+    (6, 0, 6, 0): (6.71e6, 2.47e6, 5.43e5), (1, 1, 1, 1): (2.59e8, 2.05e8, 5.27e7),
+    (2, 2, 2, 2): (2.25e7, 1.04e7, 2.12e6), (3, 3, 3, 3): (2.47e6, 8.00e5, 1.69e5),
+    (4, 4, 4, 4): (3.25e5, 9.59e4, 2.05e4), (5, 5, 5, 5): (1.11e5, 3.14e4, 6.73e3),
+    (6, 6, 6, 6): (3.47e4, 9.74e3, 1.99e3)}
+
+
+def sph_main(args):
+    """Solid-harmonic 4-center integrals (the paper's basis) per class of the paper's Tab. nps4: [ll|ll] and
+    [l0|l0], contraction columns {K_bra, K_ket} = {1,1}, {1,5}, {5,5} (one shell of a contracted pair has
+    K = 5). Random shells as in the class sweep; each class on a seeded grid sized to about 0.15 TFLOP of
+    executed work. Classes of the team kernel contract the solid-harmonic coefficients into the transforms
+    (mdx_batch_eri4_sph); [ll|ll] with l >= 4 is also timed through the Cartesian kernel on the same
+    quartets. The paper's V100 rates are quoted beside ours as context (another machine)."""
+    import math
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    stream = torch.cuda.current_stream()
+    peak = max(mdx.fp64_peak(0, 3), mdx.fp64_peak(1, 3)) * 1e9
+    kcols = (("{1,1}", (1, 1, 1, 1)), ("{1,5}", (1, 1, 5, 1)), ("{5,5}", (5, 1, 5, 1)))
+    rows = []
+    for lq in sorted(PAPER_NPS4_V100, key=lambda x: (sum(x), x)):
+        for ki, (kname, K) in enumerate(kcols):
+            est = mdx.plan_info(*lq, K[0] * K[1], K[2] * K[3]).exec_fma
+            n = int(min(50176, max(1024, 0.15e12 / max(est, 1.0))))
+            side = int(math.ceil(math.sqrt(n)))
+            b, q = inputs.class_sweep(lq, n_bra=side, n_ket=side, seed=1002, K=K)
+            db = mdx.DeviceBasis(b)
+            bt = eng.batch_eri4_sph(db, q)
+            out = torch.empty(bt.total, dtype=torch.float64, device="cuda")
+            ms = _event_ms(torch, stream, lambda: bt.run(out), args.steps, args.warmup)
+            row = {"class": "[%d%d|%d%d]" % lq, "K": kname, "shellsets": len(q), "ms": round(ms, 4),
+                   "shellsets_per_s": round(len(q) / (ms * 1e-3), 1),
+                   "exec_gflops": round(2 * bt.exec_fma / (ms * 1e-3) * 1e-9, 2),
+                   "exec_frac_of_peak": round(2 * bt.exec_fma / (ms * 1e-3) / peak, 4),
+                   "exec_fma_per_shellset": round(bt.exec_fma / len(q), 1),
+                   "model_gflops": round(bt.model_flops / (ms * 1e-3) * 1e-9, 2),
+                   "paper_v100_shellsets_per_s": PAPER_NPS4_V100[lq][ki]}
+            bt.close()
+            if lq[0] == lq[2] and lq[0] == lq[1] and lq[0] >= 4:
+                bc = eng.batch_eri4(db, q)
+                oc = torch.empty(bc.total, dtype=torch.float64, device="cuda")
+                msc = _event_ms(torch, stream, lambda: bc.run(oc), args.steps, args.warmup)
+                row["cartesian_ms"] = round(msc, 4)
+                row["cartesian_exec_fma_per_shellset"] = round(bc.exec_fma / len(q), 1)
+                bc.close()
+            rows.append(row)
+    eng.sync()
+    line = {"metric": "solid-harmonic [ab|cd]: shellsets/s and FP64 GFLOP/s per class of the paper's Tab. nps4",
+            "unit": "shellsets/s", "value": next(r["shellsets_per_s"] for r in rows if r["class"] == "[66|66]" and
+                                                r["K"] == "{1,1}"),
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic", "steps": args.steps,
+            "warmup": args.warmup, "fp64_peak_gflops": round(peak * 1e-9, 1),
+            "config": {"workload": "solid-harmonic class sweep: random shells (centres in a 10-bohr box, exponents "
+                                   "log-uniform [0.05, 50]), [ll|ll] and [l0|l0], {K_bra, K_ket} = {1,1}, {1,5}, "
+                                   "{5,5}; value: [66|66] {1,1}"},
+            "paper_context": "Tab. nps4 of the paper: one V100 (FP64 7 TFLOP/s), solid harmonics",
+            "per_class": rows}
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def peak_main(args):
     """FP64 throughput of this GPU: scalar DFMA against the FP64 tensor instruction (DMMA) in its three
     shapes (mdx_fp64_peak), with the SM clocks sampled meanwhile. The engine's transforms use DFMA
@@ -504,7 +574,7 @@ def peak_main(args):
     mhz = (clocks or {}).get("sm_mhz") or 0.0
     line = {"metric": "FP64 throughput: scalar DFMA vs the FP64 tensor instruction", "unit": "GFLOP/s",
             "value": max(res.values()), "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "steps": args.steps, "config": {"workload": "register-resident FP64 multiply-add loops, 4 x 256 threads "
+            "steps": args.steps, "config": {"workload": "register-resident FP64 multiply-add loops, 8 x 256 threads "
                                                         "per SM, %d SMs" % props.multi_processor_count},
             "per_kind": res,
             "per_sm_per_clock": ({k: round(v * 1e9 / (props.multi_processor_count * mhz * 1e6), 3)
@@ -527,6 +597,8 @@ def main():
         return ab_main(args)
     if args.workload == "peak":
         return peak_main(args)
+    if args.workload == "sph":
+        return sph_main(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

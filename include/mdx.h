@@ -120,15 +120,20 @@ mdx_status mdx_sync(mdx_ctx* ctx, void* stream);
 mdx_status mdx_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, const double* bound, int64_t n,
                     double tau, double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
 
-/* mdx_eri4 over real solid harmonics (the paper's basis, Eqs. solid2herm):
- * shell of angular momentum l contributes 2l+1 functions S_lm, m = -l..l,
+/* mdx_eri4 over real solid harmonics (the paper's basis, Eqs. solid2herm-1/2):
+ * a shell of angular momentum l contributes 2l+1 functions S_lm, m = -l..l,
  * S_lm = N_lm sum C x^.. y^.. z^.. with the standard real-solid-harmonic
  * coefficients, each with the angular norm of z^l (so x^l-normalised
- * contraction coefficients give normalised spherical functions). The
- * Cartesian shellsets are evaluated first into context workspace and
- * transformed index by index on the GPU. Output per quartet [a][b][c][d] in
- * solid-harmonic components at out + out_offsets[q]. Same synchronisation and
- * errors as mdx_eri4. */
+ * contraction coefficients give normalised spherical functions; l = 1 is
+ * (y, z, x)). Output per quartet [a][b][c][d] in solid-harmonic components at
+ * out + out_offsets[q]; offsets and out_capacity count those doubles.
+ * Classes evaluated by the team kernel contract the solid-harmonic
+ * coefficients into the transforms, as the paper's H matrices do: the
+ * Cartesian ket columns [p|cd] are staged in device memory (allocated by the
+ * call), turned into [p|c'd'] one index at a time, and the bra steps and
+ * everything after them run on 2l+1 components per shell. Small classes with
+ * a register kernel are evaluated over Cartesians and transformed index by
+ * index. Synchronises `stream`; results are complete on return. */
 mdx_status mdx_eri4_sph(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n, double* out,
                         int64_t out_capacity, int64_t* out_offsets, void* stream);
 
@@ -159,6 +164,14 @@ typedef struct mdx_batch mdx_batch;
  * `stream`. n must be >= 1. */
 mdx_status mdx_batch_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
                           mdx_batch** batch, void* stream);
+
+/* Prepare the quartets of mdx_eri4_sph (same arguments): a batch whose
+ * offsets, total and run output are in solid-harmonic components. Its device
+ * arrays, including the staging of the solid-harmonic team kernel, belong to
+ * the batch. Synchronises `stream`. n must be >= 1. mdx_batch_autotune and
+ * mdx_batch_run_materialized return MDX_EUNSUPPORTED for such a batch. */
+mdx_status mdx_batch_eri4_sph(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
+                              mdx_batch** batch, void* stream);
 
 /* Prepare the triplets of mdx_eri3 (same arguments). Synchronises `stream`. */
 mdx_status mdx_batch_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
@@ -363,8 +376,8 @@ mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* quartets, int
  * kind 0: scalar FP64 fused multiply-add (DFMA), 8 independent chains per
  * thread; 1, 2, 3: the FP64 tensor-core instruction (mma.sync .f64) in the
  * shapes m8n8k4, m16n8k4 and m16n8k16, 4 independent accumulators per warp.
- * Register-resident loops over 4 blocks of 256 threads per SM; one warm-up
- * launch, then `reps` launches of about 50 ms timed with CUDA events on
+ * Register-resident loops over 8 blocks of 256 threads per SM; one warm-up
+ * launch, then `reps` launches of about 100 ms timed with CUDA events on
  * `stream`. *gflops receives 2 x multiply-adds / second / 1e9. Synchronises
  * `stream`; allocates nothing. MDX_EINVAL for a kind outside 0..3, reps < 1
  * or a NULL gflops; MDX_ECUDA if a CUDA call fails. */

@@ -57,7 +57,7 @@ def _load():
             lib.orc_exchange_grad.argtypes = [P] * 8 + [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
                                                         ctypes.c_int]
             lib.orc_solid_coefs.argtypes = [ctypes.c_int, P]
-            lib.orc_eri4_sph.argtypes = [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int]
+            lib.orc_eri4_sph.argtypes = [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -188,8 +188,9 @@ def solid_coefs(l: int) -> np.ndarray:
     return C.reshape(2 * l + 1, ncart(l))
 
 
-def eri4_sph(basis, quartets, nthreads: int = 0):
-    """[ab|cd] over real solid harmonics (m = -l..l per shell); returns (values, offsets)."""
+def eri4_sph(basis, quartets, nthreads: int = 0, precision: int = 0):
+    """[ab|cd] over real solid harmonics (m = -l..l per shell); returns (values, offsets).
+    precision 1: the long double build (Cartesian shellsets and transform), rounded at the end."""
     q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
     l = np.asarray(basis.l)
     ns = 2 * l + 1
@@ -198,5 +199,5 @@ def eri4_sph(basis, quartets, nthreads: int = 0):
     np.cumsum(sizes, out=off[1:])
     out = np.zeros(int(off[-1]))
     arrs = _basis_arrays(basis)
-    _load().orc_eri4_sph(*[_p(a) for a in arrs], _p(q), len(q), _p(out), _p(off), nthreads)
+    _load().orc_eri4_sph(*[_p(a) for a in arrs], _p(q), len(q), _p(out), _p(off), nthreads, precision)
     return out, off

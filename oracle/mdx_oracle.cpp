@@ -480,38 +480,54 @@ void orc_solid_coefs(int l, double* C) {
 }
 
 // Batch of 4-center shellsets over real solid harmonics: the Cartesian shellset of
-// shellset4 transformed index by index with solid_coefs, written [a][b][c][d] with
-// m = -l..l in every position; shellset q at out + offsets[q].
-void orc_eri4_sph(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,
-                  const double* exps, const double* coefs, const int32_t* quartets, int64_t n, double* out,
-                  const int64_t* offsets, int nthreads) {
-  Basis bs{l, nprim, prim_off, center, exps, coefs};
+// shellset4 contracted with solid_coefs on each of its four indices,
+//   [a'b'|c'd'] = sum_{abcd} C_{a'a} C_{b'b} C_{c'c} C_{d'd} [ab|cd],
+// applied one index at a time (d, then c, b, a: the same sum regrouped), written
+// [a][b][c][d] with m = -l..l in every position; shellset q at out + offsets[q].
+// precision 1 runs the long double build (Cartesian shellset and transform),
+// rounded at the end.
+}  // extern "C"
+
+template <typename T>
+void eri4_sph_batch(const Basis& bs, const int32_t* l, const int32_t* quartets, int64_t n, double* out,
+                    const int64_t* offsets, int nthreads) {
   const int nt = nthreads_or_default(nthreads);
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
   for (int64_t q = 0; q < n; ++q) {
     const int32_t* s4 = quartets + 4 * q;
     const int L[4] = {l[s4[0]], l[s4[1]], l[s4[2]], l[s4[3]]};
-    const int nc[4] = {ncart(L[0]), ncart(L[1]), ncart(L[2]), ncart(L[3])};
-    const int ns[4] = {2 * L[0] + 1, 2 * L[1] + 1, 2 * L[2] + 1, 2 * L[3] + 1};
-    std::vector<double> v((size_t)nc[0] * nc[1] * nc[2] * nc[3]);
-    shellset4<double>(bs, s4[0], s4[1], s4[2], s4[3], v.data());
-    std::vector<double> C[4];
-    for (int k = 0; k < 4; ++k) C[k] = solid_coefs(L[k]);
-    double* o = out + offsets[q];
-    for (int a = 0; a < ns[0]; ++a)
-      for (int b = 0; b < ns[1]; ++b)
-        for (int c = 0; c < ns[2]; ++c)
-          for (int d = 0; d < ns[3]; ++d) {
-            double acc = 0.0;
-            for (int i = 0; i < nc[0]; ++i)
-              for (int j = 0; j < nc[1]; ++j)
-                for (int k = 0; k < nc[2]; ++k)
-                  for (int m = 0; m < nc[3]; ++m)
-                    acc += C[0][(size_t)a * nc[0] + i] * C[1][(size_t)b * nc[1] + j] * C[2][(size_t)c * nc[2] + k] *
-                           C[3][(size_t)d * nc[3] + m] * v[(((size_t)i * nc[1] + j) * nc[2] + k) * nc[3] + m];
-            o[((a * ns[1] + b) * ns[2] + c) * ns[3] + d] = acc;
+    int dim[4] = {ncart(L[0]), ncart(L[1]), ncart(L[2]), ncart(L[3])};
+    std::vector<T> v((size_t)dim[0] * dim[1] * dim[2] * dim[3]);
+    shellset4<T>(bs, s4[0], s4[1], s4[2], s4[3], v.data());
+    for (int axis = 3; axis >= 0; --axis) {   // contract index `axis`: ncart -> 2l+1
+      const std::vector<double> C = solid_coefs(L[axis]);
+      const int nc = dim[axis], ns = 2 * L[axis] + 1;
+      size_t outer = 1, inner = 1;
+      for (int k = 0; k < axis; ++k) outer *= dim[k];
+      for (int k = axis + 1; k < 4; ++k) inner *= dim[k];
+      std::vector<T> w(outer * ns * inner, T(0));
+      for (size_t o = 0; o < outer; ++o)
+        for (int m = 0; m < ns; ++m)
+          for (int c = 0; c < nc; ++c) {
+            const T f = T(C[(size_t)m * nc + c]);
+            for (size_t i = 0; i < inner; ++i) w[(o * ns + m) * inner + i] += f * v[(o * nc + c) * inner + i];
           }
+      v.swap(w);
+      dim[axis] = ns;
+    }
+    double* o = out + offsets[q];
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (double)v[i];
   }
+}
+
+extern "C" {
+
+void orc_eri4_sph(const int32_t* l, const int32_t* nprim, const int32_t* prim_off, const double* center,
+                  const double* exps, const double* coefs, const int32_t* quartets, int64_t n, double* out,
+                  const int64_t* offsets, int nthreads, int precision) {
+  Basis bs{l, nprim, prim_off, center, exps, coefs};
+  if (precision == 1) eri4_sph_batch<long double>(bs, l, quartets, n, out, offsets, nthreads);
+  else eri4_sph_batch<double>(bs, l, quartets, n, out, offsets, nthreads);
 }
 
 // Batch of 3-center shellsets [a|cd]; triplets[n][3] = (aux shell, orb shell, orb shell).

@@ -74,6 +74,14 @@ class Eri4Evaluator:
         return self.oracle.eri4(b, self.q[sel], precision=precision)[0]
 
 
+class Eri4SphEvaluator(Eri4Evaluator):
+    """Oracle solid-harmonic [ab|cd] of a subset of the quartets, optionally on a perturbed basis."""
+
+    def __call__(self, sel, precision, seed=None):
+        b = self.basis if seed is None else _perturbed(self.basis, seed)
+        return self.oracle.eri4_sph(b, self.q[sel], precision=precision)[0]
+
+
 class Eri3Evaluator:
     """Oracle [a|cd] of a subset of the triplets, optionally on perturbed bases."""
 

@@ -223,7 +223,17 @@ struct mdx_batch {
   int64_t* offsets = nullptr;     // [n+1] in caller order
   int64_t* zero = nullptr;        // [nzero][2] (offset, doubles) of screened-out shellsets
   int64_t nzero = 0;
-  struct Range { Plan* plan; int64_t begin, count; ClassKey key; };
+  // solid-harmonic batches: offsets, total and qoff count solid-harmonic doubles. Classes without a
+  // register kernel run the solid-harmonic team kernel (splan, `grid` CTAs, staging in xg); the
+  // others evaluate Cartesian shellsets into `cart` (offsets cqoff) and transform them index by index
+  // (scratch `tmp`, offsets tqoff).
+  bool sph = false;
+  int64_t* cqoff = nullptr;
+  int64_t* tqoff = nullptr;
+  double* cart = nullptr;
+  double* tmp = nullptr;
+  double* xg = nullptr;
+  struct Range { Plan* plan; int64_t begin, count; ClassKey key; Plan* splan; int grid; };
   std::vector<Range> ranges;
   std::vector<int64_t> qorig;     // caller index of each class-sorted quartet
   double model_flops = 0.0;
@@ -279,6 +289,7 @@ void batch_free(mdx_batch* b) {
   if (b->owned) {
     cudaFree(b->jobs); cudaFree(b->pair_rec); cudaFree(b->recs); cudaFree(b->recs_s);
     cudaFree(b->qp); cudaFree(b->qoff); cudaFree(b->offsets); cudaFree(b->zero);
+    cudaFree(b->cqoff); cudaFree(b->tqoff); cudaFree(b->cart); cudaFree(b->tmp); cudaFree(b->xg);
   }
   delete b;
 }
@@ -338,13 +349,24 @@ struct Fanout {
   }
 };
 
-double model_flops_class(const ClassKey& k) {
+// The paper's Table 1 work model of one contracted shellset; sph: with the
+// solid-harmonic component counts 2l+1 (the paper's own basis), else Cartesian.
+double model_flops_class(const ClassKey& k, bool sph = false) {
   auto nh = [](int l) { return (double)nherm(l); };
   auto rl = [](int L) { return (2.0 + L) * (7.0 + L) * (12.0 + 5.0 * L + (double)L * L) / 8.0; };
+  auto nf = [sph](int l) { return sph ? 2.0 * l + 1.0 : (double)ncart(l); };
   const int Lb = k.la + k.lb, Lk = k.lc + k.ld;
-  const double Nb = (double)ncart(k.la) * ncart(k.lb), Nk = (double)ncart(k.lc) * ncart(k.ld);
+  const double Nb = nf(k.la) * nf(k.lb), Nk = nf(k.lc) * nf(k.ld);
   return k.Kb * (double)k.Kk * (rl(Lb + Lk) + nh(Lb) * nh(Lk) / 2 + 2 * nh(Lb) * nh(Lk) * Nk) +
          k.Kb * 2.0 * Nb * nh(Lb) * Nk;
+}
+
+// FP64 multiply-adds of k_cart2sph on one shellset (one index at a time, zero coefficients skipped).
+double cart2sph_fma(const ClassKey& k) {
+  const double nca = ncart(k.la), ncb = ncart(k.lb), ncc = ncart(k.lc);
+  const double nsa = 2 * k.la + 1, nsb = 2 * k.lb + 1, nsc = 2 * k.lc + 1, nsd = 2 * k.ld + 1;
+  return nca * ncb * (ncc * solid_nnz(k.ld) + solid_nnz(k.lc) * nsd) +
+         nsc * nsd * (nca * solid_nnz(k.lb) + solid_nnz(k.la) * nsb);
 }
 
 // Host preparation of a batch: primitive-pair jobs, class grouping, plans,
@@ -354,9 +376,11 @@ double model_flops_class(const ClassKey& k) {
 // stall other streams; consecutive calls on one stream reuse it in order).
 mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, const HostBasis& h0,
                          const HostBasis& h1, const Batch& bt, const std::vector<int64_t>& offs, mdx_batch** out,
-                         cudaStream_t s, bool call_ws = false) {
+                         cudaStream_t s, bool call_ws = false, bool sph = false) {
   std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> B(new mdx_batch(), batch_free);
+  if (sph && call_ws) return fail(c, MDX_EINVAL, "solid-harmonic batches own their arrays");
   B->owned = !call_ws;
+  B->sph = sph;
   B->ctx = c;
   B->n = (int64_t)offs.size() - 1;
   B->total = offs.back();
@@ -393,9 +417,10 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     classes[key].push_back((int64_t)q);
   }
   std::vector<int2> qp_sorted;
-  std::vector<int64_t> qoff_sorted;
+  std::vector<int64_t> qoff_sorted, cqoff, tqoff;
   qp_sorted.reserve(bt.qp.size());
   qoff_sorted.reserve(bt.qp.size());
+  int64_t cart_total = 0, tmp_total = 0, xg_total = 0;
   mdx_status st;
   for (auto& kv : classes) {
     const int64_t b = (int64_t)qp_sorted.size();
@@ -404,11 +429,38 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
       qoff_sorted.push_back(bt.qoff[q]);
       B->qorig.push_back(bt.qcaller.empty() ? q : bt.qcaller[q]);
     }
+    const int64_t cnt = (int64_t)kv.second.size();
     Plan* plan;
     if ((st = get_plan(c, kv.first, &plan, s)) != MDX_OK) return st;
-    B->ranges.push_back({plan, b, (int64_t)kv.second.size(), kv.first});
-    B->model_flops += model_flops_class(kv.first) * (double)kv.second.size();
-    B->exec_fma += plan->exec_fma * (double)kv.second.size();
+    Plan* splan = nullptr;
+    int grid = 0;
+    double fma = plan->exec_fma;
+    if (sph && !plan->d.reg) {
+      ClassKey k2 = kv.first;
+      k2.store = 2;
+      if ((st = get_plan(c, k2, &splan, s)) != MDX_OK) return st;
+      cudaError_t e = sph_grid(splan->d, cnt, &grid);
+      if (e != cudaSuccess) return cuda_fail(c, e, "solid-harmonic launch shape");
+      xg_total = std::max<int64_t>(xg_total, (int64_t)grid * splan->d.teams_per_cta * splan->d.xg_doubles);
+      fma = splan->exec_fma;
+    }
+    if (sph) {
+      cqoff.resize(qp_sorted.size(), 0);
+      tqoff.resize(qp_sorted.size(), 0);
+      if (!splan) {
+        const ClassKey& k = kv.first;
+        const int64_t nct = (int64_t)ncart(k.la) * ncart(k.lb) * ncart(k.lc) * ncart(k.ld);
+        const int64_t ntm = (int64_t)ncart(k.la) * ncart(k.lb) * (2 * k.lc + 1) * (2 * k.ld + 1);
+        for (int64_t i = b; i < b + cnt; ++i) {
+          cqoff[i] = cart_total; cart_total += nct;
+          tqoff[i] = tmp_total; tmp_total += ntm;
+        }
+        fma += cart2sph_fma(k);
+      }
+    }
+    B->ranges.push_back({plan, b, cnt, kv.first, splan, grid});
+    B->model_flops += model_flops_class(kv.first, sph) * (double)cnt;
+    B->exec_fma += fma * (double)cnt;
   }
   B->njobs = (int64_t)jobs.size();
   if (call_ws) {
@@ -433,6 +485,16 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
         cudaMalloc(&B->recs_s, roff * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return fail(c, MDX_ENOMEM, "record allocation failed");
+    }
+  }
+  if (sph) {
+    if ((st = dev_upload(c, cqoff, &B->cqoff, s)) != MDX_OK) return st;
+    if ((st = dev_upload(c, tqoff, &B->tqoff, s)) != MDX_OK) return st;
+    if ((cart_total > 0 && cudaMalloc(&B->cart, cart_total * sizeof(double)) != cudaSuccess) ||
+        (tmp_total > 0 && cudaMalloc(&B->tmp, tmp_total * sizeof(double)) != cudaSuccess) ||
+        (xg_total > 0 && cudaMalloc(&B->xg, xg_total * sizeof(double)) != cudaSuccess)) {
+      cudaGetLastError();
+      return fail(c, MDX_ENOMEM, "solid-harmonic scratch allocation failed");
     }
   }
   cudaError_t e = cudaStreamSynchronize(s);
@@ -467,9 +529,28 @@ mdx_status batch_run(mdx_ctx* c, mdx_batch* B, double* out, int32_t* nlaunch, cu
     a.rprog_off = c->d_rprog_off;
     a.out = out;
     a.err = c->d_err;
+    if (B->sph && r.splan) {   // solid harmonics folded into the transforms
+      a.plan = r.splan->d;
+      a.sph_scratch = B->xg;
+      e = launch_quartets_sph(a, r.grid, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "solid-harmonic quartet kernel launch");
+      if (r.count > 0) ++nl;
+      continue;
+    }
+    if (B->sph) {              // Cartesian shellsets, then the index-by-index transform
+      a.qout = B->cqoff + r.begin;
+      a.out = B->cart;
+    }
     e = launch_quartets(a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "quartet kernel launch");
     if (r.count > 0) ++nl;
+    if (B->sph) {
+      SphLaunch t{r.key.la, r.key.lb, r.key.lc, r.key.ld, r.count, B->cart, B->cqoff + r.begin, B->tmp,
+                  B->tqoff + r.begin, out, B->qoff + r.begin};
+      e = launch_cart2sph(t, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "solid-harmonic transform");
+      if (r.count > 0) ++nl;
+    }
   }
   if (nlaunch) *nlaunch = nl;
   return MDX_OK;
@@ -525,7 +606,8 @@ void batch_add(Batch& bt, int64_t q, int2 qp, int64_t off, int64_t size, const s
 }
 
 mdx_status make_batch4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,
-                       cudaStream_t s, bool call_ws = false, const double* bound = nullptr, double tau = 0.0) {
+                       cudaStream_t s, bool call_ws = false, const double* bound = nullptr, double tau = 0.0,
+                       bool sph = false) {
   HostBasis hb;
   mdx_status st = fetch_basis(c, basis, hb, s);
   if (st != MDX_OK) return st;
@@ -544,13 +626,14 @@ mdx_status make_batch4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quarte
     const int32_t* s4 = &hq[(size_t)q * 4];
     for (int k = 0; k < 4; ++k)
       if (s4[k] < 0 || s4[k] >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
-    const int64_t size = (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * ncart(hb.l[s4[2]]) * ncart(hb.l[s4[3]]);
+    auto nf = [&](int sh) { return (int64_t)(sph ? 2 * hb.l[sh] + 1 : ncart(hb.l[sh])); };
+    const int64_t size = nf(s4[0]) * nf(s4[1]) * nf(s4[2]) * nf(s4[3]);
     offs[q + 1] = offs[q] + size;
     const int2 qp = hbound.empty() || hbound[(size_t)q] >= tau
                         ? make_int2(pix(s4[0], s4[1], 0), pix(s4[2], s4[3], 0)) : make_int2(0, 0);
     batch_add(bt, q, qp, offs[q], size, hbound, tau);
   }
-  return batch_prepare(c, basis, nullptr, hb, hb, bt, offs, out, s, call_ws);
+  return batch_prepare(c, basis, nullptr, hb, hb, bt, offs, out, s, call_ws, sph);
 }
 
 mdx_status make_batch3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
@@ -689,49 +772,28 @@ mdx_status mdx_eri4_sph(mdx_ctx* c, const mdx_basis* basis, const int32_t* quart
     return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
   }
   mdx_batch* B = nullptr;
-  mdx_status st = make_batch4(c, basis, quartets, n, &B, s);
+  mdx_status st = make_batch4(c, basis, quartets, n, &B, s, false, nullptr, 0.0, true);
   if (st != MDX_OK) return st;
   std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
-  // spherical sizes and offsets in caller order; scratch offsets in class order
-  HostBasis hb;
-  if ((st = fetch_basis(c, basis, hb, s)) != MDX_OK) return st;
-  std::vector<int32_t> hq;
-  if ((st = read_quartets(c, quartets, n, 4, hq, s)) != MDX_OK) return st;
-  std::vector<int64_t> soff(n + 1, 0);
-  for (int64_t q = 0; q < n; ++q) {
-    const int32_t* s4 = &hq[(size_t)q * 4];
-    soff[q + 1] = soff[q] + (int64_t)(2 * hb.l[s4[0]] + 1) * (2 * hb.l[s4[1]] + 1) * (2 * hb.l[s4[2]] + 1) *
-                                (2 * hb.l[s4[3]] + 1);
-  }
-  if (soff[n] > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
-  std::vector<int64_t> coff_s(n), toff_s(n), ooff_s(n);
-  std::vector<int64_t> cart_off(n);
-  int64_t ttot = 0;
-  for (size_t i = 0; i < B->qorig.size(); ++i) {
-    const int64_t q = B->qorig[i];
-    const int32_t* s4 = &hq[(size_t)q * 4];
-    ooff_s[i] = soff[q];
-    toff_s[i] = ttot;
-    ttot += (int64_t)ncart(hb.l[s4[0]]) * ncart(hb.l[s4[1]]) * (2 * hb.l[s4[2]] + 1) * (2 * hb.l[s4[3]] + 1);
-  }
-  double *d_cart, *d_tmp; int64_t *d_co, *d_to, *d_oo;
-  if ((st = ensure(c, "sph_cart", (size_t)B->total, &d_cart, s)) != MDX_OK) return st;
-  if ((st = ensure(c, "sph_tmp", (size_t)std::max<int64_t>(ttot, 1), &d_tmp, s)) != MDX_OK) return st;
-  if ((st = upload(c, "sph_to", toff_s, &d_to, s)) != MDX_OK) return st;
-  if ((st = upload(c, "sph_oo", ooff_s, &d_oo, s)) != MDX_OK) return st;
-  d_co = B->qoff;   // the batch's class-sorted Cartesian offsets
-  cudaError_t e = cudaMemcpyAsync(out_offsets, soff.data(), soff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (B->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  if ((st = check_device_error(c, s)) != MDX_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(out_offsets, B->offsets, (B->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "offsets");
-  if ((st = batch_run(c, B, d_cart, nullptr, s)) != MDX_OK) return st;
-  for (auto& r : B->ranges) {
-    SphLaunch a{r.key.la, r.key.lb, r.key.lc, r.key.ld, r.count, d_cart, d_co + r.begin, d_tmp, d_to + r.begin, out,
-                d_oo + r.begin};
-    e = launch_cart2sph(a, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "solid-harmonic transform");
-  }
-  e = cudaStreamSynchronize(s);
+  if ((st = batch_run(c, B, out, nullptr, s)) != MDX_OK) return st;
+  e = cudaStreamSynchronize(s);   // the batch's arrays are released on return
   if (e != cudaSuccess) return cuda_fail(c, e, "eri4_sph");
   return check_device_error(c, s);
+}
+
+mdx_status mdx_batch_eri4_sph(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,
+                              void* stream) {
+  const NvtxRange nvtx_range("mdx_batch_eri4_sph");
+  if (!c || !out) return MDX_EINVAL;
+  *out = nullptr;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  if (n < 1 || !quartets) return fail(c, MDX_EINVAL, "invalid arguments");
+  return make_batch4(c, basis, quartets, n, out, (cudaStream_t)stream, false, nullptr, 0.0, true);
 }
 
 mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
@@ -809,6 +871,7 @@ mdx_status mdx_batch_run_materialized(mdx_ctx* c, mdx_batch* B, double* out, int
   if (!c || !B || !out) return MDX_EINVAL;
   if (B->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
   if (B->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  if (B->sph) return fail(c, MDX_EUNSUPPORTED, "materialized path: Cartesian batches only");
   for (auto& r : B->ranges)
     if (r.count > 0 && (r.key.Kb != 1 || r.key.Kk != 1 || r.key.onec))
       return fail(c, MDX_EUNSUPPORTED, "materialized path: uncontracted 4-center classes only");
@@ -904,6 +967,7 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
   if (!c || !b || !out || max_trial < 1) return MDX_EINVAL;
   if (b->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
   if (b->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  if (b->sph) return fail(c, MDX_EUNSUPPORTED, "autotuner: Cartesian batches only");
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_pair_records(b->b0, b->b1, b->jobs, b->njobs, b->recs, b->recs_s, c->d_err, s);

@@ -35,6 +35,12 @@ __constant__ uint32_t c_cart[8][36];
 // real solid harmonics l <= 6 as Cartesian polynomials: c_sph[c_sph_off[l] + (m+l)*ncart(l) + k]
 __constant__ double c_sph[840];
 __constant__ int c_sph_off[kLmax + 2];
+// the same, sparse: row m' = m + l of shell l has c_spn[l][m'] non-zero terms, Cartesian
+// components c_spk[l][m'][j] with coefficients c_spv[l][m'][j]
+constexpr int kSphNnzMax = 12;
+__constant__ int c_spn[kLmax + 1][2 * kLmax + 1];
+__constant__ uint8_t c_spk[kLmax + 1][2 * kLmax + 1][kSphNnzMax];
+__constant__ double c_spv[kLmax + 1][2 * kLmax + 1][kSphNnzMax];
 
 cudaError_t kernel_attributes_init();
 
@@ -531,6 +537,77 @@ cudaError_t launch_grad_contract(const QuartetLaunch& a, const double* V, cudaSt
   return cudaGetLastError();
 }
 
+// b1: C1 = Ex (x) X for `ncols` columns (X column stride hb at o_X, C1 column
+// stride c1stride at o_C1); two entries per lane (see run_step).
+__device__ __forceinline__ void bra_b1(const PlanDev& P, double* ws, int o_X, int o_C1, int c1stride, int ncols, int tl,
+                                       int T) {
+  const int tot = P.nb1 * ncols;
+  for (int e = tl; e < tot; e += 2 * T) {
+    const int e1 = e + T < tot ? e + T : e;
+    const int ent0 = e / ncols, col0 = e - ent0 * ncols;
+    const int ent1 = e1 / ncols, col1 = e1 - ent1 * ncols;
+    const StepEntry s0 = P.b1[ent0], s1 = P.b1[ent1];
+    const double* c0 = ws + s0.coef;
+    const double* x0 = ws + o_X + col0 * P.hb + s0.src;
+    const double* c1 = ws + s1.coef;
+    const double* x1 = ws + o_X + col1 * P.hb + s1.src;
+    double v0 = 0.0, v1 = 0.0;
+    dual_dot(c0, x0, s0.stride, s0.n, c1, x1, s1.stride, s1.n, v0, v1);
+    ws[o_C1 + col0 * c1stride + s0.out] = v0;
+    if (e1 != e) ws[o_C1 + col1 * c1stride + s1.out] = v1;
+  }
+}
+
+// b23: OUT[ab][col] (+)= Ez (x) Ey (x) C1 for `ncols` columns; two Hermite
+// z-indices v in flight per lane (independent inner sums over u). to_global:
+// the finished value goes to outq[ab * out_stride + cm[col]] instead of OUT.
+__device__ __forceinline__ void bra_b23(const PlanDev& P, double* ws, int o_C1, int c1stride, int o_OUT, int ncols,
+                                        bool accumulate, bool to_global, double* outq, const uint16_t* cm,
+                                        int out_stride, bool active, int tl, int T) {
+  const int tot = P.nb23 * ncols;
+  for (int e = tl; e < tot; e += T) {
+    const int ent = e / ncols, col = e - ent * ncols;
+    const B23Entry s = P.b23[ent];
+    const double* c1 = ws + o_C1 + col * c1stride + s.src + s.u0;
+    double* o = ws + o_OUT + s.out * ncols + col;
+    double acc = accumulate ? *o : 0.0;
+    const int r1 = s.r + 1;
+    const double* ey = ws + s.ey;
+    const double* ez = ws + s.ez;
+    const int su = s.su, sv = s.sv, nu = s.nu;
+    int iv = 0;
+    for (; iv + 1 < s.nv; iv += 2) {
+      const int va = s.v0 + iv * sv, vb = va + sv;
+      const double* ra = c1 + va * r1 - (va * (va - 1)) / 2;
+      const double* rb = c1 + vb * r1 - (vb * (vb - 1)) / 2;
+      double ia = 0.0, ib = 0.0;
+      double y = ey[0], xa = ra[0], xb = rb[0];
+      for (int iu = 1; iu < nu; ++iu) {
+        const double ny = ey[iu * su], nxa = ra[iu * su], nxb = rb[iu * su];
+        ia = fma(y, xa, ia);
+        ib = fma(y, xb, ib);
+        y = ny; xa = nxa; xb = nxb;
+      }
+      ia = fma(y, xa, ia);
+      ib = fma(y, xb, ib);
+      acc = fma(ez[iv * sv], ia, acc);
+      acc = fma(ez[(iv + 1) * sv], ib, acc);
+    }
+    if (iv < s.nv) {
+      const int va = s.v0 + iv * sv;
+      const double* ra = c1 + va * r1 - (va * (va - 1)) / 2;
+      double ia = 0.0;
+      for (int iu = 0; iu < nu; ++iu) ia = fma(ey[iu * su], ra[iu * su], ia);
+      acc = fma(ez[iv * sv], ia, acc);
+    }
+    if (to_global) {
+      if (active) outq[(int64_t)s.out * out_stride + cm[col]] = acc;
+    } else {
+      *o = acc;
+    }
+  }
+}
+
 // The work of one team on one shell quartet q (all groups, all primitives,
 // store / digestion / gradient epilogue). Inactive teams run the same control
 // flow on a shadow quartet (so that barriers match) and write nothing global.
@@ -574,74 +651,10 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
         run_step(P.kprog + grp.k3_off, grp.k3_n, ws, tl, T, pk > 0);
         team_sync<CTA>(mask);
       }
-      // b1: C1 = Ex (x) X, per column (two entries per lane, see run_step)
-      {
-        const int tot = P.nb1 * ncols;
-        int e = tl;
-        for (; e < tot; e += 2 * T) {
-          const int e1 = e + T < tot ? e + T : e;
-          const int ent0 = e / ncols, col0 = e - ent0 * ncols;
-          const int ent1 = e1 / ncols, col1 = e1 - ent1 * ncols;
-          const StepEntry s0 = P.b1[ent0], s1 = P.b1[ent1];
-          const double* c0 = ws + s0.coef;
-          const double* x0 = ws + P.o_X + col0 * P.hb + s0.src;
-          const double* c1 = ws + s1.coef;
-          const double* x1 = ws + P.o_X + col1 * P.hb + s1.src;
-          double v0 = 0.0, v1 = 0.0;
-          dual_dot(c0, x0, s0.stride, s0.n, c1, x1, s1.stride, s1.n, v0, v1);
-          ws[P.o_C1 + col0 * P.c1size + s0.out] = v0;
-          if (e1 != e) ws[P.o_C1 + col1 * P.c1size + s1.out] = v1;
-        }
-      }
+      bra_b1(P, ws, P.o_X, P.o_C1, P.c1size, ncols, tl, T);
       team_sync<CTA>(mask);
-      // b23: OUT += Ez (x) Ey (x) C1, per column; two Hermite z-indices v in
-      // flight per lane (independent inner sums over u)
-      {
-        const bool to_global = direct && pb == Kb - 1;
-        const uint16_t* cm = P.colmap + grp.col_off;
-        const int tot = P.nb23 * ncols;
-        for (int e = tl; e < tot; e += T) {
-          const int ent = e / ncols, col = e - ent * ncols;
-          const B23Entry s = P.b23[ent];
-          const double* c1 = ws + P.o_C1 + col * P.c1size + s.src + s.u0;
-          double* o = ws + P.o_OUT + s.out * ncols + col;
-          double acc = pb > 0 ? *o : 0.0;
-          const int r1 = s.r + 1;
-          const double* ey = ws + s.ey;
-          const double* ez = ws + s.ez;
-          const int su = s.su, sv = s.sv, nu = s.nu;
-          int iv = 0;
-          for (; iv + 1 < s.nv; iv += 2) {
-            const int va = s.v0 + iv * sv, vb = va + sv;
-            const double* ra = c1 + va * r1 - (va * (va - 1)) / 2;
-            const double* rb = c1 + vb * r1 - (vb * (vb - 1)) / 2;
-            double ia = 0.0, ib = 0.0;
-            double y = ey[0], xa = ra[0], xb = rb[0];
-            for (int iu = 1; iu < nu; ++iu) {
-              const double ny = ey[iu * su], nxa = ra[iu * su], nxb = rb[iu * su];
-              ia = fma(y, xa, ia);
-              ib = fma(y, xb, ib);
-              y = ny; xa = nxa; xb = nxb;
-            }
-            ia = fma(y, xa, ia);
-            ib = fma(y, xb, ib);
-            acc = fma(ez[iv * sv], ia, acc);
-            acc = fma(ez[(iv + 1) * sv], ib, acc);
-          }
-          if (iv < s.nv) {
-            const int va = s.v0 + iv * sv;
-            const double* ra = c1 + va * r1 - (va * (va - 1)) / 2;
-            double ia = 0.0;
-            for (int iu = 0; iu < nu; ++iu) ia = fma(ey[iu * su], ra[iu * su], ia);
-            acc = fma(ez[iv * sv], ia, acc);
-          }
-          if (to_global) {
-            if (active) outq[(int64_t)s.out * P.Nk + cm[col]] = acc;
-          } else {
-            *o = acc;
-          }
-        }
-      }
+      bra_b23(P, ws, P.o_C1, P.c1size, P.o_OUT, ncols, pb > 0, direct && pb == Kb - 1, outq,
+              P.colmap + grp.col_off, P.Nk, active, tl, T);
       // Barrier before the next writer of what b23 reads: the bra record (reloaded
       // per bra primitive unless the class has one primitive quartet) or OUT (read
       // by other lanes in the digestion / gradient epilogue). C1 is overwritten by
@@ -682,6 +695,186 @@ __global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets(const QuartetLaun
   const bool active = q < a.nq;
   if (!active) q = a.nq - 1;   // idle teams shadow the last quartet and store nothing
   quartet_body<CTA>(a, ws, q, active, tl, mask);
+}
+
+// One quartet over real solid harmonics (Eqs. solid2herm-1/2: the
+// Cartesian-to-solid coefficients are contracted into the transforms, so the
+// bra steps and everything after them run on 2l+1 components per shell). For
+// every bra primitive pair:
+//   1. the ket groups build the Cartesian columns [p|cd] as in the Cartesian
+//      kernel and stage them in the team's global area Xg[cd][p];
+//   2. ket pass d -> d':  Yg[c][d'][p] = sum_d C^{ld}_{d'd} Xg[c][d][p];
+//   3. per group of spherical columns c'd':
+//        ket pass c -> c': Xs[c'd'][p] = sum_c C^{lc}_{c'c} Yg[c][d'][p]   (shared memory)
+//        bra steps b1/b23 on those columns: OUT[ab][c'd']                  (Eq. bra-from-hermite)
+//        bra pass b -> b': T[a][b'][c'd'] = sum_b C^{lb}_{b'b} OUT[ab][c'd']
+//        bra pass a -> a': out[a'b'][c'd'] (+)= sum_a C^{la}_{a'a} T[a][b'][c'd']
+// Each pass is a sparse product (the solid harmonics of l have few Cartesian
+// terms per row); applied one index at a time it costs far less than the
+// Cartesian bra steps it removes.
+template <bool CTA>
+__device__ void quartet_sph(const QuartetLaunch& a, double* ws, double* xg, int64_t q, bool active, int tl,
+                            unsigned mask) {
+  const PlanDev& P = a.plan;
+  const int T = P.T;
+  const int2 qp = a.qpairs[q];
+  const int64_t bra0 = a.pair_rec[qp.x + a.bra_var_off];
+  const int64_t ket0 = a.pair_rec[qp.y + a.ket_var_off];
+  const int Kb = P.Kb, Kk = P.Kk;
+  const int hbp = P.hbp;
+  const int la = P.la, lb = P.lb, lc = P.lc, ld = P.ld;
+  const int nb = d_ncart(lb), nd = d_ncart(ld), nc = d_ncart(lc);
+  const int nsb = P.nsb, nsd = P.nsd;
+  const int nks = P.nsc * nsd;
+  double* yg = xg + (int64_t)P.Nk * hbp;
+  double* outq = a.out + a.qout[q];
+  if (P.cache_R) {
+    load_record(ws + P.o_recb, a.recs + bra0, P.recb, tl, T);
+    load_record(ws + P.o_reck, a.recs_signed + ket0, P.reck, tl, T);
+    team_sync<CTA>(mask);
+    compute_R<CTA>(a, ws, tl, mask);
+  }
+  for (int pb = 0; pb < Kb; ++pb) {
+    if (!P.cache_R) load_record(ws + P.o_recb, a.recs + bra0 + (int64_t)pb * P.recb, P.recb, tl, T);
+    // 1. Cartesian ket columns, group by group, staged in Xg
+    for (int g = 0; g < P.ngroups; ++g) {
+      const Group grp = P.groups[g];
+      for (int pk = 0; pk < Kk; ++pk) {
+        if (!P.cache_R) {
+          load_record(ws + P.o_reck, a.recs_signed + ket0 + (int64_t)pk * P.reck, P.reck, tl, T);
+          team_sync<CTA>(mask);
+          compute_R<CTA>(a, ws, tl, mask);
+        }
+        if (grp.k1_n > 0) {
+          run_step(P.kprog + grp.k1_off, grp.k1_n, ws, tl, T, false);
+          team_sync<CTA>(mask);
+        }
+        run_step(P.kprog + grp.k2_off, grp.k2_n, ws, tl, T, false);
+        team_sync<CTA>(mask);
+        run_step(P.kprog + grp.k3_off, grp.k3_n, ws, tl, T, pk > 0);
+        team_sync<CTA>(mask);
+      }
+      const uint16_t* cm = P.colmap + grp.col_off;
+      const int tot = grp.ncols * hbp;
+      for (int e = tl; e < tot; e += T) {
+        const int col = e / hbp, i = e - col * hbp;
+        xg[(int64_t)cm[col] * hbp + i] = ws[P.o_X + col * P.hb + i];
+      }
+      team_sync<CTA>(mask);   // the next group's k3 rewrites X; every lane reads Xg below
+    }
+    // 2. ket pass d -> d'
+    {
+      const int tot = nc * nsd * hbp;
+      for (int e = tl; e < tot; e += T) {
+        const int cdp = e / hbp, i = e - cdp * hbp;
+        const int c = cdp / nsd, dp = cdp - c * nsd;
+        const int n = c_spn[ld][dp];
+        double v = 0.0;
+        for (int j = 0; j < n; ++j) v = fma(c_spv[ld][dp][j], xg[((int64_t)c * nd + c_spk[ld][dp][j]) * hbp + i], v);
+        yg[(int64_t)cdp * hbp + i] = v;
+      }
+      team_sync<CTA>(mask);
+    }
+    // 3. groups of spherical ket columns
+    for (int c0 = 0; c0 < nks; c0 += P.ncols_s) {
+      const int ncols = min(P.ncols_s, nks - c0);
+      // ket pass c -> c' into shared memory (the X layout the bra steps read)
+      for (int e = tl; e < ncols * hbp; e += T) {
+        const int col = e / hbp, i = e - col * hbp;
+        const int gcol = c0 + col, cp = gcol / nsd, dp = gcol - cp * nsd;
+        const int n = c_spn[lc][cp];
+        double v = 0.0;
+        for (int j = 0; j < n; ++j) v = fma(c_spv[lc][cp][j], yg[((int64_t)c_spk[lc][cp][j] * nsd + dp) * hbp + i], v);
+        ws[P.o_Xs + col * P.hb + i] = v;
+      }
+      team_sync<CTA>(mask);
+      bra_b1(P, ws, P.o_Xs, P.o_C1s, P.c1s, ncols, tl, T);
+      team_sync<CTA>(mask);
+      bra_b23(P, ws, P.o_C1s, P.c1s, P.o_OUTs, ncols, false, false, nullptr, nullptr, 0, active, tl, T);
+      team_sync<CTA>(mask);
+      // bra pass b -> b' into the C1 slots: T[col][a][b']
+      {
+        const int na = d_ncart(la);
+        for (int e = tl; e < na * nsb * ncols; e += T) {
+          const int ab = e / ncols, col = e - ab * ncols;
+          const int aa = ab / nsb, bp = ab - aa * nsb;
+          const int n = c_spn[lb][bp];
+          double v = 0.0;
+          for (int j = 0; j < n; ++j)
+            v = fma(c_spv[lb][bp][j], ws[P.o_OUTs + (aa * nb + c_spk[lb][bp][j]) * ncols + col], v);
+          ws[P.o_C1s + col * P.c1s + ab] = v;
+        }
+      }
+      team_sync<CTA>(mask);
+      // bra pass a -> a' into the output (summed over the bra primitive pairs)
+      for (int e = tl; e < P.nsa * nsb * ncols; e += T) {
+        const int ab = e / ncols, col = e - ab * ncols;
+        const int ap = ab / nsb, bp = ab - ap * nsb;
+        const int n = c_spn[la][ap];
+        double v = 0.0;
+        for (int j = 0; j < n; ++j) v = fma(c_spv[la][ap][j], ws[P.o_C1s + col * P.c1s + c_spk[la][ap][j] * nsb + bp], v);
+        if (active) {
+          double* o = outq + (int64_t)ab * nks + c0 + col;
+          *o = pb > 0 ? *o + v : v;
+        }
+      }
+      team_sync<CTA>(mask);
+    }
+  }
+}
+
+// Solid-harmonic launches: as many CTAs as can be resident (`grid`, chosen
+// by the host), each looping over quartets; team `slot` owns global staging
+// area slot * xg_doubles of a.sph_scratch.
+template <bool CTA>
+__global__ void __launch_bounds__(CTA ? 1024 : 128) k_quartets_sph(const QuartetLaunch a) {
+  extern __shared__ __align__(16) double smem[];
+  const PlanDev& P = a.plan;
+  const int T = P.T;
+  const int team = threadIdx.x / T;
+  const int tl = threadIdx.x - team * T;
+  double* ws = smem + (size_t)team * P.team_doubles;
+  unsigned mask = CTA ? 0u : 0xffffffffu;
+  if (!CTA) {
+    const int wbase = threadIdx.x & ~31;
+    const int live = blockDim.x - wbase;
+    if (live < 32) mask = (1u << live) - 1u;
+  }
+  const int64_t slot = (int64_t)blockIdx.x * P.teams_per_cta + team;
+  double* xg = a.sph_scratch + slot * P.xg_doubles;
+  const int64_t stride = (int64_t)gridDim.x * P.teams_per_cta;
+  const int64_t rounds = (a.nq + stride - 1) / stride;
+  for (int64_t r = 0; r < rounds; ++r) {
+    int64_t q = r * stride + slot;
+    const bool active = q < a.nq;
+    if (!active) q = a.nq - 1;   // idle teams shadow the last quartet and store nothing
+    quartet_sph<CTA>(a, ws, xg, q, active, tl, mask);
+  }
+}
+
+cudaError_t sph_grid(const PlanDev& P, int64_t nq, int* grid) {
+  const int block = P.teams_per_cta * P.T;
+  const size_t shm = (size_t)P.teams_per_cta * P.team_doubles * sizeof(double);
+  int bps = 0, dev = 0, sms = 0;
+  cudaError_t e = P.T > 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_quartets_sph<true>, block, shm)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_quartets_sph<false>, block, shm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (nq + P.teams_per_cta - 1) / P.teams_per_cta;
+  *grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(1, bps) * sms));
+  return cudaSuccess;
+}
+
+cudaError_t launch_quartets_sph(const QuartetLaunch& a, int grid, cudaStream_t s) {
+  if (a.nq <= 0) return cudaSuccess;
+  const PlanDev& P = a.plan;
+  if (!P.sph || !a.sph_scratch || !a.qout || grid < 1) return cudaErrorInvalidValue;
+  const int block = P.teams_per_cta * P.T;
+  const size_t shm = (size_t)P.teams_per_cta * P.team_doubles * sizeof(double);
+  if (P.T > 32) k_quartets_sph<true><<<grid, block, shm, s>>>(a);
+  else k_quartets_sph<false><<<grid, block, shm, s>>>(a);
+  return cudaGetLastError();
 }
 
 // Persistent kernel over a queue of work items from many launches (classes,
@@ -1102,11 +1295,34 @@ cudaError_t kernel_attributes_init() {
     e = cudaMemcpyToSymbol(c_sph, flat.data(), flat.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sph_off, offs, sizeof(offs));
     if (e != cudaSuccess) return e;
+    int spn[kLmax + 1][2 * kLmax + 1] = {};
+    uint8_t spk[kLmax + 1][2 * kLmax + 1][kSphNnzMax] = {};
+    double spv[kLmax + 1][2 * kLmax + 1][kSphNnzMax] = {};
+    for (int l = 0; l <= kLmax; ++l) {
+      const int nc = ncart(l);
+      for (int m = 0; m < 2 * l + 1; ++m)
+        for (int k = 0; k < nc; ++k) {
+          const double c = tabs[l][(size_t)m * nc + k];
+          if (c == 0.0) continue;
+          if (spn[l][m] >= kSphNnzMax) return cudaErrorInvalidValue;
+          spk[l][m][spn[l][m]] = (uint8_t)k;
+          spv[l][m][spn[l][m]] = c;
+          ++spn[l][m];
+        }
+    }
+    e = cudaMemcpyToSymbol(c_spn, spn, sizeof(spn));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_spk, spk, sizeof(spk));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_spv, spv, sizeof(spv));
+    if (e != cudaSuccess) return e;
   }
   const int maxshm = 227 * 1024;
   e = cudaFuncSetAttribute(k_quartets<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_quartets<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_quartets_sph<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_quartets_sph<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm);
   if (e != cudaSuccess) return e;
   // the persistent kernel also holds ~0.5 KB of static shared memory (item index, launch descriptor)
   e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, maxshm - 1024);

@@ -67,6 +67,8 @@ struct QuartetLaunch {
   const double* const* mol_D;
   double* const* mol_K;
   const int32_t* mol_nao;
+  // solid-harmonic launches (plan.sph): global staging, xg_doubles per team of the launch grid
+  double* sph_scratch;
 };
 
 static_assert(sizeof(QuartetLaunch) % sizeof(int) == 0, "descriptor copied word by word");
@@ -90,6 +92,11 @@ cudaError_t launch_persistent(const PersistLaunch& pl, int64_t smem_bytes, int g
 const void* persistent_kernel_ptr();
 
 cudaError_t launch_quartets(const QuartetLaunch& a, cudaStream_t s);
+// Solid-harmonic shellsets (plan.sph, store at a.out + a.qout[q]): `grid` CTAs loop over the quartets;
+// sph_grid gives the grid for nq quartets (resident CTAs at most), and a.sph_scratch must hold
+// grid * teams_per_cta * xg_doubles doubles.
+cudaError_t sph_grid(const PlanDev& P, int64_t nq, int* grid);
+cudaError_t launch_quartets_sph(const QuartetLaunch& a, int grid, cudaStream_t s);
 // Writes zeros over n output ranges given as (offset, doubles) pairs (screened-out shellsets).
 cudaError_t launch_zero_ranges(const int64_t* ranges, int64_t n, double* out, cudaStream_t s);
 // Gradient epilogue over shellsets already in memory (V + q N_b N_k for quartet q of launch a).

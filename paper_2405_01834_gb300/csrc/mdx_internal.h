@@ -131,7 +131,8 @@ struct Group {
 
 struct ClassKey {
   int la, lb, lc, ld, Kb, Kk, onec;
-  int store = 0;   // 1: plan for the store epilogue only (no OUT region when Kb = 1)
+  int store = 0;   // 1: plan for the store epilogue only (no OUT region when Kb = 1);
+                   // 2: solid-harmonic store (k_quartets_sph; see PlanDev::sph)
   bool operator<(const ClassKey& o) const {
     const int a[8] = {la, lb, lc, ld, Kb, Kk, onec, store}, b[8] = {o.la, o.lb, o.lc, o.ld, o.Kb, o.Kk, o.onec, o.store};
     for (int i = 0; i < 8; ++i) if (a[i] != b[i]) return a[i] < b[i];
@@ -152,6 +153,16 @@ struct PlanDev {
   int32_t cache_R;                       // R computed once (single primitive quartet)
   int32_t reg;                           // launch the register kernel (store / digestion launches)
   int32_t has_out;                       // OUT region present (0: store-only plan, b23 writes global memory)
+  // Solid-harmonic output (store = 2). The ket groups write their Cartesian columns [p|cd] to a
+  // per-team global staging area Xg; two sparse passes (d -> d', then c -> c') form the spherical
+  // ket columns [p|c'd'] in shared memory, group by group of ncols_s columns; the bra steps b1/b23
+  // run on those columns, and two sparse passes (b -> b', a -> a') write the spherical shellset.
+  int32_t sph;
+  int32_t nsa, nsb, nsc, nsd;            // 2l + 1 per shell
+  int32_t ncols_s;                       // spherical ket columns per bra-pass group
+  int32_t o_Xs, o_C1s, o_OUTs, c1s;      // bra-pass layout (C1 stride c1s also holds the [a][b'] pass)
+  int32_t hbp;                           // Hermite entries of the bra: length of one staged column
+  int64_t xg_doubles;                    // staging per team: Xg [Nk][hbp] then Yg [nc_c * nsd][hbp]
   const Group* groups;
   const StepEntry* kprog;
   const StepEntry* b1;
@@ -199,4 +210,6 @@ namespace mdx {
 // Real solid harmonics as Cartesian polynomials, rows m = -l..l, columns the
 // Cartesian components in library order: tables[l][(m+l)*ncart(l) + k].
 std::vector<std::vector<double>> build_solid_tables(int lmax);
+// Non-zero coefficients of the real solid harmonics of angular momentum l (over all m).
+int solid_nnz(int l);
 }  // namespace mdx

@@ -16,7 +16,7 @@
 namespace {
 
 constexpr int kProbeBlock = 256;
-constexpr int kBlocksPerSm = 4;
+constexpr int kBlocksPerSm = 8;
 constexpr int kSink = 4096;
 
 // target of the never-taken stores (a valid device address all the same)
@@ -112,7 +112,7 @@ extern "C" mdx_status mdx_fp64_peak(int kind, int reps, double* gflops, void* st
     return MDX_ECUDA;
   }
   const int blocks = sms * kBlocksPerSm;
-  // about 50 ms per launch at ~1.2 TFLOP/s (the DMMA loops do more work per iteration)
+  // about 100 ms per launch at ~1.2 TFLOP/s (the DMMA loops do more work per iteration)
   const int iters = kind == 0 ? 24576 : (kind == 3 ? 1024 : (kind == 2 ? 4096 : 8192));
   double* sink = nullptr;   // never written: the store's condition never holds
   if (cudaGetSymbolAddress((void**)&sink, g_probe_sink) != cudaSuccess) {

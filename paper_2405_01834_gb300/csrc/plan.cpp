@@ -155,7 +155,11 @@ bool validate_plan(const Plan& plan, std::string& err) {
   const PlanDev& P = plan.d;
   const long W = P.team_doubles;
   auto in = [&](long lo, long hi, long a) { return a >= lo && a < hi; };
-  const long xr = P.o_X, cr = P.o_C1, orr = P.o_OUT;
+  const long xr = P.o_X;   // the ket groups' X columns
+  // the bra steps' layout: the plan's own, or the bra pass of a solid-harmonic plan
+  const long bx = P.sph ? P.o_Xs : P.o_X, cr = P.sph ? P.o_C1s : P.o_C1, orr = P.sph ? P.o_OUTs : P.o_OUT;
+  const long c1stride = P.sph ? P.c1s : P.c1size;
+  const long out_cols = P.sph ? (long)P.ncols_s * P.Nb : (P.has_out ? (long)P.ncols_max * P.Nb : 0);
   for (const Group& g : plan.groups) {
     if (g.ncols < 1 || g.ncols > P.ncols_max) { err = "bad group width"; return false; }
     const StepEntry* k = plan.kprog.data();
@@ -187,12 +191,12 @@ bool validate_plan(const Plan& plan, std::string& err) {
     for (int i = g.col_off; i < g.col_off + g.ncols; ++i)
       if (plan.colmap[i] >= P.Nk) { err = "column map out of range"; return false; }
   }
-  const long ncm = P.ncols_max;
+  const long ncm = P.sph ? P.ncols_s : P.ncols_max;
   for (const StepEntry& s : plan.b1) {
     const long last = (long)(s.n - 1) * s.stride;
     if (!in(0, P.hb, s.src) || !in(0, P.hb, s.src + last) || !in(0, P.c1size, s.out) ||
         !in(P.o_recb, P.o_recb + P.recb, s.coef) || !in(P.o_recb, P.o_recb + P.recb, s.coef + last) ||
-        xr + (ncm - 1) * P.hb + P.hb > cr) { err = "b1 entry out of range"; return false; }
+        bx + (ncm - 1) * P.hb + P.hb > cr) { err = "b1 entry out of range"; return false; }
   }
   for (const B23Entry& s : plan.b23) {
     const int vmax = s.v0 + (s.nv - 1) * s.sv;
@@ -201,13 +205,23 @@ bool validate_plan(const Plan& plan, std::string& err) {
     if (s.out >= P.Nb || !in(0, P.c1size, s.src + rowmax + umax) || umax > s.r - vmax ||
         !in(P.o_recb, P.o_recb + P.recb, s.ey + (long)(s.nu - 1) * s.su) ||
         !in(P.o_recb, P.o_recb + P.recb, s.ez + (long)(s.nv - 1) * s.sv) ||
-        cr + ncm * P.c1size > orr || orr + (P.has_out ? ncm * P.Nb : 0) > W) {
+        cr + ncm * c1stride > orr || orr + out_cols > W) {
       err = "b23 entry out of range";
       return false;
     }
   }
   if (P.o_R1 + tet(P.L) > P.o_X || P.o_R0 + tet(P.L + 1) > P.o_R1 || P.o_G + P.L + 1 > P.o_R0 ||
       P.o_reck + P.reck > P.o_scal) { err = "fixed regions overlap"; return false; }
+  if (P.sph) {
+    // the bra pass starts where the ket groups' region starts (R at level 0 stays below it), and the
+    // [a][b'] pass of each column fits its C1 slot
+    if (P.o_Xs < P.o_R0 + tet(P.L + 1) || P.c1size > P.c1s || ncart(P.la) * P.nsb > P.c1s || P.ncols_s < 1 ||
+        P.ncols_s > P.nsc * P.nsd || P.o_C1s < P.o_Xs + (long)P.ncols_s * P.hb ||
+        P.o_OUTs < P.o_C1s + (long)P.ncols_s * P.c1s || P.hbp > P.hb) {
+      err = "solid-harmonic bra pass out of range";
+      return false;
+    }
+  }
   return true;
 }
 
@@ -331,13 +345,17 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   for (size_t ic = 0; ic < cc.size(); ++ic)
     for (size_t id = 0; id < cd.size(); ++id) allcols.push_back({cc[ic], cd[id], (int)(ic * cd.size() + id)});
 
-  // store-only plans of uncontracted-bra classes need no OUT region: b23 writes the shellset to global memory
-  P.has_out = (key.store && key.Kb == 1) ? 0 : 1;
+  // store-only plans of uncontracted-bra classes need no OUT region: b23 writes the shellset to global memory;
+  // the ket groups of a solid-harmonic plan hold only their X columns (the bra pass has its own layout)
+  const bool sph = key.store == 2;
+  P.sph = sph ? 1 : 0;
+  P.has_out = sph ? 0 : ((key.store && key.Kb == 1) ? 0 : 1);
   const int out_per_col = P.has_out ? P.Nb : 0;
+  const int c1_per_col = sph ? 0 : P.c1size;
   auto region_size = [&](int a_size, int b_size) { return std::max(r1size, a_size + b_size); };
   auto team_doubles = [&](int a_size, int b_size, int ncols) {
     int reg = (region_size(a_size, b_size) + 1) & ~1;
-    int tot = o_region + reg + ncols * P.hb + ncols * P.c1size + ncols * out_per_col;
+    int tot = o_region + reg + ncols * P.hb + ncols * c1_per_col + ncols * out_per_col;
     return (tot + 1) & ~1;
   };
 
@@ -390,7 +408,7 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
           cmax = std::max(cmax, (int)groups.back().size());
         }
       }
-      const int td = o_region + ((regmax + 1) & ~1) + cmax * (P.hb + P.c1size + out_per_col);
+      const int td = o_region + ((regmax + 1) & ~1) + cmax * (P.hb + c1_per_col + out_per_col);
       return ok && td * 8 <= smem_budget_bytes;
     };
     // the largest cap that fits (binary search; the workspace grows with the cap)
@@ -415,11 +433,33 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   P.o_B = o_region;   // per group: o_A + that group's A size (programs carry absolute offsets)
   P.o_X = o_region + reg;
   P.o_C1 = P.o_X + cmax * P.hb;
-  P.o_OUT = P.o_C1 + cmax * P.c1size;
+  P.o_OUT = P.o_C1 + cmax * c1_per_col;
   // odd: the workspaces of the teams of a CTA start on different shared-memory
   // bank pairs, so lanes of different teams at the same offset do not conflict
   P.team_doubles = (P.o_OUT + cmax * out_per_col) | 1;
   P.ncols_max = cmax;
+  if (sph) {
+    // bra pass: spherical ket columns in groups of ncols_s, each column holding X (hb), C1 or the
+    // [a][b'] pass (c1s) and OUT (Nb), laid out from o_region (the ket groups are finished by then)
+    P.nsa = 2 * key.la + 1; P.nsb = 2 * key.lb + 1; P.nsc = 2 * key.lc + 1; P.nsd = 2 * key.ld + 1;
+    P.c1s = std::max(P.c1size, ncart(key.la) * P.nsb) | 1;
+    const int nks = P.nsc * P.nsd;
+    const int per = P.hb + P.c1s + P.Nb;
+    // as wide as fits in the ket groups' footprint (the workspace, and so the CTAs per SM, stay as the
+    // ket part needs them), at least one column within the budget
+    const int room = std::max(P.team_doubles - o_region, per);
+    int cs = std::min(nks, std::min(room, smem_budget_bytes / 8 - o_region) / per);
+    if (cs < 1) { err = "solid-harmonic bra pass does not fit the shared-memory budget"; return false; }
+    const int ngs = (nks + cs - 1) / cs;
+    cs = (nks + ngs - 1) / ngs;
+    P.ncols_s = cs;
+    P.o_Xs = o_region;
+    P.o_C1s = P.o_Xs + cs * P.hb;
+    P.o_OUTs = P.o_C1s + cs * P.c1s;
+    P.team_doubles = std::max(P.team_doubles, P.o_OUTs + cs * P.Nb) | 1;
+    P.hbp = nherm(P.Lb);
+    P.xg_doubles = (int64_t)P.hbp * (P.Nk + (int64_t)ncart(key.lc) * P.nsd);
+  }
   if (P.team_doubles >= 65536 || P.team_doubles * 8 > smem_budget_bytes) {
     err = "workspace exceeds the shared-memory budget";
     return false;
@@ -461,14 +501,23 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   for (int n = 0; n < P.L; ++n) fma_r += tet(P.L - n + 1) - 1;
   const double nrec = (P.cache_R || P.ngroups == 1) ? 1.0 : P.ngroups;
   plan.exec_fma = key.Kb * key.Kk * (fma_k + nrec * (fma_r + 8.0 * (P.L + 1))) + key.Kb * fma_b * P.Nk;
+  if (sph) {
+    // per bra primitive: the two ket passes over the staged columns, the bra steps on the spherical
+    // columns, and the two bra passes
+    const double nks = (double)P.nsc * P.nsd;
+    const double ket_sph = (double)P.hbp * ((double)ncart(key.lc) * solid_nnz(key.ld) + (double)solid_nnz(key.lc) * P.nsd);
+    const double bra_sph = nks * ((double)ncart(key.la) * solid_nnz(key.lb) + (double)solid_nnz(key.la) * P.nsb);
+    plan.exec_fma = key.Kb * key.Kk * (fma_k + nrec * (fma_r + 8.0 * (P.L + 1))) +
+                    key.Kb * (ket_sph + fma_b * nks + bra_sph);
+  }
   const double team_fma_per_prim = plan.exec_fma / ((double)key.Kb * key.Kk);
 
   // register kernel (one thread per quartet) where the class has one
   const bool has_reg = reg_eligible(key.la, key.lb, key.lc, key.ld) || reg_xs_eligible(key.la, key.lb, key.lc, key.ld);
-  if (cfg.variant == 2 && !has_reg) { err = "class has no register kernel"; return false; }
+  if (cfg.variant == 2 && !has_reg && !sph) { err = "class has no register kernel"; return false; }
   // default: the register kernel (either variant) where the class has one; measured 1.6-4.4x faster than
   // the team kernel on contracted and uncontracted classes of total angular momentum <= 6
-  P.reg = (has_reg && cfg.variant != 1) ? 1 : 0;
+  P.reg = (has_reg && cfg.variant != 1 && !sph) ? 1 : 0;
   if (P.reg) {
     // its FP64 work: per primitive quartet Boys, R, the ket E products and
     // X += E R; per bra primitive the bra E products and V += E X

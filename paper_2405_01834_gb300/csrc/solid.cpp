@@ -81,4 +81,12 @@ std::vector<std::vector<double>> build_solid_tables(int lmax) {
   return out;
 }
 
+int solid_nnz(int l) {
+  static const std::vector<std::vector<double>> tabs = build_solid_tables(kLmax);
+  if (l < 0 || l > kLmax) return 0;
+  int n = 0;
+  for (double c : tabs[l]) n += c != 0.0;
+  return n;
+}
+
 }  // namespace mdx

@@ -118,6 +118,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_batch_eri3.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, I64,
                                    ctypes.POINTER(ctypes.c_void_p), P]
     lib.mdx_batch_eri3.restype = I32
+    lib.mdx_batch_eri4_sph.argtypes = [P, ctypes.POINTER(_Basis), P, I64, ctypes.POINTER(ctypes.c_void_p), P]
+    lib.mdx_batch_eri4_sph.restype = I32
     lib.mdx_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.mdx_batch_info.restype = I32
@@ -370,6 +372,14 @@ class Engine:
         h = ctypes.c_void_p()
         self._check(self.lib.mdx_batch_eri4(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), q.shape[0],
                                             ctypes.byref(h), _stream()), "mdx_batch_eri4")
+        return Batch(self, h, (basis,))
+
+    def batch_eri4_sph(self, basis: DeviceBasis, quartets) -> "Batch":
+        """Prepare quartets [n,4] for solid-harmonic output (see mdx_batch_eri4_sph)."""
+        q = torch.as_tensor(quartets, dtype=torch.int32, device="cuda").contiguous()
+        h = ctypes.c_void_p()
+        self._check(self.lib.mdx_batch_eri4_sph(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), q.shape[0],
+                                                ctypes.byref(h), _stream()), "mdx_batch_eri4_sph")
         return Batch(self, h, (basis,))
 
     def batch_eri3(self, aux: DeviceBasis, orb: DeviceBasis, triplets) -> "Batch":

@@ -54,7 +54,8 @@ int shim_scalars(int32_t* out, int cap) {
   const int32_t v[] = {P.la, P.lb, P.lc, P.ld, P.Kb, P.Kk, P.onec, P.L, P.Lb, P.Lk, P.Nb, P.Nk, P.hb,
                        P.T, P.teams_per_cta, P.team_doubles, P.recb, P.reck, P.o_recb, P.o_reck, P.o_scal,
                        P.o_G, P.o_R0, P.o_R1, P.o_A, P.o_B, P.o_X, P.o_C1, P.o_OUT, P.c1size, P.ngroups,
-                       P.ncols_max, P.nb1, P.nb23, P.cache_R, P.has_out};
+                       P.ncols_max, P.nb1, P.nb23, P.cache_R, P.has_out, P.sph, P.nsa, P.nsb, P.nsc, P.nsd,
+                       P.ncols_s, P.o_Xs, P.o_C1s, P.o_OUTs, P.c1s, P.hbp, (int32_t)P.xg_doubles};
   const int n = (int)(sizeof(v) / sizeof(v[0]));
   if (out && cap >= n) std::memcpy(out, v, sizeof(v));
   return n;

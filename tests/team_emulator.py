@@ -41,7 +41,8 @@ BUILD = os.path.join(HERE, "_build")
 SHIM_LIB = os.path.join(BUILD, "libplanner_shim.so")
 
 SCALARS = ("la lb lc ld Kb Kk onec L Lb Lk Nb Nk hb T teams_per_cta team_doubles recb reck o_recb o_reck o_scal "
-           "o_G o_R0 o_R1 o_A o_B o_X o_C1 o_OUT c1size ngroups ncols_max nb1 nb23 cache_R has_out").split()
+           "o_G o_R0 o_R1 o_A o_B o_X o_C1 o_OUT c1size ngroups ncols_max nb1 nb23 cache_R has_out "
+           "sph nsa nsb nsc nsd ncols_s o_Xs o_C1s o_OUTs c1s hbp xg_doubles").split()
 STEP = np.dtype([("out", "<u2"), ("src", "<u2"), ("coef", "<u2"), ("n", "u1"), ("stride", "u1")])
 B23 = np.dtype([("out", "<u2"), ("src", "<u2"), ("ey", "<u2"), ("ez", "<u2"), ("u0", "u1"), ("nu", "u1"),
                 ("su", "u1"), ("v0", "u1"), ("nv", "u1"), ("sv", "u1"), ("r", "u1"), ("pad", "u1")])
@@ -120,7 +121,8 @@ class PlanError(RuntimeError):
 
 
 def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, single_max=0) -> Plan:
-    """The planner's team-kernel programs for one class and shape."""
+    """The planner's team-kernel programs for one class and shape (store: False/True, or 2 for the
+    solid-harmonic store plan)."""
     lib = _load()
     err = ctypes.create_string_buffer(256)
     if lib.shim_build(la, lb, lc, ld, Kb, Kk, int(onec), int(store), T, budget, single_max, err, 256):
@@ -404,6 +406,93 @@ def emulate(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
                 else:
                     ws[o] = acc
     return out.reshape(Nb, Nk)
+
+
+def emulate_sph(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
+    """Run one quartet through a solid-harmonic plan (store = 2) the way k_quartets_sph does: the ket
+    groups' Cartesian columns staged in a global area, the passes d -> d' and c -> c', the bra steps on
+    groups of ncols_s spherical columns, the passes b -> b' (into the C1 slots) and a -> a'. Returns the
+    shellset [2la+1][2lb+1][2lc+1][2ld+1] flattened to [Nb_sph][Nk_sph]. Every shared-memory access is
+    checked against the team workspace."""
+    if count is None:
+        count = {}
+    count.setdefault("fma", 0)
+    s = pl.s
+    assert s["sph"] == 1
+    la, lb, lc, ld = s["la"], s["lb"], s["lc"], s["ld"]
+    na, nb, nc, nd = [(l + 1) * (l + 2) // 2 for l in (la, lb, lc, ld)]
+    nsa, nsb, nsc, nsd = s["nsa"], s["nsb"], s["nsc"], s["nsd"]
+    Ca, Cb, Cc, Cd = solid_table(la), solid_table(lb), solid_table(lc), solid_table(ld)
+    hb, hbp, c1s, ncs = s["hb"], s["hbp"], s["c1s"], s["ncols_s"]
+    nks = nsc * nsd
+    W = s["team_doubles"]
+    ws = np.zeros(W)
+    xg = np.full((s["Nk"], hbp), np.nan)
+    out = np.zeros((nsa * nsb, nks))
+    ob, ok = s["o_recb"], s["o_reck"]
+
+    def span(lo, n):
+        assert 0 <= lo and lo + n <= W, "workspace access out of range"
+        return slice(lo, lo + n)
+
+    if s["cache_R"]:
+        ws[span(ob, s["recb"])] = bra_recs[0][:s["recb"]]
+        ws[span(ok, s["reck"])] = ket_recs_signed[0][:s["reck"]]
+        _compute_R(pl, ws, count)
+    for pb in range(s["Kb"]):
+        if not s["cache_R"]:
+            ws[span(ob, s["recb"])] = bra_recs[pb][:s["recb"]]
+        for g in pl.groups:
+            ncols = int(g["ncols"])
+            for pk in range(s["Kk"]):
+                if not s["cache_R"]:
+                    ws[span(ok, s["reck"])] = ket_recs_signed[pk][:s["reck"]]
+                    _compute_R(pl, ws, count)
+                if g["k1_n"] > 0:
+                    _run_step(ws, pl.kprog[g["k1_off"]:g["k1_off"] + g["k1_n"]], False, count)
+                _run_step(ws, pl.kprog[g["k2_off"]:g["k2_off"] + g["k2_n"]], False, count)
+                _run_step(ws, pl.kprog[g["k3_off"]:g["k3_off"] + g["k3_n"]], pk > 0, count)
+            cm = pl.colmap[g["col_off"]:g["col_off"] + ncols].astype(np.int64)
+            for col in range(ncols):
+                xg[cm[col]] = ws[span(s["o_X"] + col * hb, hbp)]
+        assert not np.isnan(xg).any(), "a Cartesian ket column was never staged"
+        Y = np.einsum("ed,cdp->cep", Cd, xg.reshape(nc, nd, hbp))          # pass d -> d'
+        count["fma"] += hbp * (nc * int((Cd != 0).sum()) + int((Cc != 0).sum()) * nsd)
+        for c0 in range(0, nks, ncs):
+            ncols = min(ncs, nks - c0)
+            cols = np.arange(ncols)
+            for col in range(ncols):                                       # pass c -> c'
+                cp, dp = divmod(c0 + col, nsd)
+                ws[span(s["o_Xs"] + col * hb, hbp)] = Cc[cp] @ Y[:, dp, :]
+            count["fma"] += int(pl.b1["n"].astype(np.int64).sum()) * ncols
+            count["fma"] += int((pl.b23["nv"].astype(np.int64) * (pl.b23["nu"].astype(np.int64) + 1)).sum()) * ncols
+            for e in pl.b1:                                                # b1 into the C1 slots
+                k = np.arange(int(e["n"])) * int(e["stride"])
+                c = ws[int(e["coef"]) + k]
+                assert int(e["out"]) < c1s and s["o_Xs"] + (ncols - 1) * hb + int(e["src"]) + k[-1] < W
+                x = ws[s["o_Xs"] + cols[:, None] * hb + int(e["src"]) + k[None, :]]
+                ws[s["o_C1s"] + cols * c1s + int(e["out"])] = x @ c
+            OUT = np.zeros((s["Nb"], ncols))
+            for e in pl.b23:                                               # b23, fresh per bra primitive
+                r1 = int(e["r"]) + 1
+                iu = np.arange(int(e["nu"])) * int(e["su"])
+                ey = ws[int(e["ey"]) + iu]
+                acc = np.zeros(ncols)
+                for iv in range(int(e["nv"])):
+                    va = int(e["v0"]) + iv * int(e["sv"])
+                    row = int(e["src"]) + int(e["u0"]) + va * r1 - va * (va - 1) // 2
+                    c1 = ws[s["o_C1s"] + cols[:, None] * c1s + row + iu[None, :]]
+                    acc += ws[int(e["ez"]) + iv * int(e["sv"])] * (c1 @ ey)
+                OUT[int(e["out"])] = acc
+            ws[span(s["o_OUTs"], s["Nb"] * ncols)] = OUT.reshape(-1)
+            T1 = np.einsum("eb,abk->aek", Cb, OUT.reshape(na, nb, ncols))   # pass b -> b'
+            assert na * nsb <= c1s
+            for col in range(ncols):
+                ws[span(s["o_C1s"] + col * c1s, na * nsb)] = T1[:, :, col].reshape(-1)
+            T1 = np.stack([ws[span(s["o_C1s"] + col * c1s, na * nsb)].reshape(na, nsb) for col in range(ncols)], -1)
+            out[:, c0:c0 + ncols] += np.einsum("fa,aek->fek", Ca, T1).reshape(nsa * nsb, ncols)   # pass a -> a'
+            count["fma"] += ncols * (na * int((Cb != 0).sum()) + int((Ca != 0).sum()) * nsb)
+    return out
 
 
 # ----------------------------------------------------------------- lane efficiency

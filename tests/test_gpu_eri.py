@@ -180,17 +180,53 @@ def test_autotuned_batch_matches(eng):
     bt.close()
 
 
-@pytest.mark.parametrize("lq", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 1, 0, 3), (3, 3, 2, 2), (4, 2, 4, 1), (6, 5, 6, 4)])
+SPH = [(0, 0, 0, 0), (1, 1, 1, 1), (2, 2, 2, 2), (3, 3, 3, 3), (4, 4, 4, 4), (5, 5, 5, 5), (6, 6, 6, 6),
+       (2, 1, 0, 3), (3, 3, 2, 2), (4, 2, 4, 1), (6, 5, 6, 4), (6, 0, 6, 0), (5, 5, 0, 0), (0, 6, 2, 6)]
+
+
+@pytest.mark.parametrize("lq", SPH)
 def test_solid_harmonic_eri4(eng, lq):
-    """mdx_eri4_sph against the oracle's spherical shellsets (solid harmonics, m = -l..l)."""
-    K = (1, 2, 1, 2) if max(lq) < 4 else (1, 1, 1, 1)
-    b, q = inputs.class_sweep(lq, n_bra=3, n_ket=2, seed=13, K=K)
+    """mdx_eri4_sph against the oracle's solid-harmonic shellsets (m = -l..l): the classes of the team
+    kernel contract the solid-harmonic coefficients into the transforms, the small classes transform
+    Cartesian shellsets index by index. Contracted bras and kets where the class is small enough."""
+    K = (1, 2, 1, 2) if max(lq) < 4 else ((2, 1, 1, 1) if sum(lq) <= 12 else (1, 1, 1, 1))
+    nb, nk = (3, 2) if sum(lq) < 20 else (2, 2)
+    b, q = inputs.class_sweep(lq, n_bra=nb, n_ket=nk, seed=13, K=K)
     db = mdx.DeviceBasis(b)
     v, off = eng.eri4_sph(db, q)
     torch.cuda.synchronize()
     ref, roff = oracle.eri4_sph(b, q)
     assert np.array_equal(off.cpu().numpy(), roff)
-    print(parity.check(v.cpu().numpy()[: roff[-1]], ref, roff, "solid %s" % (lq,)))
+    print(parity.check(v.cpu().numpy()[: roff[-1]], ref, roff, "solid %s" % (lq,), parity.Eri4SphEvaluator(b, q)))
+
+
+def test_solid_harmonic_batch_repeats_and_matches(eng):
+    """A prepared solid-harmonic batch (mixed classes: team-kernel and register-kernel ones) gives the
+    mdx_eri4_sph result bit for bit, run after run, and reports solid-harmonic sizes."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    bb = inputs.BasisBuilder()
+    for i in range(10):
+        l = [0, 1, 2, 3, 4, 6, 5, 2, 3, 1][i]
+        inputs.random_shell(rng, bb, l, rng.uniform(0, 4, 3), 1 + (i % 2 if l < 3 else 0), 0.1, 20.0)
+    b = bb.build()
+    q = inputs.random_quartets(b, 60, seed=5)
+    q = q[b.l[q].sum(axis=1) <= 16]
+    db = mdx.DeviceBasis(b)
+    v, off = eng.eri4_sph(db, q)
+    bt = eng.batch_eri4_sph(db, q)
+    assert bt.n == len(q) and bt.total == int(off[-1])
+    assert torch.equal(bt.offsets(), off)
+    for _ in range(2):
+        w = torch.full((bt.total,), float("nan"), dtype=torch.float64, device="cuda")
+        bt.run(w)
+        torch.cuda.synchronize()
+        eng.sync()
+        assert torch.equal(w, v[: bt.total])
+    ref, roff = oracle.eri4_sph(b, q)
+    print(parity.check(v.cpu().numpy()[: roff[-1]], ref, roff, "solid batch", parity.Eri4SphEvaluator(b, q)))
+    with pytest.raises(mdx.MdxError, match="EUNSUPPORTED"):
+        bt.autotune(w, max_trial=4)
+    bt.close()
 
 
 def test_bound_screens_quartets(eng):

@@ -274,3 +274,45 @@ def test_boys_asymptotic_form_above_the_table():
             got = c[m] * T ** (-(m + 0.5))
             worst = max(worst, abs(got - ref[m]) / ref[m])
     assert worst <= 2e-15, worst
+
+
+def _emulate_sph(pl, b, q):
+    out = []
+    for a, bb, c, d in q:
+        br = te.shell_pair_records(b, a, bb, signed=False)
+        kr = te.shell_pair_records(b, c, d, signed=True)
+        out.append(te.emulate_sph(pl, br, kr).reshape(-1))
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("lq,K,budget", [((2, 1, 2, 1), (1, 1, 1, 1), 0), ((3, 3, 3, 3), (1, 1, 1, 1), 0),
+                                         ((2, 2, 3, 1), (2, 1, 1, 3), 0), ((4, 2, 3, 3), (1, 1, 1, 1), 48),
+                                         ((6, 6, 1, 0), (1, 1, 1, 1), 0), ((0, 0, 5, 4), (1, 1, 1, 1), 0),
+                                         ((4, 4, 4, 4), (1, 1, 1, 1), 0), ((1, 3, 2, 2), (2, 2, 1, 1), 24)])
+def test_solid_harmonic_plans(lq, K, budget):
+    """Solid-harmonic store plans (Cartesian ket groups staged, ket passes d -> d' and c -> c', bra steps
+    on spherical columns, bra passes b -> b' and a -> a') reproduce the oracle's solid-harmonic shellsets,
+    including plans squeezed into small shared-memory budgets (many ket and bra-pass groups) and
+    contracted bras (summed over bra primitives in the output)."""
+    b, q = _basis_4c(lq, K, 71)
+    pl = te.plan(*lq, K[0] * K[1], K[2] * K[3], store=2, budget=budget * 1024)
+    assert pl.s["sph"] == 1
+    te.check_hazards(pl)
+    cnt = {}
+    got = _emulate_sph(pl, b, q)
+    ref, off = oracle.eri4_sph(b, q)
+    assert np.max(np.abs(ref)) > 1e-4
+    parity.check(got, ref, off, what="emulated sph %s K=%s" % (lq, K), evaluate=parity.Eri4SphEvaluator(b, q))
+    te.emulate_sph(pl, te.shell_pair_records(b, *q[0][:2], signed=False),
+                   te.shell_pair_records(b, *q[0][2:], signed=True), cnt)
+    assert cnt["fma"] == pytest.approx(pl.exec_fma, rel=1e-9)
+
+
+def test_solid_harmonic_plan_executes_fewer_operations():
+    """At [ii|ii] the solid-harmonic plan executes well under half the FP64 multiply-adds of the
+    Cartesian plan followed by the index-by-index transform."""
+    cart = te.plan(6, 6, 6, 6, store=True).exec_fma
+    sph = te.plan(6, 6, 6, 6, store=2).exec_fma
+    ncs = 28 * 28
+    transform = ncs * (28 * 70 + 70 * 13) + 169 * (28 * 70 + 70 * 13)   # k_cart2sph, zeros skipped
+    assert sph < 0.5 * (cart + transform)
