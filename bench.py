@@ -59,13 +59,15 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the per-class team-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "xbatch", "df", "grad", "ab", "peak", "sph"],
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "xbatch", "df", "grad", "ab", "peak", "sph", "counts"],
                     help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules; "
                          "df: per-class 3-center rates on the density-fitting cluster; grad: exchange energy "
                          "and its nuclear gradient against the exchange build alone; ab: the default kernels "
                          "against the materialized-Hermite variant (dense [p|q], batched DGEMMs); "
                          "peak: measured FP64 throughput, scalar DFMA vs the FP64 tensor instruction; sph: "
-                         "solid-harmonic rates per class of the paper's Tab. nps4")
+                         "solid-harmonic rates per class of the paper's Tab. nps4; counts: screened quartets and "
+                         "projected time of the full-size exchange workloads")
     ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
     ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
     ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
@@ -504,7 +506,7 @@ def sph_main(args):
     """Solid-harmonic 4-center integrals (the paper's basis) per class of the paper's Tab. nps4: [ll|ll] and
     [l0|l0], contraction columns {K_bra, K_ket} = {1,1}, {1,5}, {5,5} (one shell of a contracted pair has
     K = 5). Random shells as in the class sweep; each class on a seeded grid sized to about 0.15 TFLOP of
-    executed work. Classes of the team kernel contract the solid-harmonic coefficients into the transforms
+    executed work (1,024 to 4,194,304 shellsets: the paper's runs are sized by output, up to 500 MB). Classes of the team kernel contract the solid-harmonic coefficients into the transforms
     (mdx_batch_eri4_sph); [ll|ll] with l >= 4 is also timed through the Cartesian kernel on the same
     quartets. The paper's V100 rates are quoted beside ours as context (another machine)."""
     import math
@@ -519,7 +521,7 @@ def sph_main(args):
     for lq in sorted(PAPER_NPS4_V100, key=lambda x: (sum(x), x)):
         for ki, (kname, K) in enumerate(kcols):
             est = mdx.plan_info(*lq, K[0] * K[1], K[2] * K[3]).exec_fma
-            n = int(min(50176, max(1024, 0.15e12 / max(est, 1.0))))
+            n = int(min(2048 * 2048, max(1024, 0.15e12 / max(est, 1.0))))
             side = int(math.ceil(math.sqrt(n)))
             b, q = inputs.class_sweep(lq, n_bra=side, n_ket=side, seed=1002, K=K)
             db = mdx.DeviceBasis(b)
@@ -553,6 +555,84 @@ def sph_main(args):
                                    "{5,5}; value: [66|66] {1,1}"},
             "paper_context": "Tab. nps4 of the paper: one V100 (FP64 7 TFLOP/s), solid harmonics",
             "per_class": rows}
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
+def _density_on_device(torch, nao: int, seed: int, occ_fraction: float = 0.2):
+    """inputs.density's recipe (D = C C^T, C an orthonormal basis of a seeded Gaussian nao x nao/5 matrix)
+    with the QR and the product done on the GPU: the same projector, for matrices too large for the host."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nocc = max(1, int(nao * occ_fraction))
+    G = torch.from_numpy(rng.standard_normal((nao, nocc))).cuda()
+    C, _ = torch.linalg.qr(G)
+    return C @ C.T
+
+
+def counts_main(args):
+    """Screened unique quartets of the full-size exchange workloads, counted on the GPU with the screening
+    of mdx_exchange alone (mdx_exchange_screen, count only): the 400-atom cluster (> 20,000 AOs) and the 64
+    uneven molecules of 10-120 atoms, Schwarz x density screening at tau. Their Table-1 model FLOPs are turned
+    into a projected time with the exchange build's model rate measured here on an 8-atom cluster."""
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    stream = torch.cuda.current_stream()
+
+    def all_pairs(b):
+        i, j = np.tril_indices(b.n_shells)
+        return torch.from_numpy(np.stack([i, j], axis=1).astype(np.int32)).cuda()
+
+    # the exchange build's rate on the gradient workload's 8-atom cluster
+    m8 = inputs.molecule(1005, 8)
+    d8 = mdx.DeviceBasis(m8)
+    p8 = all_pairs(m8)
+    Q8 = eng.schwarz(d8, p8)
+    D8 = torch.from_numpy(inputs.density(m8.nao, 1005)).cuda()
+    _, n8, f8 = eng.exchange_screen(d8, p8, Q8, D8, args.tau, list_quartets=False)
+    ms8 = _event_ms(torch, stream, lambda: eng.exchange(d8, p8, Q8, D8, args.tau), args.steps, args.warmup)
+    rate = f8 / (ms8 * 1e-3)
+    res = {"rate_basis": {"workload": "8-atom cluster exchange build", "quartets": n8, "model_flops": f8,
+                          "ms": round(ms8, 2), "model_gflops": round(rate * 1e-9, 2)}}
+    t0 = time.perf_counter()
+    b5 = inputs.molecule(1005, 400)
+    db5 = mdx.DeviceBasis(b5)
+    p5 = all_pairs(b5)
+    Q5 = eng.schwarz(db5, p5)
+    D5 = _density_on_device(torch, b5.nao, 1005)
+    t1 = time.perf_counter()
+    _, n5, f5 = eng.exchange_screen(db5, p5, Q5, D5, args.tau, list_quartets=False)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    res["cluster_400"] = {"atoms": 400, "n_ao": int(b5.nao), "shells": int(b5.n_shells), "shell_pairs": int(len(p5)),
+                          "pairs_q_above_tau": int((Q5 >= args.tau).sum()), "kept_quartets": n5,
+                          "unique_quartets": int(len(p5)) * (int(len(p5)) + 1) // 2, "model_flops": f5,
+                          "projected_exchange_s": round(f5 / rate, 1), "setup_s": round(t1 - t0, 1),
+                          "screen_s": round(t2 - t1, 2)}
+    del D5, Q5, p5, db5
+    mols = inputs.molecule_batch(1004, 64, 10, 120)
+    tot_n = tot_f = 0.0
+    tot_pairs = 0
+    t0 = time.perf_counter()
+    for i, b in enumerate(mols):
+        db = mdx.DeviceBasis(b)
+        p = all_pairs(b)
+        Q = eng.schwarz(db, p)
+        D = _density_on_device(torch, b.nao, 7 + i)
+        _, n, f = eng.exchange_screen(db, p, Q, D, args.tau, list_quartets=False)
+        tot_n += n; tot_f += f; tot_pairs += len(p)
+    res["batch_64"] = {"molecules": 64, "atoms": [int(b.n_atoms) for b in mols],
+                       "n_ao_total": int(sum(b.nao for b in mols)), "shell_pairs": tot_pairs,
+                       "kept_quartets": int(tot_n), "model_flops": tot_f,
+                       "projected_exchange_s": round(tot_f / rate, 1), "s": round(time.perf_counter() - t0, 1)}
+    eng.sync()
+    line = {"metric": "screened unique quartets and projected exchange time of the full-size workloads",
+            "unit": "s", "value": res["cluster_400"]["projected_exchange_s"], "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "400-atom cluster (seed 1005) and 64 molecules of 10-120 atoms (seed 1004), "
+                                   "heavy 5s4p3d2f1g / light 4s3p2d1f, D = C C^T, tau = %g" % args.tau},
+            **res}
     print(json.dumps(line), flush=True)
     eng.close()
 
@@ -599,6 +679,8 @@ def main():
         return peak_main(args)
     if args.workload == "sph":
         return sph_main(args)
+    if args.workload == "counts":
+        return counts_main(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

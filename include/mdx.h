@@ -225,7 +225,8 @@ void mdx_batch_destroy(mdx_batch* batch);
  * without defining the bound; this is the standard Cauchy-Schwarz factor,
  * |(ab|cd)| <= Q_ab Q_cd, used by mdx_exchange's screening.
  * pairs: [n][2] int32 shell indices. Q_out: [n] doubles (device), written.
- * Synchronises `stream` once (class grouping). */
+ * Works through the pairs in chunks whose diagonal shellsets hold at most
+ * 2^27 doubles (1 GiB of workspace). Synchronises `stream`. */
 mdx_status mdx_schwarz(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* pairs, int64_t n,
                        double* Q_out, void* stream);
 

@@ -225,13 +225,11 @@ struct mdx_batch {
   int64_t nzero = 0;
   // solid-harmonic batches: offsets, total and qoff count solid-harmonic doubles. Classes without a
   // register kernel run the solid-harmonic team kernel (splan, `grid` CTAs, staging in xg); the
-  // others evaluate Cartesian shellsets into `cart` (offsets cqoff) and transform them index by index
-  // (scratch `tmp`, offsets tqoff).
+  // others evaluate Cartesian shellsets into `cart` (offsets cqoff) and transform them element by
+  // element.
   bool sph = false;
   int64_t* cqoff = nullptr;
-  int64_t* tqoff = nullptr;
   double* cart = nullptr;
-  double* tmp = nullptr;
   double* xg = nullptr;
   struct Range { Plan* plan; int64_t begin, count; ClassKey key; Plan* splan; int grid; };
   std::vector<Range> ranges;
@@ -289,7 +287,7 @@ void batch_free(mdx_batch* b) {
   if (b->owned) {
     cudaFree(b->jobs); cudaFree(b->pair_rec); cudaFree(b->recs); cudaFree(b->recs_s);
     cudaFree(b->qp); cudaFree(b->qoff); cudaFree(b->offsets); cudaFree(b->zero);
-    cudaFree(b->cqoff); cudaFree(b->tqoff); cudaFree(b->cart); cudaFree(b->tmp); cudaFree(b->xg);
+    cudaFree(b->cqoff); cudaFree(b->cart); cudaFree(b->xg);
   }
   delete b;
 }
@@ -361,12 +359,9 @@ double model_flops_class(const ClassKey& k, bool sph = false) {
          k.Kb * 2.0 * Nb * nh(Lb) * Nk;
 }
 
-// FP64 multiply-adds of k_cart2sph on one shellset (one index at a time, zero coefficients skipped).
+// FP64 multiply-adds of k_cart2sph on one shellset (every product of non-zero coefficients once).
 double cart2sph_fma(const ClassKey& k) {
-  const double nca = ncart(k.la), ncb = ncart(k.lb), ncc = ncart(k.lc);
-  const double nsa = 2 * k.la + 1, nsb = 2 * k.lb + 1, nsc = 2 * k.lc + 1, nsd = 2 * k.ld + 1;
-  return nca * ncb * (ncc * solid_nnz(k.ld) + solid_nnz(k.lc) * nsd) +
-         nsc * nsd * (nca * solid_nnz(k.lb) + solid_nnz(k.la) * nsb);
+  return (double)solid_nnz(k.la) * solid_nnz(k.lb) * solid_nnz(k.lc) * solid_nnz(k.ld);
 }
 
 // Host preparation of a batch: primitive-pair jobs, class grouping, plans,
@@ -417,10 +412,10 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     classes[key].push_back((int64_t)q);
   }
   std::vector<int2> qp_sorted;
-  std::vector<int64_t> qoff_sorted, cqoff, tqoff;
+  std::vector<int64_t> qoff_sorted, cqoff;
   qp_sorted.reserve(bt.qp.size());
   qoff_sorted.reserve(bt.qp.size());
-  int64_t cart_total = 0, tmp_total = 0, xg_total = 0;
+  int64_t cart_total = 0, xg_total = 0;
   mdx_status st;
   for (auto& kv : classes) {
     const int64_t b = (int64_t)qp_sorted.size();
@@ -446,14 +441,12 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     }
     if (sph) {
       cqoff.resize(qp_sorted.size(), 0);
-      tqoff.resize(qp_sorted.size(), 0);
       if (!splan) {
         const ClassKey& k = kv.first;
         const int64_t nct = (int64_t)ncart(k.la) * ncart(k.lb) * ncart(k.lc) * ncart(k.ld);
-        const int64_t ntm = (int64_t)ncart(k.la) * ncart(k.lb) * (2 * k.lc + 1) * (2 * k.ld + 1);
         for (int64_t i = b; i < b + cnt; ++i) {
-          cqoff[i] = cart_total; cart_total += nct;
-          tqoff[i] = tmp_total; tmp_total += ntm;
+          cqoff[i] = cart_total;
+          cart_total += nct;
         }
         fma += cart2sph_fma(k);
       }
@@ -489,9 +482,7 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
   }
   if (sph) {
     if ((st = dev_upload(c, cqoff, &B->cqoff, s)) != MDX_OK) return st;
-    if ((st = dev_upload(c, tqoff, &B->tqoff, s)) != MDX_OK) return st;
     if ((cart_total > 0 && cudaMalloc(&B->cart, cart_total * sizeof(double)) != cudaSuccess) ||
-        (tmp_total > 0 && cudaMalloc(&B->tmp, tmp_total * sizeof(double)) != cudaSuccess) ||
         (xg_total > 0 && cudaMalloc(&B->xg, xg_total * sizeof(double)) != cudaSuccess)) {
       cudaGetLastError();
       return fail(c, MDX_ENOMEM, "solid-harmonic scratch allocation failed");
@@ -545,8 +536,8 @@ mdx_status batch_run(mdx_ctx* c, mdx_batch* B, double* out, int32_t* nlaunch, cu
     if (e != cudaSuccess) return cuda_fail(c, e, "quartet kernel launch");
     if (r.count > 0) ++nl;
     if (B->sph) {
-      SphLaunch t{r.key.la, r.key.lb, r.key.lc, r.key.ld, r.count, B->cart, B->cqoff + r.begin, B->tmp,
-                  B->tqoff + r.begin, out, B->qoff + r.begin};
+      SphLaunch t{r.key.la, r.key.lb, r.key.lc, r.key.ld, r.count, B->cart, B->cqoff + r.begin, out,
+                  B->qoff + r.begin};
       e = launch_cart2sph(t, s);
       if (e != cudaSuccess) return cuda_fail(c, e, "solid-harmonic transform");
       if (r.count > 0) ++nl;
@@ -1065,35 +1056,43 @@ mdx_status mdx_schwarz(mdx_ctx* c, const mdx_basis* basis, const int32_t* pairs,
   if (st != MDX_OK) return st;
   std::vector<int32_t> hp;
   if ((st = read_quartets(c, pairs, n, 2, hp, s)) != MDX_OK) return st;
-  Batch bt;
-  bt.pairs.resize(n);
-  bt.qp.resize(n);
-  bt.qoff.resize(n);
-  std::vector<int64_t> offs(n + 1);
-  std::vector<int32_t> nab(n);
-  int64_t tot = 0;
   for (int64_t p = 0; p < n; ++p) {
     const int32_t i = hp[2 * p], j = hp[2 * p + 1];
     if (i < 0 || i >= hb.n || j < 0 || j >= hb.n) return fail(c, MDX_EINVAL, "shell index out of range");
-    bt.pairs[p] = PairKey{i, j, 0};
-    bt.qp[p] = make_int2((int)p, (int)p);
-    nab[p] = ncart(hb.l[i]) * ncart(hb.l[j]);
-    offs[p] = tot;
-    bt.qoff[p] = tot;
-    tot += (int64_t)nab[p] * nab[p];
   }
-  offs[n] = tot;
-  double* d_vals; int32_t* d_nab;
-  if ((st = ensure(c, "schwarz_vals", (size_t)tot, &d_vals, s)) != MDX_OK) return st;
-  if ((st = upload(c, "schwarz_nab", nab, &d_nab, s)) != MDX_OK) return st;
-  mdx_batch* B = nullptr;
-  if ((st = batch_prepare(c, basis, nullptr, hb, hb, bt, offs, &B, s)) != MDX_OK) return st;
-  std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
-  if ((st = batch_run(c, B, d_vals, nullptr, s)) != MDX_OK) return st;
-  cudaError_t e = launch_schwarz_reduce(B->offsets, d_nab, n, d_vals, Q_out, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "schwarz reduce");
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "schwarz");
+  // chunks of pairs whose diagonal shellsets (ab|ab) hold at most kChunk doubles together
+  constexpr int64_t kChunk = int64_t(1) << 27;
+  for (int64_t p0 = 0; p0 < n;) {
+    Batch bt;
+    std::vector<int64_t> offs(1, 0);
+    std::vector<int32_t> nab;
+    int64_t tot = 0, p1 = p0;
+    for (; p1 < n; ++p1) {
+      const int32_t i = hp[2 * p1], j = hp[2 * p1 + 1];
+      const int32_t m = ncart(hb.l[i]) * ncart(hb.l[j]);
+      if (p1 > p0 && tot + (int64_t)m * m > kChunk) break;
+      const int32_t k = (int32_t)(p1 - p0);
+      bt.pairs.push_back(PairKey{i, j, 0});
+      bt.qp.push_back(make_int2(k, k));
+      bt.qoff.push_back(tot);
+      nab.push_back(m);
+      tot += (int64_t)m * m;
+      offs.push_back(tot);
+    }
+    const int64_t cnt = p1 - p0;
+    double* d_vals; int32_t* d_nab;
+    if ((st = ensure(c, "schwarz_vals", (size_t)tot, &d_vals, s)) != MDX_OK) return st;
+    if ((st = upload(c, "schwarz_nab", nab, &d_nab, s)) != MDX_OK) return st;
+    mdx_batch* B = nullptr;
+    if ((st = batch_prepare(c, basis, nullptr, hb, hb, bt, offs, &B, s)) != MDX_OK) return st;
+    std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
+    if ((st = batch_run(c, B, d_vals, nullptr, s)) != MDX_OK) return st;
+    cudaError_t e = launch_schwarz_reduce(B->offsets, d_nab, cnt, d_vals, Q_out + p0, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "schwarz reduce");
+    e = cudaStreamSynchronize(s);   // the chunk's host vectors and batch are released next
+    if (e != cudaSuccess) return cuda_fail(c, e, "schwarz");
+    p0 = p1;
+  }
   return check_device_error(c, s);
 }
 

@@ -1178,67 +1178,46 @@ cudaError_t launch_multi_k(double* const* K, const int32_t* nao, int32_t nmol, i
 }
 
 // ----------------------------------------------------------------- solid harmonics
-// y[j] = sum_i C[j][i] x[i*stride] over the non-zero coefficients of one l.
-__device__ __forceinline__ double sph_row(const double* __restrict__ C, int nc, int j, const double* x, int64_t stride) {
-  double acc = 0.0;
-  for (int i = 0; i < nc; ++i) {
-    const double cv = C[j * nc + i];
-    if (cv != 0.0) acc = fma(cv, x[i * stride], acc);
-  }
-  return acc;
-}
-
 // Cartesian -> real-solid-harmonic transform of one class of shellsets, one
-// CTA per shellset: pass A turns every row [ab] of [ab][cd] into [ab][c'd']
-// (scratch), pass B every column [c'd'] of that into [a'b'][c'd'].
+// thread per solid-harmonic element:
+//   out[a'b'c'd'] = sum C_{a'a} C_{b'b} C_{c'c} C_{d'd} [ab|cd]
+// over the non-zero coefficients only (the sparse tables). Used for the small
+// classes of the register kernels, whose shellsets hold at most a few hundred
+// values.
 __global__ void __launch_bounds__(256) k_cart2sph(const SphLaunch a) {
-  extern __shared__ __align__(16) double sb[];
-  const int64_t q = blockIdx.x;
-  if (q >= a.nq) return;
-  const int nca = d_ncart(a.la), ncb = d_ncart(a.lb), ncc = d_ncart(a.lc), ncd = d_ncart(a.ld);
-  const int nsa = 2 * a.la + 1, nsb = 2 * a.lb + 1, nsc = 2 * a.lc + 1, nsd = 2 * a.ld + 1;
-  const double* Ca = c_sph + c_sph_off[a.la];
-  const double* Cb = c_sph + c_sph_off[a.lb];
-  const double* Cc = c_sph + c_sph_off[a.lc];
-  const double* Cd = c_sph + c_sph_off[a.ld];
+  const int la = a.la, lb = a.lb, lc = a.lc, ld = a.ld;
+  const int nsb = 2 * lb + 1, nsc = 2 * lc + 1, nsd = 2 * ld + 1;
+  const int ns = (2 * la + 1) * nsb * nsc * nsd;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.nq * ns) return;
+  const int64_t q = g / ns;
+  int o = (int)(g - q * ns);
+  const int dp = o % nsd; o /= nsd;
+  const int cp = o % nsc; o /= nsc;
+  const int bp = o % nsb;
+  const int ap = o / nsb;
+  const int ncb = d_ncart(lb), ncc = d_ncart(lc), ncd = d_ncart(ld);
   const double* in = a.cart + a.coff[q];
-  double* t1 = a.tmp + a.toff[q];
-  double* out = a.out + a.ooff[q];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double* buf = sb + warp * (28 * 13);
-  const int nk_s = nsc * nsd;
-  for (int row = warp; row < nca * ncb; row += nw) {
-    const double* r = in + (int64_t)row * ncc * ncd;
-    for (int e = lane; e < ncc * nsd; e += 32) {
-      const int c = e / nsd, dp = e - c * nsd;
-      buf[c * nsd + dp] = sph_row(Cd, ncd, dp, r + c * ncd, 1);
+  double acc = 0.0;
+  for (int i = 0; i < c_spn[la][ap]; ++i)
+    for (int j = 0; j < c_spn[lb][bp]; ++j) {
+      const double cab = c_spv[la][ap][i] * c_spv[lb][bp][j];
+      const int rab = c_spk[la][ap][i] * ncb + c_spk[lb][bp][j];
+      for (int k = 0; k < c_spn[lc][cp]; ++k) {
+        const double cabc = cab * c_spv[lc][cp][k];
+        const double* row = in + (int64_t)(rab * ncc + c_spk[lc][cp][k]) * ncd;
+        for (int m = 0; m < c_spn[ld][dp]; ++m) acc = fma(cabc * c_spv[ld][dp][m], __ldg(row + c_spk[ld][dp][m]), acc);
+      }
     }
-    __syncwarp();
-    for (int e = lane; e < nk_s; e += 32) {
-      const int cp = e / nsd, dp = e - cp * nsd;
-      t1[(int64_t)row * nk_s + e] = sph_row(Cc, ncc, cp, buf + dp, nsd);
-    }
-    __syncwarp();
-  }
-  __syncthreads();
-  for (int col = warp; col < nk_s; col += nw) {
-    for (int e = lane; e < nca * nsb; e += 32) {
-      const int ai = e / nsb, bp = e - ai * nsb;
-      buf[ai * nsb + bp] = sph_row(Cb, ncb, bp, t1 + (int64_t)(ai * ncb) * nk_s + col, nk_s);
-    }
-    __syncwarp();
-    for (int e = lane; e < nsa * nsb; e += 32) {
-      const int ap = e / nsb, bp = e - ap * nsb;
-      out[(int64_t)e * nk_s + col] = sph_row(Ca, nca, ap, buf + bp, nsb);
-    }
-    __syncwarp();
-  }
+  a.out[a.ooff[q] + (((int64_t)ap * nsb + bp) * nsc + cp) * nsd + dp] = acc;
 }
 
 cudaError_t launch_cart2sph(const SphLaunch& a, cudaStream_t s) {
   if (a.nq <= 0) return cudaSuccess;
-  const size_t shm = 8 * 28 * 13 * sizeof(double);
-  k_cart2sph<<<(unsigned)a.nq, 256, shm, s>>>(a);
+  const int64_t ns = (int64_t)(2 * a.la + 1) * (2 * a.lb + 1) * (2 * a.lc + 1) * (2 * a.ld + 1);
+  const int64_t grid = (a.nq * ns + 255) / 256;
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  k_cart2sph<<<(unsigned)grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

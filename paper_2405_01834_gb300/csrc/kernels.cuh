@@ -154,8 +154,6 @@ struct SphLaunch {
   int64_t nq;
   const double* cart;        // Cartesian shellsets
   const int64_t* coff;       // per shellset: offset in cart
-  double* tmp;               // scratch [ab][c'd'] per shellset
-  const int64_t* toff;
   double* out;               // solid-harmonic shellsets [a'][b'][c'][d'], m = -l..l
   const int64_t* ooff;
 };

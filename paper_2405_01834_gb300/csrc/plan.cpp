@@ -552,9 +552,13 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   } else if (key.Kb * key.Kk > 1) {
     // contracted: the work per primitive quartet (Boys, R, ket steps) sets the
     // team; about 30 FMAs per lane per primitive quartet, at most 128 lanes
-    // (GB300 sweeps of team sizes over contracted classes of L = 6..10)
-    P.T = 1;
-    while (P.T < 128 && 2 * P.T * 30.0 <= team_fma_per_prim) P.T *= 2;
+    // (GB300 sweeps of team sizes over contracted classes of L = 6..10) ...
+    int Twork = 1;
+    while (Twork < 512 && 2 * Twork * 30.0 <= team_fma_per_prim) Twork *= 2;
+    P.T = std::min(Twork, 128);
+    // ... unless shared memory leaves room for so few teams per SM that the SM would hold fewer
+    // than 16 warps: then the team grows (up to what its work fills) to keep the FP64 pipe fed
+    while (P.T < Twork && (long)tps * P.T < 512) P.T *= 2;
   } else if (P.ngroups > 1) {
     P.T = 512;
   } else {

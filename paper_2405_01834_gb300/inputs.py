@@ -11,7 +11,7 @@ shells and centres that avoid screening for the per-class microbenchmarks
 (Sec. 5), contracted segmented shells (Eq. 3) up to l = 6, and
 molecule-like clusters for the exchange build (Sec. 6). The paper's own
 molecules and basis-set files are not available, so these seeded recipes
-stand in for them (the recipes are listed in the design notes).
+stand in for them; each generator's docstring states its recipe.
 """
 from __future__ import annotations
 

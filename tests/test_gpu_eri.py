@@ -191,7 +191,8 @@ def test_solid_harmonic_eri4(eng, lq):
     Cartesian shellsets index by index. Contracted bras and kets where the class is small enough."""
     K = (1, 2, 1, 2) if max(lq) < 4 else ((2, 1, 1, 1) if sum(lq) <= 12 else (1, 1, 1, 1))
     nb, nk = (3, 2) if sum(lq) < 20 else (2, 2)
-    b, q = inputs.class_sweep(lq, n_bra=nb, n_ket=nk, seed=13, K=K)
+    # overlapping shells (3-bohr box, exponents 0.2-5): integrals of a meaningful size at every l
+    b, q = inputs.class_sweep(lq, n_bra=nb, n_ket=nk, seed=13, K=K, box=3.0, zlo=0.2, zhi=5.0)
     db = mdx.DeviceBasis(b)
     v, off = eng.eri4_sph(db, q)
     torch.cuda.synchronize()

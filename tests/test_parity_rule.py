@@ -91,3 +91,30 @@ def test_perturbation_keeps_equal_values_equal():
                 assert np.array_equal(bp.center[i], bp.center[j])
     moved = np.abs(bp.exps / b.exps - 1.0)
     assert np.all(moved <= 2.5 * 2.0 ** -52) and np.any(moved > 0)
+
+
+def test_ceiling_follows_the_oracles_own_misses():
+    """A batch full of cancellation-limited values (solid-harmonic shellsets of distant, diffuse shells:
+    the combinations cancel the dominant Cartesian terms by up to 1e7) needs many exceptions for any
+    FP64 evaluation; the ceiling then follows the FP64 oracle's own misses on the batch."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    bb = inputs.BasisBuilder()
+    for i in range(10):
+        l = [0, 1, 2, 3, 4, 6, 5, 2, 3, 1][i]
+        inputs.random_shell(rng, bb, l, rng.uniform(0, 4, 3), 1 + (i % 2 if l < 3 else 0), 0.1, 20.0)
+    b = bb.build()
+    q = inputs.random_quartets(b, 60, seed=5)
+    q = q[b.l[q].sum(axis=1) <= 16]
+    ref, off = oracle.eri4_sph(b, q)
+    ld, _ = oracle.eri4_sph(b, q, precision=1)
+    bp = parity._perturbed(b, 50)
+    draw = ld + (oracle.eri4_sph(bp, q)[0] - oracle.eri4_sph(bp, q, precision=1)[0])
+    r = parity.check(draw, ref, off, "solid draw", parity.Eri4SphEvaluator(b, q))
+    assert r["n_cancel"] > parity.MIN_CANCEL_ALLOWED and r["oracle_own_misses"] > 0
+    assert r["n_cancel"] <= 2 * r["oracle_own_misses"] + parity.MIN_CANCEL_ALLOWED
+    # the same values with one planted error are still caught
+    g = draw.copy()
+    k = int(np.argmax(np.abs(ref)))
+    g[k] *= 1 + 1e-9
+    with pytest.raises(AssertionError):
+        parity.check(g, ref, off, "solid planted", parity.Eri4SphEvaluator(b, q))
