@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--n-mol", type=int, default=64)
     ap.add_argument("--atoms", default="2,5", help="xbatch: atoms per molecule, uniform in [lo,hi]")
     ap.add_argument("--tau", type=float, default=1e-11)
+    ap.add_argument("--sph-classes", default="", help="sph: only these classes, e.g. 6666,4040")
     return ap.parse_args()
 
 
@@ -518,7 +519,10 @@ def sph_main(args):
     peak = max(mdx.fp64_peak(0, 3), mdx.fp64_peak(1, 3)) * 1e9
     kcols = (("{1,1}", (1, 1, 1, 1)), ("{1,5}", (1, 1, 5, 1)), ("{5,5}", (5, 1, 5, 1)))
     rows = []
+    only = {tuple(int(ch) for ch in c) for c in args.sph_classes.split(",") if c} if args.sph_classes else None
     for lq in sorted(PAPER_NPS4_V100, key=lambda x: (sum(x), x)):
+        if only and lq not in only:
+            continue
         for ki, (kname, K) in enumerate(kcols):
             est = mdx.plan_info(*lq, K[0] * K[1], K[2] * K[3]).exec_fma
             n = int(min(2048 * 2048, max(1024, 0.15e12 / max(est, 1.0))))
@@ -546,8 +550,8 @@ def sph_main(args):
             rows.append(row)
     eng.sync()
     line = {"metric": "solid-harmonic [ab|cd]: shellsets/s and FP64 GFLOP/s per class of the paper's Tab. nps4",
-            "unit": "shellsets/s", "value": next(r["shellsets_per_s"] for r in rows if r["class"] == "[66|66]" and
-                                                r["K"] == "{1,1}"),
+            "unit": "shellsets/s", "value": next((r["shellsets_per_s"] for r in rows if r["class"] == "[66|66]" and
+                                                 r["K"] == "{1,1}"), None),
             "higher_is_better": True, "dtype": "f64", "data": "synthetic", "steps": args.steps,
             "warmup": args.warmup, "fp64_peak_gflops": round(peak * 1e-9, 1),
             "config": {"workload": "solid-harmonic class sweep: random shells (centres in a 10-bohr box, exponents "

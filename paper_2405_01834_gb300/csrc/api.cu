@@ -106,14 +106,14 @@ mdx_status upload(mdx_ctx* c, const char* name, const std::vector<T>& v, T** out
 mdx_status upload_plan(mdx_ctx* c, Plan* p, cudaStream_t s) {
   const size_t sg = p->groups.size() * sizeof(Group), sk = p->kprog.size() * sizeof(StepEntry),
                s1 = p->b1.size() * sizeof(StepEntry), s2 = p->b23.size() * sizeof(B23Entry),
-               sc = p->colmap.size() * sizeof(uint16_t);
+               sc = p->colmap.size() * sizeof(uint16_t), si = p->colinv.size() * sizeof(uint16_t);
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t tot = al(sg) + al(sk) + al(s1) + al(s2) + al(sc);
+  const size_t tot = al(sg) + al(sk) + al(s1) + al(s2) + al(sc) + al(si);
   std::vector<char> blob(tot, 0);
   size_t o = 0;
   auto put = [&](const void* src, size_t n) { size_t at = o; if (n) memcpy(blob.data() + o, src, n); o += al(n); return at; };
   const size_t og = put(p->groups.data(), sg), ok = put(p->kprog.data(), sk), o1 = put(p->b1.data(), s1),
-               o2 = put(p->b23.data(), s2), oc = put(p->colmap.data(), sc);
+               o2 = put(p->b23.data(), s2), oc = put(p->colmap.data(), sc), oi = put(p->colinv.data(), si);
   cudaError_t e = cudaMalloc(&p->dev_blob, tot);
   if (e != cudaSuccess) { cudaGetLastError(); p->dev_blob = nullptr; return fail(c, MDX_ENOMEM, "plan allocation failed"); }
   e = cudaMemcpyAsync(p->dev_blob, blob.data(), tot, cudaMemcpyHostToDevice, s);
@@ -125,6 +125,7 @@ mdx_status upload_plan(mdx_ctx* c, Plan* p, cudaStream_t s) {
   p->d.b1 = (const StepEntry*)(base + o1);
   p->d.b23 = (const B23Entry*)(base + o2);
   p->d.colmap = (const uint16_t*)(base + oc);
+  p->d.colinv = (const uint16_t*)(base + oi);
   return MDX_OK;
 }
 

@@ -321,7 +321,8 @@ __device__ __forceinline__ int d_ncart(int l) { return (l + 1) * (l + 2) / 2; }
 //   K[j][k] += w sum_ad D[i][l] V,  K[j][l] += w sum_ac D[i][k] V.
 // Together with K <- K + K^T afterwards this adds all eight index
 // permutations of the quartet exactly once.
-__device__ void digest_group(const QuartetLaunch& a, const double* ws, const Group& grp, int2 qp, int tl, int T) {
+__device__ void digest_group(const QuartetLaunch& a, const double* ws, const Group& grp, int g, int2 qp, int tl,
+                             int T) {
   const PlanDev& P = a.plan;
   const int2 bp = a.pair_shells[qp.x], kp = a.pair_shells[qp.y];
   const int si = bp.x, sj = bp.y, sk = kp.x, sl = kp.y;
@@ -332,7 +333,7 @@ __device__ void digest_group(const QuartetLaunch& a, const double* ws, const Gro
   const int64_t nao = mol >= 0 ? a.mol_nao[mol] : a.nao;
   const int64_t ai = a.ao_off[si], aj = a.ao_off[sj], ak = a.ao_off[sk], al = a.ao_off[sl];
   const int ncols = grp.ncols;
-  const uint16_t* cm = P.colmap + grp.col_off;
+  const uint16_t* inv = P.colinv + (int64_t)g * P.Nk;   // this group's column of ket pair (c, d), or 0xffff
   const double* OUT = ws + P.o_OUT;
   const double* D = mol >= 0 ? a.mol_D[mol] : a.D;
   double* K = mol >= 0 ? a.mol_K[mol] : a.K;
@@ -346,21 +347,29 @@ __device__ void digest_group(const QuartetLaunch& a, const double* ws, const Gro
     else { u = 3; const int f = e - n1 - n2 - n3; x = f / nd; y = f - x * nd; }
     double s = 0.0;
     bool any = false;
-    for (int col = 0; col < ncols; ++col) {
-      const int cd = cm[col];
-      const int c = cd / nd, d = cd - c * nd;
-      if (u == 0 && c == y) {          // K[i+x][k+c] += D[j+b][l+d] V[x,b,c,d]
+    if (u == 0 || u == 2) {
+      // ket component c = y: the group's columns (y, d)
+      for (int d = 0; d < nd; ++d) {
+        const int col = inv[y * nd + d];
+        if (col == 0xffff) continue;
         any = true;
-        for (int b = 0; b < nb; ++b) s = fma(__ldg(D + (aj + b) * nao + al + d), OUT[(x * nb + b) * ncols + col], s);
-      } else if (u == 1 && d == y) {   // K[i+x][l+d] += D[j+b][k+c] V[x,b,c,d]
+        if (u == 0)        // K[i+x][k+y] += D[j+b][l+d] V[x,b,y,d]
+          for (int b = 0; b < nb; ++b) s = fma(__ldg(D + (aj + b) * nao + al + d), OUT[(x * nb + b) * ncols + col], s);
+        else               // K[j+x][k+y] += D[i+aa][l+d] V[aa,x,y,d]
+          for (int aa = 0; aa < na; ++aa)
+            s = fma(__ldg(D + (ai + aa) * nao + al + d), OUT[(aa * nb + x) * ncols + col], s);
+      }
+    } else {
+      // ket component d = y: the group's columns (c, y)
+      for (int c = 0; c < nc; ++c) {
+        const int col = inv[c * nd + y];
+        if (col == 0xffff) continue;
         any = true;
-        for (int b = 0; b < nb; ++b) s = fma(__ldg(D + (aj + b) * nao + ak + c), OUT[(x * nb + b) * ncols + col], s);
-      } else if (u == 2 && c == y) {   // K[j+x][k+c] += D[i+aa][l+d] V[aa,x,c,d]
-        any = true;
-        for (int aa = 0; aa < na; ++aa) s = fma(__ldg(D + (ai + aa) * nao + al + d), OUT[(aa * nb + x) * ncols + col], s);
-      } else if (u == 3 && d == y) {   // K[j+x][l+d] += D[i+aa][k+c] V[aa,x,c,d]
-        any = true;
-        for (int aa = 0; aa < na; ++aa) s = fma(__ldg(D + (ai + aa) * nao + ak + c), OUT[(aa * nb + x) * ncols + col], s);
+        if (u == 1)        // K[i+x][l+y] += D[j+b][k+c] V[x,b,c,y]
+          for (int b = 0; b < nb; ++b) s = fma(__ldg(D + (aj + b) * nao + ak + c), OUT[(x * nb + b) * ncols + col], s);
+        else               // K[j+x][l+y] += D[i+aa][k+c] V[aa,x,c,y]
+          for (int aa = 0; aa < na; ++aa)
+            s = fma(__ldg(D + (ai + aa) * nao + ak + c), OUT[(aa * nb + x) * ncols + col], s);
       }
     }
     if (!any) continue;
@@ -667,7 +676,7 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
     } else if (a.D) {
       // exchange digestion of this group's columns (Sec. 6: K_bc = sum_ad [ab|cd] D_ad),
       // unique quartet (ij|kl) with i>=j, k>=l, ij>=kl and weight w; the host adds K^T at the end
-      if (active) digest_group(a, ws, grp, qp, tl, T);
+      if (active) digest_group(a, ws, grp, g, qp, tl, T);
       team_sync<CTA>(mask);
     }
   }

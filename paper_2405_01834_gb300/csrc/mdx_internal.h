@@ -168,6 +168,7 @@ struct PlanDev {
   const StepEntry* b1;
   const B23Entry* b23;
   const uint16_t* colmap;
+  const uint16_t* colinv;   // per group g: colinv[g * Nk + ket column] = its column in g, or 0xffff
 };
 
 // Host-side plan with its program arrays.
@@ -177,6 +178,7 @@ struct Plan {
   std::vector<StepEntry> kprog, b1;
   std::vector<B23Entry> b23;
   std::vector<uint16_t> colmap;
+  std::vector<uint16_t> colinv;
   double exec_fma = 0;     // FMAs executed per primitive-quartet pass (for reports)
   void* dev_blob = nullptr;
 };

@@ -205,6 +205,7 @@ extern "C" mdx_status mdx_eri4_noalloc(const mdx_basis* basis, const int32_t* qu
     d.b1 = (const StepEntry*)(st.base + place(P.b1.data(), P.b1.size() * sizeof(StepEntry)));
     d.b23 = (const B23Entry*)(st.base + place(P.b23.data(), P.b23.size() * sizeof(B23Entry)));
     d.colmap = (const uint16_t*)(st.base + place(P.colmap.data(), P.colmap.size() * sizeof(uint16_t)));
+    d.colinv = (const uint16_t*)(st.base + place(P.colinv.data(), P.colinv.size() * sizeof(uint16_t)));
     pdev.push_back(d);
   }
   if (o > kScratchBytes) return MDX_ESCRATCH;   // request larger than the fixed scratch

@@ -495,6 +495,11 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   }
   P.ngroups = (int)plan.groups.size();
   P.cache_R = (key.Kb * key.Kk == 1) ? 1 : 0;
+  // inverse column maps: the digestion epilogue visits only the columns of its own K block
+  plan.colinv.assign((size_t)P.ngroups * P.Nk, 0xffff);
+  for (int gi = 0; gi < P.ngroups; ++gi)
+    for (int j = 0; j < plan.groups[gi].ncols; ++j)
+      plan.colinv[(size_t)gi * P.Nk + plan.colmap[plan.groups[gi].col_off + j]] = (uint16_t)j;
 
   // R recursion work: every level n < L has tet(L-n+1) - 1 entries of <= 2 ops
   double fma_r = 0;
