@@ -61,20 +61,23 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "xbatch", "df", "grad", "ab", "peak", "sph", "counts"],
+                    choices=["sweep", "xbatch", "df", "grad", "ab", "peak", "sph", "counts", "xchain"],
                     help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules; "
                          "df: per-class 3-center rates on the density-fitting cluster; grad: exchange energy "
                          "and its nuclear gradient against the exchange build alone; ab: the default kernels "
                          "against the materialized-Hermite variant (dense [p|q], batched DGEMMs); "
                          "peak: measured FP64 throughput, scalar DFMA vs the FP64 tensor instruction; sph: "
                          "solid-harmonic rates per class of the paper's Tab. nps4; counts: screened quartets and "
-                         "projected time of the full-size exchange workloads")
+                         "projected time of the full-size exchange workloads; xchain: the exchange build on a long "
+                         "chain molecule whose D and K are far larger than L2")
     ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
     ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
     ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
     ap.add_argument("--n-mol", type=int, default=64)
     ap.add_argument("--atoms", default="2,5", help="xbatch: atoms per molecule, uniform in [lo,hi]")
     ap.add_argument("--tau", type=float, default=1e-11)
+    ap.add_argument("--chain-atoms", type=int, default=500, help="xchain: atoms of the chain")
+    ap.add_argument("--chain-k", type=int, default=1, help="xchain: contraction of every shell")
     ap.add_argument("--sph-classes", default="", help="sph: only these classes, e.g. 6666,4040")
     return ap.parse_args()
 
@@ -454,6 +457,56 @@ def grad_main(args):
     eng.close()
 
 
+def xchain_main(args):
+    """The exchange build where D and K are far larger than the GPU's L2: a chain of --chain-atoms atoms
+    (s,p,d shells of contraction --chain-k, 10 AOs per atom), D = C C^T, tau. Reports the build time, its quartet and model
+    FLOP rates, the size of D and K, and the algorithmic bytes of the digestion (the four D blocks read and
+    the four K blocks updated per unique quartet); the DRAM bytes it really moves come from ncu."""
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    stream = torch.cuda.current_stream()
+    b = inputs.chain(1006, args.chain_atoms, K=args.chain_k)
+    db = mdx.DeviceBasis(b)
+    i, j = np.tril_indices(b.n_shells)
+    pairs = torch.from_numpy(np.stack([i, j], axis=1).astype(np.int32)).cuda()
+    Q = eng.schwarz(db, pairs)
+    D = torch.from_numpy(inputs.density(b.nao, 1006)).cuda()
+    kept, n, f = eng.exchange_screen(db, pairs, Q, D, args.tau)
+    # algorithmic digestion bytes: per kept quartet (ij|kl), D blocks ik, il, jk, jl read once and the
+    # same K blocks read and written once (8 bytes per element)
+    nc = torch.tensor([inputs.ncart(int(l)) for l in b.l], dtype=torch.float64, device="cuda")
+    nbytes = 0.0
+    for c0 in range(0, n, 1 << 24):
+        kq = kept[c0:c0 + (1 << 24)].long()
+        pi, pj = pairs[kq[:, 0]].long(), pairs[kq[:, 1]].long()
+        ni, nj, nk, nl = nc[pi[:, 0]], nc[pi[:, 1]], nc[pj[:, 0]], nc[pj[:, 1]]
+        nbytes += float(((ni * nk + ni * nl + nj * nk + nj * nl) * 8 * 3).sum())
+    del kept
+    clk = ClockSampler(0)
+    clk.start()
+    ms = _event_ms(torch, stream, lambda: eng.exchange(db, pairs, Q, D, args.tau), args.steps, args.warmup)
+    clocks = clk.stop()
+    assert eng.last_quartet_count() == n
+    eng.sync()
+    line = {"metric": "exchange build with D and K beyond L2: ms, shell quartets/s, model FP64 GFLOP/s",
+            "unit": "ms", "value": round(ms, 3), "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "chain of %d atoms at 3.0 bohr (jitter 0.5), s,p,d shells K = %d, exponents "
+                                   "log-uniform [0.1, 10], D = C C^T, tau = %g" % (args.chain_atoms, args.chain_k,
+                                                                                   args.tau),
+                       "n_ao": int(b.nao), "n_shells": int(b.n_shells), "shell_pairs": int(len(pairs))},
+            "d_and_k_bytes": 2 * 8 * int(b.nao) ** 2, "l2_bytes": 129 * 2 ** 20,
+            "quartets": n, "model_flops": f, "quartets_per_s": round(n / (ms * 1e-3), 1),
+            "model_gflops": round(f / (ms * 1e-3) * 1e-9, 2),
+            "digestion_algorithmic_bytes": nbytes,
+            "digestion_algorithmic_gbs": round(nbytes / (ms * 1e-3) * 1e-9, 2),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def ab_main(args):
     """A/B of the two designs on the class sweep: the axis-factored kernels (mdx_batch_run) against the
     materialized-Hermite variant of the paper (mdx_batch_run_materialized: [p|q] matrices in HBM, both
@@ -684,6 +737,8 @@ def main():
         return peak_main(args)
     if args.workload == "sph":
         return sph_main(args)
+    if args.workload == "xchain":
+        return xchain_main(args)
     if args.workload == "counts":
         return counts_main(args)
     import torch

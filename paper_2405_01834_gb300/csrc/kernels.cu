@@ -617,6 +617,36 @@ __device__ __forceinline__ void bra_b23(const PlanDev& P, double* ws, int o_C1, 
   }
 }
 
+// R of primitive quartet i from the cache into R0, where the k1 programs read it.
+__device__ __forceinline__ void load_cached_R(const PlanDev& P, double* ws, int i, int tl) {
+  const int nR = d_tet(P.L + 1);
+  const double* src = ws + P.o_Rc + (int64_t)i * P.rstride;
+  for (int e = tl; e < nR; e += P.T) ws[P.o_R0 + e] = src[e];
+}
+
+// The R tables of the primitive quartets of bra primitives pb0 <= pb < pb1 of
+// q, computed once and kept in the workspace region o_Rc, table
+// (pb - pb0) Kk + pk (plans with cache_R == 2: every primitive quartet, filled
+// once per quartet; cache_R == 3, solid-harmonic plans: those of one bra
+// primitive, filled per bra primitive). Contracted classes of several column
+// groups would otherwise compute each R once per group.
+template <bool CTA>
+__device__ __forceinline__ void fill_R_cache(const QuartetLaunch& a, double* ws, int64_t bra0, int64_t ket0, int pb0,
+                                             int pb1, int tl, unsigned mask) {
+  const PlanDev& P = a.plan;
+  const int nR = d_tet(P.L + 1);
+  for (int pb = pb0; pb < pb1; ++pb)
+    for (int pk = 0; pk < P.Kk; ++pk) {
+      load_record(ws + P.o_recb, a.recs + bra0 + (int64_t)pb * P.recb, P.recb, tl, P.T);
+      load_record(ws + P.o_reck, a.recs_signed + ket0 + (int64_t)pk * P.reck, P.reck, tl, P.T);
+      team_sync<CTA>(mask);   // also orders the previous table's copy before compute_R rewrites R0
+      compute_R<CTA>(a, ws, tl, mask);
+      double* dst = ws + P.o_Rc + (int64_t)((pb - pb0) * P.Kk + pk) * P.rstride;
+      for (int e = tl; e < nR; e += P.T) dst[e] = ws[P.o_R0 + e];
+    }
+  team_sync<CTA>(mask);
+}
+
 // The work of one team on one shell quartet q (all groups, all primitives,
 // store / digestion / gradient epilogue). Inactive teams run the same control
 // flow on a shadow quartet (so that barriers match) and write nothing global.
@@ -629,11 +659,13 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
   const int64_t bra0 = a.pair_rec[qp.x + a.bra_var_off];
   const int64_t ket0 = a.pair_rec[qp.y + a.ket_var_off];
   const int Kb = P.Kb, Kk = P.Kk;
-  if (P.cache_R) {
+  if (P.cache_R == 1) {
     load_record(ws + P.o_recb, a.recs + bra0, P.recb, tl, T);
     load_record(ws + P.o_reck, a.recs_signed + ket0, P.reck, tl, T);
     team_sync<CTA>(mask);
     compute_R<CTA>(a, ws, tl, mask);
+  } else if (P.cache_R == 2) {
+    fill_R_cache<CTA>(a, ws, bra0, ket0, 0, Kb, tl, mask);
   }
   // qout == nullptr: shellsets back to back, N_b N_k doubles each
   double* outq = a.D ? nullptr : a.out + (a.qout ? a.qout[q] : q * (int64_t)P.Nb * P.Nk);
@@ -644,12 +676,13 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
     const Group grp = P.groups[g];
     const int ncols = grp.ncols;
     for (int pb = 0; pb < Kb; ++pb) {
-      if (!P.cache_R) load_record(ws + P.o_recb, a.recs + bra0 + (int64_t)pb * P.recb, P.recb, tl, T);
+      if (P.cache_R != 1) load_record(ws + P.o_recb, a.recs + bra0 + (int64_t)pb * P.recb, P.recb, tl, T);
       for (int pk = 0; pk < Kk; ++pk) {
-        if (!P.cache_R) {
+        if (P.cache_R != 1) {
           load_record(ws + P.o_reck, a.recs_signed + ket0 + (int64_t)pk * P.reck, P.reck, tl, T);
+          if (P.cache_R == 2) load_cached_R(P, ws, pb * Kk + pk, tl);
           team_sync<CTA>(mask);
-          compute_R<CTA>(a, ws, tl, mask);
+          if (P.cache_R == 0) compute_R<CTA>(a, ws, tl, mask);
         }
         if (grp.k1_n > 0) {   // groups after the first of a z-pair reuse its A (uncontracted classes)
           run_step(P.kprog + grp.k1_off, grp.k1_n, ws, tl, T, false);
@@ -668,7 +701,7 @@ __device__ __forceinline__ void quartet_body(const QuartetLaunch& a, double* ws,
       // per bra primitive unless the class has one primitive quartet) or OUT (read
       // by other lanes in the digestion / gradient epilogue). C1 is overwritten by
       // the next b1 only after the k-step barriers.
-      if (!P.cache_R || (!direct && pb == Kb - 1)) team_sync<CTA>(mask);
+      if (P.cache_R != 1 || (!direct && pb == Kb - 1)) team_sync<CTA>(mask);
     }
     if (a.grad) {
       grad_group<CTA>(a, ws, grp, qp, tl, T, active, mask);
@@ -737,22 +770,26 @@ __device__ void quartet_sph(const QuartetLaunch& a, double* ws, double* xg, int6
   const int nks = P.nsc * nsd;
   double* yg = xg + (int64_t)P.Nk * hbp;
   double* outq = a.out + a.qout[q];
-  if (P.cache_R) {
+  if (P.cache_R == 1) {
     load_record(ws + P.o_recb, a.recs + bra0, P.recb, tl, T);
     load_record(ws + P.o_reck, a.recs_signed + ket0, P.reck, tl, T);
     team_sync<CTA>(mask);
     compute_R<CTA>(a, ws, tl, mask);
+  } else if (P.cache_R == 2) {
+    fill_R_cache<CTA>(a, ws, bra0, ket0, 0, Kb, tl, mask);
   }
   for (int pb = 0; pb < Kb; ++pb) {
-    if (!P.cache_R) load_record(ws + P.o_recb, a.recs + bra0 + (int64_t)pb * P.recb, P.recb, tl, T);
+    if (P.cache_R == 3) fill_R_cache<CTA>(a, ws, bra0, ket0, pb, pb + 1, tl, mask);
+    if (P.cache_R != 1) load_record(ws + P.o_recb, a.recs + bra0 + (int64_t)pb * P.recb, P.recb, tl, T);
     // 1. Cartesian ket columns, group by group, staged in Xg
     for (int g = 0; g < P.ngroups; ++g) {
       const Group grp = P.groups[g];
       for (int pk = 0; pk < Kk; ++pk) {
-        if (!P.cache_R) {
+        if (P.cache_R != 1) {
           load_record(ws + P.o_reck, a.recs_signed + ket0 + (int64_t)pk * P.reck, P.reck, tl, T);
+          if (P.cache_R >= 2) load_cached_R(P, ws, P.cache_R == 2 ? pb * Kk + pk : pk, tl);
           team_sync<CTA>(mask);
-          compute_R<CTA>(a, ws, tl, mask);
+          if (P.cache_R == 0) compute_R<CTA>(a, ws, tl, mask);
         }
         if (grp.k1_n > 0) {
           run_step(P.kprog + grp.k1_off, grp.k1_n, ws, tl, T, false);
@@ -771,8 +808,26 @@ __device__ void quartet_sph(const QuartetLaunch& a, double* ws, double* xg, int6
       }
       team_sync<CTA>(mask);   // the next group's k3 rewrites X; every lane reads Xg below
     }
-    // 2. ket pass d -> d'
-    {
+    // 2. ket pass d -> d'. Where the workspace past the fixed regions holds the nd staged columns of one
+    // Cartesian c (the ket groups are done with it; cached R tables that outlive this bra primitive stay
+    // untouched), they are copied there first, c by c: independent, coalesced loads in flight together
+    // instead of one global load per multiply-add.
+    if ((int64_t)P.o_Xs + (int64_t)nd * hbp <= (P.cache_R == 2 ? P.o_Rc : P.team_doubles)) {
+      double* st = ws + P.o_Xs;
+      for (int c = 0; c < nc; ++c) {
+        const double* src = xg + (int64_t)c * nd * hbp;
+        for (int e = tl; e < nd * hbp; e += T) st[e] = src[e];
+        team_sync<CTA>(mask);
+        for (int e = tl; e < nsd * hbp; e += T) {
+          const int dp = e / hbp, i = e - dp * hbp;
+          const int n = c_spn[ld][dp];
+          double v = 0.0;
+          for (int j = 0; j < n; ++j) v = fma(c_spv[ld][dp][j], st[c_spk[ld][dp][j] * hbp + i], v);
+          yg[((int64_t)c * nsd + dp) * hbp + i] = v;
+        }
+        team_sync<CTA>(mask);
+      }
+    } else {
       const int tot = nc * nsd * hbp;
       for (int e = tl; e < tot; e += T) {
         const int cdp = e / hbp, i = e - cdp * hbp;
@@ -792,8 +847,20 @@ __device__ void quartet_sph(const QuartetLaunch& a, double* ws, double* xg, int6
         const int col = e / hbp, i = e - col * hbp;
         const int gcol = c0 + col, cp = gcol / nsd, dp = gcol - cp * nsd;
         const int n = c_spn[lc][cp];
+        const double* y = yg + (int64_t)dp * hbp + i;
+        const int64_t cs = (int64_t)nsd * hbp;
+        // loads four terms ahead of their multiply-adds (independent global loads in flight together)
         double v = 0.0;
-        for (int j = 0; j < n; ++j) v = fma(c_spv[lc][cp][j], yg[((int64_t)c_spk[lc][cp][j] * nsd + dp) * hbp + i], v);
+        int j = 0;
+        for (; j + 4 <= n; j += 4) {
+          const double y0 = y[c_spk[lc][cp][j] * cs], y1 = y[c_spk[lc][cp][j + 1] * cs];
+          const double y2 = y[c_spk[lc][cp][j + 2] * cs], y3 = y[c_spk[lc][cp][j + 3] * cs];
+          v = fma(c_spv[lc][cp][j], y0, v);
+          v = fma(c_spv[lc][cp][j + 1], y1, v);
+          v = fma(c_spv[lc][cp][j + 2], y2, v);
+          v = fma(c_spv[lc][cp][j + 3], y3, v);
+        }
+        for (; j < n; ++j) v = fma(c_spv[lc][cp][j], y[c_spk[lc][cp][j] * cs], v);
         ws[P.o_Xs + col * P.hb + i] = v;
       }
       team_sync<CTA>(mask);
@@ -1055,6 +1122,8 @@ __global__ void __launch_bounds__(256) k_screen(const ScreenArgs a, bool fill) {
     if (cq > cp) break;
     const int64_t b0 = a.seg_begin[g];
     const int64_t e0 = cq == cp ? a.pos[p] + 1 : a.seg_begin[g + 1];
+    // the segment's largest Q first: most pairs of a large molecule meet none of its pairs
+    if (b0 >= e0 || qp * a.Q[a.order[b0]] * dr < tau) continue;
     // first position whose Q_p Q_q rowmax falls below tau (Q decreasing along the segment)
     int64_t lo = b0, hi = e0;
     while (lo < hi) {

@@ -150,7 +150,10 @@ struct PlanDev {
   int32_t c1size;                        // C1 doubles per column
   int32_t ngroups, ncols_max;
   int32_t nb1, nb23;
-  int32_t cache_R;                       // R computed once (single primitive quartet)
+  int32_t cache_R;                       // 1: R computed once (single primitive quartet); 2: the R tables of all
+                                         // primitive quartets kept at o_Rc (rstride doubles each); 3 (solid-
+                                         // harmonic plans): those of the current bra primitive; 0: R per group
+  int32_t o_Rc, rstride;
   int32_t reg;                           // launch the register kernel (store / digestion launches)
   int32_t has_out;                       // OUT region present (0: store-only plan, b23 writes global memory)
   // Solid-harmonic output (store = 2). The ket groups write their Cartesian columns [p|cd] to a
@@ -189,8 +192,11 @@ struct PlanConfig {
   int budget = 200 * 1024;   // shared-memory bytes per team
   int single_max = 96 * 1024;  // largest workspace for which all ket columns form one group
   int variant = 0;           // 0: register kernel where the class has one, else team; 1: team; 2: register
+  int rcache = -1;           // cached R tables of contracted multi-group classes: -1 where they fit without
+                             // costing occupancy, 0 never, 1 wherever they fit
   bool operator==(const PlanConfig& o) const {
-    return T == o.T && budget == o.budget && single_max == o.single_max && variant == o.variant;
+    return T == o.T && budget == o.budget && single_max == o.single_max && variant == o.variant &&
+           rcache == o.rcache;
   }
 };
 

@@ -212,6 +212,17 @@ bool validate_plan(const Plan& plan, std::string& err) {
   }
   if (P.o_R1 + tet(P.L) > P.o_X || P.o_R0 + tet(P.L + 1) > P.o_R1 || P.o_G + P.L + 1 > P.o_R0 ||
       P.o_reck + P.reck > P.o_scal) { err = "fixed regions overlap"; return false; }
+  if (P.cache_R >= 2) {
+    // the cached R tables lie after every other region of the workspace
+    const long end_other = P.sph ? std::max<long>(P.o_OUT + (long)P.ncols_max * (P.has_out ? P.Nb : 0),
+                                                  P.o_OUTs + (long)P.ncols_s * P.Nb)
+                                 : P.o_OUT + (long)P.ncols_max * (P.has_out ? P.Nb : 0);
+    if (P.o_Rc < end_other || P.o_Rc < P.o_X + (long)P.ncols_max * P.hb || P.rstride < tet(P.L + 1) ||
+        P.o_Rc + (long)(P.cache_R == 2 ? P.Kb : 1) * P.Kk * P.rstride > W || (P.cache_R == 3 && !P.sph)) {
+      err = "cached R tables out of range";
+      return false;
+    }
+  }
   if (P.sph) {
     // the bra pass starts where the ket groups' region starts (R at level 0 stays below it), and the
     // [a][b'] pass of each column fits its C1 slot
@@ -495,6 +506,27 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   }
   P.ngroups = (int)plan.groups.size();
   P.cache_R = (key.Kb * key.Kk == 1) ? 1 : 0;
+  // Contracted classes of several column groups would compute every primitive quartet's R once per
+  // group: keep all Kb Kk tables in a region of their own instead (computed once per quartet, copied
+  // into R0 before each group's k1), where it fits and the SM keeps as many teams (or at least two)
+  P.rstride = (tet(P.L + 1) + 1) & ~1;
+  P.o_Rc = 0;
+  // (solid-harmonic plans, whose bra-primitive loop is outermost, fall back to the tables of one bra
+  // primitive at a time)
+  if (!P.cache_R && P.ngroups > 1 && cfg.rcache != 0) {
+    const int o_Rc = (P.team_doubles + 1) & ~1;
+    const int tps0 = std::max(1, (220 * 1024) / (P.team_doubles * 8));
+    for (int mode = 2; mode <= (sph && key.Kb > 1 ? 3 : 2); ++mode) {
+      const long td = ((long)o_Rc + (long)(mode == 2 ? key.Kb : 1) * key.Kk * P.rstride) | 1;
+      const int tps1 = (int)((220L * 1024) / (td * 8));
+      if (td * 8 <= smem_budget_bytes && td < 65536 && (cfg.rcache > 0 || tps1 >= std::min(tps0, 2))) {
+        P.cache_R = mode;
+        P.o_Rc = o_Rc;
+        P.team_doubles = (int)td;
+        break;
+      }
+    }
+  }
   // inverse column maps: the digestion epilogue visits only the columns of its own K block
   plan.colinv.assign((size_t)P.ngroups * P.Nk, 0xffff);
   for (int gi = 0; gi < P.ngroups; ++gi)
@@ -577,10 +609,21 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   if (P.T > 32) {
     P.teams_per_cta = 1;
   } else {
-    int tpc = std::max(1, 128 / P.T);
-    tpc = std::min(tpc, tps);
-    while (tpc > 1 && tpc * bytes > smem_budget_bytes) --tpc;
-    P.teams_per_cta = tpc;
+    // warp-sized teams share CTAs of at most 128 threads in whole warps; pick the count that keeps the
+    // most teams resident per SM (228 KB of shared memory per SM, 1 KB of it reserved per CTA; at most
+    // 32 CTAs and 2048 threads), the fewest teams per CTA among equals
+    const int cap = std::min(std::max(1, 128 / P.T), tps);
+    int best = cap;
+    while (best > 1 && (long)best * bytes > smem_budget_bytes) --best;
+    long best_res = -1;
+    for (int tpc = 1; tpc <= cap; ++tpc) {
+      const long cta = (long)tpc * bytes;
+      if (cta > smem_budget_bytes) break;
+      if ((tpc * P.T) % 32 != 0) continue;   // a part-filled warp idles FP64 lanes
+      const long ctas = std::min({228L * 1024 / (cta + 1024), 2048L / ((long)tpc * P.T), 32L});
+      if (ctas * tpc > best_res) { best_res = ctas * tpc; best = tpc; }
+    }
+    P.teams_per_cta = best;
   }
   if (P.T * P.teams_per_cta > 1024 || (long)P.teams_per_cta * P.team_doubles * 8 > 227 * 1024) {
     err = "team shape exceeds the CTA limits";

@@ -162,6 +162,23 @@ def small_molecule(seed: int = 1001, n_atoms: int = 6, box: float = 6.0, K: int 
     return bb.build()
 
 
+def chain(seed: int = 1006, n_atoms: int = 500, spacing: float = 3.0, jitter: float = 0.5, K: int = 3,
+          shells=(0, 1, 2), zlo: float = 0.1, zhi: float = 10.0) -> Basis:
+    """A long chain of atoms: atom i at (i * spacing, 0, 0) moved by a uniform jitter in [-jitter, jitter]
+    on each axis, each atom with s,p,d shells of contraction K (exponents log-uniform in [zlo, zhi],
+    coefficients as in small_molecule). Many AOs (10 per atom) with few significant shell pairs per shell,
+    so that the density and exchange matrices are far larger than the GPU's L2 while the number of
+    screened quartets stays moderate."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bb = BasisBuilder()
+    for a in range(n_atoms):
+        xyz = np.array([a * spacing, 0.0, 0.0]) + rng.uniform(-jitter, jitter, 3)
+        bb.add_atom(xyz)
+        for l in shells:
+            random_shell(rng, bb, l, xyz, K, zlo, zhi, a)
+    return bb.build()
+
+
 # ---------------------------------------------------------------- per-class quartet grids
 def class_sweep(lq, n_bra: int = 224, n_ket: int = 224, seed: int = 1002, box: float = 10.0,
                 zlo: float = 0.05, zhi: float = 50.0, K=(1, 1, 1, 1)):

@@ -29,10 +29,11 @@ extern "C" {
 // Plan one class (team kernel programs). Returns 0 on success, else 1 with a
 // message in err.
 int shim_build(int la, int lb, int lc, int ld, int Kb, int Kk, int onec, int store, int T, int budget,
-               int single_max, char* err, int errcap) {
+               int single_max, int rcache, char* err, int errcap) {
   mdx::ClassKey key{la, lb, lc, ld, Kb, Kk, onec, store};
   mdx::PlanConfig cfg;
   cfg.T = T;
+  cfg.rcache = rcache;
   if (budget > 0) cfg.budget = budget;
   if (single_max > 0) cfg.single_max = single_max;
   cfg.variant = 1;
@@ -55,7 +56,8 @@ int shim_scalars(int32_t* out, int cap) {
                        P.T, P.teams_per_cta, P.team_doubles, P.recb, P.reck, P.o_recb, P.o_reck, P.o_scal,
                        P.o_G, P.o_R0, P.o_R1, P.o_A, P.o_B, P.o_X, P.o_C1, P.o_OUT, P.c1size, P.ngroups,
                        P.ncols_max, P.nb1, P.nb23, P.cache_R, P.has_out, P.sph, P.nsa, P.nsb, P.nsc, P.nsd,
-                       P.ncols_s, P.o_Xs, P.o_C1s, P.o_OUTs, P.c1s, P.hbp, (int32_t)P.xg_doubles};
+                       P.ncols_s, P.o_Xs, P.o_C1s, P.o_OUTs, P.c1s, P.hbp, (int32_t)P.xg_doubles, P.o_Rc,
+                       P.rstride};
   const int n = (int)(sizeof(v) / sizeof(v[0]));
   if (out && cap >= n) std::memcpy(out, v, sizeof(v));
   return n;

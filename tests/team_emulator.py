@@ -42,7 +42,7 @@ SHIM_LIB = os.path.join(BUILD, "libplanner_shim.so")
 
 SCALARS = ("la lb lc ld Kb Kk onec L Lb Lk Nb Nk hb T teams_per_cta team_doubles recb reck o_recb o_reck o_scal "
            "o_G o_R0 o_R1 o_A o_B o_X o_C1 o_OUT c1size ngroups ncols_max nb1 nb23 cache_R has_out "
-           "sph nsa nsb nsc nsd ncols_s o_Xs o_C1s o_OUTs c1s hbp xg_doubles").split()
+           "sph nsa nsb nsc nsd ncols_s o_Xs o_C1s o_OUTs c1s hbp xg_doubles o_Rc rstride").split()
 STEP = np.dtype([("out", "<u2"), ("src", "<u2"), ("coef", "<u2"), ("n", "u1"), ("stride", "u1")])
 B23 = np.dtype([("out", "<u2"), ("src", "<u2"), ("ey", "<u2"), ("ez", "<u2"), ("u0", "u1"), ("nu", "u1"),
                 ("su", "u1"), ("v0", "u1"), ("nv", "u1"), ("sv", "u1"), ("r", "u1"), ("pad", "u1")])
@@ -72,7 +72,7 @@ def _load():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(_build_shim())
-            lib.shim_build.argtypes = [ctypes.c_int] * 11 + [ctypes.c_char_p, ctypes.c_int]
+            lib.shim_build.argtypes = [ctypes.c_int] * 12 + [ctypes.c_char_p, ctypes.c_int]
             lib.shim_build.restype = ctypes.c_int
             lib.shim_scalars.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.shim_scalars.restype = ctypes.c_int
@@ -120,12 +120,13 @@ class PlanError(RuntimeError):
     pass
 
 
-def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, single_max=0) -> Plan:
+def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, single_max=0, rcache=-1) -> Plan:
     """The planner's team-kernel programs for one class and shape (store: False/True, or 2 for the
-    solid-harmonic store plan)."""
+    solid-harmonic store plan; rcache: the planner's choice of cached R tables, -1 default, 0 never,
+    1 wherever they fit)."""
     lib = _load()
     err = ctypes.create_string_buffer(256)
-    if lib.shim_build(la, lb, lc, ld, Kb, Kk, int(onec), int(store), T, budget, single_max, err, 256):
+    if lib.shim_build(la, lb, lc, ld, Kb, Kk, int(onec), int(store), T, budget, single_max, rcache, err, 256):
         raise PlanError(err.value.decode())
     sc = np.zeros(64, dtype=np.int32)
     n = lib.shim_scalars(sc.ctypes.data, 64)
@@ -337,6 +338,29 @@ def _compute_R(pl: Plan, ws, count):
         ws[dst:dst + len(val)] = val
 
 
+def _fill_R_cache(pl: Plan, ws, bra_recs, ket_recs_signed, count, pbs=None):
+    """cache_R == 2: the R table of every primitive quartet, computed once into the region o_Rc;
+    cache_R == 3: those of the bra primitives `pbs` (one at a time), table pk."""
+    s = pl.s
+    nR = (s["L"] + 1) * (s["L"] + 2) * (s["L"] + 3) // 6
+    pbs = range(s["Kb"]) if pbs is None else pbs
+    ntab = s["Kb"] * s["Kk"] if s["cache_R"] == 2 else s["Kk"]
+    assert s["rstride"] >= nR and s["o_Rc"] + ntab * s["rstride"] <= s["team_doubles"]
+    for i, pb in enumerate(pbs):
+        for pk in range(s["Kk"]):
+            ws[s["o_recb"]:s["o_recb"] + s["recb"]] = bra_recs[pb][:s["recb"]]
+            ws[s["o_reck"]:s["o_reck"] + s["reck"]] = ket_recs_signed[pk][:s["reck"]]
+            _compute_R(pl, ws, count)
+            o = s["o_Rc"] + (i * s["Kk"] + pk) * s["rstride"]
+            ws[o:o + nR] = ws[s["o_R0"]:s["o_R0"] + nR]
+
+
+def _load_cached_R(pl: Plan, ws, i, nR):
+    s = pl.s
+    o = s["o_Rc"] + i * s["rstride"]
+    ws[s["o_R0"]:s["o_R0"] + nR] = ws[o:o + nR]
+
+
 def emulate(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
     """Run one quartet through the plan's programs (store epilogue); returns
     the shellset [Nb][Nk] (row-major, bra Cartesian pair major). `count`, a
@@ -357,10 +381,13 @@ def emulate(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
     def load_ket(r):
         ws[ok:ok + s["reck"]] = r[:s["reck"]]
 
-    if s["cache_R"]:
+    nR = (s["L"] + 1) * (s["L"] + 2) * (s["L"] + 3) // 6
+    if s["cache_R"] == 1:
         load_bra(bra_recs[0])
         load_ket(ket_recs_signed[0])
         _compute_R(pl, ws, count)
+    elif s["cache_R"] == 2:
+        _fill_R_cache(pl, ws, bra_recs, ket_recs_signed, count)
     b1 = pl.b1
     b23 = pl.b23
     for g in pl.groups:
@@ -368,12 +395,15 @@ def emulate(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
         cols = np.arange(ncols)
         cm = pl.colmap[g["col_off"]:g["col_off"] + ncols].astype(np.int64)
         for pb in range(s["Kb"]):
-            if not s["cache_R"]:
+            if s["cache_R"] != 1:
                 load_bra(bra_recs[pb])
             for pk in range(s["Kk"]):
-                if not s["cache_R"]:
+                if s["cache_R"] != 1:
                     load_ket(ket_recs_signed[pk])
-                    _compute_R(pl, ws, count)
+                    if s["cache_R"] == 2:
+                        _load_cached_R(pl, ws, pb * s["Kk"] + pk, nR)
+                    else:
+                        _compute_R(pl, ws, count)
                 if g["k1_n"] > 0:
                     _run_step(ws, pl.kprog[g["k1_off"]:g["k1_off"] + g["k1_n"]], False, count)
                 _run_step(ws, pl.kprog[g["k2_off"]:g["k2_off"] + g["k2_n"]], False, count)
@@ -435,19 +465,29 @@ def emulate_sph(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
         assert 0 <= lo and lo + n <= W, "workspace access out of range"
         return slice(lo, lo + n)
 
-    if s["cache_R"]:
+    nR = (s["L"] + 1) * (s["L"] + 2) * (s["L"] + 3) // 6
+    if s["cache_R"] == 1:
         ws[span(ob, s["recb"])] = bra_recs[0][:s["recb"]]
         ws[span(ok, s["reck"])] = ket_recs_signed[0][:s["reck"]]
         _compute_R(pl, ws, count)
+    elif s["cache_R"] == 2:
+        span(s["o_Rc"], s["Kb"] * s["Kk"] * s["rstride"])
+        _fill_R_cache(pl, ws, bra_recs, ket_recs_signed, count)
     for pb in range(s["Kb"]):
-        if not s["cache_R"]:
+        if s["cache_R"] == 3:
+            span(s["o_Rc"], s["Kk"] * s["rstride"])
+            _fill_R_cache(pl, ws, bra_recs, ket_recs_signed, count, [pb])
+        if s["cache_R"] != 1:
             ws[span(ob, s["recb"])] = bra_recs[pb][:s["recb"]]
         for g in pl.groups:
             ncols = int(g["ncols"])
             for pk in range(s["Kk"]):
-                if not s["cache_R"]:
+                if s["cache_R"] != 1:
                     ws[span(ok, s["reck"])] = ket_recs_signed[pk][:s["reck"]]
-                    _compute_R(pl, ws, count)
+                    if s["cache_R"] >= 2:
+                        _load_cached_R(pl, ws, pb * s["Kk"] + pk if s["cache_R"] == 2 else pk, nR)
+                    else:
+                        _compute_R(pl, ws, count)
                 if g["k1_n"] > 0:
                     _run_step(ws, pl.kprog[g["k1_off"]:g["k1_off"] + g["k1_n"]], False, count)
                 _run_step(ws, pl.kprog[g["k2_off"]:g["k2_off"] + g["k2_n"]], False, count)

@@ -94,7 +94,7 @@ def test_contracted(lq, K):
     """Contracted shells: primitive loops over bra and ket pairs, R per primitive
     quartet; up to the largest contraction degree the engine accepts (32)."""
     pl = _check_4c(lq, K=K, seed=21)
-    assert pl.s["cache_R"] == 0
+    assert pl.s["cache_R"] in (0, 2)
 
 
 @pytest.mark.parametrize("lq,K,store", [((1, 1, 1, 1), (1, 1, 1, 1), True), ((2, 2, 2, 2), (1, 1, 1, 1), True),
@@ -316,3 +316,33 @@ def test_solid_harmonic_plan_executes_fewer_operations():
     ncs = 28 * 28
     transform = ncs * (28 * 70 + 70 * 13) + 169 * (28 * 70 + 70 * 13)   # k_cart2sph, zeros skipped
     assert sph < 0.5 * (cart + transform)
+
+
+@pytest.mark.parametrize("lq,K,store,shape", [((2, 2, 2, 1), (2, 1, 2, 1), True, {"single_max": 4000, "budget": 24 * 1024}),
+                                              ((3, 2, 2, 2), (1, 1, 2, 3), True, {"single_max": 4000}),
+                                              ((2, 1, 2, 2), (2, 2, 1, 1), False, {"single_max": 3000}),
+                                              ((3, 3, 3, 3), (1, 1, 1, 3), 2, {}),
+                                              ((2, 2, 3, 1), (2, 1, 1, 3), 2, {"budget": 24 * 1024}),
+                                              ((3, 3, 3, 2), (2, 2, 1, 2), 2, {"budget": 48 * 1024})])
+def test_cached_R_tables(lq, K, store, shape):
+    """Contracted classes of several column groups keep the R table of every primitive quartet in a
+    region of their own (computed once, copied into R0 before each group's k1) instead of computing it
+    once per group: both plans give the oracle's shellsets, and the cached plan executes fewer FP64
+    operations, exactly as many as the planner reports."""
+    b, q = _basis_4c(lq, K, 81)
+    emul, ref_fn, ev = ((_emulate_sph, oracle.eri4_sph, parity.Eri4SphEvaluator) if store == 2 else
+                        (_emulate_4c, oracle.eri4, parity.Eri4Evaluator))
+    ref, off = ref_fn(b, q)
+    fma = {}
+    for rc in (0, 1):
+        pl = te.plan(*lq, K[0] * K[1], K[2] * K[3], store=store, rcache=rc, **shape)
+        assert pl.s["ngroups"] > 1
+        assert pl.s["cache_R"] in ((2, 3) if rc else (0,))
+        te.check_hazards(pl)
+        parity.check(emul(pl, b, q), ref, off, what="cached R %d %s K=%s" % (rc, lq, K), evaluate=ev(b, q))
+        cnt = {}
+        recs = (te.shell_pair_records(b, *q[0][:2], signed=False), te.shell_pair_records(b, *q[0][2:], signed=True))
+        (te.emulate_sph if store == 2 else te.emulate)(pl, *recs, cnt)
+        assert cnt["fma"] == pytest.approx(pl.exec_fma, rel=1e-12)
+        fma[rc] = pl.exec_fma
+    assert fma[1] < fma[0]
