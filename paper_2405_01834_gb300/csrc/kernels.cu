@@ -808,26 +808,8 @@ __device__ void quartet_sph(const QuartetLaunch& a, double* ws, double* xg, int6
       }
       team_sync<CTA>(mask);   // the next group's k3 rewrites X; every lane reads Xg below
     }
-    // 2. ket pass d -> d'. Where the workspace past the fixed regions holds the nd staged columns of one
-    // Cartesian c (the ket groups are done with it; cached R tables that outlive this bra primitive stay
-    // untouched), they are copied there first, c by c: independent, coalesced loads in flight together
-    // instead of one global load per multiply-add.
-    if ((int64_t)P.o_Xs + (int64_t)nd * hbp <= (P.cache_R == 2 ? P.o_Rc : P.team_doubles)) {
-      double* st = ws + P.o_Xs;
-      for (int c = 0; c < nc; ++c) {
-        const double* src = xg + (int64_t)c * nd * hbp;
-        for (int e = tl; e < nd * hbp; e += T) st[e] = src[e];
-        team_sync<CTA>(mask);
-        for (int e = tl; e < nsd * hbp; e += T) {
-          const int dp = e / hbp, i = e - dp * hbp;
-          const int n = c_spn[ld][dp];
-          double v = 0.0;
-          for (int j = 0; j < n; ++j) v = fma(c_spv[ld][dp][j], st[c_spk[ld][dp][j] * hbp + i], v);
-          yg[((int64_t)c * nsd + dp) * hbp + i] = v;
-        }
-        team_sync<CTA>(mask);
-      }
-    } else {
+    // 2. ket pass d -> d'
+    {
       const int tot = nc * nsd * hbp;
       for (int e = tl; e < tot; e += T) {
         const int cdp = e / hbp, i = e - cdp * hbp;
@@ -847,20 +829,8 @@ __device__ void quartet_sph(const QuartetLaunch& a, double* ws, double* xg, int6
         const int col = e / hbp, i = e - col * hbp;
         const int gcol = c0 + col, cp = gcol / nsd, dp = gcol - cp * nsd;
         const int n = c_spn[lc][cp];
-        const double* y = yg + (int64_t)dp * hbp + i;
-        const int64_t cs = (int64_t)nsd * hbp;
-        // loads four terms ahead of their multiply-adds (independent global loads in flight together)
         double v = 0.0;
-        int j = 0;
-        for (; j + 4 <= n; j += 4) {
-          const double y0 = y[c_spk[lc][cp][j] * cs], y1 = y[c_spk[lc][cp][j + 1] * cs];
-          const double y2 = y[c_spk[lc][cp][j + 2] * cs], y3 = y[c_spk[lc][cp][j + 3] * cs];
-          v = fma(c_spv[lc][cp][j], y0, v);
-          v = fma(c_spv[lc][cp][j + 1], y1, v);
-          v = fma(c_spv[lc][cp][j + 2], y2, v);
-          v = fma(c_spv[lc][cp][j + 3], y3, v);
-        }
-        for (; j < n; ++j) v = fma(c_spv[lc][cp][j], y[c_spk[lc][cp][j] * cs], v);
+        for (int j = 0; j < n; ++j) v = fma(c_spv[lc][cp][j], yg[((int64_t)c_spk[lc][cp][j] * nsd + dp) * hbp + i], v);
         ws[P.o_Xs + col * P.hb + i] = v;
       }
       team_sync<CTA>(mask);
