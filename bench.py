@@ -562,8 +562,9 @@ def sph_main(args):
     [l0|l0], contraction columns {K_bra, K_ket} = {1,1}, {1,5}, {5,5} (one shell of a contracted pair has
     K = 5). Random shells as in the class sweep; each class on a seeded grid sized to about 0.15 TFLOP of
     executed work (1,024 to 4,194,304 shellsets: the paper's runs are sized by output, up to 500 MB). Classes of the team kernel contract the solid-harmonic coefficients into the transforms
-    (mdx_batch_eri4_sph); [ll|ll] with l >= 4 is also timed through the Cartesian kernel on the same
-    quartets. The paper's V100 rates are quoted beside ours as context (another machine)."""
+    (mdx_batch_eri4_sph; autotuned per class unless --no-tune); [ll|ll] with l >= 4 is also timed through
+    the Cartesian kernel on the same quartets. The paper's V100 rates are quoted beside ours as context
+    (another machine)."""
     import math
     import torch
     from paper_2405_01834_gb300 import mdx
@@ -585,6 +586,8 @@ def sph_main(args):
             db = mdx.DeviceBasis(b)
             bt = eng.batch_eri4_sph(db, q)
             out = torch.empty(bt.total, dtype=torch.float64, device="cuda")
+            if not args.no_tune:   # team size, budget and cached R tables per class, on about 2 GFMA of work
+                bt.autotune(out, max_trial=int(min(len(q), max(152, 2e9 / max(est, 1.0)))))
             ms = _event_ms(torch, stream, lambda: bt.run(out), args.steps, args.warmup)
             row = {"class": "[%d%d|%d%d]" % lq, "K": kname, "shellsets": len(q), "ms": round(ms, 4),
                    "shellsets_per_s": round(len(q) / (ms * 1e-3), 1),

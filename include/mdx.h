@@ -168,8 +168,9 @@ mdx_status mdx_batch_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* q
 /* Prepare the quartets of mdx_eri4_sph (same arguments): a batch whose
  * offsets, total and run output are in solid-harmonic components. Its device
  * arrays, including the staging of the solid-harmonic team kernel, belong to
- * the batch. Synchronises `stream`. n must be >= 1. mdx_batch_autotune and
- * mdx_batch_run_materialized return MDX_EUNSUPPORTED for such a batch. */
+ * the batch. Synchronises `stream`. n must be >= 1. mdx_batch_run_materialized
+ * returns MDX_EUNSUPPORTED for such a batch; mdx_batch_autotune tunes its
+ * solid-harmonic team-kernel classes (and may grow the staging area). */
 mdx_status mdx_batch_eri4_sph(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
                               mdx_batch** batch, void* stream);
 
@@ -202,7 +203,11 @@ mdx_status mdx_batch_run(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t ou
  * the first max_trial quartets of that class, keep the fastest for the
  * context (later batches of the class use it) and switch this batch to it.
  * Writes trial results into `out` (batch->total doubles needed) and
- * synchronises `stream`. Results are identical up to FP64 summation order. */
+ * synchronises `stream`. Results are identical up to FP64 summation order.
+ * For a solid-harmonic batch: the classes that run the solid-harmonic team
+ * kernel, over team sizes, shared-memory budgets and the cached R tables of
+ * contracted classes (MDX_ENOMEM if the chosen shape's staging area cannot be
+ * allocated). */
 mdx_status mdx_batch_autotune(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t out_capacity,
                               int64_t max_trial, void* stream);
 

@@ -232,6 +232,7 @@ struct mdx_batch {
   int64_t* cqoff = nullptr;
   double* cart = nullptr;
   double* xg = nullptr;
+  int64_t nxg = 0;                // doubles allocated at xg
   struct Range { Plan* plan; int64_t begin, count; ClassKey key; Plan* splan; int grid; };
   std::vector<Range> ranges;
   std::vector<int64_t> qorig;     // caller index of each class-sorted quartet
@@ -484,7 +485,7 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
   if (sph) {
     if ((st = dev_upload(c, cqoff, &B->cqoff, s)) != MDX_OK) return st;
     if ((cart_total > 0 && cudaMalloc(&B->cart, cart_total * sizeof(double)) != cudaSuccess) ||
-        (xg_total > 0 && cudaMalloc(&B->xg, xg_total * sizeof(double)) != cudaSuccess)) {
+        (xg_total > 0 && (B->nxg = xg_total, cudaMalloc(&B->xg, xg_total * sizeof(double)) != cudaSuccess))) {
       cudaGetLastError();
       return fail(c, MDX_ENOMEM, "solid-harmonic scratch allocation failed");
     }
@@ -953,15 +954,134 @@ mdx_status mdx_batch_run_materialized(mdx_ctx* c, mdx_batch* B, double* out, int
 
 void mdx_batch_destroy(mdx_batch* b) { batch_free(b); }
 
+// Autotuner of a solid-harmonic batch: for every class that runs the solid-harmonic team kernel, the team
+// size (and, for classes of several column groups, the shared-memory budget and the cached R tables) that
+// times fastest on the first max_trial quartets of the class. The staging area grows if the chosen shape
+// needs more.
+mdx_status autotune_sph(mdx_ctx* c, mdx_batch* b, double* out, int64_t max_trial, cudaStream_t s) {
+  cudaError_t e = launch_pair_records(b->b0, b->b1, b->jobs, b->njobs, b->recs, b->recs_s, c->d_err, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto done = [&](mdx_status st) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  };
+  for (auto& r : b->ranges) {
+    if (!r.splan || r.count == 0) continue;
+    ClassKey k2 = r.key;
+    k2.store = 2;
+    std::vector<PlanConfig> cands;
+    if (r.splan->d.ngroups > 1) {
+      for (int budget : {200 * 1024, 108 * 1024})
+        for (int T : {128, 256, 512, 1024})
+          for (int rc : {-1, 0, 1}) cands.push_back(PlanConfig{T, budget, 96 * 1024, 1, rc});
+    } else {
+      for (int T : {0, 4, 8, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, 96 * 1024, 1, -1});
+    }
+    const int64_t nq = std::min(r.count, max_trial);
+    float best_ms = 1e30f;
+    PlanConfig best{};
+    std::unique_ptr<Plan> best_plan;
+    std::vector<std::array<int, 5>> seen;   // shapes already timed
+    for (const PlanConfig& cfg : cands) {
+      std::unique_ptr<Plan> p(new Plan());
+      std::string err;
+      if (!build_plan(k2, cfg, *p, err)) continue;
+      const std::array<int, 5> sig{p->d.T, p->d.teams_per_cta, p->d.team_doubles, p->d.ngroups, p->d.cache_R};
+      if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+      seen.push_back(sig);
+      int grid = 0;
+      if ((e = sph_grid(p->d, nq, &grid)) != cudaSuccess) return done(cuda_fail(c, e, "solid-harmonic launch shape"));
+      const int64_t need = (int64_t)grid * p->d.teams_per_cta * p->d.xg_doubles;
+      if (need > b->nxg) {   // a larger staging area for this shape (all launches so far have completed)
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return done(cuda_fail(c, e, "autotune"));
+        cudaFree(b->xg);
+        b->xg = nullptr;
+        b->nxg = 0;
+        if (cudaMalloc(&b->xg, need * sizeof(double)) != cudaSuccess) {
+          cudaGetLastError();
+          continue;   // this shape's staging does not fit the device: not a candidate
+        }
+        b->nxg = need;
+      }
+      mdx_status st = upload_plan(c, p.get(), s);
+      if (st != MDX_OK) { if (p->dev_blob) cudaFree(p->dev_blob); return done(st); }
+      QuartetLaunch a{};
+      a.plan = p->d;
+      a.nq = nq;
+      a.qpairs = b->qp + r.begin;
+      a.qout = b->qoff + r.begin;
+      a.pair_rec = b->pair_rec;
+      a.recs = b->recs;
+      a.recs_signed = b->recs_s;
+      a.boys = c->d_boys;
+      a.rprog = c->d_rprog;
+      a.rprog_off = c->d_rprog_off;
+      a.out = out;
+      a.err = c->d_err;
+      a.sph_scratch = b->xg;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        e = launch_quartets_sph(a, grid, s);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { cudaFree(p->dev_blob); return done(cuda_fail(c, e, "autotune")); }
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cfg;
+        if (best_plan && best_plan->dev_blob) cudaFree(best_plan->dev_blob);
+        best_plan = std::move(p);
+      } else {
+        cudaFree(p->dev_blob);
+      }
+    }
+    if (!best_plan) continue;
+    int grid = 0;
+    if ((e = sph_grid(best_plan->d, r.count, &grid)) != cudaSuccess) return done(cuda_fail(c, e, "solid-harmonic launch shape"));
+    const int64_t need = (int64_t)grid * best_plan->d.teams_per_cta * best_plan->d.xg_doubles;
+    if (need > b->nxg) {
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return done(cuda_fail(c, e, "autotune"));
+      cudaFree(b->xg);
+      b->xg = nullptr;
+      b->nxg = 0;
+      if (cudaMalloc(&b->xg, need * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return done(fail(c, MDX_ENOMEM, "solid-harmonic staging area"));
+      }
+      b->nxg = need;
+    }
+    c->tuned[k2] = best;
+    auto it = c->plans.find(k2);
+    if (it != c->plans.end()) c->retired.push_back(std::move(it->second));
+    r.splan = best_plan.get();
+    r.grid = grid;
+    c->plans[k2] = std::move(best_plan);
+  }
+  // the staging area must serve every class of the batch
+  for (auto& r : b->ranges)
+    if (r.splan && (int64_t)r.grid * r.splan->d.teams_per_cta * r.splan->d.xg_doubles > b->nxg)
+      return done(fail(c, MDX_EINVAL, "solid-harmonic staging area smaller than a class needs"));
+  done(MDX_OK);
+  return check_device_error(c, s);
+}
+
 mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out_capacity, int64_t max_trial,
                               void* stream) {
   const NvtxRange nvtx_range("mdx_batch_autotune");
   if (!c || !b || !out || max_trial < 1) return MDX_EINVAL;
   if (b->ctx != c) return fail(c, MDX_EINVAL, "batch belongs to another context");
   if (b->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
-  if (b->sph) return fail(c, MDX_EUNSUPPORTED, "autotuner: Cartesian batches only");
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (b->sph) return autotune_sph(c, b, out, max_trial, s);
   cudaError_t e = launch_pair_records(b->b0, b->b1, b->jobs, b->njobs, b->recs, b->recs_s, c->d_err, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
   cudaEvent_t e0, e1;

@@ -226,8 +226,32 @@ def test_solid_harmonic_batch_repeats_and_matches(eng):
     ref, roff = oracle.eri4_sph(b, q)
     print(parity.check(v.cpu().numpy()[: roff[-1]], ref, roff, "solid batch", parity.Eri4SphEvaluator(b, q)))
     with pytest.raises(mdx.MdxError, match="EUNSUPPORTED"):
-        bt.autotune(w, max_trial=4)
+        bt.run_materialized(w)
     bt.close()
+
+
+@pytest.mark.parametrize("lq,K", [((3, 3, 3, 3), (1, 1, 1, 3)), ((4, 0, 4, 0), (1, 1, 1, 1)), ((2, 2, 3, 1), (2, 1, 1, 3))])
+def test_solid_harmonic_batch_autotuned(lq, K):
+    """The autotuner on a solid-harmonic batch (team sizes, budgets, cached R tables of contracted classes)
+    keeps the oracle's results, and the tuned batch repeats them bit for bit."""
+    e = mdx.Engine(0)
+    b, q = inputs.class_sweep(lq, n_bra=3, n_ket=3, seed=17, K=K, box=3.0, zlo=0.2, zhi=5.0)
+    db = mdx.DeviceBasis(b)
+    bt = e.batch_eri4_sph(db, q)
+    w = torch.full((bt.total,), float("nan"), dtype=torch.float64, device="cuda")
+    bt.autotune(w, max_trial=9)
+    w2 = torch.full((bt.total,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        bt.run(w)
+        bt.run(w2)
+        torch.cuda.synchronize()
+        e.sync()
+        assert torch.equal(w, w2)
+    ref, roff = oracle.eri4_sph(b, q)
+    assert np.array_equal(bt.offsets().cpu().numpy(), roff)
+    print(parity.check(w.cpu().numpy(), ref, roff, "autotuned solid %s K=%s" % (lq, K), parity.Eri4SphEvaluator(b, q)))
+    bt.close()
+    e.close()
 
 
 def test_bound_screens_quartets(eng):
