@@ -425,7 +425,8 @@ mdx_status mdx_plan_info(mdx_ctx* ctx, int la, int lb, int lc, int ld, int Kb, i
  * the planner's choice), smem_budget (shared-memory bytes per team, 0 for the
  * default 200 KB) and variant (0: register kernel where the class has one,
  * else teams; 1: teams; 2: register kernel, MDX_EUNSUPPORTED when the class
- * has none). Plans already built for the class are replaced; batches
+ * has none; the solid-harmonic plan of the class takes the team shape and
+ * always runs teams). Plans already built for the class are replaced; batches
  * prepared before keep theirs. */
 mdx_status mdx_set_class_shape(mdx_ctx* ctx, int la, int lb, int lc, int ld, int Kb, int Kk, int one_centre,
                                int team_threads, int smem_budget, int variant);

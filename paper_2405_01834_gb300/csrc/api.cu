@@ -1722,7 +1722,7 @@ mdx_status mdx_set_class_shape(mdx_ctx* c, int la, int lb, int lc, int ld, int K
   Plan p;
   std::string err;
   if (!build_plan(key, cfg, p, err)) return fail(c, MDX_EUNSUPPORTED, "planner: " + err);
-  for (int store = 0; store <= 1; ++store) {   // the general plan and the store-only plan of the class
+  for (int store = 0; store <= 2; ++store) {   // the general, the store-only and the solid-harmonic plan
     ClassKey k2 = key;
     k2.store = store;
     c->tuned[k2] = cfg;

@@ -73,10 +73,9 @@ __device__ __forceinline__ void sfor(F&& f) {
 
 // Per-thread array of N doubles: in registers (SH = false), or one column of a
 // block-wide shared-memory table (element i of thread t at p[i * kXsBlock]).
-// One warp per block: the shared-memory variant's classes hold up to ~2 KB of
-// [p|cd] and shellset per thread, and single-warp blocks pack the SM's 228 KB
-// more tightly (3 warps per SM at 2.2 KB where 64-thread blocks fit 2).
-constexpr int kXsBlock = 32;
+// (Single-warp blocks pack the shared memory more tightly but measured slower
+// on [pp|pp] (-5 %) and no faster on the exchange, gradient and 3-center runs.)
+constexpr int kXsBlock = 64;
 constexpr int kRegMaxDevices = 64;
 template <bool SH, int N>
 struct TArr {
