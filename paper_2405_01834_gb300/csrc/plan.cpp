@@ -519,7 +519,9 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
     for (int mode = 2; mode <= (sph && key.Kb > 1 ? 3 : 2); ++mode) {
       const long td = ((long)o_Rc + (long)(mode == 2 ? key.Kb : 1) * key.Kk * P.rstride) | 1;
       const int tps1 = (int)((220L * 1024) / (td * 8));
-      if (td * 8 <= smem_budget_bytes && td < 65536 && (cfg.rcache > 0 || tps1 >= std::min(tps0, 2))) {
+      // (the cache may take the team past its planning budget, up to what one team can have: a smaller
+      // budget means more column groups and so more R tables saved)
+      if (td * 8 <= 220 * 1024 && td < 65536 && (cfg.rcache > 0 || tps1 >= std::min(tps0, 2))) {
         P.cache_R = mode;
         P.o_Rc = o_Rc;
         P.team_doubles = (int)td;
