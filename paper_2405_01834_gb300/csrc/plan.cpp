@@ -603,7 +603,11 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   } else {
     int Tocc = 1;
     while (Tocc * tps < 512 && Tocc < 512) Tocc *= 2;
-    int work = std::max(1, P.Nb * P.Nk / 8);
+    // about 8 output elements per lane, but at least half as many lanes as the largest R level has
+    // entries: classes with few Cartesian components and a high total angular momentum ([l0|l0]) are
+    // bound by their barrier-separated R levels (GB300 sweeps of the team size: [40|40] 16 -> 64 lanes
+    // 1.9x, [50|50] 32 -> 128 lanes 1.9x, solid-harmonic output)
+    int work = std::max({1, P.Nb * P.Nk / 8, nherm(P.L) / 2});
     int Twork = 1;
     while (Twork * 2 <= work && Twork < 512) Twork *= 2;
     P.T = std::min(Tocc, Twork);
