@@ -251,7 +251,7 @@ def xbatch_main(args):
     """Exchange builds of n_mol uneven molecules (heavy 5s4p3d2f1g / light 4s3p2d1f shells, K = 6 s shells,
     D = C C^T): per-molecule mdx_exchange calls vs one launch per class vs one persistent launch vs the
     register-kernel classes per class plus one persistent launch for the rest, the last two also
-    replayed from a CUDA graph."""
+    replayed from a CUDA graph; then the per-class launches after the batched-exchange autotuner."""
     import torch
     from paper_2405_01834_gb300 import mdx
     torch.cuda.set_device(0)
@@ -306,6 +306,16 @@ def xbatch_main(args):
                 xb.run(persistent=mode)
         torch.cuda.synchronize()
         res[name] = round(timed(g.replay), 3)
+    # the per-class launches again after the autotuner (register kernel or team shape per class, digestion
+    # epilogue, timed on up to 65,536 quartets of each class)
+    tune_s = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        xb.autotune(max_trial=65536)
+        torch.cuda.synchronize()
+        tune_s = round(time.perf_counter() - t0, 2)
+        res["per_class_launches_autotuned_ms"] = round(timed(lambda: xb.run(persistent=0)), 3)
+        res["hybrid_autotuned_ms"] = round(timed(lambda: xb.run(persistent=2)), 3)
     # per-class breakdown: every class launch alone, bracketed by events (one pass after the runs above)
     n_l = xb.n_class_launches
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_l + 1)]
@@ -337,6 +347,7 @@ def xbatch_main(args):
                        "n_ao_total": int(sum(b.nao for b in mols))},
             "quartets": xb.n_quartets, "model_flops": xb.model_flops, "work_items": xb.n_items,
             "class_launches": xb.n_class_launches, "kernel_launches_per_build": launches, "modes_ms": res,
+            "autotune_s": tune_s,
             "quartets_per_s": {k.replace("_ms", ""): round(xb.n_quartets / (v * 1e-3), 1) for k, v in res.items()},
             "per_class": per_class}
     print(json.dumps(line), flush=True)

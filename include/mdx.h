@@ -334,6 +334,17 @@ mdx_status mdx_xbatch_info(const mdx_xbatch* xbatch, int64_t* n_quartets, int64_
  * the kernels enqueued. */
 mdx_status mdx_xbatch_run(mdx_ctx* ctx, mdx_xbatch* xbatch, int32_t persistent, int32_t* n_launches, void* stream);
 
+/* Autotuner of the per-class launches of a batched exchange (the analogue of
+ * mdx_batch_autotune with the digestion epilogue): for every class launch,
+ * time the register kernel (where the class has one) and team shapes (team
+ * size; for classes of several column groups also the shared-memory budget
+ * and the cached R tables) on its first max_trial quartets, keep the fastest
+ * for the context and switch the batch's per-class launches to it. The
+ * persistent work queue keeps the shapes it was built with. The trial
+ * launches add into the K_m; the next mdx_xbatch_run zeroes them first.
+ * Synchronises `stream`. */
+mdx_status mdx_xbatch_autotune(mdx_ctx* ctx, mdx_xbatch* xbatch, int64_t max_trial, void* stream);
+
 /* Per-class launch i of a batch (0 <= i < n_class_launches): its class
  * lk = {la, lb, lc, ld, K_ab, K_cd} (K = primitive pairs of the bra / ket
  * shell pairs), its kept quartets and their Table-1 model FLOPs (any output

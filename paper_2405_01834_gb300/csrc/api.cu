@@ -2141,6 +2141,86 @@ mdx_status mdx_xbatch_run(mdx_ctx* c, mdx_xbatch* xb, int32_t persistent, int32_
   return MDX_OK;
 }
 
+mdx_status mdx_xbatch_autotune(mdx_ctx* c, mdx_xbatch* xb, int64_t max_trial, void* stream) {
+  const NvtxRange nvtx_range("mdx_xbatch_autotune");
+  if (!c || !xb || xb->ctx != c || max_trial < 1) return MDX_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto done = [&](mdx_status st) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  };
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < xb->launches.size(); ++i) {
+    QuartetLaunch& a0 = xb->launches[i];
+    if (a0.nq == 0) continue;
+    const ClassKey& key = xb->lkey[i];
+    // the digestion launch's shapes: register kernel where the class has one, team sizes (with budgets
+    // and the cached R tables for classes of several column groups)
+    std::vector<PlanConfig> cands;
+    if (reg_eligible(key.la, key.lb, key.lc, key.ld) || reg_xs_eligible(key.la, key.lb, key.lc, key.ld))
+      cands.push_back(PlanConfig{0, 200 * 1024, 96 * 1024, 2, -1});
+    if (a0.plan.ngroups > 1) {
+      for (int budget : {200 * 1024, 108 * 1024})
+        for (int T : {128, 256, 512})
+          for (int rc : {-1, 0, 1}) cands.push_back(PlanConfig{T, budget, 96 * 1024, 1, rc});
+    } else {
+      for (int T : {0, 4, 8, 16, 32, 64, 128, 256}) cands.push_back(PlanConfig{T, 200 * 1024, 96 * 1024, 1, -1});
+    }
+    float best_ms = 1e30f;
+    PlanConfig best{};
+    std::unique_ptr<Plan> best_plan;
+    std::vector<std::array<int, 6>> seen;
+    for (const PlanConfig& cfg : cands) {
+      std::unique_ptr<Plan> p(new Plan());
+      std::string err;
+      if (!build_plan(key, cfg, *p, err)) continue;
+      if (!p->d.reg && !p->d.has_out) continue;   // the digestion epilogue reads OUT
+      const std::array<int, 6> sig{p->d.reg, p->d.T, p->d.teams_per_cta, p->d.team_doubles, p->d.ngroups,
+                                   p->d.cache_R};
+      if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+      seen.push_back(sig);
+      mdx_status st = upload_plan(c, p.get(), s);
+      if (st != MDX_OK) { if (p->dev_blob) cudaFree(p->dev_blob); return done(st); }
+      QuartetLaunch a = a0;
+      a.plan = p->d;
+      a.nq = std::min(a0.nq, max_trial);
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        e = launch_quartets(a, s);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { cudaFree(p->dev_blob); return done(cuda_fail(c, e, "autotune")); }
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cfg;
+        if (best_plan && best_plan->dev_blob) cudaFree(best_plan->dev_blob);
+        best_plan = std::move(p);
+      } else {
+        cudaFree(p->dev_blob);
+      }
+    }
+    if (!best_plan) continue;
+    c->tuned[key] = best;
+    auto it = c->plans.find(key);
+    if (it != c->plans.end()) c->retired.push_back(std::move(it->second));
+    a0.plan = best_plan->d;
+    c->plans[key] = std::move(best_plan);
+  }
+  // the trial launches added into K: the next mdx_xbatch_run zeroes it first
+  done(MDX_OK);
+  return check_device_error(c, s);
+}
+
 mdx_status mdx_xbatch_launch_info(const mdx_xbatch* xb, int32_t i, int32_t* lk, int64_t* n_quartets,
                                   double* model_flops) {
   if (!xb || i < 0 || i >= (int32_t)xb->launches.size()) return MDX_EINVAL;

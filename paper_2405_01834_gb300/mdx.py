@@ -156,6 +156,8 @@ def load(build_if_missing: bool = True):
     lib.mdx_xbatch_launch_info.restype = I32
     lib.mdx_xbatch_run_class.argtypes = [P, P, I32, P]
     lib.mdx_xbatch_run_class.restype = I32
+    lib.mdx_xbatch_autotune.argtypes = [P, P, I64, P]
+    lib.mdx_xbatch_autotune.restype = I32
     lib.mdx_xbatch_destroy.argtypes = [P]
     lib.mdx_xbatch_destroy.restype = None
     lib.mdx_plan_info.argtypes = [P, I32, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PlanStats)]
@@ -550,6 +552,12 @@ class ExchangeBatch:
         self.eng._check(self.eng.lib.mdx_xbatch_launch_info(self.h, int(i), lk, ctypes.byref(nq), ctypes.byref(mf)),
                         "mdx_xbatch_launch_info")
         return tuple(lk), nq.value, mf.value
+
+    def autotune(self, max_trial: int = 65536):
+        """Pick the fastest shape (register kernel or team shape) of every per-class launch on this GPU
+        (kept by the engine for later calls). Leaves partial sums in self.Ks: run() again before reading them."""
+        self.eng._check(self.eng.lib.mdx_xbatch_autotune(self.eng.ctx, self.h, int(max_trial), _stream()),
+                        "mdx_xbatch_autotune")
 
     def run_class(self, i: int):
         """Enqueue the integral kernel of per-class launch i alone (no K zeroing / symmetrisation)."""

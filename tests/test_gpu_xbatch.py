@@ -118,3 +118,29 @@ def test_class_launches_one_by_one(eng):
     with pytest.raises(mdx.MdxError):
         xb.launch_info(xb.n_class_launches)
     xb.close()
+
+
+def test_autotuned_batched_exchange_keeps_K():
+    """The batched-exchange autotuner (register kernel or team shape per class launch, timed with the
+    digestion epilogue) changes only the summation order: K of the per-class and hybrid launches after
+    tuning equals K before it, and the oracle's. Own context: the tuned shapes stay with it."""
+    e = mdx.Engine(0)
+    mols = _molecules()
+    bases = [mdx.DeviceBasis(b) for b in mols]
+    Ds = [torch.from_numpy(inputs.density(b.nao, 3 + i)) for i, b in enumerate(mols)]
+    xb = e.xbatch(bases, Ds, tau=0.0)
+    xb.run(persistent=0)
+    torch.cuda.synchronize()
+    K0 = [K.clone() for K in xb.Ks]
+    xb.autotune(max_trial=64)
+    for mode in (0, 2, 1):
+        xb.run(persistent=mode)
+        torch.cuda.synchronize()
+        e.sync()
+        for K, Kr in zip(xb.Ks, K0):
+            np.testing.assert_allclose(K.cpu().numpy(), Kr.cpu().numpy(), rtol=0,
+                                       atol=1e-13 * float(Kr.abs().max()))
+    ref = oracle.exchange(mols[1], Ds[1].numpy())
+    np.testing.assert_allclose(xb.Ks[1].cpu().numpy(), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+    xb.close()
+    e.close()
