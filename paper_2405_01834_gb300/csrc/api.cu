@@ -1095,8 +1095,9 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
     // plus the register kernel (one thread per quartet) where the class has one
     std::vector<PlanConfig> cands;
     if (r.plan->d.ngroups > 1) {
-      for (int budget : {200 * 1024, 108 * 1024, 72 * 1024})
-        for (int T : {256, 512, 1024}) cands.push_back(PlanConfig{T, budget, 96 * 1024, 1});
+      for (int pack : {1, 0})
+        for (int budget : {200 * 1024, 108 * 1024, 72 * 1024})
+          for (int T : {256, 512, 1024}) cands.push_back(PlanConfig{T, budget, 96 * 1024, 1, -1, pack});
     } else {
       for (int single : {96 * 1024, 40 * 1024})
         for (int T : {0, 1, 4, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, single, 1});

@@ -194,9 +194,10 @@ struct PlanConfig {
   int variant = 0;           // 0: register kernel where the class has one, else team; 1: team; 2: register
   int rcache = -1;           // cached R tables of contracted multi-group classes: -1 where they fit without
                              // costing occupancy, 0 never, 1 wherever they fit
+  int pack_zpairs = 1;       // small ket z-pairs share column groups (0: one group or more per z-pair)
   bool operator==(const PlanConfig& o) const {
     return T == o.T && budget == o.budget && single_max == o.single_max && variant == o.variant &&
-           rcache == o.rcache;
+           rcache == o.rcache && pack_zpairs == o.pack_zpairs;
   }
 };
 

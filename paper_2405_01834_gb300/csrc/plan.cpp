@@ -400,25 +400,37 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
     for (auto& c : allcols) byz[{c.c.z, c.d.z}].push_back(c);
     size_t maxcap = 0;
     for (auto& kv : byz) maxcap = std::max(maxcap, kv.second.size());
-    // groups of at most `cap` columns, a z-pair's columns split into chunks of nearly equal size
+    // groups of at most `cap` columns: a z-pair's columns split into chunks of nearly equal size, and
+    // z-pairs of at most cap columns packed whole, in order, into shared groups (fewer barrier-separated
+    // steps and wider bra steps than one small group per z-pair; each computes its own z-pairs' A)
     auto try_cap = [&](size_t cap) {
       groups.clear(); gz.clear(); gfirst.clear();
       regmax = 0; cmax = 0;
       bool ok = true;
+      auto emit = [&](std::vector<ColInfo>&& g, const std::vector<ColInfo>* zc, bool first) {
+        groups.push_back(std::move(g));
+        gz.push_back(zc);
+        gfirst.push_back(first);
+        int as = 0, bs = 0;
+        if (!group_sizes(groups.back(), as, bs, gz.back())) ok = false;
+        regmax = std::max(regmax, region_size(as, bs));
+        cmax = std::max(cmax, (int)groups.back().size());
+      };
+      std::vector<ColInfo> pending;
       for (auto& kv : byz) {
         std::vector<ColInfo>& cs = kv.second;
+        if (cfg.pack_zpairs && cs.size() <= cap) {
+          if (pending.size() + cs.size() > cap) emit(std::move(pending), nullptr, true), pending.clear();
+          pending.insert(pending.end(), cs.begin(), cs.end());
+          continue;
+        }
         const size_t nchunk = (cs.size() + cap - 1) / cap;
         const size_t len = (cs.size() + nchunk - 1) / nchunk;
-        for (size_t s0 = 0; s0 < cs.size(); s0 += len) {
-          groups.emplace_back(cs.begin() + s0, cs.begin() + std::min(cs.size(), s0 + len));
-          gz.push_back(share_a ? &cs : nullptr);
-          gfirst.push_back(s0 == 0 || !share_a);
-          int as = 0, bs = 0;
-          if (!group_sizes(groups.back(), as, bs, gz.back())) ok = false;
-          regmax = std::max(regmax, region_size(as, bs));
-          cmax = std::max(cmax, (int)groups.back().size());
-        }
+        for (size_t s0 = 0; s0 < cs.size(); s0 += len)
+          emit(std::vector<ColInfo>(cs.begin() + s0, cs.begin() + std::min(cs.size(), s0 + len)),
+               share_a ? &cs : nullptr, s0 == 0 || !share_a);
       }
+      if (!pending.empty()) emit(std::move(pending), nullptr, true);
       const int td = o_region + ((regmax + 1) & ~1) + cmax * (P.hb + c1_per_col + out_per_col);
       return ok && td * 8 <= smem_budget_bytes;
     };

@@ -29,11 +29,12 @@ extern "C" {
 // Plan one class (team kernel programs). Returns 0 on success, else 1 with a
 // message in err.
 int shim_build(int la, int lb, int lc, int ld, int Kb, int Kk, int onec, int store, int T, int budget,
-               int single_max, int rcache, char* err, int errcap) {
+               int single_max, int rcache, int pack, char* err, int errcap) {
   mdx::ClassKey key{la, lb, lc, ld, Kb, Kk, onec, store};
   mdx::PlanConfig cfg;
   cfg.T = T;
   cfg.rcache = rcache;
+  cfg.pack_zpairs = pack;
   if (budget > 0) cfg.budget = budget;
   if (single_max > 0) cfg.single_max = single_max;
   cfg.variant = 1;

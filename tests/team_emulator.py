@@ -72,7 +72,7 @@ def _load():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(_build_shim())
-            lib.shim_build.argtypes = [ctypes.c_int] * 12 + [ctypes.c_char_p, ctypes.c_int]
+            lib.shim_build.argtypes = [ctypes.c_int] * 13 + [ctypes.c_char_p, ctypes.c_int]
             lib.shim_build.restype = ctypes.c_int
             lib.shim_scalars.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.shim_scalars.restype = ctypes.c_int
@@ -120,13 +120,14 @@ class PlanError(RuntimeError):
     pass
 
 
-def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, single_max=0, rcache=-1) -> Plan:
+def plan(la, lb, lc, ld, Kb=1, Kk=1, onec=False, store=False, T=0, budget=0, single_max=0, rcache=-1,
+         pack=1) -> Plan:
     """The planner's team-kernel programs for one class and shape (store: False/True, or 2 for the
     solid-harmonic store plan; rcache: the planner's choice of cached R tables, -1 default, 0 never,
-    1 wherever they fit)."""
+    1 wherever they fit; pack: small ket z-pairs share column groups)."""
     lib = _load()
     err = ctypes.create_string_buffer(256)
-    if lib.shim_build(la, lb, lc, ld, Kb, Kk, int(onec), int(store), T, budget, single_max, rcache, err, 256):
+    if lib.shim_build(la, lb, lc, ld, Kb, Kk, int(onec), int(store), T, budget, single_max, rcache, int(pack), err, 256):
         raise PlanError(err.value.decode())
     sc = np.zeros(64, dtype=np.int32)
     n = lib.shim_scalars(sc.ctypes.data, 64)

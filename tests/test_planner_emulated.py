@@ -346,3 +346,21 @@ def test_cached_R_tables(lq, K, store, shape):
         assert cnt["fma"] == pytest.approx(pl.exec_fma, rel=1e-12)
         fma[rc] = pl.exec_fma
     assert fma[1] < fma[0]
+
+
+@pytest.mark.parametrize("lq,K,store", [((3, 3, 3, 3), (1, 1, 1, 1), True), ((3, 2, 3, 2), (1, 1, 1, 1), True),
+                                        ((3, 3, 2, 2), (1, 2, 1, 1), False), ((3, 3, 3, 2), (1, 1, 1, 1), 2)])
+def test_packed_zpair_groups(lq, K, store):
+    """Small ket z-pairs packed whole into shared column groups (each group computes the A blocks of all
+    its z-pairs) give the oracle's shellsets, like one group per z-pair, with fewer groups and no more FP64
+    operations (R per group, where it is not cached, runs fewer times)."""
+    b, q = _basis_4c(lq, K, 91)
+    emul, ref_fn, ev = ((_emulate_sph, oracle.eri4_sph, parity.Eri4SphEvaluator) if store == 2 else
+                        (_emulate_4c, oracle.eri4, parity.Eri4Evaluator))
+    ref, off = ref_fn(b, q)
+    pls = {pk: te.plan(*lq, K[0] * K[1], K[2] * K[3], store=store, pack=pk, single_max=4000) for pk in (0, 1)}
+    for pk, pl in pls.items():
+        te.check_hazards(pl)
+        parity.check(emul(pl, b, q), ref, off, what="packed %d %s K=%s" % (pk, lq, K), evaluate=ev(b, q))
+    assert pls[1].s["ngroups"] < pls[0].s["ngroups"]
+    assert pls[1].exec_fma <= pls[0].exec_fma * (1 + 1e-12)
