@@ -297,7 +297,7 @@ def xbatch_main(args):
     res["per_class_launches_ms"] = round(timed(lambda: xb.run(persistent=0)), 3)
     res["persistent_ms"] = round(timed(lambda: xb.run(persistent=1)), 3)
     res["hybrid_ms"] = round(timed(lambda: xb.run(persistent=2)), 3)
-    for mode, name in ((1, "persistent_graph_ms"), (2, "hybrid_graph_ms")):
+    for mode, name in ((0, "per_class_graph_ms"), (1, "persistent_graph_ms"), (2, "hybrid_graph_ms")):
         g = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(stream)
@@ -316,6 +316,14 @@ def xbatch_main(args):
         tune_s = round(time.perf_counter() - t0, 2)
         res["per_class_launches_autotuned_ms"] = round(timed(lambda: xb.run(persistent=0)), 3)
         res["hybrid_autotuned_ms"] = round(timed(lambda: xb.run(persistent=2)), 3)
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                xb.run(persistent=0)
+        torch.cuda.synchronize()
+        res["per_class_autotuned_graph_ms"] = round(timed(g.replay), 3)
     # per-class breakdown: every class launch alone, bracketed by events (one pass after the runs above)
     n_l = xb.n_class_launches
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_l + 1)]

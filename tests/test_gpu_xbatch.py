@@ -60,8 +60,10 @@ def test_batched_exchange_matches_single(eng, persistent):
     xb.close()
 
 
-@pytest.mark.parametrize("persistent", [1, 2])
+@pytest.mark.parametrize("persistent", [0, 1, 2])
 def test_persistent_launch_in_cuda_graph(eng, persistent):
+    """Every mode of mdx_xbatch_run (per-class launches, one persistent launch, the hybrid) captured in a
+    CUDA graph and replayed gives the directly launched K."""
     mols = _molecules()[:4]
     bases = [mdx.DeviceBasis(b) for b in mols]
     Ds = [torch.from_numpy(inputs.density(b.nao, 30 + i)) for i, b in enumerate(mols)]
