@@ -109,13 +109,18 @@ __global__ void __launch_bounds__(XS ? kXsBlock : 128) k_reg(const QuartetLaunch
   const double* __restrict__ boys = a.boys;
   const int Kb = a.plan.Kb, Kk = a.plan.Kk;
 
+  // shared-memory variant: [p|cd] in shared memory, and the shellset too when the digestion epilogue needs
+  // it whole; the store epilogue adds each bra pair's row straight into the output instead (less shared
+  // memory per thread, more warps per SM)
+  constexpr bool VSH = XS && DIGEST;
   TArr<XS, Nb * Nk> V;
   TArr<XS, HB * Nk> X;
   if constexpr (XS) {
     V.p = xs_smem + threadIdx.x;
-    X.p = xs_smem + Nb * Nk * kXsBlock + threadIdx.x;
+    X.p = xs_smem + (VSH ? Nb * Nk : 0) * kXsBlock + threadIdx.x;
   }
-  sfor<Nb * Nk>([&](auto i) { V[i] = 0.0; });
+  if constexpr (!XS || VSH) sfor<Nb * Nk>([&](auto i) { V[i] = 0.0; });
+  double* const outq = DIGEST ? nullptr : a.out + (a.qout ? a.qout[q] : q * (int64_t)(Nb * Nk));
 
   for (int pb = 0; pb < Kb; ++pb) {
     const double* __restrict__ rb = rb0 + (int64_t)pb * RB;
@@ -256,7 +261,13 @@ __global__ void __launch_bounds__(XS ? kXsBlock : 128) k_reg(const QuartetLaunch
             }
           }
           const int o = (ia * NB + ib) * Nk;
-          sfor<Nk>([&](auto cd) { V[o + cd] += acc[cd]; });
+          if constexpr (VSH) {
+            sfor<Nk>([&](auto cd) { V[o + cd] += acc[cd]; });
+          } else if (pb == 0) {
+            sfor<Nk>([&](auto cd) { outq[o + cd] = acc[cd]; });
+          } else {
+            sfor<Nk>([&](auto cd) { outq[o + cd] += acc[cd]; });
+          }
         }
       }
     } else {
@@ -292,12 +303,8 @@ __global__ void __launch_bounds__(XS ? kXsBlock : 128) k_reg(const QuartetLaunch
   }
 
   if constexpr (!DIGEST) {
-    double* o = a.out + (a.qout ? a.qout[q] : q * (int64_t)(Nb * Nk));   // no offsets: back to back
-    if constexpr (XS) {
-      for (int i = 0; i < Nb * Nk; ++i) o[i] = V[i];
-    } else {
-      sfor<Nb * Nk>([&](auto i) { o[i] = V[i]; });
-    }
+    // (no offsets: shellsets back to back); the shared-memory variant has written its rows already
+    if constexpr (!XS) sfor<Nb * Nk>([&](auto i) { outq[i] = V[i]; });
   } else {
     // Exchange digestion of the unique quartet (ij|kl) with weight w, as in
     // the team kernel: K_ik += w D_jl V, K_il += w D_jk V, K_jk += w D_il V,
@@ -384,11 +391,12 @@ cudaError_t launch_reg_class(const QuartetLaunch& a, cudaStream_t s) {
   constexpr bool XS = !reg_eligible(LA, LB, LC, LD);
   constexpr int bs = XS ? kXsBlock : 128;
   constexpr int Nk = ncart(LC) * ncart(LD);
-  constexpr size_t shm =
-      XS ? (size_t)(ncart(LA) * ncart(LB) * Nk + nherm(LA + LB) * Nk) * kXsBlock * sizeof(double) : 0;
+  // shared memory per block: [p|cd] (and, with the digestion epilogue, the shellset) of every thread
+  constexpr size_t shm_x = XS ? (size_t)nherm(LA + LB) * Nk * kXsBlock * sizeof(double) : 0;
+  constexpr size_t shm_d = XS ? (size_t)ncart(LA) * ncart(LB) * Nk * kXsBlock * sizeof(double) + shm_x : 0;
   const int64_t grid = (a.nq + bs - 1) / bs;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  if constexpr (shm > 48 * 1024) {
+  if constexpr (shm_d > 48 * 1024) {
     // opt in to more than 48 KB of dynamic shared memory, once per instance and device
     static bool attr[kRegMaxDevices] = {};
     int dev = 0;
@@ -397,16 +405,16 @@ cudaError_t launch_reg_class(const QuartetLaunch& a, cudaStream_t s) {
     if (dev < 0 || dev >= kRegMaxDevices) return cudaErrorInvalidDevice;
     if (!attr[dev]) {
       e = cudaFuncSetAttribute(k_reg<LA, LB, LC, LD, true, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)shm);
-      if (e == cudaSuccess)
+                               (int)shm_d);
+      if (e == cudaSuccess && shm_x > 48 * 1024)
         e = cudaFuncSetAttribute(k_reg<LA, LB, LC, LD, false, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shm);
+                                 (int)shm_x);
       if (e != cudaSuccess) return e;
       attr[dev] = true;
     }
   }
-  if (a.D) k_reg<LA, LB, LC, LD, true, XS><<<(unsigned)grid, bs, shm, s>>>(a);
-  else k_reg<LA, LB, LC, LD, false, XS><<<(unsigned)grid, bs, shm, s>>>(a);
+  if (a.D) k_reg<LA, LB, LC, LD, true, XS><<<(unsigned)grid, bs, shm_d, s>>>(a);
+  else k_reg<LA, LB, LC, LD, false, XS><<<(unsigned)grid, bs, shm_x, s>>>(a);
   return cudaGetLastError();
 }
 
