@@ -611,7 +611,10 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
     // than 16 warps: then the team grows (up to what its work fills) to keep the FP64 pipe fed
     while (P.T < Twork && (long)tps * P.T < 512) P.T *= 2;
   } else if (P.ngroups > 1) {
-    P.T = 512;
+    // solid-harmonic plans that hold one team per SM take 1024 lanes: their passes over the global
+    // staging areas wait on loads, which 32 warps per SM hide better than 16 (autotuned [ii|ii]: 0.80 of
+    // the FP64 peak against 0.74)
+    P.T = (sph && tps == 1) ? 1024 : 512;
   } else {
     int Tocc = 1;
     while (Tocc * tps < 512 && Tocc < 512) Tocc *= 2;
