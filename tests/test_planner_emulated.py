@@ -364,3 +364,33 @@ def test_packed_zpair_groups(lq, K, store):
         parity.check(emul(pl, b, q), ref, off, what="packed %d %s K=%s" % (pk, lq, K), evaluate=ev(b, q))
     assert pls[1].s["ngroups"] < pls[0].s["ngroups"]
     assert pls[1].exec_fma <= pls[0].exec_fma * (1 + 1e-12)
+
+
+def test_team_shape_rules():
+    """The planner's team shapes: teams of up to 32 lanes fill whole warps of a CTA; single-group classes with
+    a high total angular momentum and few Cartesian components ([l0|l0]) take at least half as many lanes as
+    the largest R level has entries; solid-harmonic plans of several groups that hold one team per SM take
+    1024 lanes."""
+    for lq in [(2, 0, 2, 0), (3, 0, 3, 0), (1, 1, 1, 1), (2, 1, 2, 0), (0, 0, 3, 3)]:
+        for store in (True, 2):
+            s = te.plan(*lq, store=store).s
+            if s["T"] < 32:
+                assert (s["T"] * s["teams_per_cta"]) % 32 == 0, (lq, store, s["T"], s["teams_per_cta"])
+    for lq, tmin in [((4, 0, 4, 0), 64), ((5, 0, 5, 0), 128), ((6, 0, 6, 0), 128)]:
+        for store in (True, 2):
+            s = te.plan(*lq, store=store).s
+            assert s["ngroups"] == 1 and s["T"] >= tmin, (lq, store, s["T"])
+    for lq in [(4, 4, 4, 4), (5, 5, 5, 5), (6, 6, 6, 6)]:
+        assert te.plan(*lq, store=2).s["T"] == 1024
+        assert te.plan(*lq, store=True).s["T"] == 512
+
+
+@pytest.mark.parametrize("lq,K", [((5, 5, 5, 5), (1, 5)), ((6, 6, 6, 6), (1, 5)), ((5, 5, 5, 5), (5, 5))])
+def test_cached_R_fallback_budget(lq, K):
+    """Contracted solid-harmonic classes whose R tables do not fit next to a full-budget workspace get the
+    plan with a smaller budget and the tables cached by default: R once per primitive quartet, fewer FP64
+    operations than the uncached plan."""
+    dflt = te.plan(*lq, Kb=K[0], Kk=K[1], store=2)
+    plain = te.plan(*lq, Kb=K[0], Kk=K[1], store=2, rcache=0)
+    assert dflt.s["cache_R"] >= 2 and plain.s["cache_R"] == 0
+    assert dflt.exec_fma < plain.exec_fma
