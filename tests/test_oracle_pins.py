@@ -436,6 +436,26 @@ def test_spherical_eri_transform():
                                rtol=0, atol=1e-14 * np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("ls", [(2, 0, 0, 0), (3, 1, 0, 0), (2, 2, 1, 0), (4, 0, 2, 1)])
+def test_spherical_eri_rotation_invariance(ls):
+    """A rotation of the whole geometry maps the real solid harmonics of each shell onto one another by an
+    orthogonal matrix, so the Frobenius norm of a solid-harmonic shellset does not change (a wrong
+    coefficient breaks the orthogonality); the Cartesian shellset's norm does change (its components are
+    not orthonormal), which shows the test has teeth."""
+    _, specs = _random_basis(list(ls), 91)
+    rng = np.random.Generator(np.random.PCG64(92))
+    Qr, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    rot = [(l, Qr @ np.asarray(xyz), z, c) for (l, xyz, z, c) in specs]
+    w0, _ = oracle.eri4_sph(_two_shell_basis(specs), [[0, 1, 2, 3]])
+    w1, _ = oracle.eri4_sph(_two_shell_basis(rot), [[0, 1, 2, 3]])
+    n0, n1 = np.linalg.norm(w0), np.linalg.norm(w1)
+    assert n0 > 1e-6
+    assert abs(n1 - n0) <= 1e-12 * n0, (n0, n1)
+    v0, _ = oracle.eri4(_two_shell_basis(specs), [[0, 1, 2, 3]])
+    v1, _ = oracle.eri4(_two_shell_basis(rot), [[0, 1, 2, 3]])
+    assert abs(np.linalg.norm(v1) - np.linalg.norm(v0)) > 1e-6 * np.linalg.norm(v0)
+
+
 # ------------------------------------------------------------------ textbook values
 def test_h2_sto3g_textbook_integrals():
     """H2 / STO-3G at 1.4 bohr: the four distinct two-electron integrals printed
