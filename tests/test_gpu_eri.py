@@ -307,3 +307,34 @@ def test_bound_screens_triplets(eng):
             assert np.all(v1[a:z] == 0.0)
         else:
             assert np.array_equal(v1[a:z], v0[a:z])
+
+
+@pytest.mark.parametrize("lq,K,nb,nk", [((6, 6, 6, 6), (1, 1, 1, 1), 24, 19), ((5, 5, 5, 5), (1, 1, 5, 1), 12, 10),
+                                        ((4, 0, 4, 0), (1, 1, 1, 1), 64, 64)])
+def test_solid_harmonic_rotation_invariance_at_scale(lq, K, nb, nk):
+    """A property that holds at any size: rotating the whole geometry leaves the Frobenius norm of every
+    solid-harmonic shellset unchanged (the harmonics of each l map onto one another orthogonally). Checked
+    on the GPU for every shellset of a batch the size of one benchmark chunk ([ii|ii]: 456 quartets), with
+    the autotuned shape."""
+    e = mdx.Engine(0)
+    b, q = inputs.class_sweep(lq, n_bra=nb, n_ket=nk, seed=33, K=K, box=3.0, zlo=0.2, zhi=5.0)
+    rng = np.random.Generator(np.random.PCG64(34))
+    R, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    norms = []
+    for rot in (False, True):
+        bb, _ = inputs.class_sweep(lq, n_bra=nb, n_ket=nk, seed=33, K=K, box=3.0, zlo=0.2, zhi=5.0)
+        if rot:
+            bb.center = np.ascontiguousarray(bb.center @ R.T)
+        bt = e.batch_eri4_sph(mdx.DeviceBasis(bb), q)
+        out = torch.empty(bt.total, dtype=torch.float64, device="cuda")
+        bt.autotune(out, max_trial=len(q))
+        bt.run(out)
+        off = bt.offsets()
+        torch.cuda.synchronize()
+        e.sync()
+        per = int(off[1] - off[0])
+        norms.append(out.view(-1, per).norm(dim=1).cpu().numpy())
+        bt.close()
+    big = norms[0] > 1e-8 * norms[0].max()
+    np.testing.assert_allclose(norms[1][big], norms[0][big], rtol=1e-11)
+    e.close()
