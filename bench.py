@@ -61,13 +61,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.01, help="fraction of each class the oracle times")
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "xbatch", "df", "grad", "ab", "peak", "sph", "counts", "xchain"],
+                    choices=["sweep", "xbatch", "df", "grad", "ab", "peak", "sph", "sph3", "counts", "xchain"],
                     help="sweep: the 4-center class sweep (default); xbatch: batched exchange of many molecules; "
                          "df: per-class 3-center rates on the density-fitting cluster; grad: exchange energy "
                          "and its nuclear gradient against the exchange build alone; ab: the default kernels "
                          "against the materialized-Hermite variant (dense [p|q], batched DGEMMs); "
                          "peak: measured FP64 throughput, scalar DFMA vs the FP64 tensor instruction; sph: "
-                         "solid-harmonic rates per class of the paper's Tab. nps4; counts: screened quartets and "
+                         "solid-harmonic rates per class of the paper's Tab. nps4; sph3: the same for 3-center [a|cd] "
+                         "(Tab. nps3); counts: screened quartets and "
                          "projected time of the full-size exchange workloads; xchain: the exchange build on a long "
                          "chain molecule whose D and K are far larger than L2")
     ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
@@ -576,6 +577,67 @@ PAPER_NPS4_V100 = {
     (6, 6, 6, 6): (3.47e4, 9.74e3, 1.99e3)}
 
 
+# The paper's Tab. nps3 (one V100, solid harmonics): shellsets/s for {K_bra, K_ket} = {1,1}, {1,5}, {5,5}
+PAPER_NPS3_V100 = {
+    (1, 0, 0): (5.18e9, 3.29e9, 1.09e9), (2, 0, 0): (3.30e9, 2.10e9, 7.20e8), (3, 0, 0): (2.52e9, 1.44e9, 5.61e8),
+    (4, 0, 0): (1.72e9, 1.13e9, 3.70e8), (5, 0, 0): (1.34e9, 8.15e8, 2.64e8), (6, 0, 0): (9.37e8, 5.17e8, 1.46e8),
+    (0, 1, 1): (2.17e9, 1.72e9, 5.47e8), (0, 2, 2): (7.81e8, 4.48e8, 1.17e8), (0, 3, 3): (2.04e8, 1.27e8, 2.90e7),
+    (0, 4, 4): (7.05e7, 1.57e7, 3.23e6), (0, 5, 5): (2.69e7, 5.77e6, 1.29e6), (0, 6, 6): (1.97e7, 4.67e6, 2.20e6),
+    (0, 0, 0): (9.63e9, 5.15e9, 1.64e9), (1, 1, 1): (7.25e8, 8.88e8, 2.59e8), (2, 2, 2): (1.75e8, 5.43e7, 1.18e7),
+    (3, 3, 3): (3.34e7, 7.48e6, 2.67e6), (4, 4, 4): (8.88e6, 1.90e6, 8.57e5), (5, 5, 5): (4.17e6, 8.91e5, 3.98e5),
+    (6, 6, 6): (1.18e6, 2.63e5, 1.02e5)}
+
+
+def sph3_main(args):
+    """Solid-harmonic 3-center integrals [a|cd] per class of the paper's Tab. nps3: [l|00], [0|ll], [l|ll],
+    {K_bra, K_ket} = {1,1}, {1,5}, {5,5} (the auxiliary shell has K_bra; one orbital shell of the pair has
+    K = 5). Random shells (class_sweep3); each class on a seeded grid sized to about 0.1 TFLOP of executed
+    work; autotuned per class unless --no-tune. The paper's V100 rates are quoted beside ours as context."""
+    import math
+    import torch
+    from paper_2405_01834_gb300 import mdx
+    torch.cuda.set_device(0)
+    eng = mdx.Engine(0)
+    stream = torch.cuda.current_stream()
+    peak = max(mdx.fp64_peak(0, 3), mdx.fp64_peak(1, 3)) * 1e9
+    kcols = (("{1,1}", (1, 1, 1)), ("{1,5}", (1, 5, 1)), ("{5,5}", (5, 5, 1)))
+    only = {tuple(int(ch) for ch in c) for c in args.sph_classes.split(",") if c} if args.sph_classes else None
+    rows = []
+    for lt in sorted(PAPER_NPS3_V100, key=lambda x: (sum(x), x)):
+        if only and lt not in only:
+            continue
+        for ki, (kname, K) in enumerate(kcols):
+            est = mdx.plan_info(lt[0], 0, lt[1], lt[2], K[0], K[1] * K[2], one_centre=True).exec_fma
+            n = int(min(2048 * 2048, max(1024, 0.1e12 / max(est, 1.0))))
+            side = int(math.ceil(math.sqrt(n)))
+            aux, orb, t = inputs.class_sweep3(lt, n_aux=side, n_ket=side, K=K)
+            da, do = mdx.DeviceBasis(aux), mdx.DeviceBasis(orb)
+            bt = eng.batch_eri3_sph(da, do, t)
+            out = torch.empty(bt.total, dtype=torch.float64, device="cuda")
+            if not args.no_tune:
+                bt.autotune(out, max_trial=int(min(len(t), max(152, 2e9 / max(est, 1.0)))))
+            ms = _event_ms(torch, stream, lambda: bt.run(out), args.steps, args.warmup)
+            rows.append({"class": "[%d|%d%d]" % lt, "K": kname, "shellsets": len(t), "ms": round(ms, 4),
+                         "shellsets_per_s": round(len(t) / (ms * 1e-3), 1),
+                         "exec_gflops": round(2 * bt.exec_fma / (ms * 1e-3) * 1e-9, 2),
+                         "exec_frac_of_peak": round(2 * bt.exec_fma / (ms * 1e-3) / peak, 4),
+                         "paper_v100_shellsets_per_s": PAPER_NPS3_V100[lt][ki]})
+            bt.close()
+    eng.sync()
+    line = {"metric": "solid-harmonic [a|cd]: shellsets/s and FP64 GFLOP/s per class of the paper's Tab. nps3",
+            "unit": "shellsets/s", "value": next((r["shellsets_per_s"] for r in rows if r["class"] == "[6|66]" and
+                                                 r["K"] == "{1,1}"), None),
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic", "steps": args.steps,
+            "warmup": args.warmup, "fp64_peak_gflops": round(peak * 1e-9, 1),
+            "config": {"workload": "solid-harmonic 3-center class sweep: random shells (centres in a 10-bohr box, "
+                                   "exponents log-uniform [0.05, 50]), [l|00], [0|ll], [l|ll], {K_bra, K_ket} = "
+                                   "{1,1}, {1,5}, {5,5}; value: [6|66] {1,1}"},
+            "paper_context": "Tab. nps3 of the paper: one V100 (FP64 7 TFLOP/s), solid harmonics",
+            "per_class": rows}
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def sph_main(args):
     """Solid-harmonic 4-center integrals (the paper's basis) per class of the paper's Tab. nps4: [ll|ll] and
     [l0|l0], contraction columns {K_bra, K_ket} = {1,1}, {1,5}, {5,5} (one shell of a contracted pair has
@@ -761,6 +823,8 @@ def main():
         return sph_main(args)
     if args.workload == "xchain":
         return xchain_main(args)
+    if args.workload == "sph3":
+        return sph3_main(args)
     if args.workload == "counts":
         return counts_main(args)
     import torch

@@ -149,6 +149,16 @@ mdx_status mdx_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, co
                     const double* bound, int64_t n, double tau, double* out, int64_t out_capacity,
                     int64_t* out_offsets, void* stream);
 
+/* mdx_eri3 over real solid harmonics: [a|cd] (Eq. def-acd) with a, c and d
+ * in solid-harmonic components (the bra's second function is the constant
+ * s function, one component), [a][c][d] per triplet at out + out_offsets[q];
+ * offsets and out_capacity count those doubles. The same two routes as
+ * mdx_eri4_sph (coefficients contracted into the transforms for the team
+ * kernel's classes, an index-by-index transform after the register kernels).
+ * Synchronises `stream`; results are complete on return. */
+mdx_status mdx_eri3_sph(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
+                        double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
+
 /* ---- prepared batches --------------------------------------------------
  * A batch separates the host-side preparation of a call (index download,
  * shell-pair de-duplication, grouping of quartets by class, planning,
@@ -173,6 +183,11 @@ mdx_status mdx_batch_eri4(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* q
  * solid-harmonic team-kernel classes (and may grow the staging area). */
 mdx_status mdx_batch_eri4_sph(mdx_ctx* ctx, const mdx_basis* basis, const int32_t* quartets, int64_t n,
                               mdx_batch** batch, void* stream);
+
+/* Prepare the triplets of mdx_eri3_sph (same arguments): a solid-harmonic
+ * batch like those of mdx_batch_eri4_sph. Synchronises `stream`. */
+mdx_status mdx_batch_eri3_sph(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
+                              int64_t n, mdx_batch** batch, void* stream);
 
 /* Prepare the triplets of mdx_eri3 (same arguments). Synchronises `stream`. */
 mdx_status mdx_batch_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,

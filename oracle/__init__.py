@@ -51,6 +51,7 @@ def _load():
             lib.orc_rtable.argtypes = [ctypes.c_int, ctypes.c_double, P, P]
             lib.orc_eri4.argtypes = [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
             lib.orc_eri3.argtypes = [P] * 13 + [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
+            lib.orc_eri3_sph.argtypes = [P] * 13 + [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
             lib.orc_exchange.argtypes = [P] * 7 + [ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int]
             lib.orc_exchange_rows.argtypes = [P] * 7 + [ctypes.c_int32, ctypes.c_int32, P, P, P,
                                                         ctypes.c_int32, ctypes.c_int]
@@ -136,6 +137,21 @@ def eri3(aux, orb, triplets, nthreads: int = 0, precision: int = 0):
     a1 = _basis_arrays(aux); a2 = _basis_arrays(orb)
     _load().orc_eri3(*[_p(a) for a in a1], *[_p(a) for a in a2], _p(t), len(t), _p(out), _p(off),
                      nthreads, precision)
+    return out, off
+
+
+def eri3_sph(aux, orb, triplets, nthreads: int = 0, precision: int = 0):
+    """[a|cd] over real solid harmonics (m = -l..l for a, c and d); returns (values, offsets).
+    precision 1: the long double build (Cartesian shellsets and transform), rounded at the end."""
+    t = np.ascontiguousarray(np.asarray(triplets, dtype=np.int32).reshape(-1, 3))
+    la = np.asarray(aux.l); lo = np.asarray(orb.l)
+    sizes = ((2 * la[t[:, 0]] + 1) * (2 * lo[t[:, 1]] + 1) * (2 * lo[t[:, 2]] + 1)).astype(np.int64)
+    off = np.zeros(len(t) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    out = np.zeros(int(off[-1]))
+    a1 = _basis_arrays(aux); a2 = _basis_arrays(orb)
+    _load().orc_eri3_sph(*[_p(a) for a in a1], *[_p(a) for a in a2], _p(t), len(t), _p(out), _p(off),
+                         nthreads, precision)
     return out, off
 
 

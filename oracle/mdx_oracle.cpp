@@ -488,6 +488,29 @@ void orc_solid_coefs(int l, double* C) {
 // rounded at the end.
 }  // extern "C"
 
+// Cartesian shellset v (index k of extent dim[k] = ncart(L[k]), k < naxes, row-major) to real solid
+// harmonics: every index contracted with the solid-harmonic coefficients of its l, one index at a time
+// (Eqs. solid2herm-1/2 applied to the finished shellset).
+template <typename T>
+void to_solid(std::vector<T>& v, int* dim, const int* L, int naxes) {
+  for (int axis = naxes - 1; axis >= 0; --axis) {   // contract index `axis`: ncart -> 2l+1
+    const std::vector<double> C = solid_coefs(L[axis]);
+    const int nc = dim[axis], ns = 2 * L[axis] + 1;
+    size_t outer = 1, inner = 1;
+    for (int k = 0; k < axis; ++k) outer *= dim[k];
+    for (int k = axis + 1; k < naxes; ++k) inner *= dim[k];
+    std::vector<T> w(outer * ns * inner, T(0));
+    for (size_t o = 0; o < outer; ++o)
+      for (int m = 0; m < ns; ++m)
+        for (int c = 0; c < nc; ++c) {
+          const T f = T(C[(size_t)m * nc + c]);
+          for (size_t i = 0; i < inner; ++i) w[(o * ns + m) * inner + i] += f * v[(o * nc + c) * inner + i];
+        }
+    v.swap(w);
+    dim[axis] = ns;
+  }
+}
+
 template <typename T>
 void eri4_sph_batch(const Basis& bs, const int32_t* l, const int32_t* quartets, int64_t n, double* out,
                     const int64_t* offsets, int nthreads) {
@@ -499,22 +522,25 @@ void eri4_sph_batch(const Basis& bs, const int32_t* l, const int32_t* quartets, 
     int dim[4] = {ncart(L[0]), ncart(L[1]), ncart(L[2]), ncart(L[3])};
     std::vector<T> v((size_t)dim[0] * dim[1] * dim[2] * dim[3]);
     shellset4<T>(bs, s4[0], s4[1], s4[2], s4[3], v.data());
-    for (int axis = 3; axis >= 0; --axis) {   // contract index `axis`: ncart -> 2l+1
-      const std::vector<double> C = solid_coefs(L[axis]);
-      const int nc = dim[axis], ns = 2 * L[axis] + 1;
-      size_t outer = 1, inner = 1;
-      for (int k = 0; k < axis; ++k) outer *= dim[k];
-      for (int k = axis + 1; k < 4; ++k) inner *= dim[k];
-      std::vector<T> w(outer * ns * inner, T(0));
-      for (size_t o = 0; o < outer; ++o)
-        for (int m = 0; m < ns; ++m)
-          for (int c = 0; c < nc; ++c) {
-            const T f = T(C[(size_t)m * nc + c]);
-            for (size_t i = 0; i < inner; ++i) w[(o * ns + m) * inner + i] += f * v[(o * nc + c) * inner + i];
-          }
-      v.swap(w);
-      dim[axis] = ns;
-    }
+    to_solid<T>(v, dim, L, 4);
+    double* o = out + offsets[q];
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (double)v[i];
+  }
+}
+
+// [a|cd] over real solid harmonics: the 3-center shellset (Eq. def-acd) with a, c and d transformed.
+template <typename T>
+void eri3_sph_batch(const Basis& aux, const Basis& orb, const int32_t* al, const int32_t* l, const int32_t* triplets,
+                    int64_t n, double* out, const int64_t* offsets, int nthreads) {
+  const int nt = nthreads_or_default(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* s3 = triplets + 3 * q;
+    const int L[3] = {al[s3[0]], l[s3[1]], l[s3[2]]};
+    int dim[3] = {ncart(L[0]), ncart(L[1]), ncart(L[2])};
+    std::vector<T> v((size_t)dim[0] * dim[1] * dim[2]);
+    shellset3<T>(aux, orb, s3[0], s3[1], s3[2], v.data());
+    to_solid<T>(v, dim, L, 3);
     double* o = out + offsets[q];
     for (size_t i = 0; i < v.size(); ++i) o[i] = (double)v[i];
   }
@@ -528,6 +554,17 @@ void orc_eri4_sph(const int32_t* l, const int32_t* nprim, const int32_t* prim_of
   Basis bs{l, nprim, prim_off, center, exps, coefs};
   if (precision == 1) eri4_sph_batch<long double>(bs, l, quartets, n, out, offsets, nthreads);
   else eri4_sph_batch<double>(bs, l, quartets, n, out, offsets, nthreads);
+}
+
+void orc_eri3_sph(const int32_t* al, const int32_t* anprim, const int32_t* aprim_off, const double* acenter,
+                  const double* aexps, const double* acoefs, const int32_t* l, const int32_t* nprim,
+                  const int32_t* prim_off, const double* center, const double* exps, const double* coefs,
+                  const int32_t* triplets, int64_t n, double* out, const int64_t* offsets, int nthreads,
+                  int precision) {
+  Basis aux{al, anprim, aprim_off, acenter, aexps, acoefs};
+  Basis orb{l, nprim, prim_off, center, exps, coefs};
+  if (precision == 1) eri3_sph_batch<long double>(aux, orb, al, l, triplets, n, out, offsets, nthreads);
+  else eri3_sph_batch<double>(aux, orb, al, l, triplets, n, out, offsets, nthreads);
 }
 
 // Batch of 3-center shellsets [a|cd]; triplets[n][3] = (aux shell, orb shell, orb shell).

@@ -100,6 +100,15 @@ class Eri3Evaluator:
         return self.oracle.eri3(a, o, self.t[sel], precision=precision)[0]
 
 
+class Eri3SphEvaluator(Eri3Evaluator):
+    """Oracle solid-harmonic [a|cd] of a subset of the triplets, optionally on perturbed bases."""
+
+    def __call__(self, sel, precision, seed=None):
+        a = self.aux if seed is None else _perturbed(self.aux, seed)
+        o = self.orb if seed is None else _perturbed(self.orb, 1000 + seed)
+        return self.oracle.eri3_sph(a, o, self.t[sel], precision=precision)[0]
+
+
 def _envelope(evaluate, sets, ld):
     """The FP64 oracle's rounding error on shellsets `sets`: the largest over the input and ENVELOPE_RUNS
     ulp-level perturbations of it, each against the long-double build of the same input."""

@@ -631,7 +631,7 @@ mdx_status make_batch4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quarte
 
 mdx_status make_batch3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
                        mdx_batch** out, cudaStream_t s, bool call_ws = false, const double* bound = nullptr,
-                       double tau = 0.0) {
+                       double tau = 0.0, bool sph = false) {
   HostBasis ha, ho;
   mdx_status st = fetch_basis(c, aux, ha, s);
   if (st != MDX_OK) return st;
@@ -651,13 +651,14 @@ mdx_status make_batch3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, c
     const int32_t* t3 = &ht[(size_t)q * 3];
     if (t3[0] < 0 || t3[0] >= ha.n || t3[1] < 0 || t3[1] >= ho.n || t3[2] < 0 || t3[2] >= ho.n)
       return fail(c, MDX_EINVAL, "shell index out of range");
-    const int64_t size = (int64_t)ncart(ha.l[t3[0]]) * ncart(ho.l[t3[1]]) * ncart(ho.l[t3[2]]);
+    auto nf = [sph](int l) { return (int64_t)(sph ? 2 * l + 1 : ncart(l)); };
+    const int64_t size = nf(ha.l[t3[0]]) * nf(ho.l[t3[1]]) * nf(ho.l[t3[2]]);
     offs[q + 1] = offs[q] + size;
     const int2 qp = hbound.empty() || hbound[(size_t)q] >= tau
                         ? make_int2(pix(t3[0], -1, 0), pix(t3[1], t3[2], 1)) : make_int2(0, 0);
     batch_add(bt, q, qp, offs[q], size, hbound, tau);
   }
-  return batch_prepare(c, aux, orb, ha, ho, bt, offs, out, s, call_ws);
+  return batch_prepare(c, aux, orb, ha, ho, bt, offs, out, s, call_ws, sph);
 }
 
 // create, run into `out`, copy offsets, destroy (synchronous)
@@ -807,6 +808,43 @@ mdx_status mdx_eri3(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, cons
   mdx_status st = make_batch3(c, aux, orb, triplets, n, &B, s, true, bound, tau);
   if (st != MDX_OK) return st;
   return run_once(c, B, out, out_capacity, out_offsets, s);
+}
+
+mdx_status mdx_eri3_sph(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
+                        double* out, int64_t out_capacity, int64_t* out_offsets, void* stream) {
+  const NvtxRange nvtx_range("mdx_eri3_sph");
+  if (!c) return MDX_EINVAL;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n < 0 || !out_offsets || (n > 0 && (!triplets || !out))) return fail(c, MDX_EINVAL, "invalid arguments");
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), s);
+    return e == cudaSuccess ? MDX_OK : cuda_fail(c, e, "offsets");
+  }
+  mdx_batch* B = nullptr;
+  mdx_status st = make_batch3(c, aux, orb, triplets, n, &B, s, false, nullptr, 0.0, true);
+  if (st != MDX_OK) return st;
+  std::unique_ptr<mdx_batch, void (*)(mdx_batch*)> guard(B, batch_free);
+  if (B->total > out_capacity) return fail(c, MDX_ECAPACITY, "output capacity too small");
+  if ((st = check_device_error(c, s)) != MDX_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(out_offsets, B->offsets, (B->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "offsets");
+  if ((st = batch_run(c, B, out, nullptr, s)) != MDX_OK) return st;
+  e = cudaStreamSynchronize(s);   // the batch's arrays are released on return
+  if (e != cudaSuccess) return cuda_fail(c, e, "eri3_sph");
+  return check_device_error(c, s);
+}
+
+mdx_status mdx_batch_eri3_sph(mdx_ctx* c, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets,
+                              int64_t n, mdx_batch** out, void* stream) {
+  const NvtxRange nvtx_range("mdx_batch_eri3_sph");
+  if (!c || !out) return MDX_EINVAL;
+  *out = nullptr;
+  c->last_error.clear();
+  cudaSetDevice(c->device);
+  if (n < 1 || !triplets) return fail(c, MDX_EINVAL, "invalid arguments");
+  return make_batch3(c, aux, orb, triplets, n, out, (cudaStream_t)stream, false, nullptr, 0.0, true);
 }
 
 mdx_status mdx_batch_eri4(mdx_ctx* c, const mdx_basis* basis, const int32_t* quartets, int64_t n, mdx_batch** out,

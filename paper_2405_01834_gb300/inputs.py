@@ -212,6 +212,28 @@ SWEEP_CLASSES = [(1, 1, 1, 1), (2, 2, 2, 2), (3, 3, 3, 3), (4, 4, 4, 4), (5, 5, 
 
 
 # ---------------------------------------------------------------- clusters
+def class_sweep3(lt, n_aux: int = 224, n_ket: int = 224, seed: int = 1007, box: float = 10.0,
+                 zlo: float = 0.05, zhi: float = 50.0, K=(1, 1, 1)):
+    """Random triplets of one 3-center class (la|lc,ld): an n_aux x n_ket grid of independent random
+    auxiliary shells and orbital shell pairs (uniform centres in a box, log-uniform exponents), the
+    3-center counterpart of class_sweep. Returns (aux basis, orbital basis, triplets[n_aux*n_ket, 3]),
+    auxiliary index fastest."""
+    la, lc, ld = (int(x) for x in lt)
+    ss = np.random.SeedSequence([seed, la, lc, ld, n_aux, n_ket])
+    rng = np.random.Generator(np.random.PCG64(ss))
+    aux, orb = BasisBuilder(), BasisBuilder()
+    for _ in range(n_aux):
+        random_shell(rng, aux, la, rng.uniform(0, box, 3), K[0], zlo, zhi)
+    for _ in range(n_ket):
+        random_shell(rng, orb, lc, rng.uniform(0, box, 3), K[1], zlo, zhi)
+        random_shell(rng, orb, ld, rng.uniform(0, box, 3), K[2], zlo, zhi)
+    i = np.arange(n_aux, dtype=np.int32)
+    k = np.arange(n_ket, dtype=np.int32)
+    ii, kk = np.meshgrid(i, k, indexing="xy")
+    t = np.stack([ii.reshape(-1), 2 * kk.reshape(-1), 2 * kk.reshape(-1) + 1], axis=1).astype(np.int32)
+    return aux.build(), orb.build(), t
+
+
 def cluster(rng, n_atoms: int, min_sep: float = 2.8, density_radius: float = 2.2) -> np.ndarray:
     """Seeded sequential random insertion of atoms in a sphere at >= min_sep bohr."""
     R = density_radius * n_atoms ** (1.0 / 3.0) + min_sep

@@ -120,6 +120,11 @@ def load(build_if_missing: bool = True):
     lib.mdx_batch_eri3.restype = I32
     lib.mdx_batch_eri4_sph.argtypes = [P, ctypes.POINTER(_Basis), P, I64, ctypes.POINTER(ctypes.c_void_p), P]
     lib.mdx_batch_eri4_sph.restype = I32
+    lib.mdx_eri3_sph.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, I64, P, I64, P, P]
+    lib.mdx_eri3_sph.restype = I32
+    lib.mdx_batch_eri3_sph.argtypes = [P, ctypes.POINTER(_Basis), ctypes.POINTER(_Basis), P, I64,
+                                       ctypes.POINTER(ctypes.c_void_p), P]
+    lib.mdx_batch_eri3_sph.restype = I32
     lib.mdx_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.mdx_batch_info.restype = I32
@@ -383,6 +388,34 @@ class Engine:
         self._check(self.lib.mdx_batch_eri4_sph(self.ctx, ctypes.byref(basis.desc), q.data_ptr(), q.shape[0],
                                                 ctypes.byref(h), _stream()), "mdx_batch_eri4_sph")
         return Batch(self, h, (basis,))
+
+    def eri3_sph(self, aux: DeviceBasis, orb: DeviceBasis, triplets, out: torch.Tensor = None):
+        """[a|cd] over real solid harmonics (a, c and d: m = -l..l). Returns (values, offsets)."""
+        t = torch.as_tensor(triplets, dtype=torch.int32, device="cuda").contiguous()
+        n = t.shape[0]
+        if out is None:
+            tn = t.cpu().numpy().astype(np.int64)
+            tn[:, 0] = np.clip(tn[:, 0], 0, len(aux.nc) - 1)
+            tn[:, 1:] = np.clip(tn[:, 1:], 0, len(orb.nc) - 1)
+            na = 2 * aux.host.l.astype(np.int64) + 1
+            no = 2 * orb.host.l.astype(np.int64) + 1
+            tot = int(np.sum(na[tn[:, 0]] * no[tn[:, 1]] * no[tn[:, 2]])) if n else 0
+            out = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        _check_out(out, "mdx_eri3_sph")
+        offs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        st = self.lib.mdx_eri3_sph(self.ctx, ctypes.byref(aux.desc), ctypes.byref(orb.desc), t.data_ptr(), n,
+                                   out.data_ptr(), out.numel(), offs.data_ptr(), _stream())
+        self._check(st, "mdx_eri3_sph")
+        return out, offs
+
+    def batch_eri3_sph(self, aux: DeviceBasis, orb: DeviceBasis, triplets) -> "Batch":
+        """Prepare triplets [n,3] for solid-harmonic output (see mdx_batch_eri3_sph)."""
+        t = torch.as_tensor(triplets, dtype=torch.int32, device="cuda").contiguous()
+        h = ctypes.c_void_p()
+        self._check(self.lib.mdx_batch_eri3_sph(self.ctx, ctypes.byref(aux.desc), ctypes.byref(orb.desc),
+                                                t.data_ptr(), t.shape[0], ctypes.byref(h), _stream()),
+                    "mdx_batch_eri3_sph")
+        return Batch(self, h, (aux, orb))
 
     def batch_eri3(self, aux: DeviceBasis, orb: DeviceBasis, triplets) -> "Batch":
         t = torch.as_tensor(triplets, dtype=torch.int32, device="cuda").contiguous()

@@ -338,3 +338,41 @@ def test_solid_harmonic_rotation_invariance_at_scale(lq, K, nb, nk):
     big = norms[0] > 1e-8 * norms[0].max()
     np.testing.assert_allclose(norms[1][big], norms[0][big], rtol=1e-11)
     e.close()
+
+
+def _basis_3c_sph(la, lc, ld, K, seed, n=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    aux, orb = inputs.BasisBuilder(), inputs.BasisBuilder()
+    for _ in range(n):
+        inputs.random_shell(rng, aux, la, rng.uniform(0, 3.0, 3), K[0], 0.2, 5.0)
+        inputs.random_shell(rng, orb, lc, rng.uniform(0, 3.0, 3), K[1], 0.2, 5.0)
+        inputs.random_shell(rng, orb, ld, rng.uniform(0, 3.0, 3), K[2], 0.2, 5.0)
+    trip = np.array([[a, 2 * k, 2 * k + 1] for a in range(n) for k in range(n)], dtype=np.int32)
+    return aux.build(), orb.build(), trip
+
+
+@pytest.mark.parametrize("la,lc,ld,K", [(1, 0, 0, (1, 3, 1)), (3, 2, 1, (1, 3, 1)), (6, 0, 0, (1, 6, 6)),
+                                        (4, 3, 3, (1, 1, 1)), (6, 3, 3, (1, 1, 1)), (2, 4, 4, (1, 1, 3)),
+                                        (5, 5, 5, (1, 1, 1)), (6, 6, 6, (1, 1, 1))])
+def test_solid_harmonic_eri3(eng, la, lc, ld, K):
+    """mdx_eri3_sph (and its prepared batch, autotuned) against the oracle's solid-harmonic [a|cd]:
+    register-kernel classes transformed index by index, team-kernel classes with the coefficients
+    contracted into the transforms (one-centre bra)."""
+    aux, orb, trip = _basis_3c_sph(la, lc, ld, K, 41 + la + lc)
+    da, do = mdx.DeviceBasis(aux), mdx.DeviceBasis(orb)
+    v, off = eng.eri3_sph(da, do, trip)
+    torch.cuda.synchronize()
+    ref, roff = oracle.eri3_sph(aux, orb, trip)
+    assert np.array_equal(off.cpu().numpy(), roff)
+    ev = parity.Eri3SphEvaluator(aux, orb, trip)
+    print(parity.check(v.cpu().numpy()[: roff[-1]], ref, roff, "solid [%d|%d%d]" % (la, lc, ld), ev))
+    e = mdx.Engine(0)
+    bt = e.batch_eri3_sph(da, do, trip)
+    w = torch.full((bt.total,), float("nan"), dtype=torch.float64, device="cuda")
+    bt.autotune(w, max_trial=len(trip))
+    bt.run(w)
+    torch.cuda.synchronize()
+    e.sync()
+    print(parity.check(w.cpu().numpy(), ref, roff, "solid batch [%d|%d%d]" % (la, lc, ld), ev))
+    bt.close()
+    e.close()

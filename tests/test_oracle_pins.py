@@ -456,6 +456,41 @@ def test_spherical_eri_rotation_invariance(ls):
     assert abs(np.linalg.norm(v1) - np.linalg.norm(v0)) > 1e-6 * np.linalg.norm(v0)
 
 
+def _basis_3c_pin(la, lc, ld, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    aux, orb = inputs.BasisBuilder(), inputs.BasisBuilder()
+    z = np.exp(rng.uniform(np.log(0.2), np.log(4.0), 2))
+    aux.add_shell(la, rng.uniform(-1, 1, 3), z, rng.uniform(0.2, 1.0, 2) * inputs.primitive_norm(la, z))
+    for l in (lc, ld):
+        z = np.exp(rng.uniform(np.log(0.2), np.log(4.0), 2))
+        orb.add_shell(l, rng.uniform(-1, 1, 3), z, rng.uniform(0.2, 1.0, 2) * inputs.primitive_norm(l, z))
+    return aux.build(), orb.build()
+
+
+@pytest.mark.parametrize("la,lc,ld", [(3, 1, 2), (6, 0, 0), (2, 4, 3)])
+def test_three_center_solid_harmonic_oracle(la, lc, ld):
+    """The oracle's [a|cd] over solid harmonics equals the coefficient matrices applied to its Cartesian
+    shellset (einsum), in FP64 and in long double, and keeps its norm when the geometry is rotated."""
+    aux, orb = _basis_3c_pin(la, lc, ld, 95 + la)
+    t = [[0, 0, 1]]
+    Cs = [oracle.solid_coefs(l) for l in (la, lc, ld)]
+    for prec in (0, 1):
+        v, _ = oracle.eri3(aux, orb, t, precision=prec)
+        vc = v.reshape(inputs.ncart(la), inputs.ncart(lc), inputs.ncart(ld))
+        ref = np.einsum("ai,ck,dl,ikl->acd", *Cs, vc)
+        # the combinations cancel: bound the rounding by the sum of the magnitudes they combine
+        mag = np.einsum("ai,ck,dl,ikl->acd", *[np.abs(C) for C in Cs], np.abs(vc))
+        w, off = oracle.eri3_sph(aux, orb, t, precision=prec)
+        assert off[-1] == (2 * la + 1) * (2 * lc + 1) * (2 * ld + 1)
+        assert np.all(np.abs(w - ref.reshape(-1)) <= 1e-14 * mag.reshape(-1) + 1e-300), prec
+    rng = np.random.Generator(np.random.PCG64(96))
+    R, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    aux.center = np.ascontiguousarray(aux.center @ R.T)
+    orb.center = np.ascontiguousarray(orb.center @ R.T)
+    w1, _ = oracle.eri3_sph(aux, orb, t, precision=1)
+    assert abs(np.linalg.norm(w1) - np.linalg.norm(w)) <= 1e-12 * np.linalg.norm(w)
+
+
 # ------------------------------------------------------------------ textbook values
 def test_h2_sto3g_textbook_integrals():
     """H2 / STO-3G at 1.4 bohr: the four distinct two-electron integrals printed

@@ -394,3 +394,24 @@ def test_cached_R_fallback_budget(lq, K):
     plain = te.plan(*lq, Kb=K[0], Kk=K[1], store=2, rcache=0)
     assert dflt.s["cache_R"] >= 2 and plain.s["cache_R"] == 0
     assert dflt.exec_fma < plain.exec_fma
+
+
+@pytest.mark.parametrize("la,lc,ld,K", [(3, 2, 1, (1, 3, 1)), (6, 0, 0, (1, 6, 6)), (4, 3, 3, (1, 1, 1)),
+                                        (5, 2, 2, (2, 1, 1)), (2, 4, 4, (1, 1, 1))])
+def test_three_center_solid_harmonic_plans(la, lc, ld, K):
+    """Solid-harmonic plans of 3-center classes (one-centre bra, the b -> b' pass an identity) reproduce the
+    oracle's solid-harmonic [a|cd], including several column groups and contracted kets."""
+    aux, orb, trip = _basis_3c(la, lc, ld, *K, seed=61 + la)
+    pl = te.plan(la, 0, lc, ld, K[0], K[1] * K[2], onec=True, store=2)
+    assert pl.s["sph"] == 1
+    te.check_hazards(pl)
+    got = []
+    for a, c, d in trip:
+        br = te.shell_pair_records(aux, a, None, signed=False)
+        kr = te.shell_pair_records(orb, c, d, signed=True)
+        got.append(te.emulate_sph(pl, br, kr).reshape(-1))
+    got = np.concatenate(got)
+    ref, off = oracle.eri3_sph(aux, orb, trip)
+    assert np.max(np.abs(ref)) > 1e-4
+    parity.check(got, ref, off, what="emulated sph [%d|%d%d]" % (la, lc, ld),
+                 evaluate=parity.Eri3SphEvaluator(aux, orb, trip))
