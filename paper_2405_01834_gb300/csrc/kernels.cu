@@ -41,6 +41,9 @@ constexpr int kSphNnzMax = 12;
 __constant__ int c_spn[kLmax + 1][2 * kLmax + 1];
 __constant__ uint8_t c_spk[kLmax + 1][2 * kLmax + 1][kSphNnzMax];
 __constant__ double c_spv[kLmax + 1][2 * kLmax + 1][kSphNnzMax];
+// c_top[l][k]: offset, in an X column of bra order L_b = l, of the top Hermite index (a_x, a_y, a_z) of
+// Cartesian component k of shell l (X rows (u, v) = (a_y, a_z), t = a_x contiguous)
+__constant__ uint16_t c_top[kLmax + 1][(kLmax + 1) * (kLmax + 2) / 2];
 
 cudaError_t kernel_attributes_init();
 
@@ -834,6 +837,25 @@ __device__ void quartet_sph(const QuartetLaunch& a, double* ws, double* xg, int6
         ws[P.o_Xs + col * P.hb + i] = v;
       }
       team_sync<CTA>(mask);
+      if (P.top_only) {
+        // one-centre bra over solid harmonics: OUT[m][col] = (2 zeta)^-la sum_a C_ma X[top(a)][col]
+        const double zeta = ws[P.o_recb];
+        double f = 1.0;
+        for (int k = 0; k < la; ++k) f *= 0.5 / zeta;
+        for (int e = tl; e < P.nsa * ncols; e += T) {
+          const int m = e / ncols, col = e - m * ncols;
+          const int n = c_spn[la][m];
+          const double* x = ws + P.o_Xs + col * P.hb;
+          double v = 0.0;
+          for (int j = 0; j < n; ++j) v = fma(c_spv[la][m][j], x[c_top[la][c_spk[la][m][j]]], v);
+          if (active) {
+            double* o = outq + (int64_t)m * nks + c0 + col;
+            *o = pb > 0 ? *o + f * v : f * v;
+          }
+        }
+        team_sync<CTA>(mask);
+        continue;
+      }
       bra_b1(P, ws, P.o_Xs, P.o_C1s, P.c1s, ncols, tl, T);
       team_sync<CTA>(mask);
       bra_b23(P, ws, P.o_C1s, P.c1s, P.o_OUTs, ncols, false, false, nullptr, nullptr, 0, active, tl, T);
@@ -1340,6 +1362,19 @@ cudaError_t kernel_attributes_init() {
     e = cudaMemcpyToSymbol(c_spn, spn, sizeof(spn));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_spk, spk, sizeof(spk));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_spv, spv, sizeof(spv));
+    if (e != cudaSuccess) return e;
+    uint16_t top[kLmax + 1][(kLmax + 1) * (kLmax + 2) / 2] = {};
+    for (int l = 0; l <= kLmax; ++l) {
+      int k = 0;
+      for (int ax = l; ax >= 0; --ax)
+        for (int ay = l - ax; ay >= 0; --ay, ++k) {
+          const int az = l - ax - ay;
+          // offset of row (u, v) = (ay, az) in the [u][v][t] simplex of order l, then t = ax
+          const int row = tet(l + 1) - tet(l - ay + 1) + tri(l - ay + 1) - tri(l - ay - az + 1);
+          top[l][k] = (uint16_t)(row + ax);
+        }
+    }
+    e = cudaMemcpyToSymbol(c_top, top, sizeof(top));
     if (e != cudaSuccess) return e;
   }
   const int maxshm = 227 * 1024;

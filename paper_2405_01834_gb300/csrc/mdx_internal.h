@@ -165,6 +165,11 @@ struct PlanDev {
   int32_t ncols_s;                       // spherical ket columns per bra-pass group
   int32_t o_Xs, o_C1s, o_OUTs, c1s;      // bra-pass layout (C1 stride c1s also holds the [a][b'] pass)
   int32_t hbp;                           // Hermite entries of the bra: length of one staged column
+  // 3-center solid-harmonic plans (one-centre bra): a real solid harmonic times a Gaussian expands in the
+  // top Hermite shell alone (S_lm(grad) exp(-zeta r^2) = (-2 zeta)^l S_lm(r) exp(-zeta r^2): every
+  // lower Hermite term of its Cartesian expansion cancels), so the ket steps form only the rows |p| = l_a
+  // and the bra step is OUT[m] = (2 zeta)^-l_a sum_a C_ma [a|cd] over those rows
+  int32_t top_only;
   int64_t xg_doubles;                    // staging per team: Xg [Nk][hbp] then Yg [nc_c * nsd][hbp]
   const Group* groups;
   const StepEntry* kprog;

@@ -46,19 +46,24 @@ std::vector<CartC> carts(int l) {
 // offset of row (t,u) in a [t][u][v] simplex layout of total order N
 inline int roff(int N, int t, int u) { return tet(N + 1) - tet(N - t + 1) + tri(N - t + 1) - tri(N - t - u + 1); }
 
-struct Layout {                  // a set of rows, each a contiguous run of doubles
-  std::map<std::pair<int, int>, int> rowlen;   // row key -> length
+struct Layout {                  // a set of rows, each a contiguous run of doubles from its lowest used index
+  std::map<std::pair<int, int>, std::pair<int, int>> rows;   // row key -> [lo, hi] of the used indices
   std::map<std::pair<int, int>, int> rowoff;
   int size = 0;
-  void need(int r0, int r1, int idx) {         // element idx of row (r0,r1) is used
-    auto& len = rowlen[{r0, r1}];
-    len = std::max(len, idx + 1);
+  void need(int r0, int r1, int lo, int hi) {   // elements lo..hi of row (r0,r1) are used
+    auto it = rows.find({r0, r1});
+    if (it == rows.end()) {
+      rows[{r0, r1}] = {lo, hi};
+    } else {
+      it->second.first = std::min(it->second.first, lo);
+      it->second.second = std::max(it->second.second, hi);
+    }
   }
   void finalize() {
     size = 0;
-    for (auto& kv : rowlen) { rowoff[kv.first] = size; size += kv.second; }
+    for (auto& kv : rows) { rowoff[kv.first] = size; size += kv.second.second - kv.second.first + 1; }
   }
-  int at(int r0, int r1, int idx) const { return rowoff.at({r0, r1}) + idx; }
+  int at(int r0, int r1, int idx) const { return rowoff.at({r0, r1}) + idx - rows.at({r0, r1}).first; }
 };
 
 struct ColInfo { CartC c, d; int gcol; };
@@ -74,22 +79,24 @@ bool build_group_k(const PlanDev& P, const std::vector<ColInfo>& cols, int o_A, 
                    bool emit_k1 = true) {
   const int Lb = P.Lb, L = P.L;
   const int Tcd = etab_size(P.lc, P.ld);
-  // B layout per column: rows (u,v), t' contiguous, full rows
+  // the X rows formed: t from tlo(u,v) (all of them, or the top Hermite shell t + u + v = Lb alone)
+  auto tlo = [&](int u, int v) { return P.top_only ? Lb - u - v : 0; };
+  // B layout per column: rows (u,v), t' contiguous over what k3 reads
   std::vector<Layout> BL(cols.size());
   for (size_t j = 0; j < cols.size(); ++j) {
     const int xx = cols[j].c.x + cols[j].d.x;
     for (int u = 0; u <= Lb; ++u)
-      for (int v = 0; u + v <= Lb; ++v) BL[j].need(u, v, Lb - u - v + xx);
+      for (int v = 0; u + v <= Lb; ++v) BL[j].need(u, v, tlo(u, v), Lb - u - v + xx);
     BL[j].finalize();
   }
-  std::map<std::pair<int, int>, Layout> AL;    // per z-pair (cz,dz)
+  std::map<std::pair<int, int>, Layout> AL;    // per z-pair (cz,dz): rows (t',v), u' contiguous over what k2 reads
   for (const ColInfo& ci : a_cols ? *a_cols : cols) {
     const CartC& c = ci.c; const CartC& d = ci.d;
     const int xx = c.x + d.x, yy = c.y + d.y;
     Layout& A = AL[{c.z, d.z}];
     for (int u = 0; u <= Lb; ++u)
       for (int v = 0; u + v <= Lb; ++v)
-        for (int tp = 0; tp <= Lb - u - v + xx; ++tp) A.need(tp, v, u + yy);
+        for (int tp = tlo(u, v); tp <= Lb - u - v + xx; ++tp) A.need(tp, v, u, u + yy);
   }
   // A blocks back to back
   std::map<std::pair<int, int>, int> abase;
@@ -111,9 +118,9 @@ bool build_group_k(const PlanDev& P, const std::vector<ColInfo>& cols, int o_A, 
     if (!emit_k1) break;
     const int cz = kv.first.first, dz = kv.first.second;
     const int coef = reck + 2 * Tcd + etab_off(P.lc, P.ld, cz, dz);
-    for (auto& row : kv.second.rowlen) {
+    for (auto& row : kv.second.rows) {
       const int tp = row.first.first, v = row.first.second;
-      for (int up = 0; up < row.second; ++up) {
+      for (int up = row.second.first; up <= row.second.second; ++up) {
         if (tp + up + v + cz + dz > L) return false;   // cannot happen (see derivation)
         if (!push(k1, o_A + abase[kv.first] + kv.second.at(tp, v, up), P.o_R0 + roff(L, tp, up) + v, coef, cz + dz + 1))
           return false;
@@ -128,15 +135,15 @@ bool build_group_k(const PlanDev& P, const std::vector<ColInfo>& cols, int o_A, 
     const int coefy = reck + Tcd + etab_off(P.lc, P.ld, c.y, d.y);
     const int coefx = reck + etab_off(P.lc, P.ld, c.x, d.x);
     // k2: B[t',u,v] = sum_nu Ey'[cy,dy][nu] A[t',u+nu,v]
-    for (auto& row : BL[j].rowlen) {
+    for (auto& row : BL[j].rows) {
       const int u = row.first.first, v = row.first.second;
-      for (int tp = 0; tp < row.second; ++tp)
+      for (int tp = row.second.first; tp <= row.second.second; ++tp)
         if (!push(k2, o_B + bbase[j] + BL[j].at(u, v, tp), ab0 + A.at(tp, v, u), coefy, yy + 1)) return false;
     }
-    // k3: X[t,u,v] += sum_tau Ex'[cx,dx][tau] B[t+tau,u,v]
+    // k3: X[t,u,v] += sum_tau Ex'[cx,dx][tau] B[t+tau,u,v]   (top_only: the rows t + u + v = Lb alone)
     for (int u = 0; u <= Lb; ++u)
       for (int v = 0; u + v <= Lb; ++v)
-        for (int t = 0; t + u + v <= Lb; ++t) {
+        for (int t = tlo(u, v); t + u + v <= Lb; ++t) {
           const int xo = o_X + (int)j * P.hb + roff(Lb, u, v) + t;   // X rows (u,v), t contiguous
           if (!push(k3, xo, o_B + bbase[j] + BL[j].at(u, v, t), coefx, xx + 1)) return false;
         }
@@ -360,6 +367,7 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
   // the ket groups of a solid-harmonic plan hold only their X columns (the bra pass has its own layout)
   const bool sph = key.store == 2;
   P.sph = sph ? 1 : 0;
+  P.top_only = (sph && key.onec) ? 1 : 0;
   P.has_out = sph ? 0 : ((key.store && key.Kb == 1) ? 0 : 1);
   const int out_per_col = P.has_out ? P.Nb : 0;
   const int c1_per_col = sph ? 0 : P.c1size;
@@ -558,8 +566,9 @@ bool build_plan(const ClassKey& key, const PlanConfig& cfg, Plan& plan, std::str
     const double nks = (double)P.nsc * P.nsd;
     const double ket_sph = (double)P.hbp * ((double)ncart(key.lc) * solid_nnz(key.ld) + (double)solid_nnz(key.lc) * P.nsd);
     const double bra_sph = nks * ((double)ncart(key.la) * solid_nnz(key.lb) + (double)solid_nnz(key.la) * P.nsb);
-    plan.exec_fma = key.Kb * key.Kk * (fma_k + nrec * (fma_r + 8.0 * (P.L + 1))) +
-                    key.Kb * (ket_sph + fma_b * nks + bra_sph);
+    // top_only: one sparse sum over the top Hermite shell per solid-harmonic bra component and column
+    const double bra = P.top_only ? nks * (double)solid_nnz(key.la) : fma_b * nks + bra_sph;
+    plan.exec_fma = key.Kb * key.Kk * (fma_k + nrec * (fma_r + 8.0 * (P.L + 1))) + key.Kb * (ket_sph + bra);
   }
   const double team_fma_per_prim = plan.exec_fma / ((double)key.Kb * key.Kk);
 

@@ -58,7 +58,7 @@ int shim_scalars(int32_t* out, int cap) {
                        P.o_G, P.o_R0, P.o_R1, P.o_A, P.o_B, P.o_X, P.o_C1, P.o_OUT, P.c1size, P.ngroups,
                        P.ncols_max, P.nb1, P.nb23, P.cache_R, P.has_out, P.sph, P.nsa, P.nsb, P.nsc, P.nsd,
                        P.ncols_s, P.o_Xs, P.o_C1s, P.o_OUTs, P.c1s, P.hbp, (int32_t)P.xg_doubles, P.o_Rc,
-                       P.rstride};
+                       P.rstride, P.top_only};
   const int n = (int)(sizeof(v) / sizeof(v[0]));
   if (out && cap >= n) std::memcpy(out, v, sizeof(v));
   return n;

@@ -42,7 +42,7 @@ SHIM_LIB = os.path.join(BUILD, "libplanner_shim.so")
 
 SCALARS = ("la lb lc ld Kb Kk onec L Lb Lk Nb Nk hb T teams_per_cta team_doubles recb reck o_recb o_reck o_scal "
            "o_G o_R0 o_R1 o_A o_B o_X o_C1 o_OUT c1size ngroups ncols_max nb1 nb23 cache_R has_out "
-           "sph nsa nsb nsc nsd ncols_s o_Xs o_C1s o_OUTs c1s hbp xg_doubles o_Rc rstride").split()
+           "sph nsa nsb nsc nsd ncols_s o_Xs o_C1s o_OUTs c1s hbp xg_doubles o_Rc rstride top_only").split()
 STEP = np.dtype([("out", "<u2"), ("src", "<u2"), ("coef", "<u2"), ("n", "u1"), ("stride", "u1")])
 B23 = np.dtype([("out", "<u2"), ("src", "<u2"), ("ey", "<u2"), ("ez", "<u2"), ("u0", "u1"), ("nu", "u1"),
                 ("su", "u1"), ("v0", "u1"), ("nv", "u1"), ("sv", "u1"), ("r", "u1"), ("pad", "u1")])
@@ -505,6 +505,22 @@ def emulate_sph(pl: Plan, bra_recs, ket_recs_signed, count=None) -> np.ndarray:
             for col in range(ncols):                                       # pass c -> c'
                 cp, dp = divmod(c0 + col, nsd)
                 ws[span(s["o_Xs"] + col * hb, hbp)] = Cc[cp] @ Y[:, dp, :]
+            if s["top_only"]:
+                # one-centre bra: OUT[m] = (2 zeta)^-la sum_a C_ma X[top(a)] (the lower Hermite terms of a
+                # solid harmonic's Cartesian expansion cancel)
+                L = la
+                top = []
+                for ax in range(L, -1, -1):
+                    for ay in range(L - ax, -1, -1):
+                        az = L - ax - ay
+                        row = (L + 1) * (L + 2) * (L + 3) // 6 - (L - ay + 1) * (L - ay + 2) * (L - ay + 3) // 6 \
+                            + (L - ay + 1) * (L - ay + 2) // 2 - (L - ay - az + 1) * (L - ay - az + 2) // 2
+                        top.append(row + ax)
+                f = (0.5 / ws[ob]) ** L
+                Xt = np.stack([ws[span(s["o_Xs"] + col * hb, hbp)][top] for col in range(ncols)], -1)
+                out[:, c0:c0 + ncols] += f * (Ca @ Xt)
+                count["fma"] += ncols * int((Ca != 0).sum())
+                continue
             count["fma"] += int(pl.b1["n"].astype(np.int64).sum()) * ncols
             count["fma"] += int((pl.b23["nv"].astype(np.int64) * (pl.b23["nu"].astype(np.int64) + 1)).sum()) * ncols
             for e in pl.b1:                                                # b1 into the C1 slots

@@ -399,8 +399,10 @@ def test_cached_R_fallback_budget(lq, K):
 @pytest.mark.parametrize("la,lc,ld,K", [(3, 2, 1, (1, 3, 1)), (6, 0, 0, (1, 6, 6)), (4, 3, 3, (1, 1, 1)),
                                         (5, 2, 2, (2, 1, 1)), (2, 4, 4, (1, 1, 1))])
 def test_three_center_solid_harmonic_plans(la, lc, ld, K):
-    """Solid-harmonic plans of 3-center classes (one-centre bra, the b -> b' pass an identity) reproduce the
-    oracle's solid-harmonic [a|cd], including several column groups and contracted kets."""
+    """Solid-harmonic plans of 3-center classes reproduce the oracle's solid-harmonic [a|cd], including several
+    column groups and contracted kets. The one-centre bra over solid harmonics needs only the top Hermite
+    shell (the lower terms of a solid harmonic's Cartesian expansion cancel): the k3 step forms those rows
+    alone and the bra step is one sparse sum per component, fewer operations than the Cartesian plan."""
     aux, orb, trip = _basis_3c(la, lc, ld, *K, seed=61 + la)
     pl = te.plan(la, 0, lc, ld, K[0], K[1] * K[2], onec=True, store=2)
     assert pl.s["sph"] == 1
@@ -415,3 +417,10 @@ def test_three_center_solid_harmonic_plans(la, lc, ld, K):
     assert np.max(np.abs(ref)) > 1e-4
     parity.check(got, ref, off, what="emulated sph [%d|%d%d]" % (la, lc, ld),
                  evaluate=parity.Eri3SphEvaluator(aux, orb, trip))
+    # only the top Hermite shell of the bra is formed, and the planner counts what the programs execute
+    assert pl.s["top_only"] == 1
+    cnt = {}
+    te.emulate_sph(pl, te.shell_pair_records(aux, trip[0][0], None, signed=False),
+                   te.shell_pair_records(orb, trip[0][1], trip[0][2], signed=True), cnt)
+    assert cnt["fma"] == pytest.approx(pl.exec_fma, rel=1e-9)
+    assert pl.exec_fma < te.plan(la, 0, lc, ld, K[0], K[1] * K[2], onec=True, store=True).exec_fma
