@@ -73,6 +73,7 @@ def parse():
                          "chain molecule whose D and K are far larger than L2")
     ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
     ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
+    ap.add_argument("--df-sph", action="store_true", help="df: solid-harmonic functions (mdx_batch_eri3_sph)")
     ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
     ap.add_argument("--n-mol", type=int, default=64)
     ap.add_argument("--atoms", default="2,5", help="xbatch: atoms per molecule, uniform in [lo,hi]")
@@ -410,7 +411,7 @@ def df_main(args):
                 Pp = pc[rng.choice(len(pc), npr, replace=False)]
                 trip = np.stack([np.repeat(A, npr), np.tile(Pp[:, 0], na), np.tile(Pp[:, 1], na)],
                                 axis=1).astype(np.int32)
-                bt = eng.batch_eri3(daux, dorb, trip)
+                bt = (eng.batch_eri3_sph if args.df_sph else eng.batch_eri3)(daux, dorb, trip)
                 out = torch.empty(max(bt.total, 1), dtype=torch.float64, device="cuda")
                 ms = _event_ms(torch, stream, lambda: bt.run(out), args.steps, args.warmup)
                 Kc, Kd = int(orb.nprim[Pp[0, 0]]), int(orb.nprim[Pp[0, 1]])
@@ -431,7 +432,8 @@ def df_main(args):
             "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "density-fitting cluster: 100 atoms (>= 2.8 bohr apart), orbital 4s3p2d1f "
                                    "(K 6/3/1/1), auxiliary s..i (K 1, even-tempered ratio 2.5); orbital pairs "
-                                   "kept at Q >= 1e-12; per class a grid of <= 64 auxiliary shells x kept pairs",
+                                   "kept at Q >= 1e-12; per class a grid of <= 64 auxiliary shells x kept pairs; "
+                                   + ("solid-harmonic" if args.df_sph else "Cartesian") + " functions",
                        "orbital_pairs": int(len(pairs)), "kept_pairs": int(len(kept)),
                        "aux_shells": int(aux.n_shells)},
             "full_tensor": {"triplets": int(full_trip), "estimated_s": round(full_s, 3)},
