@@ -152,10 +152,14 @@ mdx_status mdx_eri3(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, co
 /* mdx_eri3 over real solid harmonics: [a|cd] (Eq. def-acd) with a, c and d
  * in solid-harmonic components (the bra's second function is the constant
  * s function, one component), [a][c][d] per triplet at out + out_offsets[q];
- * offsets and out_capacity count those doubles. The same two routes as
- * mdx_eri4_sph (coefficients contracted into the transforms for the team
- * kernel's classes, an index-by-index transform after the register kernels).
- * Synchronises `stream`; results are complete on return. */
+ * offsets and out_capacity count those doubles. Classes evaluated by the team
+ * kernel use that a solid harmonic times a Gaussian expands in the top
+ * Hermite shell |p| = l_a alone (the lower terms of Eq. E1rr cancel): only
+ * those rows of [p|cd] are formed, the c and d indices are transformed as in
+ * mdx_eri4_sph, and each component is (2 zeta_a)^-l_a sum_a C_ma [a|cd].
+ * Small classes with a register kernel are evaluated over Cartesians and
+ * transformed index by index. Synchronises `stream`; results are complete on
+ * return. */
 mdx_status mdx_eri3_sph(mdx_ctx* ctx, const mdx_basis* aux, const mdx_basis* orb, const int32_t* triplets, int64_t n,
                         double* out, int64_t out_capacity, int64_t* out_offsets, void* stream);
 
