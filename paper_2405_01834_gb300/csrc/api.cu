@@ -432,9 +432,11 @@ mdx_status batch_prepare(mdx_ctx* c, const mdx_basis* b0, const mdx_basis* b1, c
     Plan* splan = nullptr;
     int grid = 0;
     double fma = plan->exec_fma;
-    if (sph && !plan->d.reg) {
-      ClassKey k2 = kv.first;
-      k2.store = 2;
+    ClassKey ks = kv.first;
+    ks.store = 2;
+    // the solid-harmonic team kernel: every class without a register kernel, and those the autotuner moved
+    if (sph && (!plan->d.reg || c->tuned.count(ks))) {
+      const ClassKey& k2 = ks;
       if ((st = get_plan(c, k2, &splan, s)) != MDX_OK) return st;
       cudaError_t e = sph_grid(splan->d, cnt, &grid);
       if (e != cudaSuccess) return cuda_fail(c, e, "solid-harmonic launch shape");
@@ -1008,19 +1010,58 @@ mdx_status autotune_sph(mdx_ctx* c, mdx_batch* b, double* out, int64_t max_trial
     return st;
   };
   for (auto& r : b->ranges) {
-    if (!r.splan || r.count == 0) continue;
+    if (r.count == 0) continue;
     ClassKey k2 = r.key;
     k2.store = 2;
+    const int64_t nq = std::min(r.count, max_trial);
+    // classes on the register-kernel route (Cartesian shellsets, then the transform) also try the
+    // solid-harmonic team kernel, and move to it when it is faster
+    float reg_ms = 1e30f;
+    if (!r.splan) {
+      QuartetLaunch a{};
+      a.plan = r.plan->d;
+      a.nq = nq;
+      a.qpairs = b->qp + r.begin;
+      a.qout = b->cqoff + r.begin;
+      a.pair_rec = b->pair_rec;
+      a.recs = b->recs;
+      a.recs_signed = b->recs_s;
+      a.boys = c->d_boys;
+      a.rprog = c->d_rprog;
+      a.rprog_off = c->d_rprog_off;
+      a.out = b->cart;
+      a.err = c->d_err;
+      const SphLaunch t{r.key.la, r.key.lb, r.key.lc, r.key.ld, nq, b->cart, b->cqoff + r.begin, out,
+                        b->qoff + r.begin};
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        e = launch_quartets(a, s);
+        if (e == cudaSuccess) e = launch_cart2sph(t, s);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return done(cuda_fail(c, e, "autotune"));
+        float tm = 0;
+        cudaEventElapsedTime(&tm, e0, e1);
+        reg_ms = std::min(reg_ms, tm);
+      }
+    }
     std::vector<PlanConfig> cands;
-    if (r.splan->d.ngroups > 1) {
+    Plan* dflt = r.splan;
+    std::unique_ptr<Plan> dflt_own;
+    if (!dflt) {   // the team plan's default shape decides which candidate family applies
+      dflt_own.reset(new Plan());
+      std::string err;
+      if (!build_plan(k2, PlanConfig{}, *dflt_own, err)) continue;
+      dflt = dflt_own.get();
+    }
+    if (dflt->d.ngroups > 1) {
       for (int budget : {200 * 1024, 108 * 1024})
         for (int T : {128, 256, 512, 1024})
           for (int rc : {-1, 0, 1}) cands.push_back(PlanConfig{T, budget, 96 * 1024, 1, rc});
     } else {
       for (int T : {0, 4, 8, 16, 32, 64, 128, 256, 512}) cands.push_back(PlanConfig{T, 200 * 1024, 96 * 1024, 1, -1});
     }
-    const int64_t nq = std::min(r.count, max_trial);
-    float best_ms = 1e30f;
+    float best_ms = reg_ms;   // a register-kernel class keeps its route unless a team shape beats it
     PlanConfig best{};
     std::unique_ptr<Plan> best_plan;
     std::vector<std::array<int, 5>> seen;   // shapes already timed
@@ -1097,6 +1138,9 @@ mdx_status autotune_sph(mdx_ctx* c, mdx_batch* b, double* out, int64_t max_trial
       b->nxg = need;
     }
     c->tuned[k2] = best;
+    // the batch's executed-FMA count follows the route and shape the class runs now
+    const double old_fma = r.splan ? r.splan->exec_fma : r.plan->exec_fma + cart2sph_fma(r.key);
+    b->exec_fma += (best_plan->exec_fma - old_fma) * (double)r.count;
     auto it = c->plans.find(k2);
     if (it != c->plans.end()) c->retired.push_back(std::move(it->second));
     r.splan = best_plan.get();
@@ -1192,6 +1236,7 @@ mdx_status mdx_batch_autotune(mdx_ctx* c, mdx_batch* b, double* out, int64_t out
     }
     if (!best_plan) continue;
     c->tuned[r.key] = best;
+    b->exec_fma += (best_plan->exec_fma - r.plan->exec_fma) * (double)r.count;   // the shape it runs now
     auto it = c->plans.find(r.key);
     if (it != c->plans.end()) c->retired.push_back(std::move(it->second));
     r.plan = best_plan.get();
