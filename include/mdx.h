@@ -299,14 +299,15 @@ mdx_status mdx_exchange_screen(mdx_ctx* ctx, const mdx_basis* basis, const int32
  * (ij|kl), with D held fixed (alpha = -1 for a closed-shell D = C C^T; the
  * paper lists geometric derivatives as future work, Sec. 7).
  * Same pairs, Q, tau and screening as mdx_exchange. For every kept unique
- * quartet the centres of its first three shells are differentiated through
+ * quartet the centres of three of its shells are differentiated through
  * the derivative of a primitive Cartesian Gaussian (Eq. 1),
  *   d/dA_x x_A^a e^(-zeta x_A^2) = 2 zeta x_A^(a+1) e - a x_A^(a-1) e,
  * i.e. classes with that shell's l raised (coefficients 2 zeta c) and lowered
  * by one, evaluated by the same Hermite machinery (Hermite index reaching
  * L+1) with [tuv] recomputed per launch, never stored, and contracted inside
  * the kernel with G = D_ik (x) D_jl + D_il (x) D_jk; the fourth centre follows
- * from translational invariance.
+ * from translational invariance. Per class the fourth is the shell whose
+ * raised and lowered classes cost most (an s shell has no lowered class).
  * basis->atom is required (atom of each shell, 0 <= atom < n_atoms).
  * Shells must have l <= MDX_LMAX - 1 (the raised classes reach l + 1);
  * MDX_EUNSUPPORTED otherwise (after the screening, before any integral

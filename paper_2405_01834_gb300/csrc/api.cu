@@ -1671,9 +1671,12 @@ mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* 
   if ((st = ensure(c, "g_recs_s", (size_t)roff, &d_recs_s, s)) != MDX_OK) return st;
   e = launch_pair_records(b3, b3, d_jobs, (int64_t)jobs.size(), d_recs, d_recs_s, c->d_err, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair records");
-  // per bucket: centre A (+/-), B (+/-), C (+/-) and, if asked, the energy
+  // per bucket: three of the centres i, j, k, l raised (+) and lowered (-), and, if asked, the energy;
+  // the fourth centre follows from translational invariance. A position's raised and lowered shells
+  // are record variants 1/2 (first shell of the pair) or 3/4 (second shell) of its pair.
   struct Var { int bra, ket, pos, sign; };
-  const Var vars[7] = {{1, 0, 0, 1}, {2, 0, 0, -1}, {3, 0, 1, 1}, {4, 0, 1, -1}, {0, 1, 2, 1}, {0, 2, 2, -1}, {0, 0, -1, 0}};
+  const Var all_vars[9] = {{1, 0, 0, 1}, {2, 0, 0, -1}, {3, 0, 1, 1}, {4, 0, 1, -1}, {0, 1, 2, 1},
+                           {0, 2, 2, -1}, {0, 3, 3, 1}, {0, 4, 3, -1}, {0, 0, -1, 0}};
   // all plans first (their uploads go to s before the fork), then the launches
   // spread over the streams, heaviest first
   struct GradJob {
@@ -1689,8 +1692,23 @@ mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* 
       const int64_t b = (int64_t)cp * (cp + 1) / 2 + cq;
       if (X.counts[b] == 0) continue;
       const int l0[4] = {X.classes[cp][0], X.classes[cp][1], X.classes[cq][0], X.classes[cq][1]};
-      for (const Var& v : vars) {
+      // the centre left to translational invariance: the one whose shifted classes cost most (an s shell
+      // has no lowered class, so a class with s shells drops a whole evaluation)
+      int ginv = 0;
+      double worst = -1.0;
+      for (int pos = 0; pos < 4; ++pos) {
+        double cost = 0.0;
+        for (int sg = 1; sg >= -1; sg -= 2) {
+          if (sg < 0 && l0[pos] == 0) continue;
+          int ls[4] = {l0[0], l0[1], l0[2], l0[3]};
+          ls[pos] += sg;
+          cost += model_flops_class(ClassKey{ls[0], ls[1], ls[2], ls[3], X.classes[cp][2], X.classes[cq][2], 0});
+        }
+        if (cost > worst) { worst = cost; ginv = pos; }
+      }
+      for (const Var& v : all_vars) {
         if (v.pos < 0 && !energy) continue;
+        if (v.pos == ginv) continue;
         if (v.sign < 0 && l0[v.pos] == 0) continue;   // no l-1 term for s shells
         int ls[4] = {l0[0], l0[1], l0[2], l0[3]};
         if (v.pos >= 0) ls[v.pos] += v.sign;
@@ -1710,6 +1728,7 @@ mdx_status mdx_exchange_grad(mdx_ctx* c, const mdx_basis* basis, const int32_t* 
         a.alpha = alpha;
         a.gpos = v.pos;
         a.gsign = v.sign;
+        a.ginv = ginv;
         for (int k = 0; k < 4; ++k) a.lorig[k] = l0[k];
         GradJob g{a, model_flops_class(key) * (double)a.nq, 0, 0};
         if (plan->d.reg) {

@@ -398,9 +398,10 @@ __device__ __forceinline__ double dens_G(const double* __restrict__ D, int64_t n
 //   d/dA_x phi_a = 2 zeta phi_{a+1_x} - a_x phi_{a-1_x},
 // i.e. this launch's shifted class: every element of the l+1 shellset feeds
 // each direction x whose component is >= 1 (weight +1), every element of the
-// l-1 shellset each direction (weight -(a_x + 1)). The fourth centre follows
-// from translational invariance: what centre gpos gains, the atom of shell l
-// loses. gpos = -1 accumulates the energy alpha S instead.
+// l-1 shellset each direction (weight -(a_x + 1)). Three of the four centres
+// are differentiated; the fourth (position ginv) follows from translational
+// invariance: what centre gpos gains, its atom loses. gpos = -1 accumulates
+// the energy alpha S instead.
 template <bool CTA>
 __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group& grp, int2 qp, int tl, int T,
                            bool active, unsigned mask) {
@@ -415,7 +416,7 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
   const uint16_t* cm = P.colmap + grp.col_off;
   const double* OUT = ws + P.o_OUT;
   const int pos = a.gpos, sg = a.gsign;
-  const int lsh = pos == 0 ? P.la : (pos == 1 ? P.lb : P.lc);
+  const int lsh = pos == 0 ? P.la : (pos == 1 ? P.lb : (pos == 2 ? P.lc : P.ld));
   const int lorg = pos >= 0 ? a.lorig[pos] : 0;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   const int tot = P.Nb * ncols;
@@ -428,7 +429,7 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
       s0 = fma(v, dens_G(a.D, nao, ai + ia, aj + ib, ak + ic, al + id), s0);
       continue;
     }
-    const int sidx = pos == 0 ? ia : (pos == 1 ? ib : ic);
+    const int sidx = pos == 0 ? ia : (pos == 1 ? ib : (pos == 2 ? ic : id));
     const uint32_t xyz = c_cart[lsh][sidx];
     const int cmp[3] = {(int)(xyz & 0xff), (int)((xyz >> 8) & 0xff), (int)((xyz >> 16) & 0xff)};
 #pragma unroll
@@ -445,7 +446,8 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
       }
       const int oidx = d_tri(lorg - o[0]) + o[2];
       const int ja = pos == 0 ? oidx : ia, jb = pos == 1 ? oidx : ib, jc = pos == 2 ? oidx : ic;
-      const double t = wt * v * dens_G(a.D, nao, ai + ja, aj + jb, ak + jc, al + id);
+      const int jd = pos == 3 ? oidx : id;
+      const double t = wt * v * dens_G(a.D, nao, ai + ja, aj + jb, ak + jc, al + jd);
       if (dir == 0) s0 += t; else if (dir == 1) s1 += t; else s2 += t;
     }
   }
@@ -463,9 +465,10 @@ __device__ void grad_group(const QuartetLaunch& a, const double* ws, const Group
     atomicAdd(a.energy, f * s0);
     return;
   }
-  const int sh = pos == 0 ? si : (pos == 1 ? sj : sk);
+  const int sh = pos == 0 ? si : (pos == 1 ? sj : (pos == 2 ? sk : sl));
+  const int sv = a.ginv == 0 ? si : (a.ginv == 1 ? sj : (a.ginv == 2 ? sk : sl));
   double* gA = a.grad + 3 * (int64_t)a.atom[sh];
-  double* gD = a.grad + 3 * (int64_t)a.atom[sl];
+  double* gD = a.grad + 3 * (int64_t)a.atom[sv];
   atomicAdd(gA + 0, f * s0); atomicAdd(gA + 1, f * s1); atomicAdd(gA + 2, f * s2);
   atomicAdd(gD + 0, -f * s0); atomicAdd(gD + 1, -f * s1); atomicAdd(gD + 2, -f * s2);
 }
@@ -487,7 +490,7 @@ __global__ void k_grad_contract(const QuartetLaunch a, const double* __restrict_
   const int64_t nao = a.nao;
   const int64_t ai = a.ao_off[si], aj = a.ao_off[sj], ak = a.ao_off[sk], al = a.ao_off[sl];
   const int pos = a.gpos, sg = a.gsign;
-  const int lsh = pos == 0 ? P.la : (pos == 1 ? P.lb : P.lc);
+  const int lsh = pos == 0 ? P.la : (pos == 1 ? P.lb : (pos == 2 ? P.lc : P.ld));
   const int lorg = pos >= 0 ? a.lorig[pos] : 0;
   const int Nk = P.Nk, tot = P.Nb * P.Nk;
   const double* v0 = V + q * (int64_t)tot;
@@ -500,7 +503,7 @@ __global__ void k_grad_contract(const QuartetLaunch a, const double* __restrict_
       s0 = fma(v, dens_G(a.D, nao, ai + ia, aj + ib, ak + ic, al + id), s0);
       continue;
     }
-    const int sidx = pos == 0 ? ia : (pos == 1 ? ib : ic);
+    const int sidx = pos == 0 ? ia : (pos == 1 ? ib : (pos == 2 ? ic : id));
     const uint32_t xyz = c_cart[lsh][sidx];
     const int cmp[3] = {(int)(xyz & 0xff), (int)((xyz >> 8) & 0xff), (int)((xyz >> 16) & 0xff)};
 #pragma unroll
@@ -517,7 +520,8 @@ __global__ void k_grad_contract(const QuartetLaunch a, const double* __restrict_
       }
       const int oidx = d_tri(lorg - o[0]) + o[2];
       const int ja = pos == 0 ? oidx : ia, jb = pos == 1 ? oidx : ib, jc = pos == 2 ? oidx : ic;
-      const double t = wt * v * dens_G(a.D, nao, ai + ja, aj + jb, ak + jc, al + id);
+      const int jd = pos == 3 ? oidx : id;
+      const double t = wt * v * dens_G(a.D, nao, ai + ja, aj + jb, ak + jc, al + jd);
       if (dir == 0) s0 += t; else if (dir == 1) s1 += t; else s2 += t;
     }
   }
@@ -532,9 +536,10 @@ __global__ void k_grad_contract(const QuartetLaunch a, const double* __restrict_
     atomicAdd(a.energy, f * s0);
     return;
   }
-  const int sh = pos == 0 ? si : (pos == 1 ? sj : sk);
+  const int sh = pos == 0 ? si : (pos == 1 ? sj : (pos == 2 ? sk : sl));
+  const int sv = a.ginv == 0 ? si : (a.ginv == 1 ? sj : (a.ginv == 2 ? sk : sl));
   double* gA = a.grad + 3 * (int64_t)a.atom[sh];
-  double* gD = a.grad + 3 * (int64_t)a.atom[sl];
+  double* gD = a.grad + 3 * (int64_t)a.atom[sv];
   atomicAdd(gA + 0, f * s0); atomicAdd(gA + 1, f * s1); atomicAdd(gA + 2, f * s2);
   atomicAdd(gD + 0, -f * s0); atomicAdd(gD + 1, -f * s1); atomicAdd(gD + 2, -f * s2);
 }

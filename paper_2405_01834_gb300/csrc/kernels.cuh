@@ -54,13 +54,14 @@ struct QuartetLaunch {
   // record variants: quartet (p, q) reads the records of pairs p + bra_var_off and q + ket_var_off
   int64_t bra_var_off, ket_var_off;
   // exchange gradient (grad != nullptr): this launch evaluates the class with the shell at
-  // position gpos (0: i, 1: j, 2: k) replaced by its l+1 (gsign = +1, coefficients 2 zeta c) or
-  // l-1 (gsign = -1) partner and contracts with G = D_ik D_jl + D_il D_jk; gpos = -1: the energy
+  // position gpos (0: i, 1: j, 2: k, 3: l) replaced by its l+1 (gsign = +1, coefficients 2 zeta c) or
+  // l-1 (gsign = -1) partner and contracts with G = D_ik D_jl + D_il D_jk; gpos = -1: the energy.
+  // The atom of the shell at position ginv (never gpos) takes minus what gpos gains.
   double* grad;              // [n_atoms][3]
   double* energy;
   const int32_t* atom;       // per shell
   double alpha;
-  int32_t gpos, gsign;
+  int32_t gpos, gsign, ginv;
   int32_t lorig[4];          // unshifted l of positions i, j, k, l
   // several molecules in one launch (exchange): molecule of each pair and its D, K, nao
   const int32_t* pair_mol;

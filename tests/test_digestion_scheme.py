@@ -12,6 +12,7 @@ over all ordered quartets, so a wrong weight or a missing block fails here
 without a GPU.
 """
 import numpy as np
+import pytest
 
 import oracle
 from paper_2405_01834_gb300 import inputs
@@ -96,14 +97,16 @@ def _cart(l):
     return [(ax, ay, l - ax - ay) for ax in range(l, -1, -1) for ay in range(l - ax, -1, -1)]
 
 
-def test_shifted_class_gradient_scheme():
-    """The GPU's gradient scheme: per unique quartet and each of its first three
+@pytest.mark.parametrize("omit", [0, 1, 2, 3])
+def test_shifted_class_gradient_scheme(omit):
+    """The GPU's gradient scheme: per unique quartet and each of three of its
     shells, the class with that shell raised (l+1, coefficients 2 zeta c) and
     lowered (l-1), contracted with G = D_ik D_jl + D_il D_jk at the unshifted
     component (raised element a' feeds a' - 1_x with weight +1, lowered element
-    a' feeds a' + 1_x with weight -(a'_x + 1)); the fourth shell's atom takes
-    minus the sum (translational invariance). Against the oracle's gradient,
-    which differentiates all four centres explicitly."""
+    a' feeds a' + 1_x with weight -(a'_x + 1)); the atom of the fourth shell
+    (position `omit`, chosen per class on the GPU) takes minus the sum
+    (translational invariance). Against the oracle's gradient, which
+    differentiates all four centres explicitly."""
     b = inputs.small_molecule(seed=23, n_atoms=3, shells=(0, 1, 2), K=2)
     D = inputs.density(b.nao, 8, occ_fraction=0.4)
     ref = oracle.exchange_grad(b, D)
@@ -128,9 +131,11 @@ def test_shifted_class_gradient_scheme():
     jobs = []
     for (i, j), (k, l), same in _unique(ns):
         w = (0.5 if i == j else 1.0) * (0.5 if k == l else 1.0) * (0.5 if same else 1.0)
-        for pos in range(3):
+        for pos in range(4):
+            if pos == omit:
+                continue
             for sign in (1, -1):
-                sh = (i, j, k)[pos]
+                sh = (i, j, k, l)[pos]
                 if sign < 0 and b.l[sh] == 0:
                     continue
                 q = [i, j, k, l]
@@ -142,7 +147,7 @@ def test_shifted_class_gradient_scheme():
         V = vals[off[n]:off[n + 1]].reshape([inputs.ncart(x) for x in ls])
         G = np.einsum("ac,bd->abcd", D[sl[i], sl[k]], D[sl[j], sl[l]]) + \
             np.einsum("ad,bc->abcd", D[sl[i], sl[l]], D[sl[j], sl[k]])
-        lorg = int(b.l[(i, j, k)[pos]])
+        lorg = int(b.l[(i, j, k, l)[pos]])
         orig_index = {c: idx for idx, c in enumerate(_cart(lorg))}
         for sidx, comp in enumerate(_cart(ls[pos])):
             Vs = np.take(V, sidx, axis=pos)
@@ -158,6 +163,6 @@ def test_shifted_class_gradient_scheme():
                     wt = -float(o[x])
                 Gs = np.take(G, orig_index[tuple(o)], axis=pos)
                 t = 4.0 * w * wt * float(np.sum(Vs * Gs))
-                g[b.atom[(i, j, k)[pos]], x] += t
-                g[b.atom[l], x] -= t
+                g[b.atom[(i, j, k, l)[pos]], x] += t
+                g[b.atom[(i, j, k, l)[omit]], x] -= t
     np.testing.assert_allclose(g, ref, rtol=0, atol=1e-11 * np.max(np.abs(ref)))
