@@ -444,9 +444,10 @@ def df_main(args):
 
 
 def grad_main(args):
-    """Exchange energy and its nuclear gradient (adjoint kernel) on one cluster molecule (heavy
-    5s4p3d2f1g / light 4s3p2d1f, K = 6 s shells, D = C C^T, tau): the gradient call against the
-    exchange build alone on the same quartets (whole calls, host screening included)."""
+    """Exchange energy and its nuclear gradient (shifted-class derivative integrals contracted with D (x) D
+    in the kernel) on one cluster molecule (heavy 5s4p3d2f1g / light 4s3p2d1f, K = 6 s shells, D = C C^T,
+    tau): the gradient call against the exchange build alone on the same quartets (whole calls, host
+    screening included)."""
     import torch
     from paper_2405_01834_gb300 import mdx
     torch.cuda.set_device(0)
@@ -465,7 +466,7 @@ def grad_main(args):
                      args.steps, args.warmup)
     eng.sync()
     g = res["g"][0] if isinstance(res["g"], tuple) else res["g"]
-    line = {"metric": "exchange energy nuclear gradient (adjoint) vs exchange build: ms and shell quartets/s",
+    line = {"metric": "exchange energy nuclear gradient (shifted-class derivative integrals) vs exchange build: ms and shell quartets/s",
             "unit": "ms", "value": round(ms_g, 3), "higher_is_better": False, "dtype": "f64",
             "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "cluster molecule of %d atoms (heavy 5s4p3d2f1g / light 4s3p2d1f, K = 6 s "

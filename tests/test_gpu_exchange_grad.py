@@ -1,5 +1,5 @@
-"""GPU exchange-energy gradient (adjoint contraction of derivative integrals with
-D (x) D) against the oracle's explicit gradient and central finite differences."""
+"""GPU exchange-energy gradient (shifted-class derivative integrals contracted with
+D (x) D in the kernel) against the oracle's explicit gradient and central finite differences."""
 import numpy as np
 import pytest
 import torch
