@@ -43,7 +43,7 @@ CHUNK_BYTES = 2 << 30
 # DRAM bytes (read + write) per [ii|ii] quartet of one k_quartets launch of the benchmark (456 quartets,
 # autotuned plan): ncu --nvtx --nvtx-include "mdx_batch_run/" -k regex:k_quartets -c 1 --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum on `bench.py --classes 6 --n-bra 24 --n-ket 19 --steps 1
-# --warmup 3 --no-cpu --no-e2e`: 5,658,310,656 B read + 7,210,691,584 B written
+# --warmup 3 --no-cpu --no-e2e`: 5,659,966,464 B read + 7,211,322,368 B written
 NCU_DRAM_BYTES_PER_II_QUARTET = (5659966464 + 7211322368) / 456
 
 
