@@ -72,7 +72,9 @@ def parse():
                          "projected time of the full-size exchange workloads; xchain: the exchange build on a long "
                          "chain molecule whose D and K are far larger than L2")
     ap.add_argument("--ab-grid", type=int, default=32, help="ab: bra x ket grid per class")
-    ap.add_argument("--df-sample", type=int, default=8192, help="df: triplets timed per class")
+    ap.add_argument("--df-sample", type=int, default=65536, help="df: triplets timed per team-kernel class")
+    ap.add_argument("--df-sample-reg", type=int, default=262144,
+                    help="df: triplets timed per register-kernel class (one thread per triplet)")
     ap.add_argument("--df-sph", action="store_true", help="df: solid-harmonic functions (mdx_batch_eri3_sph)")
     ap.add_argument("--grad-atoms", type=int, default=8, help="grad: atoms of the cluster molecule")
     ap.add_argument("--n-mol", type=int, default=64)
@@ -381,8 +383,10 @@ def _event_ms(torch, stream, fn, steps, warmup):
 def df_main(args):
     """3-center [a|cd] rates per class on the density-fitting cluster (100 atoms, orbital 4s3p2d1f at
     K 6/3/1/1, auxiliary s..i): orbital pairs Schwarz-screened at 1e-12, then for every (l_a | l_c l_d)
-    class a seeded grid of up to --df-sample triplets (auxiliary shells x kept pairs of the class) is
-    timed alone; the full tensor's time is extrapolated from the per-class rates."""
+    class a seeded grid of auxiliary shells x kept pairs of the class is timed alone; the full tensor's
+    time is extrapolated from the per-class rates. The grid holds up to --df-sample triplets for classes of
+    the team kernel (a team per triplet) and up to --df-sample-reg for classes of the register kernel (a
+    thread per triplet), so that either launch fills every SM several times over."""
     import torch
     from paper_2405_01834_gb300 import mdx
     torch.cuda.set_device(0)
@@ -405,8 +409,12 @@ def df_main(args):
                 pc = kept[(lo[kept[:, 0]] == lc) & (lo[kept[:, 1]] == ld)]
                 if len(pc) == 0 or len(a_sh) == 0:
                     continue
+                Kcd = int(orb.nprim[pc[0, 0]]) * int(orb.nprim[pc[0, 1]])
+                reg = eng.plan_info(la, 0, lc, ld, 1, Kcd, True).register_kernel != 0
+                target = args.df_sample_reg if reg else args.df_sample
                 na = min(len(a_sh), 64)
-                npr = max(1, min(len(pc), args.df_sample // na))
+                npr = max(1, min(len(pc), target // na))
+                na = min(len(a_sh), max(na, -(-target // npr)))   # few kept pairs: more auxiliary shells
                 A = rng.choice(a_sh, na, replace=False)
                 Pp = pc[rng.choice(len(pc), npr, replace=False)]
                 trip = np.stack([np.repeat(A, npr), np.tile(Pp[:, 0], na), np.tile(Pp[:, 1], na)],
@@ -419,6 +427,7 @@ def df_main(args):
                 f = bt.model_flops
                 full = len(a_sh) * len(pc)
                 rows.append({"class": "[%d|%d%d]" % (la, lc, ld), "K_cd": Kc * Kd, "triplets": n,
+                             "kernel": "register" if reg else "team",
                              "ms": round(ms, 4), "triplets_per_s": round(n / (ms * 1e-3), 1),
                              "model_gflops": round(f / (ms * 1e-3) * 1e-9, 2),
                              "executed_frac": round(2 * bt.exec_fma / (ms * 1e-3) / peak, 4),
@@ -432,7 +441,9 @@ def df_main(args):
             "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "density-fitting cluster: 100 atoms (>= 2.8 bohr apart), orbital 4s3p2d1f "
                                    "(K 6/3/1/1), auxiliary s..i (K 1, even-tempered ratio 2.5); orbital pairs "
-                                   "kept at Q >= 1e-12; per class a grid of <= 64 auxiliary shells x kept pairs; "
+                                   "kept at Q >= 1e-12; per class a grid of auxiliary shells x kept pairs (<= %d "
+                                   "triplets for team-kernel classes, <= %d for register-kernel classes); "
+                                   % (args.df_sample, args.df_sample_reg)
                                    + ("solid-harmonic" if args.df_sph else "Cartesian") + " functions",
                        "orbital_pairs": int(len(pairs)), "kept_pairs": int(len(kept)),
                        "aux_shells": int(aux.n_shells)},
