@@ -380,6 +380,15 @@ def _event_ms(torch, stream, fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def df_grid(n_aux: int, n_pairs: int, target: int):
+    """Auxiliary shells x kept pairs of one class's timing grid: up to 64 auxiliary shells and as many pairs
+    as make about `target` triplets; a class with few kept pairs takes more auxiliary shells instead."""
+    na = min(n_aux, 64)
+    npr = max(1, min(n_pairs, target // na))
+    na = min(n_aux, max(na, -(-target // npr)))
+    return na, npr
+
+
 def df_main(args):
     """3-center [a|cd] rates per class on the density-fitting cluster (100 atoms, orbital 4s3p2d1f at
     K 6/3/1/1, auxiliary s..i): orbital pairs Schwarz-screened at 1e-12, then for every (l_a | l_c l_d)
@@ -412,9 +421,7 @@ def df_main(args):
                 Kcd = int(orb.nprim[pc[0, 0]]) * int(orb.nprim[pc[0, 1]])
                 reg = eng.plan_info(la, 0, lc, ld, 1, Kcd, True).register_kernel != 0
                 target = args.df_sample_reg if reg else args.df_sample
-                na = min(len(a_sh), 64)
-                npr = max(1, min(len(pc), target // na))
-                na = min(len(a_sh), max(na, -(-target // npr)))   # few kept pairs: more auxiliary shells
+                na, npr = df_grid(len(a_sh), len(pc), target)
                 A = rng.choice(a_sh, na, replace=False)
                 Pp = pc[rng.choice(len(pc), npr, replace=False)]
                 trip = np.stack([np.repeat(A, npr), np.tile(Pp[:, 0], na), np.tile(Pp[:, 1], na)],

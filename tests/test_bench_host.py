@@ -31,3 +31,16 @@ def test_model_flops_is_the_table1_model():
 def test_whole_job_rate_is_weak_scaling():
     assert bench.whole_job_rate(100.0, 1, 1000.0) == pytest.approx(100.0)
     assert bench.whole_job_rate(100.0, 4, 2000.0) == pytest.approx(200.0)
+
+
+@pytest.mark.parametrize("n_aux", [1, 50, 64, 600, 2300])
+@pytest.mark.parametrize("n_pairs", [1, 7, 128, 4096, 100000])
+@pytest.mark.parametrize("target", [8192, 65536, 262144])
+def test_df_grid_fills_to_its_target(n_aux, n_pairs, target):
+    """A class's density-fitting timing grid stays inside the class (distinct shells and pairs), comes within
+    one column of auxiliary shells of the target triplet count (or takes the whole class when it is smaller),
+    and overshoots the target by less than one row of pairs."""
+    na, npr = bench.df_grid(n_aux, n_pairs, target)
+    assert 1 <= na <= n_aux and 1 <= npr <= n_pairs
+    assert na * npr > min(target, n_aux * n_pairs) - na or (na == n_aux and npr == n_pairs)
+    assert na * npr < target + npr or na <= 64
