@@ -439,10 +439,13 @@ class Batch:
 
     def __init__(self, eng: Engine, handle, keep):
         self.eng, self.h, self._keep = eng, handle, keep
+        self._read_info()
+
+    def _read_info(self):
         n, tot = ctypes.c_int64(), ctypes.c_int64()
         mf, ef = ctypes.c_double(), ctypes.c_double()
-        eng._check(eng.lib.mdx_batch_info(handle, ctypes.byref(n), ctypes.byref(tot), ctypes.byref(mf),
-                                          ctypes.byref(ef)), "mdx_batch_info")
+        self.eng._check(self.eng.lib.mdx_batch_info(self.h, ctypes.byref(n), ctypes.byref(tot), ctypes.byref(mf),
+                                                    ctypes.byref(ef)), "mdx_batch_info")
         self.n, self.total, self.model_flops, self.exec_fma = n.value, tot.value, mf.value, ef.value
 
     def offsets(self) -> torch.Tensor:
@@ -469,10 +472,12 @@ class Batch:
         return nl.value
 
     def autotune(self, out: torch.Tensor, max_trial: int = 256):
-        """Pick the fastest team shape per class on this GPU (kept by the engine)."""
+        """Pick the fastest team shape per class on this GPU (kept by the engine); exec_fma then counts
+        the shapes the batch runs."""
         _check_out(out, "mdx_batch_autotune")
         self.eng._check(self.eng.lib.mdx_batch_autotune(self.eng.ctx, self.h, out.data_ptr(), out.numel(), max_trial,
                                                         _stream()), "mdx_batch_autotune")
+        self._read_info()
 
     def close(self):
         if self.h:

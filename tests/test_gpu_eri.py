@@ -351,6 +351,28 @@ def _basis_3c_sph(la, lc, ld, K, seed, n=3):
     return aux.build(), orb.build(), trip
 
 
+@pytest.mark.parametrize("la,lc,ld,K", [(5, 0, 0, (1, 6, 6)), (6, 1, 0, (1, 6, 3)), (4, 1, 1, (1, 3, 3)),
+                                        (2, 2, 1, (1, 1, 3))])
+def test_three_center_batch_autotuned(la, lc, ld, K):
+    """A Cartesian [a|cd] batch after the autotuner (register kernel or team shapes of the one-centre classes,
+    as the density-fitting benchmark tunes them) against the oracle. Own context: the tuned shapes stay
+    with it."""
+    aux, orb, trip = _basis_3c_sph(la, lc, ld, K, 61 + la + lc)
+    e = mdx.Engine(0)
+    bt = e.batch_eri3(mdx.DeviceBasis(aux), mdx.DeviceBasis(orb), trip)
+    w = torch.full((bt.total,), float("nan"), dtype=torch.float64, device="cuda")
+    bt.autotune(w, max_trial=len(trip))
+    bt.run(w)
+    torch.cuda.synchronize()
+    e.sync()
+    ref, roff = oracle.eri3(aux, orb, trip)
+    assert np.array_equal(bt.offsets().cpu().numpy(), roff)
+    print(parity.check(w.cpu().numpy(), ref, roff, "tuned 3c [%d|%d%d]" % (la, lc, ld),
+                       parity.Eri3Evaluator(aux, orb, trip)))
+    bt.close()
+    e.close()
+
+
 @pytest.mark.parametrize("la,lc,ld,K", [(1, 0, 0, (1, 3, 1)), (3, 2, 1, (1, 3, 1)), (6, 0, 0, (1, 6, 6)),
                                         (4, 3, 3, (1, 1, 1)), (6, 3, 3, (1, 1, 1)), (2, 4, 4, (1, 1, 3)),
                                         (5, 5, 5, (1, 1, 1)), (6, 6, 6, (1, 1, 1))])
