@@ -170,6 +170,13 @@ def omp_threads():
     return int(n) if n else (os.cpu_count() or 1)
 
 
+def sweep_config(args, world: int) -> dict:
+    """The class-sweep workload as both arms name it in their line."""
+    return {"workload": "4-center class sweep [pp|pp]..[ii|ii], %dx%d random uncontracted quartets per class, "
+                        "Cartesian, FP64" % (args.n_bra, args.n_ket),
+            "classes": args.classes, "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
 def reference_main(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -190,8 +197,7 @@ def reference_main(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_t / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "4-center class sweep [pp|pp]..[ii|ii], 224x224 random uncontracted quartets "
-                                   "per class, Cartesian, FP64", "classes": args.classes},
+            "config": sweep_config(args, world),
             "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -990,9 +996,7 @@ def main():
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "4-center class sweep [pp|pp]..[ii|ii], %dx%d random uncontracted quartets per "
-                                   "class, Cartesian, FP64" % (args.n_bra, args.n_ket), "classes": args.classes,
-                       "l2": "256 MB buffer written between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "config": dict(sweep_config(args, world), l2="256 MB buffer written between timed steps"),
             "quartets_per_s": round(whole_job_rate(sum(len(q) for _, _, q, _ in prepared), world, ms_step), 1),
             "exec_gflops": round(world * total_exec / (ms_step * 1e-3) * 1e-9, 3),
             "exec_frac_of_peak": round(total_exec / (ms_step * 1e-3) * 1e-9 / peak_gflops, 4),
