@@ -44,3 +44,21 @@ def test_df_grid_fills_to_its_target(n_aux, n_pairs, target):
     assert 1 <= na <= n_aux and 1 <= npr <= n_pairs
     assert na * npr > min(target, n_aux * n_pairs) - na or (na == n_aux and npr == n_pairs)
     assert na * npr < target + npr or na <= 64
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """`bench.py --impl reference` (the oracle on the host cores, no GPU): one JSON line with the keys the
+    run's contract names, the same workload config as the GPU arm, and its e2e equal to its value."""
+    import json
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--classes", "1", "--steps", "1",
+                                     "--warmup", "0", "--cpu-sample", "0.002"])
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    args = bench.parse()
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["config"] == bench.sweep_config(args, 1)
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
