@@ -223,10 +223,13 @@ mdx_status mdx_batch_run(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t ou
  * context (later batches of the class use it) and switch this batch to it.
  * Writes trial results into `out` (batch->total doubles needed) and
  * synchronises `stream`. Results are identical up to FP64 summation order.
+ * Cartesian batches also time the register kernel where the class has one.
  * For a solid-harmonic batch: the classes that run the solid-harmonic team
  * kernel, over team sizes, shared-memory budgets and the cached R tables of
- * contracted classes (MDX_ENOMEM if the chosen shape's staging area cannot be
- * allocated). */
+ * contracted classes, and the classes on the register-kernel route (Cartesian
+ * shellsets, then the element-wise transform) against those team shapes
+ * (MDX_ENOMEM if the chosen shape's staging area cannot be allocated).
+ * Afterwards mdx_batch_info's exec_fma counts the shapes the batch runs. */
 mdx_status mdx_batch_autotune(mdx_ctx* ctx, mdx_batch* batch, double* out, int64_t out_capacity,
                               int64_t max_trial, void* stream);
 
